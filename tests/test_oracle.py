@@ -1,0 +1,263 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test ties a piece of the oracle to a closed form, a value printed in the
+paper, brute-force dense diagonalisation, a finite difference or an invariant,
+chosen so that a dropped term, a wrong sign or index or a transposed operand in
+the oracle fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import trm_inputs as ti
+from oracle import operator as op
+from oracle import trm
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _edge_m(lam, lo, hi, min_gap=1e-3):
+    """Smallest m in [lo, hi] with lambda_{m+1} - lambda_m >= min_gap."""
+    for m in range(lo, hi + 1):
+        if lam[m] - lam[m - 1] >= min_gap:
+            return m
+    raise AssertionError("no gapped m in range")
+
+
+# ---------------------------------------------------------------------------
+# Operator and closed forms (Sec. 3, Eq. LAPLACE and the eigenvalue formula)
+# ---------------------------------------------------------------------------
+def test_laplace_block_form_equals_kronecker_form():
+    n = 9
+    A = op.laplace2d(n).toarray()
+    B = op.grid_hamiltonian((n, n, 1), 2, math.sqrt(0.5)).toarray()
+    assert np.allclose(A, B, rtol=0, atol=1e-15)
+    assert np.allclose(np.diag(A), 4.0)
+    assert A[0, 1] == -1.0 and A[0, n] == -1.0 and A[n - 1, n] == 0.0
+
+
+def test_laplace_closed_form_vs_dense():
+    for n in (5, 12):
+        dense = op.dense_spectrum(op.laplace2d(n))
+        assert np.allclose(op.laplace2d_spectrum(n), dense, atol=1e-12)
+
+
+def test_order2_closed_form_vs_dense():
+    shape = (7, 6, 5)
+    dense = op.dense_spectrum(op.grid_hamiltonian(shape, 2, 1.3))
+    assert np.allclose(op.order2_spectrum(shape, 1.3), dense, atol=1e-12)
+
+
+def test_order4_kronecker_spectrum_vs_dense():
+    shape = (7, 6, 5)
+    dense = op.dense_spectrum(op.grid_hamiltonian(shape, 4, 0.9))
+    assert np.allclose(op.kron_sum_spectrum(shape, 4, 0.9), dense, atol=1e-12)
+
+
+def test_table_restbl_E_G_and_gap_from_closed_form():
+    """E_G = sum of the m lowest lambda_{p,q} and eps_gap = lambda_{m+1} - lambda_m
+    reproduce the printed columns of Table RESTBL to the printed figures."""
+    tab = json.load(open(os.path.join(GOLDEN, "table_restbl.json")))
+    for row in tab["rows"]:
+        lam = op.laplace2d_spectrum(row["n"])
+        m = row["m"]
+        E = float(np.sum(lam[:m]))
+        gap = lam[m] - lam[m - 1]
+        assert float(f"{E:.{row['E_G_sig']}g}") == pytest.approx(row["E_G"], rel=1e-12)
+        assert float(f"{gap:.{row['gap_sig']}g}") == pytest.approx(row["gap"], rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Fig. ONFIG
+# ---------------------------------------------------------------------------
+def test_orthonormalize_is_orthonormal_and_keeps_span():
+    C = ti.random_block(400, 9, seed=5)
+    Q = trm.orthonormalize(C)
+    assert np.max(np.abs(Q.T @ Q - np.eye(9))) < 1e-13
+    assert trm.sin_max_angle(C, Q) < 1e-12
+    # Q = C U^{-1} with U upper triangular: Q^T C is upper triangular
+    R = Q.T @ C
+    assert np.max(np.abs(np.tril(R, -1))) < 1e-12
+
+
+def test_printed_onfig_product_is_not_orthonormal():
+    """The literal C_in L^{-1} of Fig. ONFIG step (4) fails C^T C = I for a
+    generic C; the transposed product (the reading used) passes."""
+    C = ti.random_block(50, 4, seed=9)
+    L = np.linalg.cholesky(C.T @ C)
+    Li = np.linalg.inv(L)
+    assert np.max(np.abs((C @ Li).T @ (C @ Li) - np.eye(4))) > 1e-3
+    assert np.max(np.abs((C @ Li.T).T @ (C @ Li.T) - np.eye(4))) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Fig. EGFIG
+# ---------------------------------------------------------------------------
+def _small_problem(seed=1, shape=(6, 5, 4), order=4, m=5):
+    V = ti.gaussian_wells(shape, 3, seed=seed)
+    H = op.grid_hamiltonian(shape, order, 1.0, V)
+    C = trm.orthonormalize(ti.random_block(H.shape[0], m, seed=seed + 100))
+    return H, C
+
+
+def test_energy_is_sum_of_rayleigh_terms():
+    H, C = _small_problem()
+    Hd = H.toarray()
+    E, G, X, Hc = trm.energy_gradient_alg1(H, C)
+    E_direct = sum(float(C[:, j] @ Hd @ C[:, j]) for j in range(C.shape[1]))
+    assert E == pytest.approx(E_direct, rel=1e-13)
+
+
+def test_algorithm1_equals_algorithm2():
+    H, C = _small_problem()
+    E1, G1, _, _ = trm.energy_gradient_alg1(H, C)
+    E2, G2, _, HD, Xp, Hp = trm.energy_gradient_alg2(H, C)
+    assert E1 == pytest.approx(E2, rel=1e-14)
+    assert np.max(np.abs(G1 - G2)) < 1e-12
+    # with C^T C = I, H' has (numerically) zero diagonal, so zeroing it is harmless
+    assert np.max(np.abs(np.diag(Hp))) < 1e-13
+    _, G3, _, _, _, _ = trm.energy_gradient_alg2(H, C, zero_diag=True)
+    assert np.max(np.abs(G3 - G1)) < 1e-12
+
+
+def test_gradient_is_minus_directional_derivative():
+    """d/de E(orthonormalize(C + e D)) at e = 0 equals -tr(D^T G)."""
+    H, C = _small_problem()
+    E, G, _, _ = trm.energy_gradient_alg1(H, C)
+    D = ti.random_block(C.shape[0], C.shape[1], seed=77)
+    eps = 1e-5
+    Ep = trm.energy_gradient_alg1(H, trm.orthonormalize(C + eps * D))[0]
+    Em = trm.energy_gradient_alg1(H, trm.orthonormalize(C - eps * D))[0]
+    fd = (Ep - Em) / (2 * eps)
+    assert fd == pytest.approx(-float(np.sum(D * G)), rel=1e-7)
+
+
+def test_gradient_orthogonal_to_C_and_trace_invariance():
+    H, C = _small_problem()
+    E, G, _, _ = trm.energy_gradient_alg1(H, C)
+    assert np.max(np.abs(C.T @ G)) < 1e-12
+    Q, _ = np.linalg.qr(ti.random_block(C.shape[1], C.shape[1], seed=3))
+    E_rot, G_rot, _, _ = trm.energy_gradient_alg1(H, C @ Q)
+    assert E_rot == pytest.approx(E, rel=1e-13)
+    assert np.max(np.abs(G_rot - G @ Q)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Line minimization
+# ---------------------------------------------------------------------------
+def _line_setup():
+    H, C = _small_problem(m=4)
+    E, G, X, _ = trm.energy_gradient_alg1(H, C)
+    P = G
+    HP = op.apply_h(H, P)
+    return H, C, P, G, trm.line_matrices(C, P, X, HP)
+
+
+def test_line_energy_equals_explicit_orthonormalize_and_evaluate():
+    H, C, P, G, M = _line_setup()
+    for a in (0.0, 0.05, 0.3, 1.2):
+        explicit = trm.energy_gradient_alg1(H, trm.orthonormalize(C + a * P))[0]
+        assert trm.line_energy(a, M) == pytest.approx(explicit, rel=1e-12)
+
+
+def test_line_slope_matches_finite_difference_and_gradient():
+    H, C, P, G, M = _line_setup()
+    assert trm.line_slope(0.0, M) == pytest.approx(-float(np.sum(G * P)), rel=1e-10)
+    for a in (0.02, 0.2, 0.7):
+        h = 1e-5 * max(a, 1e-3)
+        fd = (trm.line_energy(a + h, M) - trm.line_energy(a - h, M)) / (2 * h)
+        assert trm.line_slope(a, M) == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_line_minimize_finds_minimum():
+    H, C, P, G, M = _line_setup()
+    a, g0 = trm.line_minimize(M, 1e-3)
+    assert g0 < 0 and a > 0
+    assert abs(trm.line_slope(a, M)) <= 1e-8 * abs(g0)
+    Ea = trm.line_energy(a, M)
+    for b in np.linspace(0.0, 3 * a, 31):
+        assert Ea <= trm.line_energy(b, M) + 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Rayleigh-Ritz and the full loop (Fig. TMFIG)
+# ---------------------------------------------------------------------------
+def test_rayleigh_ritz_on_exact_eigenvectors():
+    H, _ = _small_problem()
+    w, Z = sla.eigh(H.toarray())
+    m = 5
+    Q, _ = np.linalg.qr(ti.random_block(m, m, seed=8))
+    lam, Cr, res = trm.rayleigh_ritz(H, Z[:, :m] @ Q * 3.0)
+    assert np.allclose(lam, w[:m], atol=1e-12)
+    assert np.max(res) < 1e-12
+    assert np.max(np.abs(Cr.T @ Cr - np.eye(m))) < 1e-12
+
+
+def test_solve_laplace2d_vs_closed_form():
+    n = 20
+    lam_ex = op.laplace2d_spectrum(n)
+    m = _edge_m(lam_ex, 12, 40, min_gap=2e-2)
+    H = op.laplace2d(n)
+    res = trm.solve(H, ti.random_block(n * n, m, seed=2), tol=1e-10)
+    assert res.converged
+    assert res.E_G == pytest.approx(float(np.sum(lam_ex[:m])), rel=1e-12)
+    assert np.max(np.abs(res.lam - lam_ex[:m])) < 1e-10
+    # energies decrease monotonically with an exact line search in FP64
+    e = np.array(res.energies)
+    assert np.all(np.diff(e) <= 1e-12 * np.abs(e[1:]))
+
+
+def test_solve_order2_3d_vs_closed_form():
+    shape = (8, 7, 6)
+    lam_ex = op.order2_spectrum(shape, 1.0)
+    m = _edge_m(lam_ex, 8, 30, min_gap=1e-2)
+    H = op.grid_hamiltonian(shape, 2, 1.0)
+    res = trm.solve(H, ti.random_block(H.shape[0], m, seed=4), tol=1e-10)
+    assert res.converged
+    assert res.E_G == pytest.approx(float(np.sum(lam_ex[:m])), rel=1e-12)
+    assert np.max(np.abs(res.lam - lam_ex[:m])) < 1e-10
+
+
+def test_solve_order4_wells_vs_dense_and_preconditioned():
+    shape = (8, 8, 8)
+    V = ti.gaussian_wells(shape, 6, seed=3)
+    H = op.grid_hamiltonian(shape, 4, 1.0, V)
+    dense = op.dense_spectrum(H)
+    m = _edge_m(dense, 10, 30, min_gap=1e-2)
+    C0 = ti.random_block(512, m, seed=6)
+    for pc in (False, True):
+        res = trm.solve(H, C0, tol=1e-10, precond=pc)
+        assert res.converged
+        assert res.E_G == pytest.approx(float(np.sum(dense[:m])), rel=1e-12)
+        assert np.max(np.abs(res.lam - dense[:m])) < 1e-10
+        assert np.max(res.residuals) < 1e-8
+
+
+def test_ritz_values_interlace_before_convergence():
+    """Cauchy interlacing: on any m-dimensional subspace the Ritz values are
+    bounded below by the exact lambda_j, and E_i >= E_G."""
+    shape = (7, 7, 7)
+    H = op.grid_hamiltonian(shape, 4, 1.0, ti.gaussian_wells(shape, 4, seed=2))
+    dense = op.dense_spectrum(H)
+    res = trm.solve(H, ti.random_block(343, 10, seed=1), tol=0.0, max_iter=8)
+    assert not res.converged
+    assert np.all(res.lam >= dense[:10] - 1e-12)
+    assert min(res.energies) >= float(np.sum(dense[:10])) - 1e-12
+
+
+def test_polak_ribiere_beats_steepest_descent():
+    """With the Polak-Ribiere term the loop converges far faster than with
+    gamma = 0; a sign or index slip in gamma would not."""
+    n = 16
+    lam_ex = op.laplace2d_spectrum(n)
+    m = _edge_m(lam_ex, 10, 30, min_gap=2e-2)
+    H = op.laplace2d(n)
+    C0 = ti.random_block(n * n, m, seed=7)
+    cg = trm.solve(H, C0, tol=1e-8)
+    sd = trm.solve(H, C0, tol=1e-8, cg=False, max_iter=3 * cg.iterations)
+    assert cg.converged
+    assert (not sd.converged) or sd.iterations > 2 * cg.iterations
