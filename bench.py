@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark: time to E_G at 1e-10 relative error on one GB300.
+
+One timed step is one complete trace-minimization solve (Fig. TMFIG to the
+stopping tolerance, then the FP64 Rayleigh-Ritz step) of the workload
+"48^3 grid, 13-point 4th-order -1/2 nabla^2 + 64 Gaussian wells, m = 128,
+diagonal preconditioner", in the mixed-precision ladder, with the operator
+already resident in HBM. Every step's E_G is checked against the stored
+reference; a step that misses 1e-10 relative error is reported.
+
+Printed JSON keys beyond the base contract: roofline (dominant kernel class,
+timed live with CUDA events around each of its launches in the timed region),
+spmm (the H-application GB/s), fp64_path (the same solve with every operation
+in FP64), e2e (the solve through the C ABI from host buffers, copies
+included), clocks (nvidia-smi sampled during the timed region), cpu_baseline
+(the FP64 oracle on the host cores, a bounded sample scaled to a solve).
+
+--impl reference times the oracle itself (the CPU program), bounded samples.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "grid48_o4_w64_m128"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "workloads.json")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Fallback peaks when the measured file is absent (one earlier GB300 run).
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# Peaks derived from unit counts and the 2070 MHz maximum SM clock:
+# FP32 SIMT = 152 SMs x 128 FMA/clk x 2; FP64 = the 1.25 TFLOP/s nominal.
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_TFLOPS = 1.25
+METRIC = "time-to-E_G at 1e-10 rel err (mixed precision)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tol", type=float, default=1e-8,
+                    help="RMS residual at which a solve stops")
+    ap.add_argument("--fp64", type=int, default=1,
+                    help="also time one solve of the all-FP64 path")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="budget of the oracle CPU sample")
+    return ap.parse_args()
+
+
+def load_json(path, default=None):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return default
+
+
+def workload():
+    import trm_inputs as ti
+    g = load_json(GOLDEN, {}).get(WORKLOAD, {})
+    seed = int(g.get("seed", 1))
+    return ti.workload(WORKLOAD, seed=seed), g
+
+
+def describe(w, g, tol):
+    return {"workload": (f"{w.name}: {w.shape[0]}^3 grid, 13-point 4th-order "
+                         f"-1/2 nabla^2 + {w.nwells} Gaussian wells (seed "
+                         f"{w.seed}), m={w.m}, diagonal preconditioner"),
+            "N": w.N, "m": w.m, "tol_rms": tol,
+            "E_G_ref": g.get("E_G"), "gap": g.get("gap"),
+            "inputs": "synthetic, seeded",
+            "l2": "256 MB buffer written between timed steps",
+            "parallelism": "replicas (one independent solve per GPU)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores, bounded sample
+# ---------------------------------------------------------------------------
+_CPU_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+import trm_inputs as ti
+from oracle import operator as op, trm
+w = ti.workload(%(name)r, seed=%(seed)d)
+H = op.grid_hamiltonian(w.shape, w.order, w.h, w.potential())
+C0 = ti.random_block(w.N, w.m, seed=1)
+budget = %(budget)f
+t0 = time.time()
+stamps = []
+def cb(it, E, r):
+    stamps.append(time.time())
+    if stamps[-1] - t0 > budget:
+        raise StopIteration
+try:
+    trm.solve(H, C0, tol=0.0, max_iter=100000, precond=True, callback=cb)
+except StopIteration:
+    pass
+n = len(stamps) - 1
+per = (stamps[-1] - stamps[0]) / max(n, 1)
+print(json.dumps({"per_iter_s": per, "iters": n, "wall": time.time() - t0}))
+"""
+
+
+def cpu_sample(w, budget, threads):
+    env = dict(os.environ)
+    env["OPENBLAS_NUM_THREADS"] = str(threads)
+    env["OMP_NUM_THREADS"] = str(threads)
+    code = _CPU_SNIPPET % {"root": ROOT, "name": w.name, "seed": w.seed,
+                           "budget": budget}
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True,
+                       text=True, env=env, timeout=budget * 10 + 300)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(w, g, budget, iters_to_solve):
+    s = cpu_sample(w, budget, 1)
+    value = s["per_iter_s"] * iters_to_solve
+    return {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"{s['iters']} FP64 oracle iterations (numpy, one BLAS "
+                       f"thread) of the same workload, {s['per_iter_s']:.3f} s "
+                       f"each, scaled by {iters_to_solve} iterations per "
+                       f"solve")}
+
+
+def iterations_to_solve(g, fallback):
+    it = g.get("oracle_iterations_tol_1e-8")
+    return int(it) if it else int(fallback)
+
+
+# ---------------------------------------------------------------------------
+# nvidia-smi clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# roofline of the dominant kernel class
+# ---------------------------------------------------------------------------
+def roofline(prof, peaks, src):
+    classes = {k: v for k, v in prof.items() if v["launches"] > 0 and v["ms"] > 0}
+    if not classes:
+        return None, None
+    name = max(classes, key=lambda k: classes[k]["ms"])
+    c = classes[name]
+    per_launch_s = c["ms"] / 1e3 / c["launches"]
+
+    def entry(cname, cc):
+        pl = cc["ms"] / 1e3 / cc["launches"]
+        if cname.startswith("spmm"):
+            ach = cc["bytes"] / cc["launches"] / pl / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                    "peak_source": src}
+        ach = cc["flops"] / cc["launches"] / pl / 1e12
+        if cname.endswith("f64") or cname in ("small_mm", "eig"):
+            pk, ps = FP64_TFLOPS, "nominal FP64 (1.25 TFLOP/s)"
+        else:
+            pk, ps = FP32_SIMT_TFLOPS, "derived FP32 SIMT (152 SMs x 128 FMA x 2070 MHz)"
+        return {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "peak_source": ps}
+
+    r = entry(name, c)
+    r.update({"kernel": name, "launches": c["launches"],
+              "avg_launch_ms": per_launch_s * 1e3, "traffic": None,
+              "share_of_timed": c["ms"] / sum(v["ms"] for v in classes.values())})
+    sp = None
+    for k in ("spmm_f32", "spmm_f64"):
+        if k in classes:
+            e = entry(k, classes[k])
+            e.update({"kernel": k, "launches": classes[k]["launches"]})
+            sp = sp or {}
+            sp[k] = e
+    return r, sp
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, g = workload()
+    its = iterations_to_solve(g, g.get("gpu_iterations_hint", 2000))
+    budget = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_sample(w, min(budget, 5.0), 1)
+    vals, samples = [], []
+    for _ in range(args.steps):
+        s = cpu_sample(w, budget, 1)
+        samples.append(s)
+        vals.append(s["per_iter_s"] * its)
+    v = statistics.mean(vals)
+    out = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": describe(w, g, args.tol),
+           "cpu_baseline": {"value": v, "unit": "s", "cores": 1,
+                            "kind": "oracle",
+                            "sample": (f"per step: FP64 oracle iterations for "
+                                       f"{budget:.0f} s, scaled by {its} "
+                                       f"iterations per solve")},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_1108_4509_gb300 as trm
+
+    w, g = workload()
+    V = w.potential()
+    E_ref = g.get("E_G")
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    nx, ny, nz = w.shape
+    opt = trm.trm_default_options(precision=trm.TRM_MIXED, precond=1,
+                                  stream=sptr, seed=w.seed + 100)
+    h = trm.trm_create_stencil(nx, ny, nz, w.order, w.h, V, w.m, args.tol, opt)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def solve_once():
+        lam, eg, st, status = trm.trm_solve(h, w.N, w.m)
+        return lam, eg, st, status
+
+    for _ in range(args.warmup):
+        solve_once()
+    torch.cuda.synchronize()
+    trm.trm_profile(h, True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    launches0 = trm.trm_launch_count()
+    times, errs, iters, statuses = [], [], [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lam, eg, st, status = solve_once()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        errs.append(abs(eg - E_ref) / abs(E_ref) if E_ref else None)
+        iters.append(st.iterations)
+        statuses.append(status)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = trm.trm_launch_count() - launches0
+    clocks = sampler.stop()
+    prof = trm.trm_profile_read(h)
+    trm.trm_profile(h, False)
+    t_step = statistics.mean(times)
+    if dist:
+        t = torch.tensor([t_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+
+    peaks_file = load_json(PEAKS)
+    peaks = peaks_file if peaks_file else FALLBACK
+    src = "measured" if peaks_file else "fallback"
+    roof, spmm = roofline(prof, peaks, src)
+
+    # all-FP64 path, one solve (not part of the timed region)
+    fp64 = None
+    if args.fp64 and rank == 0:
+        opt64 = trm.trm_default_options(precision=trm.TRM_FP64, precond=1,
+                                        stream=sptr, seed=w.seed + 100)
+        h64 = trm.trm_create_stencil(nx, ny, nz, w.order, w.h, V, w.m,
+                                     args.tol, opt64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lam64, eg64, st64, status64 = trm.trm_solve(h64, w.N, w.m)
+        e1.record(stream)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        trm.trm_destroy(h64)
+        fp64 = {"seconds": t64, "iterations": st64.iterations,
+                "status": status64,
+                "rel_err_E_G": abs(eg64 - E_ref) / abs(E_ref) if E_ref else None,
+                "mixed_speedup": t64 / t_step}
+
+    # end to end through the C ABI from host buffers: create (V host->device)
+    # + solve + C and lambda device->host, per step
+    e2e_times = []
+    C_host = np.zeros((w.N, w.m), order="F")
+    n_e2e = max(1, min(2, args.steps))
+    for _ in range(n_e2e):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2 = trm.trm_create_stencil(nx, ny, nz, w.order, w.h, V, w.m,
+                                    args.tol, opt)
+        lam2, eg2, st2, status2 = trm.trm_solve(h2, w.N, w.m, C_out=C_host)
+        trm.trm_destroy(h2)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e = {"value": statistics.mean(e2e_times), "unit": "s",
+           "h2d_bytes_per_step": 8 * w.N,
+           "d2h_bytes_per_step": 8 * w.N * w.m + 8 * w.m + 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        try:
+            cpu = cpu_baseline(w, g, args.cpu_seconds,
+                               iterations_to_solve(g, statistics.mean(iters)))
+        except Exception as exc:  # reported, not fatal
+            cpu = {"error": str(exc)[:300]}
+
+    trm.trm_destroy(h)
+    if rank == 0:
+        out = {"metric": METRIC, "value": t_step, "unit": "s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": t_step * 1e3, "higher_is_better": False,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+               "data": "synthetic", "config": describe(w, g, args.tol),
+               "solves_per_s": world / t_step,
+               "iterations": iters, "status": statuses,
+               "rel_err_E_G": errs,
+               "E_G_ok": all(e is not None and e <= 1e-10 for e in errs),
+               "roofline": roof, "spmm": spmm, "fp64_path": fp64,
+               "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+               "cpu_baseline": cpu}
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

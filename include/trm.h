@@ -1,0 +1,242 @@
+/*
+ * trm.h - C ABI of the GB300 (sm_103a) trace-minimization eigensolver.
+ *
+ * Computes the m lowest eigenvalues lambda_1..lambda_m of a large sparse
+ * symmetric matrix H, their sum E_G and an orthonormal basis C of the
+ * corresponding invariant subspace, by minimising E(C) = trace(C^T H C)
+ * subject to C^T C = I_m with nonlinear conjugate gradients (Tsuchida and Choe,
+ * "Iterative diagonalization of symmetric matrices in mixed precision",
+ * Sec. 2.1, Eqs. TRHEQ/CIJEQ, Fig. TMFIG), in full FP64 or in the mixed
+ * precision of Sec. 2.2 (MP1, MP2, full SP, and a ladder full SP -> MP2 ->
+ * FP64 Rayleigh-Ritz).
+ *
+ * Conventions used by every entry point:
+ *  - N x m blocks are column-major with leading dimension N (column j of C is
+ *    the contiguous range C[j*N .. j*N + N-1]); m x m matrices are
+ *    column-major with leading dimension m.
+ *  - "device" pointers are CUDA global-memory addresses of the current
+ *    device; "host" pointers are ordinary CPU memory (pageable or pinned).
+ *  - Inputs are owned by the caller and are copied (create) or only read
+ *    (step operations); the library never frees a caller pointer.
+ *  - No entry point throws, exits or traps: every failure is returned as a
+ *    negative trm_status, with a message from trm_last_error() where a
+ *    handle exists, or trm_last_global_error() otherwise.
+ *  - A handle may be used by one host thread at a time.
+ */
+#ifndef TRM_H
+#define TRM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct trm_ctx* trm_handle;
+
+typedef enum {
+  TRM_OK = 0,
+  TRM_EINVAL = -1,   /* invalid argument (sizes, pointers, options) */
+  TRM_ENOMEM = -2,   /* device memory for the solve could not be allocated */
+  TRM_ENOTPD = -3,   /* an overlap matrix C^T C was not positive definite */
+  TRM_ENOCONV = -4,  /* max_iter reached; outputs hold the best iterate */
+  TRM_ECUDA = -5,    /* a CUDA runtime call failed */
+  TRM_ETIMEOUT = -6, /* a bounded device wait gave up */
+  TRM_EGAP = -7      /* reserved: gap test failed */
+} trm_status;
+
+/* Precision modes (Sec. 2.2). */
+typedef enum {
+  TRM_FP64 = 0,    /* "full DP": every operation in FP64 */
+  TRM_MP1 = 1,     /* MP1: G, P stored FP32; split rotation C L_D + C L' */
+  TRM_MP2 = 2,     /* MP2: MP1 plus the two O(m^2 N) gradient GEMMs in FP32 */
+  TRM_FULL_SP = 3, /* "full SP": all block work in FP32 */
+  TRM_MIXED = 4    /* full SP until stagnation, then MP2, then FP64 Rayleigh-Ritz */
+} trm_precision;
+
+/* Element types of caller buffers in the step operations. */
+typedef enum { TRM_F32 = 0, TRM_F64 = 1 } trm_dtype;
+
+typedef struct {
+  int precision;        /* trm_precision; default TRM_MIXED */
+  int precond;          /* 0: M = I; 1: diagonal M = diag(1/(H_jj - sigma)),
+                           sigma = min_k H_kk - 1 (Eq. PCEQ). Default 0 */
+  int max_iter;         /* iteration cap over all phases; default 20000 */
+  uint64_t seed;        /* random C0 = splitmix64 block of this seed */
+  double switch_tol[2]; /* [0]: leave full SP when the RMS residual stops
+                           improving or falls below switch_tol[0]*r_0;
+                           [1]: reserved. Defaults 1e-5, 0 */
+  int reorth_every;     /* MP2 phase: exact FP64 re-orthonormalization at
+                           least every this many iterations, and whenever
+                           the residual has dropped 100-fold since the
+                           last one; default 400; 0: residual rule only */
+  int rr_every;         /* MP2 phase: subspace rotation diagonalising
+                           C^T H C (Sec. 3) at least every this many
+                           iterations, and whenever the residual has
+                           dropped 1000-fold; default 0: residual rule */
+  int lag;              /* iterations the host may run ahead of the
+                           convergence flags it has read; default 2 */
+  void* stream;         /* cudaStream_t for all work; NULL = default stream */
+} trm_options;
+
+typedef struct {
+  int iterations;           /* total iterations */
+  int iterations_phase[3];  /* full SP, MP2/MP1/FP64, reorth count */
+  int converged;            /* 1 if the residual test passed */
+  double rms_residual;      /* final FP64 ||H C - C Lambda||_F / sqrt(m) */
+  double max_residual;      /* final FP64 max_j ||H c_j - lambda_j c_j|| */
+  double E_last;            /* energy of the last iterate (FP64 trace) */
+  double seconds;           /* host wall time of trm_solve */
+  long long launches;       /* library kernel launches in the process so far */
+} trm_stats;
+
+/* Per-class kernel timing of one handle (see trm_profile). */
+typedef struct {
+  char name[16];       /* kernel class, e.g. "gram_f32", "spmm_f64" */
+  double ms;           /* summed CUDA-event time of its launches */
+  long long launches;  /* launcher calls timed (a call may be 2 kernels) */
+  double flops;        /* summed algorithmic flops of those calls */
+  double bytes;        /* summed algorithmic bytes moved by those calls */
+} trm_kernel_stats;
+
+/* Fill *opt with the defaults listed above. */
+trm_status trm_default_options(trm_options* opt);
+
+/*
+ * Create a solver for H = -1/2 nabla^2_h + diag(V) on an nx x ny x nz grid with
+ * zero Dirichlet boundaries (grid point idx = x + nx*(y + ny*z)); an axis of
+ * length 1 is absent, so nz = 1 is a 2-D problem. order = 2 uses the 3-point
+ * rule per axis (7-point stencil in 3-D), order = 4 the 5-point 4th-order
+ * rule (13-point). V: host, N = nx*ny*nz doubles, copied; NULL means V = 0.
+ * tol: the solve stops when the RMS column residual
+ * ||H C - C (C^T H C)||_F / sqrt(m) <= tol (the paper's "||G|| sufficiently
+ * small", Sec. 2.1). 1 <= m < N. opt may be NULL for defaults.
+ */
+trm_status trm_create_stencil(trm_handle* out, int nx, int ny, int nz,
+                              int order, double h, const double* V, int m,
+                              double tol, const trm_options* opt);
+
+/*
+ * Create a solver for an explicit symmetric CSR matrix (N rows, int32 row
+ * pointers and column indices, ascending columns per row, values FP32
+ * (vals_dtype = TRM_F32) or FP64 (TRM_F64)). All arrays are host memory and
+ * are copied. Symmetry is the caller's responsibility (Eq. BASICEQ).
+ */
+trm_status trm_create_csr(trm_handle* out, int64_t N, const int32_t* rowptr,
+                          const int32_t* cols, const void* vals,
+                          int vals_dtype, int m, double tol,
+                          const trm_options* opt);
+
+/*
+ * Run Fig. TMFIG to convergence, then diagonalise C^T H C (Rayleigh-Ritz,
+ * Sec. 2.1) in FP64. Outputs (any may be NULL):
+ *   lambda - host, m doubles, ascending;
+ *   E_G    - host, sum of lambda (Eq. EGEQ);
+ *   C      - N x m FP64 column-major Ritz vectors, on the device if
+ *            C_on_device != 0, else in host memory;
+ *   stats  - host.
+ * C0: optional N x m FP64 starting block (host memory, need not be
+ * orthonormal); NULL draws it from opt.seed. Returns TRM_ENOCONV (with the
+ * best result written) when max_iter is reached.
+ */
+trm_status trm_solve(trm_handle h, double* lambda, double* E_G, double* C,
+                     int C_on_device, const double* C0, trm_stats* stats);
+
+trm_status trm_destroy(trm_handle h);
+const char* trm_strerror(trm_status s);
+const char* trm_last_error(trm_handle h);
+const char* trm_last_global_error(void);
+
+/* ------------------------------------------------------------------------
+ * Step operations: one row of the per-iteration block step each, on caller
+ * device buffers and the stream in the handle's options. They synchronise
+ * that stream before returning. Used to check each step in isolation.
+ * ---------------------------------------------------------------------- */
+
+/* N of the handle's operator. */
+int64_t trm_dim(trm_handle h);
+
+/*
+ * X = H C for ncols columns (Fig. EGFIG step (1)). C, X: device, N x ncols,
+ * dtype_in / dtype_out in {TRM_F32, TRM_F64}; the sum is formed in the output
+ * precision. Stencil operators support (F32,F32) and (F64,F64); CSR
+ * operators the same two.
+ */
+trm_status trm_apply_h(trm_handle h, int dtype_in, const void* C,
+                       int dtype_out, void* X, int ncols);
+
+/*
+ * Fig. EGFIG Algorithm-2, steps (1)-(7), for an orthonormal C (device, N x m
+ * FP64). Writes E (host double), H_D (device, m doubles), H' (device, m x m
+ * FP64, diag set to 0 when zero_diag != 0, Sec. 2.2) and
+ * G = -2 (X' - C H') (device, N x m in G_dtype). With G_dtype = TRM_F32 the
+ * products of steps (6) and (7) run in FP32 as in MP2; steps (1), (2), (3),
+ * (5) stay FP64.
+ */
+trm_status trm_energy_gradient(trm_handle h, const double* C, double* E,
+                               double* HD, double* Hprime, void* G,
+                               int G_dtype, int zero_diag);
+
+/*
+ * out = A^T B (m x n, device FP64, column-major ld = m) for A: N x m and
+ * B: N x n (device, leading dimensions N, element type dtype). FP32 inputs
+ * are multiplied and summed in FP32 within a tile of rows and the tiles are
+ * summed in FP64 in a fixed order. Covers the Gram products C^T X' of
+ * Fig. EGFIG step (6), C^T C of Fig. ONFIG step (1) and the line-search
+ * projections C^T P, P^T P, P^T H P.
+ */
+trm_status trm_gram(int64_t N, int m, int n, int dtype, const void* A,
+                    const void* B, double* out, void* stream);
+
+/*
+ * Fig. ONFIG in FP64 on the device: S = C^T C, S = L L^T, C <- C L^{-T}.
+ * C: device, N x m FP64, overwritten. Returns TRM_ENOTPD if S is not
+ * positive definite.
+ */
+trm_status trm_orthonormalize(int64_t N, int m, double* C, void* stream);
+
+/*
+ * One iteration of Fig. TMFIG from the handle's current state in the given
+ * precision mode (TRM_FP64 or TRM_FULL_SP or TRM_MP2), starting a new CG
+ * sequence when restart != 0. The state is set by trm_set_block and read by
+ * trm_get_block. E_out (host) receives E_i and rms_out (host) the RMS
+ * residual of G_i, both before the update; alpha_out the step taken.
+ */
+trm_status trm_set_block(trm_handle h, const double* C_device);
+trm_status trm_get_block(trm_handle h, double* C_device);
+trm_status trm_iterate(trm_handle h, int mode, int restart, double* E_out,
+                       double* rms_out, double* alpha_out);
+
+/*
+ * Rayleigh-Ritz on span(C) in FP64 (Sec. 2.1): solves (C^T H C) y = theta
+ * (C^T C) y, overwrites C (device, N x m FP64) with C Y (unit columns, each
+ * column's largest-magnitude entry positive), and writes lambda (host, m,
+ * ascending) and the residual norms ||H c_j - lambda_j c_j|| (host, m).
+ */
+trm_status trm_rayleigh_ritz(trm_handle h, double* C, double* lambda,
+                             double* residuals);
+
+/*
+ * Timing of the library's kernels by class, with a pair of CUDA events on the
+ * handle's stream around each launcher call of a solve (no paper
+ * counterpart: measurement support). enable != 0 zeroes the counters and
+ * starts timing; 0 stops it. trm_profile_read copies up to max classes into
+ * out (host) and returns how many exist, or a negative status.
+ */
+trm_status trm_profile(trm_handle h, int enable);
+int trm_profile_read(trm_handle h, trm_kernel_stats* out, int max);
+
+/* Kernel launches issued by the library in this process (all handles). */
+long long trm_launch_count(void);
+
+/* Fill an N x m FP64 device block with the splitmix64 random guess of the
+ * given seed: entry (i, j) = u(seed, i + N j) - 0.5 (Sec. 3: random C0). */
+trm_status trm_random_block(int64_t N, int m, uint64_t seed, double* C,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRM_H */

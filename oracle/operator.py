@@ -136,7 +136,7 @@ def lowest_eigenvalues(H, k: int) -> np.ndarray:
     import scipy.sparse.linalg as sla
     if H.shape[0] <= 3000:
         return dense_spectrum(H)[:k]
-    vals = sla.eigsh(H, k=k, which="SA", tol=1e-12, maxiter=200000,
+    vals = sla.eigsh(H, k=k, which="SA", tol=0, maxiter=200000,
                      ncv=min(H.shape[0], max(2 * k + 1, k + 64)),
                      return_eigenvectors=False)
     return np.sort(vals)

@@ -1,0 +1,341 @@
+"""Python binding of libtrm, the sm_103a trace-minimization eigensolver.
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+behind the C ABI of include/trm.h, and the functions here carry the same names
+as the C entry points. Host arrays are numpy arrays; device arrays are passed
+as integer addresses (for example ``tensor.data_ptr()`` of a CUDA tensor) and
+streams as ``torch.cuda.current_stream().cuda_stream``.
+
+Importing this module loads the compiled library and raises ``ImportError``
+when it is missing: there is no CPU fallback. Build it with
+``paper_1108_4509_gb300._build.build()`` (or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+__all__ = [
+    "TRM_FP64", "TRM_MP1", "TRM_MP2", "TRM_FULL_SP", "TRM_MIXED", "TRM_F32",
+    "TRM_F64", "TrmError", "trm_options", "trm_stats", "lib", "LIB_PATH",
+    "trm_default_options", "trm_create_stencil", "trm_create_csr", "trm_solve",
+    "trm_destroy", "trm_strerror", "trm_last_error", "trm_dim", "trm_apply_h",
+    "trm_energy_gradient", "trm_gram", "trm_orthonormalize", "trm_set_block",
+    "trm_get_block", "trm_iterate", "trm_rayleigh_ritz", "trm_random_block",
+    "trm_profile", "trm_profile_read", "trm_launch_count", "trm_kernel_stats",
+    "Solver",
+]
+
+TRM_FP64, TRM_MP1, TRM_MP2, TRM_FULL_SP, TRM_MIXED = 0, 1, 2, 3, 4
+TRM_F32, TRM_F64 = 0, 1
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtrm.so")
+
+
+class trm_options(ct.Structure):
+    _fields_ = [("precision", ct.c_int), ("precond", ct.c_int),
+                ("max_iter", ct.c_int), ("seed", ct.c_uint64),
+                ("switch_tol", ct.c_double * 2), ("reorth_every", ct.c_int),
+                ("rr_every", ct.c_int), ("lag", ct.c_int),
+                ("stream", ct.c_void_p)]
+
+
+class trm_stats(ct.Structure):
+    _fields_ = [("iterations", ct.c_int), ("iterations_phase", ct.c_int * 3),
+                ("converged", ct.c_int), ("rms_residual", ct.c_double),
+                ("max_residual", ct.c_double), ("E_last", ct.c_double),
+                ("seconds", ct.c_double), ("launches", ct.c_longlong)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations,
+                "iterations_phase": list(self.iterations_phase),
+                "converged": bool(self.converged),
+                "rms_residual": self.rms_residual,
+                "max_residual": self.max_residual, "E_last": self.E_last,
+                "seconds": self.seconds, "launches": self.launches}
+
+
+class trm_kernel_stats(ct.Structure):
+    _fields_ = [("name", ct.c_char * 16), ("ms", ct.c_double),
+                ("launches", ct.c_longlong), ("flops", ct.c_double),
+                ("bytes", ct.c_double)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(paper_1108_4509_gb300._build.build())")
+lib = ct.CDLL(LIB_PATH)
+
+_h = ct.c_void_p
+_p = ct.c_void_p
+_i = ct.c_int
+_i64 = ct.c_int64
+_d = ct.c_double
+_dp = ct.POINTER(ct.c_double)
+
+_SIGS = {
+    "trm_default_options": (_i, [ct.POINTER(trm_options)]),
+    "trm_create_stencil": (_i, [ct.POINTER(_h), _i, _i, _i, _i, _d, _p, _i, _d,
+                                ct.POINTER(trm_options)]),
+    "trm_create_csr": (_i, [ct.POINTER(_h), _i64, _p, _p, _p, _i, _i, _d,
+                            ct.POINTER(trm_options)]),
+    "trm_solve": (_i, [_h, _p, _p, _p, _i, _p, ct.POINTER(trm_stats)]),
+    "trm_destroy": (_i, [_h]),
+    "trm_strerror": (ct.c_char_p, [_i]),
+    "trm_last_error": (ct.c_char_p, [_h]),
+    "trm_last_global_error": (ct.c_char_p, []),
+    "trm_dim": (_i64, [_h]),
+    "trm_apply_h": (_i, [_h, _i, _p, _i, _p, _i]),
+    "trm_energy_gradient": (_i, [_h, _p, _p, _p, _p, _p, _i, _i]),
+    "trm_gram": (_i, [_i64, _i, _i, _i, _p, _p, _p, _p]),
+    "trm_orthonormalize": (_i, [_i64, _i, _p, _p]),
+    "trm_set_block": (_i, [_h, _p]),
+    "trm_get_block": (_i, [_h, _p]),
+    "trm_iterate": (_i, [_h, _i, _i, _p, _p, _p]),
+    "trm_rayleigh_ritz": (_i, [_h, _p, _p, _p]),
+    "trm_random_block": (_i, [_i64, _i, ct.c_uint64, _p, _p]),
+    "trm_profile": (_i, [_h, _i]),
+    "trm_profile_read": (_i, [_h, ct.POINTER(trm_kernel_stats), _i]),
+    "trm_launch_count": (ct.c_longlong, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class TrmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{lib.trm_strerror(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = (lib.trm_last_error(handle) if handle else
+               lib.trm_last_global_error())
+        raise TrmError(status, (msg or b"").decode())
+    return status
+
+
+def _host(a, dtype):
+    """Pointer to a contiguous host numpy array of the given dtype (or None)."""
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype) if not (
+        isinstance(a, np.ndarray) and a.dtype == dtype
+        and (a.flags["C_CONTIGUOUS"] or a.flags["F_CONTIGUOUS"])) else a
+    return arr, arr.ctypes.data_as(ct.c_void_p)
+
+
+def _colmajor(a, dtype):
+    """Host N x m block as column-major (Fortran) memory."""
+    arr = np.asfortranarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(ct.c_void_p)
+
+
+# --------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# --------------------------------------------------------------------------
+def trm_default_options(**overrides) -> trm_options:
+    o = trm_options()
+    _check(lib.trm_default_options(ct.byref(o)))
+    for k, v in overrides.items():
+        if k == "switch_tol":
+            for i, x in enumerate(v):
+                o.switch_tol[i] = x
+        elif k == "stream":
+            o.stream = ct.c_void_p(int(v) if v else 0)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def trm_create_stencil(nx, ny, nz, order, h, V, m, tol, opt=None):
+    handle = _h()
+    Varr, Vp = _host(V, np.float64)
+    if Varr is not None and Varr.size != nx * ny * nz:
+        raise ValueError("V must have nx*ny*nz entries")
+    _check(lib.trm_create_stencil(ct.byref(handle), nx, ny, nz, order, h, Vp,
+                                  m, tol, ct.byref(opt) if opt else None))
+    return handle
+
+
+def trm_create_csr(N, rowptr, cols, vals, m, tol, opt=None):
+    handle = _h()
+    rp, rpp = _host(rowptr, np.int32)
+    ci, cip = _host(cols, np.int32)
+    vals = np.asarray(vals)
+    dt = TRM_F64 if vals.dtype == np.float64 else TRM_F32
+    va, vap = _host(vals, np.float64 if dt == TRM_F64 else np.float32)
+    _check(lib.trm_create_csr(ct.byref(handle), N, rpp, cip, vap, dt, m, tol,
+                              ct.byref(opt) if opt else None))
+    return handle
+
+
+def trm_solve(handle, N, m, C_out=None, C_on_device=False, C0=None):
+    """Returns (lambda, E_G, stats, status). C_out: device address (int) when
+    C_on_device, else a host float64 array of shape (N, m) in Fortran order
+    that receives C, or None."""
+    lam = np.zeros(m)
+    eg = ct.c_double(0.0)
+    st = trm_stats()
+    c0arr, c0p = _colmajor(C0, np.float64) if C0 is not None else (None, None)
+    if C_out is None:
+        cp = None
+    elif C_on_device:
+        cp = ct.c_void_p(int(C_out))
+    else:
+        if not (isinstance(C_out, np.ndarray) and C_out.flags["F_CONTIGUOUS"]
+                and C_out.dtype == np.float64 and C_out.shape == (N, m)):
+            raise ValueError("host C_out must be a Fortran-ordered float64 (N, m) array")
+        cp = C_out.ctypes.data_as(ct.c_void_p)
+    status = lib.trm_solve(handle, lam.ctypes.data_as(ct.c_void_p),
+                           ct.cast(ct.byref(eg), ct.c_void_p), cp,
+                           1 if C_on_device else 0, c0p, ct.byref(st))
+    if status not in (0, -4):
+        _check(status, handle)
+    return lam, eg.value, st, status
+
+
+def trm_destroy(handle):
+    if handle:
+        _check(lib.trm_destroy(handle))
+
+
+def trm_strerror(status):
+    return lib.trm_strerror(status).decode()
+
+
+def trm_last_error(handle=None):
+    r = lib.trm_last_error(handle) if handle else lib.trm_last_global_error()
+    return (r or b"").decode()
+
+
+def trm_dim(handle):
+    return int(lib.trm_dim(handle))
+
+
+def trm_apply_h(handle, dtype_in, C_ptr, dtype_out, X_ptr, ncols):
+    return _check(lib.trm_apply_h(handle, dtype_in, ct.c_void_p(C_ptr),
+                                  dtype_out, ct.c_void_p(X_ptr), ncols), handle)
+
+
+def trm_energy_gradient(handle, C_ptr, HD_ptr, Hprime_ptr, G_ptr, G_dtype,
+                        zero_diag):
+    E = ct.c_double(0.0)
+    _check(lib.trm_energy_gradient(handle, ct.c_void_p(C_ptr),
+                                   ct.cast(ct.byref(E), ct.c_void_p),
+                                   ct.c_void_p(HD_ptr) if HD_ptr else None,
+                                   ct.c_void_p(Hprime_ptr) if Hprime_ptr else None,
+                                   ct.c_void_p(G_ptr), G_dtype,
+                                   1 if zero_diag else 0), handle)
+    return E.value
+
+
+def trm_gram(N, m, n, dtype, A_ptr, B_ptr, out_ptr, stream=0):
+    return _check(lib.trm_gram(N, m, n, dtype, ct.c_void_p(A_ptr),
+                               ct.c_void_p(B_ptr), ct.c_void_p(out_ptr),
+                               ct.c_void_p(stream or 0)))
+
+
+def trm_orthonormalize(N, m, C_ptr, stream=0):
+    return _check(lib.trm_orthonormalize(N, m, ct.c_void_p(C_ptr),
+                                         ct.c_void_p(stream or 0)))
+
+
+def trm_set_block(handle, C_ptr):
+    return _check(lib.trm_set_block(handle, ct.c_void_p(C_ptr)), handle)
+
+
+def trm_get_block(handle, C_ptr):
+    return _check(lib.trm_get_block(handle, ct.c_void_p(C_ptr)), handle)
+
+
+def trm_iterate(handle, mode, restart=False):
+    E, r, a = ct.c_double(), ct.c_double(), ct.c_double()
+    _check(lib.trm_iterate(handle, mode, 1 if restart else 0,
+                           ct.cast(ct.byref(E), ct.c_void_p),
+                           ct.cast(ct.byref(r), ct.c_void_p),
+                           ct.cast(ct.byref(a), ct.c_void_p)), handle)
+    return E.value, r.value, a.value
+
+
+def trm_rayleigh_ritz(handle, C_ptr, m):
+    lam = np.zeros(m)
+    res = np.zeros(m)
+    _check(lib.trm_rayleigh_ritz(handle, ct.c_void_p(C_ptr),
+                                 lam.ctypes.data_as(ct.c_void_p),
+                                 res.ctypes.data_as(ct.c_void_p)), handle)
+    return lam, res
+
+
+def trm_random_block(N, m, seed, C_ptr, stream=0):
+    return _check(lib.trm_random_block(N, m, ct.c_uint64(seed),
+                                       ct.c_void_p(C_ptr),
+                                       ct.c_void_p(stream or 0)))
+
+
+def trm_profile(handle, enable):
+    return _check(lib.trm_profile(handle, 1 if enable else 0), handle)
+
+
+def trm_profile_read(handle):
+    """{class name: {ms, launches, flops, bytes}} of the handle's timed calls."""
+    buf = (trm_kernel_stats * 32)()
+    n = lib.trm_profile_read(handle, buf, 32)
+    if n < 0:
+        _check(n, handle)
+    return {buf[k].name.decode(): {"ms": buf[k].ms, "launches": buf[k].launches,
+                                   "flops": buf[k].flops, "bytes": buf[k].bytes}
+            for k in range(min(n, 32))}
+
+
+def trm_launch_count():
+    return int(lib.trm_launch_count())
+
+
+class Solver:
+    """Owns one handle. ``Solver.stencil(...)`` / ``Solver.csr(...)`` create
+    it; ``solve()`` runs it; ``close()`` (or the context manager) frees it."""
+
+    def __init__(self, handle, N, m):
+        self.handle, self.N, self.m = handle, N, m
+
+    @classmethod
+    def stencil(cls, shape, order, h, V, m, tol, **opts):
+        nx, ny, nz = (tuple(shape) + (1, 1))[:3]
+        opt = trm_default_options(**opts)
+        return cls(trm_create_stencil(nx, ny, nz, order, h, V, m, tol, opt),
+                   nx * ny * nz, m)
+
+    @classmethod
+    def csr(cls, N, rowptr, cols, vals, m, tol, **opts):
+        opt = trm_default_options(**opts)
+        return cls(trm_create_csr(N, rowptr, cols, vals, m, tol, opt), N, m)
+
+    def solve(self, C0=None, want_C=True):
+        C = np.zeros((self.N, self.m), order="F") if want_C else None
+        lam, eg, st, status = trm_solve(self.handle, self.N, self.m, C_out=C,
+                                        C0=C0)
+        return lam, eg, C, st.as_dict(), status
+
+    def close(self):
+        if self.handle:
+            trm_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,103 @@
+// Shared device/host helpers of the trace-minimization library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+
+namespace trm {
+
+// Library error carried to the C ABI boundary, where it becomes a status.
+struct Error : std::runtime_error {
+  int status;
+  Error(int s, const std::string& msg) : std::runtime_error(msg), status(s) {}
+};
+
+#define TRM_CUDA(expr)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (expr);                                                  \
+    if (e_ != cudaSuccess)                                                    \
+      throw ::trm::Error(-5, std::string(#expr) + ": " +                      \
+                                 cudaGetErrorString(e_) + " (" + __FILE__ +   \
+                                 ":" + std::to_string(__LINE__) + ")");       \
+  } while (0)
+
+// Every kernel launch of the library is followed by this check, which also
+// counts the launch (process-wide, all devices).
+void count_launch();
+#define TRM_CHECK_LAUNCH()           \
+  do {                               \
+    TRM_CUDA(cudaGetLastError());    \
+    ::trm::count_launch();           \
+  } while (0)
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Number of SMs of the current device (cached per process).
+int sm_count();
+// Kernel launches issued by the library so far in this process.
+long long launch_count();
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions: warp xor-shuffle trees and fixed block trees.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of NQ values over the block (blockDim.x a multiple of 32, <= 1024).
+// Result valid in thread 0. scratch: >= 32*NQ doubles of shared memory.
+template <int NQ>
+__device__ __forceinline__ void block_sum(double (&v)[NQ], double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarp = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) scratch[q * 32 + warp] = v[q];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double x = lane < nwarp ? scratch[q * 32 + lane] : 0.0;
+      v[q] = warp_sum(x);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Scalars of one iteration, resident in device memory.
+// ---------------------------------------------------------------------------
+struct IterScalars {
+  double E;        // energy trace(C^T H C) = sum_j H_D,j
+  double gg;       // tr(G^T G)
+  double gMg;      // tr(G^T M G)
+  double gpMg;     // tr(G_prev^T M G)
+  double gPp;      // tr(G^T P_prev)
+  double a_prev;   // tr(G_prev^T M G_prev)
+  double gamma;    // Polak-Ribiere coefficient used for P
+  double slope0;   // E'(0) = -tr(G^T P)
+  double alpha;    // step taken
+  double alpha_prev;
+  double rms;      // ||G||_F / (2 sqrt(m))
+  double c2;       // curvature of the quadratic line model
+  double dE;       // predicted energy change of the step
+  int restart;     // 1: next P uses gamma = 0
+  int status;      // bit flags: 1 = overlap not positive definite
+  int iter;
+  int pad;
+};
+
+}  // namespace trm

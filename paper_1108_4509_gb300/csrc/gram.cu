@@ -1,0 +1,172 @@
+// Tall-skinny Gram products out = A^T [B_0 | B_1 | ...] with K = N rows
+// (Fig. EGFIG step (6) H' = C^T X'; Fig. ONFIG step (1) S = C^T C; the
+// line-search projections C^T P, P^T P, P^T H P, P^T G).
+//
+// Split-K over the N rows: CTA (s, t) multiplies rows [s*R, (s+1)*R) of its
+// 64 x 64 output tile t, summing in the input precision, and writes the tile
+// as FP64 partials; a second kernel adds the partials of all splits in a fixed
+// order, so the result is bitwise reproducible.
+#include "ops.cuh"
+
+namespace trm {
+
+namespace {
+
+constexpr int TM = 64;   // output tile rows (columns of A)
+constexpr int TN = 64;   // output tile columns (columns of B)
+constexpr int TK = 32;   // rows of A/B per shared-memory stage
+constexpr int LDS = 68;  // padded shared row length (16-byte aligned)
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  static __device__ __forceinline__ void ld(const float* p, float (&v)[4]) {
+    float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  static __device__ __forceinline__ void ld(const double* p, double (&v)[4]) {
+    double2 a = reinterpret_cast<const double2*>(p)[0];
+    double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_gram(int64_t N, int m, const T* __restrict__ A, Blocks<T> B,
+           int64_t rows_per_split, int tiles_m, double* __restrict__ part) {
+  __shared__ __align__(16) T As[TK][LDS];
+  __shared__ __align__(16) T Bs[TK][LDS];
+  const int n = B.total();
+  const int split = blockIdx.x;
+  const int tile = blockIdx.y;
+  const int i0 = (tile % tiles_m) * TM;
+  const int j0 = (tile / tiles_m) * TN;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t rb = (int64_t)split * rows_per_split;
+  const int64_t re = min(N, rb + rows_per_split);
+
+  // Column base pointers for this thread's loads (fixed over the K loop).
+  // Thread loads elements e = tid + 256 q, q = 0..7: kk = e % 32, col = e / 32.
+  const T* pa[8];
+  const T* pb[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + 256 * q;
+    const int col = e / TK;
+    const int ia = i0 + col;
+    pa[q] = ia < m ? A + (int64_t)ia * N : nullptr;
+    const int jb = j0 + col;
+    if (jb < n) {
+      const int seg = jb / B.cols;
+      pb[q] = B.p[seg] + (int64_t)(jb - seg * B.cols) * N;
+    } else {
+      pb[q] = nullptr;
+    }
+  }
+  const int kk_ld = tid % TK;
+
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+
+  for (int64_t r0 = rb; r0 < re; r0 += TK) {
+    const int64_t r = r0 + kk_ld;
+    const bool rin = r < re;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int col = (tid + 256 * q) / TK;
+      As[kk_ld][col] = (rin && pa[q]) ? pa[q][r] : (T)0;
+      Bs[kk_ld][col] = (rin && pb[q]) ? pb[q][r] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < TK; ++kk) {
+      T a[4], b[4];
+      Vec4<T>::ld(&As[kk][tx * 4], a);
+      Vec4<T>::ld(&Bs[kk][ty * 4], b);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+    }
+    __syncthreads();
+  }
+  double* out = part + (size_t)split * m * n;
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int i = i0 + tx * 4 + x;
+    if (i >= m) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int j = j0 + ty * 4 + y;
+      if (j < n) out[i + (size_t)j * m] = (double)acc[x][y];
+    }
+  }
+}
+
+__global__ void k_sum_splits(const double* __restrict__ part, int splits,
+                             size_t count, double* __restrict__ out) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  double s = 0.0;
+  for (int k = 0; k < splits; ++k) s += part[(size_t)k * count + e];
+  out[e] = s;
+}
+
+void plan(int64_t N, int m, int n, int* splits, int64_t* rows) {
+  const int tiles = ceil_div(m, TM) * ceil_div(n, TN);
+  const int target = 4 * sm_count();
+  int s = ceil_div(target, tiles);
+  const int64_t max_s = (N + TK - 1) / TK;
+  if (s > max_s) s = (int)max_s;
+  if (s < 1) s = 1;
+  int64_t r = (N + s - 1) / s;
+  r = ((r + TK - 1) / TK) * TK;
+  s = (int)((N + r - 1) / r);
+  *splits = s;
+  *rows = r;
+}
+
+}  // namespace
+
+size_t gram_partials_doubles(int64_t N, int m, int n) {
+  int s;
+  int64_t r;
+  plan(N, m, n, &s, &r);
+  return (size_t)s * m * n;
+}
+
+template <typename T>
+void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
+          double* partials, size_t partials_cap, cudaStream_t s) {
+  const int n = B.total();
+  if (m <= 0 || n <= 0) return;
+  int splits;
+  int64_t rows;
+  plan(N, m, n, &splits, &rows);
+  if ((size_t)splits * m * n > partials_cap)
+    throw Error(-2, "gram: partials buffer too small");
+  const int tiles_m = ceil_div(m, TM);
+  dim3 grid(splits, tiles_m * ceil_div(n, TN));
+  k_gram<T><<<grid, 256, 0, s>>>(N, m, A, B, rows, tiles_m, partials);
+  TRM_CHECK_LAUNCH();
+  const size_t count = (size_t)m * n;
+  k_sum_splits<<<ceil_div(count, 256), 256, 0, s>>>(partials, splits, count,
+                                                    out);
+  TRM_CHECK_LAUNCH();
+}
+
+template void gram<float>(int64_t, int, const float*, const Blocks<float>&,
+                          double*, double*, size_t, cudaStream_t);
+template void gram<double>(int64_t, int, const double*, const Blocks<double>&,
+                           double*, double*, size_t, cudaStream_t);
+
+}  // namespace trm

@@ -1,0 +1,140 @@
+// Internal launcher declarations of the block-step kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace trm {
+
+// ---------------------------------------------------------------------------
+// H operators (Eq. BASICEQ: sparse symmetric H with O(N) nonzeros)
+// ---------------------------------------------------------------------------
+struct StencilOp {
+  int nx = 1, ny = 1, nz = 1;
+  int radius = 1;            // 1: 3-point rule per axis, 2: 5-point rule
+  double c1 = 0.0, c2 = 0.0; // coefficients of the +-1 and +-2 neighbours
+};
+
+struct CsrOp {
+  const int32_t* rowptr = nullptr;
+  const int32_t* cols = nullptr;
+  const float* vals32 = nullptr;
+  const double* vals64 = nullptr;
+  int max_row_nnz = 0;
+};
+
+struct Operator {
+  int kind = 0;  // 0 stencil, 1 csr
+  int64_t N = 0;
+  StencilOp st;
+  CsrOp csr;
+  const double* diag64 = nullptr;  // H_ii
+  const float* diag32 = nullptr;
+  const double* minv64 = nullptr;  // diagonal preconditioner M_ii
+  const float* minv32 = nullptr;
+};
+
+void apply_h(const Operator& op, const float* X, float* Y, int ncols,
+             cudaStream_t s);
+void apply_h(const Operator& op, const double* X, double* Y, int ncols,
+             cudaStream_t s);
+
+// diag[i] = t*w0*ndim + V[i] for a stencil operator
+void stencil_diag(const StencilOp& st, double t_w0_ndim, const double* V,
+                  double* diag64, float* diag32, int64_t N, cudaStream_t s);
+// diag[i] = H_ii from a CSR matrix
+void csr_diag(const Operator& op, double* diag64, float* diag32,
+              cudaStream_t s);
+// M_ii = 1 / (H_ii - sigma), sigma = min_k H_kk - 1; work: >= 1024 doubles
+void diag_preconditioner(const double* diag64, int64_t N, double* minv64,
+                         float* minv32, double* work, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Gram products out = A^T [B_0 | B_1 | ...] (FP64 m x n, column-major)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Blocks {
+  const T* p[4] = {nullptr, nullptr, nullptr, nullptr};
+  int cols = 0;   // columns per segment
+  int count = 0;  // segments
+  __host__ __device__ int total() const { return cols * count; }
+};
+
+size_t gram_partials_doubles(int64_t N, int m, int n);
+template <typename T>
+void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
+          double* partials, size_t partials_cap, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Tall-skinny products and fused row-local updates
+// ---------------------------------------------------------------------------
+// H_D[j] = sum_i C_ij X_ij (FP64), E = sum_j H_D[j] into sc->E
+template <typename T>
+void energy_diag(int64_t N, int m, const T* C, const T* X, double* HD,
+                 IterScalars* sc, double* partials, cudaStream_t s);
+// X' = X - C diag(H_D), in place on X; optional FP32 copies (MP2 phase)
+template <typename T>
+void xprime(int64_t N, int m, const T* C, T* X, const double* HD,
+            float* C32, float* Xp32, cudaStream_t s);
+// G = -2 (X' - C H') with the Polak-Ribiere partial sums; G_prev/P_prev may
+// be null (first iteration). Then the device scalar update of gamma, r.
+template <typename T>
+void gradient(int64_t N, int m, const T* C, const T* Xp, const double* Hp,
+              T* G, const T* Gprev, const T* Pprev, const T* minv,
+              IterScalars* sc, double* partials, size_t partials_cap,
+              cudaStream_t s);
+// P = M G + gamma P (gamma from sc)
+template <typename T>
+void update_p(int64_t N, int m, const T* G, T* P, const T* minv,
+              const IterScalars* sc, cudaStream_t s);
+// Cn = (C + alpha P) R, R upper triangular m x m FP64 (alpha from sc, or 0
+// when P is null)
+template <typename T, typename TP>
+void rotate(int64_t N, int m, const T* C, const TP* P, const double* R,
+            T* Cn, const IterScalars* sc, cudaStream_t s);
+// MP1 (ii): Cn = Y L_D + fl32(Y) L', Y = C + alpha P; R = L^{-T} FP64
+void rotate_split(int64_t N, int m, const double* C, const float* P,
+                  const double* R, double* Cn, const IterScalars* sc,
+                  cudaStream_t s);
+// Y = A M for A: N x k (FP64), M: k x n FP64
+void mult(int64_t N, int k, int n, const double* A, const double* M,
+          double* Y, cudaStream_t s);
+// per-column 2-norms of X - C diag(lambda) into res (FP64 device m)
+void column_residuals(int64_t N, int m, const double* X, const double* C,
+                      const double* lam, double* res, double* partials,
+                      cudaStream_t s);
+// flip each column's sign so its largest-magnitude entry is positive,
+// applied to C and X together
+void fix_signs(int64_t N, int m, double* C, double* X, double* work,
+               cudaStream_t s);
+void to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
+void to_f64(const float* x, double* y, int64_t n, cudaStream_t s);
+void random_block(int64_t N, int m, uint64_t seed, double* C, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// m x m FP64 matrices on the device
+// ---------------------------------------------------------------------------
+// Cm = alpha op(A) op(B) + beta Cm (all m x m FP64, column-major)
+void mm_gemm(int m, const double* A, bool trA, const double* B, bool trB,
+             double* Cm, double alpha, double beta, cudaStream_t s);
+// A0 = sym(H') + diag(H_D)
+void make_A0(int m, const double* Hp, const double* HD, double* A0,
+             cudaStream_t s);
+// line model: alpha from the projections (T1 = A0 B, T2 = B A0); writes
+// S = I + a (B + B^T) + a^2 Q and the step into sc
+template <typename Tm>
+void line_step(int m, const double* A0, const double* Bm, const double* Q,
+               const double* HPP, const double* W, const double* T1,
+               const double* T2, double* S, IterScalars* sc, cudaStream_t s);
+// S = L L^T (lower); writes Linv = L^{-1} and R = L^{-T}. Non-PD sets
+// sc->status bit 1 and returns identities. gwork: m*m doubles.
+template <typename Tm>
+void chol_inv(int m, const double* S, double* Linv, double* R,
+              IterScalars* sc, double* gwork, cudaStream_t s);
+// set diagonal of an m x m matrix to zero
+void zero_diag(int m, double* A, cudaStream_t s);
+// symmetric eigenproblem A = Z diag(w) Z^T (cyclic Jacobi, FP64), w
+// ascending; work: 2*m*m doubles; info (device int): sweeps or -1
+void sym_eig(int m, const double* A, double* w, double* Z, double* work,
+             int* info, cudaStream_t s);
+
+}  // namespace trm

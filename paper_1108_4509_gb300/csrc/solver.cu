@@ -1,0 +1,885 @@
+// The trace-minimization loop of Fig. TMFIG on the device, with the precision
+// modes of Sec. 2.2, driven from the host. Each iteration is a fixed sequence
+// of kernels on one stream with no host synchronisation; the host reads the
+// iteration's scalars (energy, residual, step) from a pinned ring a few
+// iterations late and decides on convergence and on phase changes.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "solver.cuh"
+
+namespace trm {
+
+namespace {
+
+constexpr int kRing = 64;
+
+__global__ void k_set_restart(IterScalars* sc) {
+  sc->restart = 1;
+  sc->status = 0;
+}
+
+double neumaier_sum(const double* x, int n) {
+  double s = 0.0, c = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double t = s + x[i];
+    if (std::fabs(s) >= std::fabs(x[i]))
+      c += (s - t) + x[i];
+    else
+      c += (x[i] - t) + s;
+    s = t;
+  }
+  return s + c;
+}
+
+}  // namespace
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+const char* const kClassNames[KC_COUNT] = {
+    "spmm_f32", "spmm_f64", "gram_f32", "gram_f64", "grad_f32", "grad_f64",
+    "rotate_f32", "rotate_f64", "rowops", "small_mm", "eig"};
+
+Profiler::~Profiler() {
+  for (auto& r : pending_) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : pool_) cudaEventDestroy(e);
+}
+
+cudaEvent_t Profiler::get() {
+  if (!pool_.empty()) {
+    cudaEvent_t e = pool_.back();
+    pool_.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  TRM_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+void Profiler::begin(int, cudaStream_t s) {
+  if (!on) return;
+  open_ = get();
+  TRM_CUDA(cudaEventRecord(open_, s));
+}
+
+void Profiler::end(int k, double fl, double by, cudaStream_t s) {
+  if (!on || !open_) return;
+  cudaEvent_t b = get();
+  TRM_CUDA(cudaEventRecord(b, s));
+  pending_.push_back({k, open_, b, fl, by});
+  open_ = nullptr;
+}
+
+void Profiler::resolve() {
+  size_t done = 0;
+  for (auto& r : pending_) {
+    if (cudaEventQuery(r.b) != cudaSuccess) break;
+    float t = 0.f;
+    TRM_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.k] += t;
+    launches[r.k] += 1;
+    flops[r.k] += r.flops;
+    bytes[r.k] += r.bytes;
+    pool_.push_back(r.a);
+    pool_.push_back(r.b);
+    ++done;
+  }
+  cudaGetLastError();
+  pending_.erase(pending_.begin(), pending_.begin() + done);
+}
+
+void Profiler::reset() {
+  for (int k = 0; k < KC_COUNT; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+    flops[k] = bytes[k] = 0.0;
+  }
+}
+
+DevArena::~DevArena() {
+  for (void* p : ptrs_) cudaFree(p);
+}
+
+void* DevArena::alloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(-2, "cudaMalloc of " + std::to_string(bytes) +
+                        " bytes failed: " + cudaGetErrorString(e));
+  }
+  ptrs_.push_back(p);
+  total_ += bytes;
+  return p;
+}
+
+Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
+    : N_(N), m_(m), tol_(tol), opt_(opt) {
+  s_ = reinterpret_cast<cudaStream_t>(opt.stream);
+  const size_t nm = (size_t)N * m;
+  const size_t mm = (size_t)m * m;
+  auto d = [&](size_t n) { return static_cast<double*>(mem_.alloc(n * 8)); };
+  auto f = [&](size_t n) { return static_cast<float*>(mem_.alloc(n * 4)); };
+  C64_ = d(nm);
+  C64n_ = d(nm);
+  X64_ = d(nm);
+  C32_ = f(nm);
+  C32n_ = f(nm);
+  X32_ = f(nm);
+  Gb_[0] = d(nm);
+  Gb_[1] = d(nm);
+  Pb_ = d(nm);
+  HPb_ = d(nm);
+  for (void* p : {Gb_[0], Gb_[1], Pb_, HPb_})
+    TRM_CUDA(cudaMemsetAsync(p, 0, nm * 8, s_));
+  HD_ = d(m);
+  Hp_ = d(mm);
+  A0_ = d(mm);
+  Bm_ = d(mm);
+  PG_ = d(3 * mm);
+  T1_ = d(mm);
+  T2_ = d(mm);
+  S_ = d(mm);
+  Linv_ = d(mm);
+  R_ = d(mm);
+  Z_ = d(mm);
+  mmw_ = d(2 * mm);
+  eigw_ = d(m);
+  lam_ = d(m);
+  res_ = d(m);
+  info_ = static_cast<int*>(mem_.alloc(16));
+  const size_t chunks = (size_t)ceil_div(N, 4096);
+  part_cap_ = std::max<size_t>(
+      {gram_partials_doubles(N, m, 3 * m), gram_partials_doubles(N, m, m),
+       (size_t)4 * ceil_div(N, 64) * ceil_div(m, 64), 3 * chunks * m + m,
+       (size_t)4096});
+  part_ = d(part_cap_);
+  sc_ = static_cast<IterScalars*>(mem_.alloc(sizeof(IterScalars)));
+  TRM_CUDA(cudaMemsetAsync(sc_, 0, sizeof(IterScalars), s_));
+  diag64_ = d(N);
+  diag32_ = f(N);
+  minv64_ = d(N);
+  minv32_ = f(N);
+  TRM_CUDA(cudaHostAlloc(&ring_, sizeof(IterScalars) * kRing,
+                         cudaHostAllocDefault));
+  ev_.resize(kRing);
+  for (auto& e : ev_) TRM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  set_restart();
+}
+
+Solver::~Solver() {
+  if (s_) cudaStreamSynchronize(s_);
+  else cudaDeviceSynchronize();
+  for (auto& e : ev_) cudaEventDestroy(e);
+  if (ring_) cudaFreeHost(ring_);
+}
+
+void Solver::init_stencil(int nx, int ny, int nz, int order, double h,
+                          const double* V_host) {
+  order_ = order;
+  const double t = 0.5 / (h * h);
+  double w0, w1, w2;
+  if (order == 2) {
+    w0 = 2.0; w1 = -1.0; w2 = 0.0;
+  } else {
+    w0 = 2.5; w1 = -4.0 / 3.0; w2 = 1.0 / 12.0;
+  }
+  const int ndim = (nx > 1) + (ny > 1) + (nz > 1);
+  op_.kind = 0;
+  op_.N = N_;
+  op_.st.nx = nx;
+  op_.st.ny = ny;
+  op_.st.nz = nz;
+  op_.st.radius = order == 2 ? 1 : 2;
+  op_.st.c1 = t * w1;
+  op_.st.c2 = t * w2;
+  double* Vd = nullptr;
+  if (V_host) {
+    Vd = static_cast<double*>(mem_.alloc((size_t)N_ * 8));
+    TRM_CUDA(cudaMemcpyAsync(Vd, V_host, (size_t)N_ * 8,
+                             cudaMemcpyHostToDevice, s_));
+  }
+  stencil_diag(op_.st, t * w0 * ndim, Vd, diag64_, diag32_, N_, s_);
+  op_.diag64 = diag64_;
+  op_.diag32 = diag32_;
+  if (opt_.precond) {
+    diag_preconditioner(diag64_, N_, minv64_, minv32_, part_, s_);
+    op_.minv64 = minv64_;
+    op_.minv32 = minv32_;
+  }
+  TRM_CUDA(cudaStreamSynchronize(s_));
+}
+
+void Solver::init_csr(const int32_t* rowptr, const int32_t* cols,
+                      const void* vals, int vals_fp64) {
+  const int64_t nnz = rowptr[N_];
+  auto* rp = static_cast<int32_t*>(mem_.alloc((size_t)(N_ + 1) * 4));
+  auto* ci = static_cast<int32_t*>(mem_.alloc((size_t)nnz * 4));
+  TRM_CUDA(cudaMemcpyAsync(rp, rowptr, (size_t)(N_ + 1) * 4,
+                           cudaMemcpyHostToDevice, s_));
+  TRM_CUDA(cudaMemcpyAsync(ci, cols, (size_t)nnz * 4, cudaMemcpyHostToDevice,
+                           s_));
+  op_.kind = 1;
+  op_.N = N_;
+  op_.csr.rowptr = rp;
+  op_.csr.cols = ci;
+  int mx = 0;
+  for (int64_t r = 0; r < N_; ++r) mx = std::max(mx, rowptr[r + 1] - rowptr[r]);
+  op_.csr.max_row_nnz = mx;
+  if (vals_fp64) {
+    auto* v = static_cast<double*>(mem_.alloc((size_t)nnz * 8));
+    TRM_CUDA(cudaMemcpyAsync(v, vals, (size_t)nnz * 8, cudaMemcpyHostToDevice,
+                             s_));
+    op_.csr.vals64 = v;
+  } else {
+    auto* v = static_cast<float*>(mem_.alloc((size_t)nnz * 4));
+    TRM_CUDA(cudaMemcpyAsync(v, vals, (size_t)nnz * 4, cudaMemcpyHostToDevice,
+                             s_));
+    op_.csr.vals32 = v;
+  }
+  csr_diag(op_, diag64_, diag32_, s_);
+  op_.diag64 = diag64_;
+  op_.diag32 = diag32_;
+  if (opt_.precond) {
+    diag_preconditioner(diag64_, N_, minv64_, minv32_, part_, s_);
+    op_.minv64 = minv64_;
+    op_.minv32 = minv32_;
+  }
+  TRM_CUDA(cudaStreamSynchronize(s_));
+}
+
+// Algorithmic flops and bytes of one H application to ncols columns of
+// element size es: every stored nonzero is one multiply-add; the block is read
+// and written once and the operator data (diagonal or CSR) read once.
+static void spmm_cost(const Operator& op, int ncols, int es, double* fl,
+                      double* by) {
+  const double N = (double)op.N;
+  double nnz_row;
+  if (op.kind == 0) {
+    const int ndim = (op.st.nx > 1) + (op.st.ny > 1) + (op.st.nz > 1);
+    nnz_row = 1.0 + 2.0 * op.st.radius * ndim;
+    *by = 2.0 * es * N * ncols + 8.0 * N;
+  } else {
+    nnz_row = 0.0;  // filled below
+    *by = 2.0 * es * N * ncols;
+  }
+  if (op.kind == 1) {
+    // nnz is not stored on the device side; the row-length bound is used
+    nnz_row = op.csr.max_row_nnz;
+    const int vs = op.csr.vals64 ? 8 : 4;
+    *by += N * nnz_row * (4.0 + vs) + 4.0 * (N + 1);
+  }
+  *fl = 2.0 * nnz_row * N * ncols;
+}
+
+#define TRM_PROF(k, fl, by, call) \
+  do {                            \
+    prof.begin((k), s_);          \
+    call;                         \
+    prof.end((k), (fl), (by), s_); \
+  } while (0)
+
+void Solver::set_restart() {
+  k_set_restart<<<1, 1, 0, s_>>>(sc_);
+  TRM_CHECK_LAUNCH();
+}
+
+void Solver::read_scalars(IterScalars* out) {
+  TRM_CUDA(cudaMemcpyAsync(&ring_[0], sc_, sizeof(IterScalars),
+                           cudaMemcpyDeviceToHost, s_));
+  TRM_CUDA(cudaStreamSynchronize(s_));
+  *out = ring_[0];
+}
+
+// ---------------------------------------------------------------------------
+// One iteration with every block in precision T and the m x m line model and
+// factorisation in Tm (full DP: double/double; full SP: float/float).
+// ---------------------------------------------------------------------------
+template <typename T, typename Tm>
+void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
+  const T* minv = nullptr;
+  if (opt_.precond) {
+    if constexpr (sizeof(T) == 4)
+      minv = minv32_;
+    else
+      minv = minv64_;
+  }
+  const size_t mm = (size_t)m_ * m_;
+  const double es = sizeof(T), Nd = (double)N_, md = m_;
+  const double nm = Nd * md, m2N = nm * md;
+  const int ksp = sizeof(T) == 4 ? KC_SPMM32 : KC_SPMM64;
+  const int kgr = sizeof(T) == 4 ? KC_GRAM32 : KC_GRAM64;
+  const int kgd = sizeof(T) == 4 ? KC_GRAD32 : KC_GRAD64;
+  const int krt = sizeof(T) == 4 ? KC_ROT32 : KC_ROT64;
+  double sfl, sby;
+  spmm_cost(op_, m_, (int)es, &sfl, &sby);
+  TRM_PROF(ksp, sfl, sby, apply_h(op_, C, X, m_, s_));               // Alg-2 (1)
+  TRM_PROF(KC_ROWOPS, 2 * nm, 2 * es * nm,
+           energy_diag<T>(N_, m_, C, X, HD_, sc_, part_, s_));        // (2), (3)
+  TRM_PROF(KC_ROWOPS, 2 * nm, 3 * es * nm,
+           xprime<T>(N_, m_, C, X, HD_, nullptr, nullptr, s_));       // (5)
+  Blocks<T> bx;
+  bx.p[0] = X;
+  bx.cols = m_;
+  bx.count = 1;
+  TRM_PROF(kgr, 2 * m2N, 2 * es * nm,
+           gram<T>(N_, m_, C, bx, Hp_, part_, part_cap_, s_));        // (6)
+  if (sizeof(T) == 4) zero_diag(m_, Hp_, s_);
+  TRM_PROF(kgd, 2 * m2N, 5 * es * nm,
+           gradient<T>(N_, m_, C, X, Hp_, G, Gp, P, minv, sc_, part_,
+                       part_cap_, s_));                               // (7)
+  TRM_PROF(KC_ROWOPS, 2 * nm, 3 * es * nm,
+           update_p<T>(N_, m_, G, P, minv, sc_, s_));                 // P
+  TRM_PROF(ksp, sfl, sby, apply_h(op_, P, HP, m_, s_));              // H P
+  Blocks<T> bp;
+  bp.p[0] = P;
+  bp.cols = m_;
+  bp.count = 1;
+  TRM_PROF(kgr, 2 * m2N, 2 * es * nm,
+           gram<T>(N_, m_, C, bp, Bm_, part_, part_cap_, s_));        // C^T P
+  Blocks<T> b3;
+  b3.p[0] = P;
+  b3.p[1] = HP;
+  b3.p[2] = G;
+  b3.cols = m_;
+  b3.count = 3;
+  TRM_PROF(kgr, 6 * m2N, 4 * es * nm,
+           gram<T>(N_, m_, P, b3, PG_, part_, part_cap_, s_));        // P^T[P HP G]
+  const double m3 = md * md * md;
+  prof.begin(KC_SMALL, s_);
+  make_A0(m_, Hp_, HD_, A0_, s_);
+  mm_gemm(m_, A0_, false, Bm_, false, T1_, 1.0, 0.0, s_);
+  mm_gemm(m_, Bm_, false, A0_, false, T2_, 1.0, 0.0, s_);
+  line_step<Tm>(m_, A0_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, T1_, T2_, S_, sc_,
+                s_);
+  chol_inv<Tm>(m_, S_, Linv_, R_, sc_, mmw_, s_);           // Fig. ONFIG
+  prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
+  TRM_PROF(krt, m2N, 3 * es * nm,
+           (rotate<T, T>(N_, m_, C, P, R_, Cn, sc_, s_)));    // (C+aP)L^-T
+  std::swap(C, Cn);
+  std::swap(G, Gp);
+}
+
+// ---------------------------------------------------------------------------
+// MP2 (Sec. 2.2): steps (1), (2), (3), (5) and E in FP64; H' and G from FP32
+// products (diag(H') = 0); G, P, HP stored FP32; m x m work in FP64; the
+// rotation split as C L_D (FP64) + C L' (FP32), C kept in FP64.
+// ---------------------------------------------------------------------------
+void Solver::iter_mp2() {
+  float* G = static_cast<float*>(Gb_[0]);
+  float* Gp = static_cast<float*>(Gb_[1]);
+  float* P = static_cast<float*>(Pb_);
+  float* HP = static_cast<float*>(HPb_);
+  const float* minv = opt_.precond ? minv32_ : nullptr;
+  const size_t mm = (size_t)m_ * m_;
+  const double Nd = (double)N_, md = m_;
+  const double nm = Nd * md, m2N = nm * md, m3 = md * md * md;
+  double f64, b64, f32, b32;
+  spmm_cost(op_, m_, 8, &f64, &b64);
+  spmm_cost(op_, m_, 4, &f32, &b32);
+  TRM_PROF(KC_SPMM64, f64, b64, apply_h(op_, C64_, X64_, m_, s_));   // (1) FP64
+  TRM_PROF(KC_ROWOPS, 2 * nm, 16 * nm,
+           energy_diag<double>(N_, m_, C64_, X64_, HD_, sc_, part_, s_));
+  TRM_PROF(KC_ROWOPS, 2 * nm, 32 * nm,
+           xprime<double>(N_, m_, C64_, X64_, HD_, C32_, X32_, s_));  // (5)
+  Blocks<float> bx;
+  bx.p[0] = X32_;
+  bx.cols = m_;
+  bx.count = 1;
+  TRM_PROF(KC_GRAM32, 2 * m2N, 8 * nm,
+           gram<float>(N_, m_, C32_, bx, Hp_, part_, part_cap_, s_)); // (6)
+  zero_diag(m_, Hp_, s_);
+  TRM_PROF(KC_GRAD32, 2 * m2N, 20 * nm,
+           gradient<float>(N_, m_, C32_, X32_, Hp_, G, Gp, P, minv, sc_,
+                           part_, part_cap_, s_));                    // (7)
+  TRM_PROF(KC_ROWOPS, 2 * nm, 12 * nm,
+           update_p<float>(N_, m_, G, P, minv, sc_, s_));
+  TRM_PROF(KC_SPMM32, f32, b32, apply_h(op_, P, HP, m_, s_));
+  Blocks<float> bp;
+  bp.p[0] = P;
+  bp.cols = m_;
+  bp.count = 1;
+  TRM_PROF(KC_GRAM32, 2 * m2N, 8 * nm,
+           gram<float>(N_, m_, C32_, bp, Bm_, part_, part_cap_, s_));
+  Blocks<float> b3;
+  b3.p[0] = P;
+  b3.p[1] = HP;
+  b3.p[2] = G;
+  b3.cols = m_;
+  b3.count = 3;
+  TRM_PROF(KC_GRAM32, 6 * m2N, 16 * nm,
+           gram<float>(N_, m_, P, b3, PG_, part_, part_cap_, s_));
+  prof.begin(KC_SMALL, s_);
+  make_A0(m_, Hp_, HD_, A0_, s_);
+  mm_gemm(m_, A0_, false, Bm_, false, T1_, 1.0, 0.0, s_);
+  mm_gemm(m_, Bm_, false, A0_, false, T2_, 1.0, 0.0, s_);
+  line_step<double>(m_, A0_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, T1_, T2_, S_,
+                    sc_, s_);
+  chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_);
+  prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
+  TRM_PROF(KC_ROT32, m2N, 20 * nm,
+           rotate_split(N_, m_, C64_, P, R_, C64n_, sc_, s_));
+  std::swap(C64_, C64n_);
+  std::swap(Gb_[0], Gb_[1]);
+}
+
+// Fig. ONFIG in FP64: S = C^T C, S = L L^T, C <- C L^{-T}.
+void Solver::orth_fp64(double*& C, double*& Cn) {
+  Blocks<double> b;
+  b.p[0] = C;
+  b.cols = m_;
+  b.count = 1;
+  const double nm = (double)N_ * m_, m2N = nm * m_;
+  TRM_PROF(KC_GRAM64, 2 * m2N, 16 * nm,
+           gram<double>(N_, m_, C, b, S_, part_, part_cap_, s_));
+  TRM_PROF(KC_SMALL, 2.0 * m_ * m_ * m_ / 3, 0.0,
+           chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_));
+  TRM_PROF(KC_ROT64, m2N, 16 * nm,
+           (rotate<double, double>(N_, m_, C, nullptr, R_, Cn, nullptr, s_)));
+  std::swap(C, Cn);
+}
+
+template <typename T>
+void Solver::orth_uniform(T*& C, T*& Cn) {
+  Blocks<T> b;
+  b.p[0] = C;
+  b.cols = m_;
+  b.count = 1;
+  gram<T>(N_, m_, C, b, S_, part_, part_cap_, s_);
+  chol_inv<T>(m_, S_, Linv_, R_, sc_, mmw_, s_);
+  rotate<T, T>(N_, m_, C, static_cast<const T*>(nullptr), R_, Cn, nullptr,
+               s_);
+  std::swap(C, Cn);
+}
+
+// Subspace rotation diagonalising C^T H C (Sec. 3, the MP2 accuracy remedy).
+void Solver::rr_rotate_fp64() {
+  apply_h(op_, C64_, X64_, m_, s_);
+  Blocks<double> b;
+  b.p[0] = X64_;
+  b.cols = m_;
+  b.count = 1;
+  gram<double>(N_, m_, C64_, b, Hp_, part_, part_cap_, s_);
+  make_A0(m_, Hp_, nullptr, A0_, s_);
+  TRM_PROF(KC_EIG, 0.0, 0.0, sym_eig(m_, A0_, eigw_, Z_, mmw_, info_, s_));
+  const double nm = (double)N_ * m_;
+  TRM_PROF(KC_ROT64, 2 * nm * m_, 16 * nm,
+           mult(N_, m_, m_, C64_, Z_, C64n_, s_));
+  std::swap(C64_, C64n_);
+}
+
+// Rayleigh-Ritz on span(C) (Sec. 2.1) in FP64, as the generalised problem
+// (C^T H C) y = theta (C^T C) y: L = chol(C^T C), A~ = L^{-1} (C^T H C) L^{-T},
+// A~ = Z diag(theta) Z^T, Y = L^{-T} Z, C Y and H C Y, column residuals.
+void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
+  apply_h(op_, C, X64_, m_, s_);
+  Blocks<double> bx;
+  bx.p[0] = X64_;
+  bx.cols = m_;
+  bx.count = 1;
+  gram<double>(N_, m_, C, bx, Hp_, part_, part_cap_, s_);
+  Blocks<double> bc;
+  bc.p[0] = C;
+  bc.cols = m_;
+  bc.count = 1;
+  gram<double>(N_, m_, C, bc, S_, part_, part_cap_, s_);
+  chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_);
+  mm_gemm(m_, Linv_, false, Hp_, false, T1_, 1.0, 0.0, s_);
+  mm_gemm(m_, T1_, false, Linv_, true, T2_, 1.0, 0.0, s_);
+  make_A0(m_, T2_, nullptr, A0_, s_);
+  sym_eig(m_, A0_, lam_, Z_, mmw_, info_, s_);
+  mm_gemm(m_, R_, false, Z_, false, T1_, 1.0, 0.0, s_);
+  mult(N_, m_, m_, C, T1_, Cfin, s_);
+  mult(N_, m_, m_, X64_, T1_, Xfin, s_);
+  fix_signs(N_, m_, Cfin, Xfin, part_, s_);
+  column_residuals(N_, m_, Xfin, Cfin, lam_, res_, part_, s_);
+}
+
+// ---------------------------------------------------------------------------
+// Fig. TMFIG with the precision ladder.
+// ---------------------------------------------------------------------------
+int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
+                  const double* C0_host, trm_stats* stats) {
+  const auto t_start = std::chrono::steady_clock::now();
+  const size_t nm = (size_t)N_ * m_;
+  if (C0_host)
+    TRM_CUDA(cudaMemcpyAsync(C64_, C0_host, nm * 8, cudaMemcpyHostToDevice,
+                             s_));
+  else
+    random_block(N_, m_, opt_.seed, C64_, s_);
+  for (void* p : {Gb_[0], Gb_[1], Pb_})
+    TRM_CUDA(cudaMemsetAsync(p, 0, nm * 8, s_));
+
+  enum { PH_SP = 0, PH_MP2 = 1, PH_FP64 = 2 };
+  const int prec = opt_.precision;
+  int phase = prec == TRM_FP64 ? PH_FP64
+              : prec == TRM_MP2 ? PH_MP2
+                                : PH_SP;
+  if (phase == PH_SP) {
+    to_f32(C64_, C32_, (int64_t)nm, s_);
+    orth_uniform<float>(C32_, C32n_);
+  } else {
+    orth_fp64(C64_, C64n_);
+  }
+  set_restart();
+
+  const int lag = std::max(1, std::min(opt_.lag, kRing / 2));
+  int enq = 0, read = 0;
+  int n_phase[3] = {0, 0, 0};
+  int n_reorth = 0;
+  bool converged = false;
+  int status = TRM_OK;
+  double r0 = -1.0, best = INFINITY;
+  int best_at = 0;
+  int since_orth = 0, since_rr = 0, rescues = 0;
+  // MP2 keeps C orthonormal between exact FP64 re-orthonormalizations only
+  // to the FP32 accuracy of its overlap update, an error proportional to the
+  // step alpha ||P|| and hence to the residual at the time. Re-orthonormalize
+  // whenever the residual has dropped 100-fold since the last time (or after
+  // reorth_every iterations), and rotate to the Ritz basis whenever it has
+  // dropped 1000-fold (or after rr_every iterations), as Sec. 3 suggests.
+  double r_orth = INFINITY, r_rr = INFINITY;
+  double E_last = NAN;
+  // A phase has stalled when its best residual has not dropped by 30 % for
+  // this many iterations (slow but steady CG on a small gap still passes).
+  const int stall_window = 250;
+  const bool trace = std::getenv("TRM_TRACE") != nullptr;
+
+  auto enqueue_one = [&]() {
+    if (phase == PH_SP) {
+      float* G = static_cast<float*>(Gb_[0]);
+      float* Gp = static_cast<float*>(Gb_[1]);
+      iter_uniform<float, float>(C32_, C32n_, X32_, G, Gp,
+                                 static_cast<float*>(Pb_),
+                                 static_cast<float*>(HPb_));
+      Gb_[0] = G;
+      Gb_[1] = Gp;
+    } else if (phase == PH_FP64) {
+      double* G = static_cast<double*>(Gb_[0]);
+      double* Gp = static_cast<double*>(Gb_[1]);
+      iter_uniform<double, double>(C64_, C64n_, X64_, G, Gp,
+                                   static_cast<double*>(Pb_),
+                                   static_cast<double*>(HPb_));
+      Gb_[0] = G;
+      Gb_[1] = Gp;
+    } else {
+      iter_mp2();
+    }
+    n_phase[phase == PH_SP ? 0 : 1]++;
+    TRM_CUDA(cudaMemcpyAsync(&ring_[enq % kRing], sc_, sizeof(IterScalars),
+                             cudaMemcpyDeviceToHost, s_));
+    TRM_CUDA(cudaEventRecord(ev_[enq % kRing], s_));
+    ++enq;
+  };
+  auto drain = [&]() {  // wait for everything enqueued
+    TRM_CUDA(cudaStreamSynchronize(s_));
+    read = enq;
+  };
+
+  while (true) {
+    if (enq >= opt_.max_iter) {
+      status = TRM_ENOCONV;
+      break;
+    }
+    enqueue_one();
+    if (enq - read <= lag) continue;
+    const int i = read++;
+    TRM_CUDA(cudaEventSynchronize(ev_[i % kRing]));
+    if (prof.on) prof.resolve();
+    const IterScalars v = ring_[i % kRing];
+    E_last = v.E;
+    if (trace)
+      std::fprintf(stderr,
+                   "trm it %5d ph %d E %.15e r %.3e alpha %.3e gamma %.3e "
+                   "c2 %.3e dE %.3e st %d\n",
+                   i, phase, v.E, v.rms, v.alpha, v.gamma, v.c2, v.dE,
+                   v.status);
+    if (!std::isfinite(v.E) || !std::isfinite(v.rms)) {
+      status = TRM_ENOCONV;
+      last_error = "non-finite energy or residual at iteration " +
+                   std::to_string(i);
+      break;
+    }
+    if (v.status & 1) {  // overlap not positive definite: re-orthonormalise
+      drain();
+      if (++rescues > 5) {
+        status = TRM_ENOTPD;
+        last_error = "overlap matrix not positive definite";
+        break;
+      }
+      if (phase == PH_SP)
+        orth_uniform<float>(C32_, C32n_);
+      else
+        orth_fp64(C64_, C64n_);
+      set_restart();
+      continue;
+    }
+    if (r0 < 0.0) r0 = v.rms;
+    if (v.rms < 0.7 * best) {
+      best = v.rms;
+      best_at = i;
+    }
+    if (phase != PH_SP || prec == TRM_FULL_SP) {
+      if (v.rms <= tol_) {
+        converged = true;
+        break;
+      }
+    }
+    if (phase == PH_SP) {
+      const bool small = v.rms <= opt_.switch_tol[0] * r0;
+      const bool stalled = i - best_at > stall_window;
+      if (prec == TRM_FULL_SP) {
+        if (stalled) {
+          status = TRM_ENOCONV;
+          last_error = "full SP stagnated above the tolerance";
+          break;
+        }
+      } else if (small || stalled) {
+        drain();
+        to_f64(C32_, C64_, (int64_t)nm, s_);
+        orth_fp64(C64_, C64n_);
+        rr_rotate_fp64();
+        set_restart();
+        phase = PH_MP2;
+        best = INFINITY;
+        best_at = enq;
+        since_orth = since_rr = 0;
+        r_orth = r_rr = v.rms;
+        continue;
+      }
+    } else {
+      if (i - best_at > stall_window) {
+        // stagnation: rotate to the Ritz basis and restart CG
+        drain();
+        if (++rescues > 5) {
+          status = TRM_ENOCONV;
+          last_error = "stagnated above the tolerance";
+          break;
+        }
+        orth_fp64(C64_, C64n_);
+        rr_rotate_fp64();
+        set_restart();
+        best = INFINITY;
+        best_at = enq;
+        continue;
+      }
+      if (phase == PH_MP2) {
+        ++since_orth;
+        ++since_rr;
+        if (!std::isfinite(r_orth)) r_orth = r_rr = v.rms;
+        const bool rr = v.rms < 1e-3 * r_rr ||
+                        (opt_.rr_every > 0 && since_rr >= opt_.rr_every);
+        const bool ro = v.rms < 1e-2 * r_orth ||
+                        (opt_.reorth_every > 0 && since_orth >= opt_.reorth_every);
+        if (rr || ro) {
+          orth_fp64(C64_, C64n_);
+          ++n_reorth;
+          since_orth = 0;
+          r_orth = v.rms;
+        }
+        if (rr) {
+          rr_rotate_fp64();
+          set_restart();
+          since_rr = 0;
+          r_rr = v.rms;
+        }
+      }
+    }
+  }
+  drain();
+  if (prof.on) prof.resolve();
+  if (phase == PH_SP) to_f64(C32_, C64_, (int64_t)nm, s_);
+  double* Cfin = C64n_;
+  double* Xfin = static_cast<double*>(Gb_[0]);
+  final_rr(C64_, Cfin, Xfin);
+  std::vector<double> lam(m_), res(m_);
+  TRM_CUDA(cudaMemcpyAsync(lam.data(), lam_, m_ * 8, cudaMemcpyDeviceToHost,
+                           s_));
+  TRM_CUDA(cudaMemcpyAsync(res.data(), res_, m_ * 8, cudaMemcpyDeviceToHost,
+                           s_));
+  if (C_out)
+    TRM_CUDA(cudaMemcpyAsync(C_out, Cfin, nm * 8,
+                             C_on_device ? cudaMemcpyDeviceToDevice
+                                         : cudaMemcpyDeviceToHost,
+                             s_));
+  TRM_CUDA(cudaStreamSynchronize(s_));
+  if (lambda) std::memcpy(lambda, lam.data(), m_ * 8);
+  if (E_G) *E_G = neumaier_sum(lam.data(), m_);
+  if (stats) {
+    double ss = 0.0, mx = 0.0;
+    for (double r : res) {
+      ss += r * r;
+      mx = std::max(mx, r);
+    }
+    stats->iterations = enq;
+    stats->iterations_phase[0] = n_phase[0];
+    stats->iterations_phase[1] = n_phase[1];
+    stats->iterations_phase[2] = n_reorth;
+    stats->converged = converged ? 1 : 0;
+    stats->rms_residual = std::sqrt(ss / m_);
+    stats->max_residual = mx;
+    stats->E_last = E_last;
+    stats->launches = launch_count();
+    stats->seconds = std::chrono::duration<double>(
+                         std::chrono::steady_clock::now() - t_start)
+                         .count();
+  }
+  if (status == TRM_OK && !converged) status = TRM_ENOCONV;
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// Step operations
+// ---------------------------------------------------------------------------
+void Solver::apply(int din, const void* in, int dout, void* out, int ncols) {
+  if (din == TRM_F32 && dout == TRM_F32)
+    apply_h(op_, static_cast<const float*>(in), static_cast<float*>(out),
+            ncols, s_);
+  else if (din == TRM_F64 && dout == TRM_F64)
+    apply_h(op_, static_cast<const double*>(in), static_cast<double*>(out),
+            ncols, s_);
+  else
+    throw Error(-1, "apply: unsupported dtype combination");
+  TRM_CUDA(cudaStreamSynchronize(s_));
+}
+
+void Solver::energy_gradient(const double* C, double* E, double* HD,
+                             double* Hprime, void* G, int G_dtype,
+                             int zdiag) {
+  apply_h(op_, C, X64_, m_, s_);
+  energy_diag<double>(N_, m_, C, X64_, HD_, sc_, part_, s_);
+  set_restart();
+  if (G_dtype == TRM_F64) {
+    xprime<double>(N_, m_, C, X64_, HD_, nullptr, nullptr, s_);
+    Blocks<double> b;
+    b.p[0] = X64_;
+    b.cols = m_;
+    b.count = 1;
+    gram<double>(N_, m_, C, b, Hp_, part_, part_cap_, s_);
+    if (zdiag) zero_diag(m_, Hp_, s_);
+    gradient<double>(N_, m_, C, X64_, Hp_, static_cast<double*>(G), nullptr,
+                     nullptr, nullptr, sc_, part_, part_cap_, s_);
+  } else if (G_dtype == TRM_F32) {
+    xprime<double>(N_, m_, C, X64_, HD_, C32_, X32_, s_);
+    Blocks<float> b;
+    b.p[0] = X32_;
+    b.cols = m_;
+    b.count = 1;
+    gram<float>(N_, m_, C32_, b, Hp_, part_, part_cap_, s_);
+    if (zdiag) zero_diag(m_, Hp_, s_);
+    gradient<float>(N_, m_, C32_, X32_, Hp_, static_cast<float*>(G), nullptr,
+                    nullptr, nullptr, sc_, part_, part_cap_, s_);
+  } else {
+    throw Error(-1, "energy_gradient: G_dtype must be TRM_F32 or TRM_F64");
+  }
+  if (HD)
+    TRM_CUDA(cudaMemcpyAsync(HD, HD_, m_ * 8, cudaMemcpyDeviceToDevice, s_));
+  if (Hprime)
+    TRM_CUDA(cudaMemcpyAsync(Hprime, Hp_, (size_t)m_ * m_ * 8,
+                             cudaMemcpyDeviceToDevice, s_));
+  IterScalars v;
+  read_scalars(&v);
+  if (E) *E = v.E;
+}
+
+void Solver::set_block(const double* C_dev) {
+  TRM_CUDA(cudaMemcpyAsync(C64_, C_dev, (size_t)N_ * m_ * 8,
+                           cudaMemcpyDeviceToDevice, s_));
+  for (void* p : {Gb_[0], Gb_[1], Pb_})
+    TRM_CUDA(cudaMemsetAsync(p, 0, (size_t)N_ * m_ * 8, s_));
+  set_restart();
+  TRM_CUDA(cudaStreamSynchronize(s_));
+}
+
+void Solver::get_block(double* C_dev) {
+  TRM_CUDA(cudaMemcpyAsync(C_dev, C64_, (size_t)N_ * m_ * 8,
+                           cudaMemcpyDeviceToDevice, s_));
+  TRM_CUDA(cudaStreamSynchronize(s_));
+}
+
+void Solver::iterate(int mode, int restart, double* E, double* rms,
+                     double* alpha) {
+  const size_t nm = (size_t)N_ * m_;
+  if (restart) {
+    for (void* p : {Gb_[0], Gb_[1], Pb_})
+      TRM_CUDA(cudaMemsetAsync(p, 0, nm * 8, s_));
+    set_restart();
+  }
+  if (mode == TRM_FP64) {
+    double* G = static_cast<double*>(Gb_[0]);
+    double* Gp = static_cast<double*>(Gb_[1]);
+    iter_uniform<double, double>(C64_, C64n_, X64_, G, Gp,
+                                 static_cast<double*>(Pb_),
+                                 static_cast<double*>(HPb_));
+    Gb_[0] = G;
+    Gb_[1] = Gp;
+  } else if (mode == TRM_FULL_SP) {
+    to_f32(C64_, C32_, (int64_t)nm, s_);
+    float* G = static_cast<float*>(Gb_[0]);
+    float* Gp = static_cast<float*>(Gb_[1]);
+    iter_uniform<float, float>(C32_, C32n_, X32_, G, Gp,
+                               static_cast<float*>(Pb_),
+                               static_cast<float*>(HPb_));
+    Gb_[0] = G;
+    Gb_[1] = Gp;
+    to_f64(C32_, C64_, (int64_t)nm, s_);
+  } else if (mode == TRM_MP2) {
+    iter_mp2();
+  } else {
+    throw Error(-1, "iterate: mode must be TRM_FP64, TRM_FULL_SP or TRM_MP2");
+  }
+  IterScalars v;
+  read_scalars(&v);
+  if (E) *E = v.E;
+  if (rms) *rms = v.rms;
+  if (alpha) *alpha = v.alpha;
+  if (v.status & 1) throw Error(-3, "overlap matrix not positive definite");
+}
+
+void Solver::rayleigh_ritz(double* C_dev, double* lambda_host,
+                           double* res_host) {
+  double* Xfin = static_cast<double*>(Gb_[0]);
+  final_rr(C_dev, C64n_, Xfin);
+  TRM_CUDA(cudaMemcpyAsync(C_dev, C64n_, (size_t)N_ * m_ * 8,
+                           cudaMemcpyDeviceToDevice, s_));
+  if (lambda_host)
+    TRM_CUDA(cudaMemcpyAsync(lambda_host, lam_, m_ * 8, cudaMemcpyDeviceToHost,
+                             s_));
+  if (res_host)
+    TRM_CUDA(cudaMemcpyAsync(res_host, res_, m_ * 8, cudaMemcpyDeviceToHost,
+                             s_));
+  TRM_CUDA(cudaStreamSynchronize(s_));
+  for (void* p : {Gb_[0], Gb_[1], Pb_})
+    TRM_CUDA(cudaMemsetAsync(p, 0, (size_t)N_ * m_ * 8, s_));
+  set_restart();
+}
+
+template void Solver::orth_uniform<float>(float*&, float*&);
+template void Solver::orth_uniform<double>(double*&, double*&);
+
+}  // namespace trm

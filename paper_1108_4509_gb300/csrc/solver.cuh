@@ -1,0 +1,127 @@
+// Host-side solver state and the per-iteration block step (internal).
+#pragma once
+
+#include <vector>
+
+#include "../../include/trm.h"
+#include "ops.cuh"
+
+namespace trm {
+
+// Per-class timing of the library's launches with CUDA events on the solver's
+// stream, plus the algorithmic flops and bytes of each launch, for roofline
+// reporting. Off unless enabled; event pairs are resolved after a solve.
+enum KClass {
+  KC_SPMM32, KC_SPMM64, KC_GRAM32, KC_GRAM64, KC_GRAD32, KC_GRAD64,
+  KC_ROT32, KC_ROT64, KC_ROWOPS, KC_SMALL, KC_EIG, KC_COUNT
+};
+extern const char* const kClassNames[KC_COUNT];
+
+class Profiler {
+ public:
+  ~Profiler();
+  bool on = false;
+  void begin(int k, cudaStream_t s);
+  void end(int k, double flops, double bytes, cudaStream_t s);
+  void resolve();  // the stream must be idle
+  void reset();
+  double ms[KC_COUNT] = {};
+  long long launches[KC_COUNT] = {};
+  double flops[KC_COUNT] = {};
+  double bytes[KC_COUNT] = {};
+
+ private:
+  struct Rec {
+    int k;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  cudaEvent_t get();
+  std::vector<Rec> pending_;
+  std::vector<cudaEvent_t> pool_;
+  cudaEvent_t open_ = nullptr;
+};
+
+// Device memory owned by one solver; freed in the destructor.
+class DevArena {
+ public:
+  ~DevArena();
+  void* alloc(size_t bytes);
+  size_t bytes() const { return total_; }
+
+ private:
+  std::vector<void*> ptrs_;
+  size_t total_ = 0;
+};
+
+class Solver {
+ public:
+  Solver(int64_t N, int m, double tol, const trm_options& opt);
+  ~Solver();
+
+  void init_stencil(int nx, int ny, int nz, int order, double h,
+                    const double* V_host);
+  void init_csr(const int32_t* rowptr, const int32_t* cols, const void* vals,
+                int vals_fp64);
+
+  // Fig. TMFIG to convergence, then Rayleigh-Ritz. Returns a trm_status.
+  int solve(double* lambda, double* E_G, double* C_out, int C_on_device,
+            const double* C0_host, trm_stats* stats);
+
+  // Step operations used by the C ABI.
+  void apply(int din, const void* in, int dout, void* out, int ncols);
+  void energy_gradient(const double* C, double* E, double* HD, double* Hprime,
+                       void* G, int G_dtype, int zero_diag);
+  void set_block(const double* C_dev);
+  void get_block(double* C_dev);
+  void iterate(int mode, int restart, double* E, double* rms, double* alpha);
+  void rayleigh_ritz(double* C_dev, double* lambda_host, double* res_host);
+
+  int64_t N() const { return N_; }
+  Profiler prof;
+  cudaStream_t stream() const { return s_; }
+  std::string last_error;
+
+ private:
+  template <typename T, typename Tm>
+  void iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP);
+  void iter_mp2();
+  void orth_fp64(double*& C, double*& Cn);
+  template <typename T>
+  void orth_uniform(T*& C, T*& Cn);
+  void rr_rotate_fp64();  // C64 <- C64 Z diagonalising C^T H C
+  // Final FP64 Rayleigh-Ritz on C64: writes lam_dev, res_dev, Cfin (=C64b)
+  void final_rr(double* C, double* Cfin, double* Xfin);
+  void set_restart();
+  void read_scalars(IterScalars* out);
+
+  int64_t N_;
+  int m_;
+  double tol_;
+  trm_options opt_;
+  cudaStream_t s_;
+  Operator op_;
+  DevArena mem_;
+  int order_ = 0;
+  // operator data
+  double* diag64_ = nullptr;
+  float* diag32_ = nullptr;
+  double* minv64_ = nullptr;
+  float* minv32_ = nullptr;
+  // blocks (G, P, HP sized for FP64 and reused as FP32)
+  double *C64_ = nullptr, *C64n_ = nullptr, *X64_ = nullptr;
+  float *C32_ = nullptr, *C32n_ = nullptr, *X32_ = nullptr;
+  void *Gb_[2] = {nullptr, nullptr}, *Pb_ = nullptr, *HPb_ = nullptr;
+  // m x m (FP64)
+  double *HD_, *Hp_, *A0_, *Bm_, *PG_, *T1_, *T2_, *S_, *Linv_, *R_, *mmw_,
+      *eigw_, *Z_, *lam_, *res_;
+  int* info_;
+  double* part_;
+  size_t part_cap_;
+  IterScalars* sc_;
+  IterScalars* ring_ = nullptr;  // pinned host ring of per-iteration scalars
+  std::vector<cudaEvent_t> ev_;
+  int state_ = 0;  // 0: C64 current, 1: C32 current
+};
+
+}  // namespace trm

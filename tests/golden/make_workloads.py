@@ -1,0 +1,92 @@
+"""Write tests/golden/workloads.json: for each named grid workload, the first
+well seed whose spectral gap lambda_{m+1} - lambda_m is at least 1e-3 (the
+gap assumption of Sec. 2.1), with the reference E_G = sum of the m lowest
+eigenvalues and the gap, all from the oracle (Lanczos on the oracle's own
+Kronecker-sum H, dense for N <= 3000).
+
+With --oracle-iterations it also runs the oracle's trace minimization
+(diagonal preconditioner, random C0 of seed 1) on each accepted workload and
+records the first iteration at which the RMS residual is <= 1e-8 and
+<= 1e-10, and the oracle's own E_G.
+
+Run from the repository root:
+    python tests/golden/make_workloads.py [--oracle-iterations] [names]
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import trm_inputs as ti  # noqa: E402
+from oracle import operator as op  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workloads.json")
+MIN_GAP = 1e-3
+
+
+def scan(name, max_seed=20):
+    for seed in range(max_seed):
+        w = ti.workload(name, seed=seed)
+        H = op.grid_hamiltonian(w.shape, w.order, w.h, w.potential())
+        t = time.time()
+        lam = op.lowest_eigenvalues(H, w.m + 4)
+        gap = float(lam[w.m] - lam[w.m - 1])
+        rec = {"seed": seed, "N": w.N, "m": w.m, "gap": gap,
+               "E_G": float(np.sum(lam[:w.m])),
+               "lambda_m": float(lam[w.m - 1]), "lambda_m1": float(lam[w.m]),
+               "lambda_1": float(lam[0]), "seconds": round(time.time() - t, 1)}
+        print(name, rec, flush=True)
+        if gap >= MIN_GAP:
+            return rec
+    raise RuntimeError(f"no seed below {max_seed} passes the gap rule for {name}")
+
+
+def oracle_iterations(name, seed):
+    from oracle import trm
+    w = ti.workload(name, seed=seed)
+    H = op.grid_hamiltonian(w.shape, w.order, w.h, w.potential())
+    first = {}
+    t = time.time()
+
+    def cb(it, E, r):
+        for tol in (1e-8, 1e-10):
+            if r <= tol and tol not in first:
+                first[tol] = it
+        if it % 100 == 0:
+            print(name, it, E, r, round(time.time() - t), flush=True)
+
+    res = trm.solve(H, ti.random_block(w.N, w.m, seed=1), tol=1e-10,
+                    precond=True, callback=cb)
+    return {"oracle_iterations_tol_1e-8": first.get(1e-8),
+            "oracle_iterations_tol_1e-10": first.get(1e-10),
+            "oracle_E_G": res.E_G, "oracle_seconds": round(time.time() - t, 1)}
+
+
+def save(data):
+    with open(OUT, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+
+
+def main(argv):
+    its = "--oracle-iterations" in argv
+    names = [a for a in argv if not a.startswith("--")] or [
+        "grid16_o2_w8_m16", "grid48_o4_w64_m128"]
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    data["_source"] = ("oracle.operator.lowest_eigenvalues on the oracle's "
+                       "grid Hamiltonian; first seed with gap >= 1e-3")
+    for name in names:
+        if name not in data:
+            data[name] = scan(name)
+            save(data)
+        if its:
+            data[name].update(oracle_iterations(name, data[name]["seed"]))
+            save(data)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

@@ -1,0 +1,177 @@
+"""GPU parity of whole solves (Fig. TMFIG to convergence plus Rayleigh-Ritz)
+through the C ABI, for every precision mode, against the FP64 oracle, the
+closed forms of Sec. 3 and brute-force dense diagonalisation.
+
+Bar (stated for the method's output): each lambda_j within 1e-9 absolute,
+|dE_G| / |E_G| <= 1e-10 and the largest principal angle between the computed
+and the reference subspaces <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import trm_inputs as ti
+from oracle import operator as op
+from oracle import trm as otrm
+
+from . import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+LAM_TOL, EG_RTOL, ANGLE_TOL = 1e-9, 1e-10, 1e-6
+
+
+@pytest.fixture(scope="module")
+def trm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1108_4509_gb300 as mod
+    return mod
+
+
+def _solve(trm, shape, order, h, V, m, tol, C0=None, **opts):
+    opts.setdefault("stream", gu.stream())
+    with trm.Solver.stencil(shape, order, h, V, m, tol, **opts) as s:
+        return s.solve(C0=C0)
+
+
+def _check(lam, eg, C, ref_lam, ref_C=None, lam_tol=LAM_TOL):
+    ref_E = float(np.sum(ref_lam))
+    assert np.max(np.abs(lam - ref_lam)) <= lam_tol, np.max(np.abs(lam - ref_lam))
+    assert abs(eg - ref_E) <= EG_RTOL * abs(ref_E), (eg, ref_E)
+    if ref_C is not None:
+        assert otrm.sin_max_angle(C, ref_C) <= ANGLE_TOL
+
+
+MODES = ["FP64", "MIXED", "MP2"]
+
+
+@pytest.fixture(scope="module")
+def grid16_ref():
+    """16^3 grid, 7-point stencil + 8 seeded wells, m = 16 (gap 0.029)."""
+    w = ti.workload("grid16_o2_w8_m16")
+    V = w.potential()
+    H = op.grid_hamiltonian(w.shape, w.order, w.h, V)
+    ref = otrm.solve(H, ti.random_block(w.N, w.m, seed=1), tol=1e-11)
+    assert ref.converged
+    dense = op.lowest_eigenvalues(H, w.m + 1)
+    assert dense[w.m] - dense[w.m - 1] >= 1e-3
+    return w, V, H, ref
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_grid16_vs_oracle(trm, grid16_ref, mode):
+    w, V, H, ref = grid16_ref
+    lam, eg, C, st, status = _solve(trm, w.shape, w.order, w.h, V, w.m, 1e-10,
+                                    precision=getattr(trm, "TRM_" + mode))
+    assert status == 0, st
+    _check(lam, eg, C, ref.lam, ref.C)
+    assert st["max_residual"] < 1e-8
+    assert np.max(np.abs(C.T @ C - np.eye(w.m))) < 1e-12
+
+
+def test_grid16_preconditioned_and_csr(trm, grid16_ref):
+    w, V, H, ref = grid16_ref
+    lam, eg, C, st, status = _solve(trm, w.shape, w.order, w.h, V, w.m, 1e-10,
+                                    precision=trm.TRM_MIXED, precond=1)
+    assert status == 0, st
+    _check(lam, eg, C, ref.lam, ref.C)
+    rp, ci, va = ti.grid_csr(w.shape, w.order, w.h, V)
+    with trm.Solver.csr(w.N, rp, ci, va, w.m, 1e-10, precision=trm.TRM_MIXED,
+                        stream=gu.stream()) as s:
+        lam2, eg2, C2, st2, status2 = s.solve()
+    assert status2 == 0, st2
+    _check(lam2, eg2, C2, ref.lam, ref.C)
+
+
+def test_full_sp_accuracy_is_limited(trm, grid16_ref):
+    """Sec. 3: full SP alone does not give 64-bit accuracy; its FP32 floor
+    stays well above the FP64 result (the closing FP64 Rayleigh-Ritz only
+    rotates within the subspace FP32 found)."""
+    w, V, H, ref = grid16_ref
+    lam, eg, C, st, status = _solve(trm, w.shape, w.order, w.h, V, w.m, 1e-4,
+                                    precision=trm.TRM_FULL_SP)
+    assert status == 0, st
+    err = abs(eg - ref.E_G) / abs(ref.E_G)
+    assert err < 1e-5
+    assert otrm.sin_max_angle(C, ref.C) < 1e-2
+
+
+@pytest.mark.parametrize("mode", ["FP64", "MIXED"])
+def test_laplace2d_table_case_vs_closed_form(trm, mode):
+    """Table RESTBL first row: N = 96^2, m = 220, E_G = 35.25 printed; the
+    closed form (Sec. 3) gives every lambda."""
+    w = ti.workload("laplace2d_96_m220")
+    lam_ex = op.laplace2d_spectrum(96) * op.kinetic_scale(w.h)  # t = 1/(2h^2)
+    lam, eg, C, st, status = _solve(trm, w.shape, w.order, w.h, None, w.m,
+                                    1e-10, precision=getattr(trm, "TRM_" + mode))
+    assert status == 0, st
+    _check(lam, eg, C, lam_ex[:w.m])
+    assert round(eg, 2) == 35.25
+
+
+def test_order4_vs_kronecker_closed_form_and_warm_start(trm):
+    shape, m = (12, 10, 9), 11
+    lam_all = op.kron_sum_spectrum(shape, 4, 1.0)
+    assert lam_all[m] - lam_all[m - 1] > 1e-3
+    H = op.grid_hamiltonian(shape, 4, 1.0)
+    lam, eg, C, st, status = _solve(trm, shape, 4, 1.0, None, m, 1e-10,
+                                    precision=trm.TRM_MIXED)
+    assert status == 0, st
+    _check(lam, eg, C, lam_all[:m])
+    # warm start from the converged block: converges at once
+    lam2, eg2, C2, st2, status2 = _solve(trm, shape, 4, 1.0, None, m, 1e-10,
+                                         C0=C, precision=trm.TRM_FP64)
+    assert status2 == 0 and st2["iterations"] <= 5, st2
+    _check(lam2, eg2, C2, lam_all[:m])
+
+
+def test_dense_brute_force_small_grids(trm):
+    """N <= 512: brute-force dense eigenvalues; m = 1 and an nx that is not a
+    multiple of 4 exercise the degenerate block and the scalar stencil path."""
+    for shape, order, nw, m in [((8, 8, 8), 4, 6, 1), ((7, 9, 8), 2, 5, 9),
+                                ((10, 10, 5), 4, 4, 20)]:
+        V = ti.gaussian_wells(shape, nw, seed=7)
+        H = op.grid_hamiltonian(shape, order, 1.0, V)
+        dense = op.dense_spectrum(H)
+        assert dense[m] - dense[m - 1] > 1e-3
+        for mode in ("FP64", "MIXED"):
+            lam, eg, C, st, status = _solve(trm, shape, order, 1.0, V, m, 1e-10,
+                                            precision=getattr(trm, "TRM_" + mode))
+            assert status == 0, (shape, mode, st)
+            _check(lam, eg, C, dense[:m])
+
+
+def test_max_iter_reports_enoconv_with_result(trm):
+    shape, m = (12, 12, 12), 6
+    V = ti.gaussian_wells(shape, 4, seed=2)
+    lam, eg, C, st, status = _solve(trm, shape, 4, 1.0, V, m, 1e-12,
+                                    precision=trm.TRM_FP64, max_iter=5)
+    assert status == -4
+    assert st["iterations"] == 5 and not st["converged"]
+    assert np.all(np.isfinite(lam)) and np.isfinite(eg)
+    assert np.max(np.abs(C.T @ C - np.eye(m))) < 1e-10
+
+
+def test_device_output_and_repeatability(trm):
+    """C written to a device buffer; two solves from the same seed give the
+    same bytes (fixed reduction orders)."""
+    torch = gu.torch_mod()
+    shape, m = (16, 12, 12), 7
+    N = int(np.prod(shape))
+    V = ti.gaussian_wells(shape, 5, seed=4)
+    opt = trm.trm_default_options(stream=gu.stream(), precision=trm.TRM_MIXED,
+                                  seed=9)
+    h = trm.trm_create_stencil(16, 12, 12, 4, 1.0, V, m, 1e-10, opt)
+    try:
+        outs = []
+        for _ in range(2):
+            cd = gu.empty(N, m, np.float64)
+            lam, eg, st, status = trm.trm_solve(h, N, m, C_out=cd.data_ptr(),
+                                                C_on_device=True)
+            assert status == 0
+            outs.append((lam, eg, gu.from_dev(cd)))
+        assert np.array_equal(outs[0][0], outs[1][0])
+        assert outs[0][1] == outs[1][1]
+        assert np.array_equal(outs[0][2], outs[1][2])
+    finally:
+        trm.trm_destroy(h)

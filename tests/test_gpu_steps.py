@@ -1,0 +1,316 @@
+"""GPU parity of each step of the block iteration, through the C ABI, against
+the FP64 oracle on the same seeded inputs.
+
+Sizes span several 64-row / 64-column tiles with ragged tails (N not a
+multiple of 4 or 64, m not a multiple of 64), plus the degenerate m = 1.
+Tolerances: FP64 paths to a few ulps of the magnitudes involved; FP32 paths
+to the standard worst-case rounding bound gamma_n = n u / (1 - n u),
+u = 2^-24, of an n-term FP32 dot product (Higham, Accuracy and Stability of
+Numerical Algorithms, Sec. 3.1) applied to |A| |B|.
+"""
+import numpy as np
+import pytest
+
+import trm_inputs as ti
+from oracle import operator as op
+from oracle import trm as otrm
+
+from . import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+def gamma(n, u=U32):
+    return n * u / (1.0 - n * u)
+
+
+@pytest.fixture(scope="module")
+def trm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1108_4509_gb300 as mod
+    return mod
+
+
+def _handle(trm, shape, order, V, m, precond=0):
+    nx, ny, nz = (tuple(shape) + (1, 1))[:3]
+    opt = trm.trm_default_options(stream=gu.stream(), precond=precond)
+    return trm.trm_create_stencil(nx, ny, nz, order, 1.0, V, m, 1e-10, opt)
+
+
+GRIDS = [((16, 12, 10), 2), ((16, 12, 10), 4), ((13, 11, 9), 4),
+         ((24, 20, 1), 2), ((5, 7, 6), 4), ((8, 8, 8), 2)]
+
+
+# ---------------------------------------------------------------------------
+# random initial block (Sec. 3: random C0)
+# ---------------------------------------------------------------------------
+def test_random_block_bit_exact(trm):
+    torch = gu.torch_mod()
+    for N, m, seed in [(1000, 7, 3), (4096, 16, 0), (777, 1, 2 ** 63 + 5)]:
+        t = gu.empty(N, m, np.float64)
+        trm.trm_random_block(N, m, seed, t.data_ptr(), gu.stream())
+        got = gu.from_dev(t)
+        ref = ti.random_block(N, m, seed)
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+
+
+# ---------------------------------------------------------------------------
+# a1: X = H C (Fig. EGFIG step (1))
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,order", GRIDS)
+@pytest.mark.parametrize("m", [1, 5, 17])
+def test_apply_h_stencil(trm, shape, order, m):
+    V = ti.gaussian_wells(shape, 3, seed=1)
+    H = op.grid_hamiltonian(shape, order, 1.0, V)
+    N = H.shape[0]
+    h = _handle(trm, shape, order, V, 1)
+    try:
+        C = ti.random_block(N, m, seed=7)
+        # FP64: agrees with the oracle's sparse product to rounding
+        cd, xd = gu.to_dev(C), gu.empty(N, m, np.float64)
+        trm.trm_apply_h(h, trm.TRM_F64, cd.data_ptr(), trm.TRM_F64,
+                        xd.data_ptr(), m)
+        X = gu.from_dev(xd)
+        ref = op.apply_h(H, C)
+        scale = np.abs(H) @ np.abs(C)
+        assert np.all(np.abs(X - ref) <= 4 * 2.0 ** -52 * 13 * scale + 1e-300)
+        # FP32: input rounded to FP32, sum in FP32; bound gamma_13 |H||C|
+        C32 = C.astype(np.float32)
+        cs, xs = gu.to_dev(C32), gu.empty(N, m, np.float32)
+        trm.trm_apply_h(h, trm.TRM_F32, cs.data_ptr(), trm.TRM_F32,
+                        xs.data_ptr(), m)
+        X32 = gu.from_dev(xs).astype(np.float64)
+        ref32 = op.apply_h(H, C32.astype(np.float64))
+        scale32 = np.abs(H) @ np.abs(C32.astype(np.float64))
+        assert np.all(np.abs(X32 - ref32) <= gamma(15) * scale32)
+    finally:
+        trm.trm_destroy(h)
+
+
+@pytest.mark.parametrize("vals_dtype", [np.float64, np.float32])
+def test_apply_h_csr_matches_oracle(trm, vals_dtype):
+    shape, order, m = (14, 12, 10), 4, 9
+    V = ti.gaussian_wells(shape, 4, seed=2)
+    H = op.grid_hamiltonian(shape, order, 1.0, V)
+    rp, ci, va = ti.grid_csr(shape, order, 1.0, V, vals_dtype)
+    N = H.shape[0]
+    opt = trm.trm_default_options(stream=gu.stream())
+    h = trm.trm_create_csr(N, rp, ci, va, 1, 1e-10, opt)
+    try:
+        C = ti.random_block(N, m, seed=4)
+        Hv = op.grid_hamiltonian(shape, order, 1.0, V)
+        Hv.data = va.astype(np.float64)  # same values the GPU holds
+        cd, xd = gu.to_dev(C), gu.empty(N, m, np.float64)
+        trm.trm_apply_h(h, trm.TRM_F64, cd.data_ptr(), trm.TRM_F64,
+                        xd.data_ptr(), m)
+        X = gu.from_dev(xd)
+        ref = op.apply_h(Hv, C)
+        scale = np.abs(Hv) @ np.abs(C)
+        assert np.all(np.abs(X - ref) <= 4 * 2.0 ** -52 * 13 * scale)
+        C32 = C.astype(np.float32)
+        cs, xs = gu.to_dev(C32), gu.empty(N, m, np.float32)
+        trm.trm_apply_h(h, trm.TRM_F32, cs.data_ptr(), trm.TRM_F32,
+                        xs.data_ptr(), m)
+        X32 = gu.from_dev(xs).astype(np.float64)
+        Hv32 = Hv.copy()
+        Hv32.data = Hv.data.astype(np.float32).astype(np.float64)
+        ref32 = op.apply_h(Hv32, C32.astype(np.float64))
+        assert np.all(np.abs(X32 - ref32) <=
+                      gamma(15) * (np.abs(Hv32) @ np.abs(C32.astype(np.float64))))
+    finally:
+        trm.trm_destroy(h)
+
+
+def test_stencil_and_csr_paths_agree(trm):
+    """The stencil kernel and the CSR kernel on the CSR built independently
+    from the same grid give the same FP64 product (same terms, sum order may
+    differ)."""
+    shape, order, m = (20, 16, 12), 4, 6
+    V = ti.gaussian_wells(shape, 5, seed=9)
+    rp, ci, va = ti.grid_csr(shape, order, 1.0, V)
+    N = int(np.prod(shape))
+    hs = _handle(trm, shape, order, V, 1)
+    hc = trm.trm_create_csr(N, rp, ci, va, 1, 1e-10,
+                            trm.trm_default_options(stream=gu.stream()))
+    try:
+        C = ti.random_block(N, m, seed=5)
+        cd = gu.to_dev(C)
+        x1, x2 = gu.empty(N, m, np.float64), gu.empty(N, m, np.float64)
+        trm.trm_apply_h(hs, 1, cd.data_ptr(), 1, x1.data_ptr(), m)
+        trm.trm_apply_h(hc, 1, cd.data_ptr(), 1, x2.data_ptr(), m)
+        a, b = gu.from_dev(x1), gu.from_dev(x2)
+        assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a))
+    finally:
+        trm.trm_destroy(hs)
+        trm.trm_destroy(hc)
+
+
+# ---------------------------------------------------------------------------
+# a3/a6: Gram products (Fig. EGFIG step (6), Fig. ONFIG step (1), line search)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,m,n", [(5000, 17, 17), (1999, 70, 130),
+                                   (64, 1, 1), (300, 128, 5), (33, 3, 200)])
+def test_gram(trm, N, m, n):
+    torch = gu.torch_mod()
+    A = ti.random_block(N, m, seed=1)
+    B = ti.random_block(N, n, seed=2)
+    ref = A.T @ B
+    scale = np.abs(A).T @ np.abs(B)
+    out = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    a, b = gu.to_dev(A), gu.to_dev(B)
+    trm.trm_gram(N, m, n, trm.TRM_F64, a.data_ptr(), b.data_ptr(),
+                 out.data_ptr(), gu.stream())
+    got = gu.from_dev(out)
+    assert np.all(np.abs(got - ref) <= gamma(N, 2.0 ** -53) * scale + 1e-300)
+    A32, B32 = A.astype(np.float32), B.astype(np.float32)
+    ref32 = A32.astype(np.float64).T @ B32.astype(np.float64)
+    a, b = gu.to_dev(A32), gu.to_dev(B32)
+    trm.trm_gram(N, m, n, trm.TRM_F32, a.data_ptr(), b.data_ptr(),
+                 out.data_ptr(), gu.stream())
+    got32 = gu.from_dev(out)
+    assert np.all(np.abs(got32 - ref32) <= gamma(N) * scale)
+    # FP32 partial sums over row tiles: typical error far below the bound
+    assert np.median(np.abs(got32 - ref32) / scale) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# a7: Fig. ONFIG
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,m", [(3001, 37), (500, 1), (4096, 130)])
+def test_orthonormalize(trm, N, m):
+    C = ti.random_block(N, m, seed=3)
+    ref = otrm.orthonormalize(C)
+    t = gu.to_dev(C)
+    trm.trm_orthonormalize(N, m, t.data_ptr(), gu.stream())
+    got = gu.from_dev(t)
+    assert np.max(np.abs(got.T @ got - np.eye(m))) < 1e-13
+    # the Cholesky factor is unique, so C L^{-T} is too
+    assert np.max(np.abs(got - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_orthonormalize_rank_deficient_reports_enotpd(trm):
+    N, m = 200, 4
+    C = ti.random_block(N, m, seed=3)
+    C[:, 3] = C[:, 1]            # exactly dependent columns
+    t = gu.to_dev(C)
+    with pytest.raises(trm.TrmError) as e:
+        trm.trm_orthonormalize(N, m, t.data_ptr(), gu.stream())
+    assert e.value.status == -3
+
+
+# ---------------------------------------------------------------------------
+# a2-a4: Fig. EGFIG Algorithm-2 (FP64, and MP2 with FP32 steps (6), (7))
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,order,m", [((16, 12, 10), 4, 17),
+                                           ((13, 11, 9), 2, 70)])
+def test_energy_gradient(trm, shape, order, m):
+    torch = gu.torch_mod()
+    V = ti.gaussian_wells(shape, 3, seed=5)
+    H = op.grid_hamiltonian(shape, order, 1.0, V)
+    N = H.shape[0]
+    C = otrm.orthonormalize(ti.random_block(N, m, seed=8))
+    E, G, X, HD, Xp, Hp = otrm.energy_gradient_alg2(H, C)
+    h = _handle(trm, shape, order, V, m)
+    try:
+        cd = gu.to_dev(C)
+        hd = torch.zeros(m, dtype=torch.float64, device="cuda")
+        hpd = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+        gd = gu.empty(N, m, np.float64)
+        Eg = trm.trm_energy_gradient(h, cd.data_ptr(), hd.data_ptr(),
+                                     hpd.data_ptr(), gd.data_ptr(),
+                                     trm.TRM_F64, 0)
+        assert Eg == pytest.approx(E, rel=1e-13)
+        assert np.allclose(gu.from_dev(hd), HD, rtol=1e-13, atol=1e-13)
+        assert np.max(np.abs(gu.from_dev(hpd) - Hp)) < 1e-12
+        xs = np.max(np.abs(X))
+        assert np.max(np.abs(gu.from_dev(gd) - G)) < 1e-12 * xs
+        # MP2: steps (6), (7) in FP32 from FP32 copies of C and X'
+        gs = gu.empty(N, m, np.float32)
+        Eg2 = trm.trm_energy_gradient(h, cd.data_ptr(), hd.data_ptr(),
+                                      hpd.data_ptr(), gs.data_ptr(),
+                                      trm.TRM_F32, 1)
+        assert Eg2 == pytest.approx(E, rel=1e-13)   # E stays FP64
+        Hp0 = Hp.copy()
+        np.fill_diagonal(Hp0, 0.0)
+        G32 = gu.from_dev(gs).astype(np.float64)
+        bound = 2 * gamma(m + 4) * (np.abs(Xp) + np.abs(C) @ np.abs(Hp0)) \
+            + 2 * gamma(N) * np.abs(C) @ (np.abs(C).T @ np.abs(Xp))
+        assert np.all(np.abs(G32 - G) <= bound + 1e-30)
+    finally:
+        trm.trm_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# a8: Rayleigh-Ritz (Sec. 2.1)
+# ---------------------------------------------------------------------------
+def test_rayleigh_ritz(trm):
+    shape, order, m = (12, 11, 10), 4, 12
+    V = ti.gaussian_wells(shape, 5, seed=4)
+    H = op.grid_hamiltonian(shape, order, 1.0, V)
+    N = H.shape[0]
+    ref = otrm.solve(H, ti.random_block(N, m, seed=1), tol=1e-6)
+    Cin = ref.C @ np.linalg.qr(ti.random_block(m, m, seed=2))[0] * 1.3
+    lam_o, C_o, res_o = otrm.rayleigh_ritz(H, Cin)
+    h = _handle(trm, shape, order, V, m)
+    try:
+        cd = gu.to_dev(Cin)
+        lam, res = trm.trm_rayleigh_ritz(h, cd.data_ptr(), m)
+        C = gu.from_dev(cd)
+        assert np.max(np.abs(lam - lam_o)) < 1e-12
+        assert np.allclose(res, res_o, rtol=1e-6, atol=1e-12)
+        assert np.max(np.abs(C.T @ C - np.eye(m))) < 1e-12
+        # Ritz values here are simple: vectors agree column by column
+        # (same sign convention on both sides)
+        assert np.max(np.abs(C - C_o)) < 1e-9
+    finally:
+        trm.trm_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# a5, a7: one step of Fig. TMFIG (FP64, full SP and MP2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["fp64", "sp", "mp2"])
+def test_iterate_one_step(trm, mode):
+    shape, order, m = (14, 12, 11), 4, 10
+    V = ti.gaussian_wells(shape, 4, seed=6)
+    H = op.grid_hamiltonian(shape, order, 1.0, V)
+    N = H.shape[0]
+    C = otrm.orthonormalize(ti.random_block(N, m, seed=3))
+    E0, G0, _, _ = otrm.energy_gradient_alg1(H, C)
+    h = _handle(trm, shape, order, V, m)
+    md = {"fp64": trm.TRM_FP64, "sp": trm.TRM_FULL_SP, "mp2": trm.TRM_MP2}[mode]
+    tol = {"fp64": 1e-13, "sp": 1e-5, "mp2": 1e-13}[mode]
+    try:
+        cd = gu.to_dev(C)
+        trm.trm_set_block(h, cd.data_ptr())
+        E, r, a = trm.trm_iterate(h, md, restart=True)
+        assert E == pytest.approx(E0, rel=tol)
+        assert r == pytest.approx(otrm.rms_residual(G0), rel=1e-5)
+        assert a > 0
+        out = gu.empty(N, m, np.float64)
+        trm.trm_get_block(h, out.data_ptr())
+        C1 = gu.from_dev(out)
+        orth = {"fp64": 1e-13, "sp": 1e-5, "mp2": 1e-6}[mode]
+        assert np.max(np.abs(C1.T @ C1 - np.eye(m))) < orth
+        # new span = span(C + a P) with P = G on a restart (M = I)
+        ang = {"fp64": 1e-10, "sp": 1e-4, "mp2": 1e-6}[mode]
+        assert otrm.sin_max_angle(C1, C + a * G0) < ang
+        E1 = otrm.energy_gradient_alg1(H, otrm.orthonormalize(C1))[0]
+        assert E1 < E0
+        # the step is close to the exact line minimum along P
+        LM = otrm.line_matrices(C, G0, op.apply_h(H, C), op.apply_h(H, G0))
+        a_ex, _ = otrm.line_minimize(LM, a)
+        drop_ex = E0 - otrm.line_energy(a_ex, LM)
+        assert E0 - E1 >= 0.5 * drop_ex
+        # the next step starts from trace(C1^T H C1) (MP2 keeps C1 orthonormal
+        # only to the FP32 accuracy of its overlap update between the FP64
+        # re-orthonormalizations, so compare with the unnormalised trace)
+        E2, _, _ = trm.trm_iterate(h, md, restart=False)
+        E1_trace = float(np.trace(C1.T @ op.apply_h(H, C1)))
+        assert E2 == pytest.approx(E1_trace, rel=max(tol, 1e-12))
+        assert E2 < E0
+    finally:
+        trm.trm_destroy(h)
