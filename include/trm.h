@@ -230,6 +230,29 @@ int trm_profile_read(trm_handle h, trm_kernel_stats* out, int max);
 /* Kernel launches issued by the library in this process (all handles). */
 long long trm_launch_count(void);
 
+/*
+ * trm_gram_noalloc: out = A^T B exactly as trm_gram computes it, for callers
+ * that must not allocate device memory (no counterpart in the paper). Some
+ * callers cannot call cudaMalloc: they have given the device's memory to their
+ * own allocator (a framework's caching pool or an arena sized at start-up),
+ * or they run under a budget that must not grow, or cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree inside a timed loop.
+ * This variant keeps its split partial sums in a fixed 8 MiB array
+ * (2^20 doubles) compiled into the library, which every GPU that loads the
+ * library holds until the process exits; it calls no allocation routine.
+ * Limit: m * n <= 2^20 (up to 1024 x 1024); larger sizes return TRM_EINVAL
+ * with a message in trm_last_global_error(). The first call on each device
+ * looks up the array's device address (with that device current) and caches
+ * it; make that first call before any stream capture. All calls share the one
+ * array and each overwrites every partial it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU (different streams or host
+ * threads at once) race on it. A, B, out: device; stream as in trm_gram. The
+ * sum order may differ from trm_gram's (fewer, longer row slices when the
+ * partials would not fit), within the same rounding bound.
+ */
+trm_status trm_gram_noalloc(int64_t N, int m, int n, int dtype, const void* A,
+                            const void* B, double* out, void* stream);
+
 /* Fill an N x m FP64 device block with the splitmix64 random guess of the
  * given seed: entry (i, j) = u(seed, i + N j) - 0.5 (Sec. 3: random C0). */
 trm_status trm_random_block(int64_t N, int m, uint64_t seed, double* C,

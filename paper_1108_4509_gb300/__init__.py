@@ -22,7 +22,8 @@ __all__ = [
     "TRM_F64", "TrmError", "trm_options", "trm_stats", "lib", "LIB_PATH",
     "trm_default_options", "trm_create_stencil", "trm_create_csr", "trm_solve",
     "trm_destroy", "trm_strerror", "trm_last_error", "trm_dim", "trm_apply_h",
-    "trm_energy_gradient", "trm_gram", "trm_orthonormalize", "trm_set_block",
+    "trm_energy_gradient", "trm_gram", "trm_gram_noalloc",
+    "trm_orthonormalize", "trm_set_block",
     "trm_get_block", "trm_iterate", "trm_rayleigh_ritz", "trm_random_block",
     "trm_profile", "trm_profile_read", "trm_launch_count", "trm_kernel_stats",
     "Solver",
@@ -91,6 +92,7 @@ _SIGS = {
     "trm_apply_h": (_i, [_h, _i, _p, _i, _p, _i]),
     "trm_energy_gradient": (_i, [_h, _p, _p, _p, _p, _p, _i, _i]),
     "trm_gram": (_i, [_i64, _i, _i, _i, _p, _p, _p, _p]),
+    "trm_gram_noalloc": (_i, [_i64, _i, _i, _i, _p, _p, _p, _p]),
     "trm_orthonormalize": (_i, [_i64, _i, _p, _p]),
     "trm_set_block": (_i, [_h, _p]),
     "trm_get_block": (_i, [_h, _p]),
@@ -240,6 +242,14 @@ def trm_gram(N, m, n, dtype, A_ptr, B_ptr, out_ptr, stream=0):
     return _check(lib.trm_gram(N, m, n, dtype, ct.c_void_p(A_ptr),
                                ct.c_void_p(B_ptr), ct.c_void_p(out_ptr),
                                ct.c_void_p(stream or 0)))
+
+
+def trm_gram_noalloc(N, m, n, dtype, A_ptr, B_ptr, out_ptr, stream=0):
+    """trm_gram without any device allocation (fixed in-library scratch)."""
+    return _check(lib.trm_gram_noalloc(N, m, n, dtype, ct.c_void_p(A_ptr),
+                                       ct.c_void_p(B_ptr),
+                                       ct.c_void_p(out_ptr),
+                                       ct.c_void_p(stream or 0)))
 
 
 def trm_orthonormalize(N, m, C_ptr, stream=0):

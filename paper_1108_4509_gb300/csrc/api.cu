@@ -72,6 +72,10 @@ trm_options resolve(const trm_options* opt) {
 
 }  // namespace
 
+namespace trm {
+void set_global_error(const std::string& msg) { g_err = msg; }
+}  // namespace trm
+
 extern "C" {
 
 trm_status trm_default_options(trm_options* opt) {

@@ -164,6 +164,40 @@ void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
   TRM_CHECK_LAUNCH();
 }
 
+template <typename T>
+void gram_in_scratch(int64_t N, int m, const T* A, const Blocks<T>& B,
+                     double* out, double* scratch, size_t scratch_doubles,
+                     cudaStream_t s) {
+  const int n = B.total();
+  if (m <= 0 || n <= 0) return;
+  if ((size_t)m * n > scratch_doubles)
+    throw Error(-1, "gram: m*n exceeds the scratch capacity");
+  int splits;
+  int64_t rows;
+  plan(N, m, n, &splits, &rows);
+  const int64_t fit = (int64_t)(scratch_doubles / ((size_t)m * n));
+  if (splits > fit) {  // fewer, longer row slices so the partials fit
+    rows = (N + fit - 1) / fit;
+    rows = ((rows + TK - 1) / TK) * TK;
+    splits = (int)((N + rows - 1) / rows);
+  }
+  const int tiles_m = ceil_div(m, TM);
+  dim3 grid(splits, tiles_m * ceil_div(n, TN));
+  k_gram<T><<<grid, 256, 0, s>>>(N, m, A, B, rows, tiles_m, scratch);
+  TRM_CHECK_LAUNCH();
+  const size_t count = (size_t)m * n;
+  k_sum_splits<<<ceil_div(count, 256), 256, 0, s>>>(scratch, splits, count,
+                                                    out);
+  TRM_CHECK_LAUNCH();
+}
+
+template void gram_in_scratch<float>(int64_t, int, const float*,
+                                     const Blocks<float>&, double*, double*,
+                                     size_t, cudaStream_t);
+template void gram_in_scratch<double>(int64_t, int, const double*,
+                                      const Blocks<double>&, double*, double*,
+                                      size_t, cudaStream_t);
+
 template void gram<float>(int64_t, int, const float*, const Blocks<float>&,
                           double*, double*, size_t, cudaStream_t);
 template void gram<double>(int64_t, int, const double*, const Blocks<double>&,

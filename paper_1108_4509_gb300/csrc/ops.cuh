@@ -64,6 +64,13 @@ template <typename T>
 void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
           double* partials, size_t partials_cap, cudaStream_t s);
 
+// Same product with the split partials in a caller-given scratch of
+// scratch_doubles doubles (fewer row slices when it is small); m*n must fit.
+template <typename T>
+void gram_in_scratch(int64_t N, int m, const T* A, const Blocks<T>& B,
+                     double* out, double* scratch, size_t scratch_doubles,
+                     cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Tall-skinny products and fused row-local updates
 // ---------------------------------------------------------------------------
