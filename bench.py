@@ -409,7 +409,11 @@ def main():
                "iterations": iters, "status": statuses,
                "rel_err_E_G": errs,
                "E_G_ok": all(e is not None and e <= 1e-10 for e in errs),
-               "roofline": roof, "spmm": spmm, "fp64_path": fp64,
+               "roofline": roof, "spmm": spmm,
+               "profile_ms_per_solve": {
+                   k: round(v["ms"] / args.steps, 3) for k, v in prof.items()
+                   if v["launches"]},
+               "fp64_path": fp64,
                "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                "cpu_baseline": cpu}
         print(json.dumps(out))

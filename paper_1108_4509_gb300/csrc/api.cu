@@ -238,28 +238,37 @@ trm_status trm_gram(int64_t N, int m, int n, int dtype, const void* A,
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t cap = trm::gram_partials_doubles(N, m, n);
     double* part = nullptr;
-    TRM_CUDA(cudaMallocAsync(&part, cap * sizeof(double), s));
+    TRM_CUDA(cudaMallocAsync(&part, (cap + 1) * sizeof(double), s));
+    int* err = reinterpret_cast<int*>(part + cap);
+    int herr = 0;
     try {
+      TRM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
       if (dtype == TRM_F32) {
         trm::Blocks<float> b;
         b.p[0] = static_cast<const float*>(B);
         b.cols = n;
         b.count = 1;
-        trm::gram<float>(N, m, static_cast<const float*>(A), b, out, part, cap, s);
+        trm::gram<float>(N, m, static_cast<const float*>(A), b, out, part, cap,
+                         s, err);
       } else {
         trm::Blocks<double> b;
         b.p[0] = static_cast<const double*>(B);
         b.cols = n;
         b.count = 1;
-        trm::gram<double>(N, m, static_cast<const double*>(A), b, out, part, cap, s);
+        trm::gram<double>(N, m, static_cast<const double*>(A), b, out, part,
+                          cap, s, err);
       }
+      TRM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost,
+                               s));
     } catch (...) {
       cudaFreeAsync(part, s);
       throw;
     }
     TRM_CUDA(cudaFreeAsync(part, s));
     TRM_CUDA(cudaStreamSynchronize(s));
-    return TRM_OK;
+    if (herr & 2)
+      return fail(nullptr, TRM_ETIMEOUT, "trm_gram: a device wait timed out");
+    return (int)TRM_OK;
   });
 }
 
@@ -270,7 +279,7 @@ trm_status trm_orthonormalize(int64_t N, int m, double* C, void* stream) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t mm = (size_t)m * m;
     const size_t cap = trm::gram_partials_doubles(N, m, m);
-    const size_t bytes = (cap + 4 * mm + (size_t)N * m) * sizeof(double) +
+    const size_t bytes = (cap + 4 * mm + m + (size_t)N * m) * sizeof(double) +
                          sizeof(trm::IterScalars);
     char* w = nullptr;
     TRM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&w), bytes, s));
@@ -278,8 +287,8 @@ trm_status trm_orthonormalize(int64_t N, int m, double* C, void* stream) {
     double* S = part + cap;
     double* Linv = S + mm;
     double* R = Linv + mm;
-    double* gw = R + mm;
-    double* Cn = gw + mm;
+    double* gw = R + mm;        // m (m + 1): padded factorisation workspace
+    double* Cn = gw + mm + m;
     auto* sc = reinterpret_cast<trm::IterScalars*>(Cn + (size_t)N * m);
     int status = 0;
     try {

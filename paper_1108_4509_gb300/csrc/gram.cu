@@ -144,11 +144,23 @@ size_t gram_partials_doubles(int64_t N, int m, int n) {
   return (size_t)s * m * n;
 }
 
+void sum_splits(const double* part, int splits, size_t count, double* out,
+                cudaStream_t s) {
+  k_sum_splits<<<ceil_div(count, 256), 256, 0, s>>>(part, splits, count, out);
+  TRM_CHECK_LAUNCH();
+}
+
 template <typename T>
 void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
-          double* partials, size_t partials_cap, cudaStream_t s) {
+          double* partials, size_t partials_cap, cudaStream_t s, int* err) {
   const int n = B.total();
   if (m <= 0 || n <= 0) return;
+  if constexpr (sizeof(T) == 4) {
+    if (gram_tc_eligible(N, m, B)) {  // tensor cores, FP32-class accuracy
+      gram_tc(N, m, A, B, out, partials, partials_cap, err, s);
+      return;
+    }
+  }
   int splits;
   int64_t rows;
   plan(N, m, n, &splits, &rows);
@@ -199,8 +211,8 @@ template void gram_in_scratch<double>(int64_t, int, const double*,
                                       size_t, cudaStream_t);
 
 template void gram<float>(int64_t, int, const float*, const Blocks<float>&,
-                          double*, double*, size_t, cudaStream_t);
+                          double*, double*, size_t, cudaStream_t, int*);
 template void gram<double>(int64_t, int, const double*, const Blocks<double>&,
-                           double*, double*, size_t, cudaStream_t);
+                           double*, double*, size_t, cudaStream_t, int*);
 
 }  // namespace trm

@@ -60,9 +60,21 @@ struct Blocks {
 };
 
 size_t gram_partials_doubles(int64_t N, int m, int n);
+// FP32 inputs go to the tensor-core kernel when gram_tc_eligible; err (device
+// int, may be null) receives bit 2 if one of its bounded waits gave up.
 template <typename T>
 void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
-          double* partials, size_t partials_cap, cudaStream_t s);
+          double* partials, size_t partials_cap, cudaStream_t s,
+          int* err = nullptr);
+void sum_splits(const double* part, int splits, size_t count, double* out,
+                cudaStream_t s);
+// tcgen05 Gram of FP32 blocks (three-term BF16 split, FP32 accumulation in
+// tensor memory): needs N % 4 == 0, m >= 64, at most 3 B segments whose
+// widths are multiples of 128 when there are several.
+bool gram_tc_eligible(int64_t N, int m, const Blocks<float>& B);
+void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
+             double* out, double* partials, size_t cap, int* err,
+             cudaStream_t s);
 
 // Same product with the split partials in a caller-given scratch of
 // scratch_doubles doubles (fewer row slices when it is small); m*n must fit.
@@ -121,8 +133,10 @@ void random_block(int64_t N, int m, uint64_t seed, double* C, cudaStream_t s);
 // m x m FP64 matrices on the device
 // ---------------------------------------------------------------------------
 // Cm = alpha op(A) op(B) + beta Cm (all m x m FP64, column-major)
+// (fp32: products and sums in FP32, inputs and outputs FP64)
 void mm_gemm(int m, const double* A, bool trA, const double* B, bool trB,
-             double* Cm, double alpha, double beta, cudaStream_t s);
+             double* Cm, double alpha, double beta, cudaStream_t s,
+             bool fp32 = false);
 // A0 = sym(H') + diag(H_D)
 void make_A0(int m, const double* Hp, const double* HD, double* A0,
              cudaStream_t s);
@@ -137,6 +151,11 @@ void line_step(int m, const double* A0, const double* Bm, const double* Q,
 template <typename Tm>
 void chol_inv(int m, const double* S, double* Linv, double* R,
               IterScalars* sc, double* gwork, cudaStream_t s);
+// The same for S close to I, in deviation form (L = I + F, L^{-1} = I + Y):
+// FP32 arithmetic on the small parts gives FP64 accuracy relative to I.
+template <typename Tm>
+void chol_inv_dev(int m, const double* S, double* Linv, double* R,
+                  IterScalars* sc, double* gwork, cudaStream_t s);
 // set diagonal of an m x m matrix to zero
 void zero_diag(int m, double* A, cudaStream_t s);
 // symmetric eigenproblem A = Z diag(w) Z^T (cyclic Jacobi, FP64), w

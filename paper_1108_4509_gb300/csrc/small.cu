@@ -13,24 +13,25 @@ namespace {
 // ---------------------------------------------------------------------------
 // Cm = alpha op(A) op(B) + beta Cm, 16 x 16 tiles, one output per thread.
 // ---------------------------------------------------------------------------
+template <typename Tc>
 __global__ void __launch_bounds__(256)
     k_mm_gemm(int m, const double* __restrict__ A, int trA,
               const double* __restrict__ B, int trB, double* Cm,
               double alpha, double beta) {
-  __shared__ double As[16][17], Bs[16][17];
+  __shared__ Tc As[16][17], Bs[16][17];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int i = blockIdx.x * 16 + tx;
   const int j = blockIdx.y * 16 + ty;
-  double acc = 0.0;
+  Tc acc = 0;
   for (int k0 = 0; k0 < m; k0 += 16) {
     const int ka = k0 + ty;
-    As[ty][tx] = (i < m && ka < m) ? (trA ? A[ka + (int64_t)i * m]
-                                          : A[i + (int64_t)ka * m])
-                                   : 0.0;
+    As[ty][tx] = (i < m && ka < m) ? (Tc)(trA ? A[ka + (int64_t)i * m]
+                                              : A[i + (int64_t)ka * m])
+                                   : (Tc)0;
     const int kb = k0 + tx;
-    Bs[ty][tx] = (kb < m && j < m) ? (trB ? B[j + (int64_t)kb * m]
-                                          : B[kb + (int64_t)j * m])
-                                   : 0.0;
+    Bs[ty][tx] = (kb < m && j < m) ? (Tc)(trB ? B[j + (int64_t)kb * m]
+                                              : B[kb + (int64_t)j * m])
+                                   : (Tc)0;
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) acc += As[kk][tx] * Bs[ty][kk];
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(256)
   }
   if (i < m && j < m) {
     const int64_t o = i + (int64_t)j * m;
-    Cm[o] = alpha * acc + (beta != 0.0 ? beta * Cm[o] : 0.0);
+    Cm[o] = alpha * (double)acc + (beta != 0.0 ? beta * Cm[o] : 0.0);
   }
 }
 
@@ -80,10 +81,11 @@ __global__ void __launch_bounds__(1024)
   __shared__ double red[4 * 32];
   __shared__ double alpha_sh;
   Tm trD1 = 0, trD2 = 0, trS1D1 = 0, trQ = 0;
-  const int64_t mm = (int64_t)m * m;
-  for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
-    const int i = (int)(e % m), j = (int)(e / m);
-    const int64_t et = j + (int64_t)i * m;  // (j, i)
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = threadIdx.x >> 5; j < m; j += nw)
+  for (int i = lane; i < m; i += 32) {
+    const int e = i + j * m;
+    const int et = j + i * m;  // (j, i)
     const Tm s1 = (Tm)Bm[e] + (Tm)Bm[et];   // S1_ij
     // D1_ji = T1_ji - T2_ji - (W_ji + W_ij)/2
     const Tm d1ji = (Tm)T1[et] - (Tm)T2[et] - (Tm)0.5 * ((Tm)W[et] + (Tm)W[e]);
@@ -120,9 +122,10 @@ __global__ void __launch_bounds__(1024)
   }
   __syncthreads();
   const double a = alpha_sh;
-  for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
-    const int i = (int)(e % m), j = (int)(e / m);
-    const int64_t et = j + (int64_t)i * m;
+  for (int j = threadIdx.x >> 5; j < m; j += nw)
+  for (int i = lane; i < m; i += 32) {
+    const int e = i + j * m;
+    const int et = j + i * m;
     const double s1 = Bm[e] + Bm[et];
     const double q = 0.5 * (Q[e] + Q[et]);
     S[e] = (i == j ? 1.0 : 0.0) + a * s1 + a * a * q;
@@ -132,73 +135,96 @@ __global__ void __launch_bounds__(1024)
 // ---------------------------------------------------------------------------
 // Cholesky S = L L^T (right-looking, lower) and L^{-1} in place (backward
 // column sweep: col j of L^{-1} below the diagonal is -(L22^{-1} l) / l_jj).
-// Writes Linv (lower) and R = L^{-T} (upper). One CTA.
+// Writes Linv (lower) and R = L^{-T} (upper). One CTA of 1024 threads; the
+// working copy has leading dimension m + 1 so that a warp walking along a
+// row touches 32 distinct banks.
+//
+// With dev = true the matrix is S = I + E and the factorisation runs in
+// deviation form: L = I + F and L^{-1} = I + Y with the identity kept exact
+// and only the small E, F, Y held in Tm. Pivot j: d = E_jj - sum_k F_jk^2,
+// f_jj = d / (1 + sqrt(1 + d)); below it F_ij = (E_ij - sum_k F_ik F_jk) /
+// (1 + f_jj). Inverse: y_jj = -f_jj / (1 + f_jj), and the column below is
+// -(1 + y_jj) (x + Y22 x) with x = F[j+1:, j]. When S - I is small, FP32
+// arithmetic here yields L to FP64 accuracy relative to I.
 // ---------------------------------------------------------------------------
-template <typename Tm>
+template <typename Tm, bool dev>
 __global__ void __launch_bounds__(1024)
     k_chol_inv(int m, const double* __restrict__ S, double* __restrict__ Linv,
                double* __restrict__ R, IterScalars* sc, Tm* gwork,
                int use_smem) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
-  __shared__ Tm tmp_static[1024];
+  __shared__ Tm tmp[1024];
   Tm* a = use_smem ? reinterpret_cast<Tm*>(smraw) : gwork;
-  Tm* tmp = tmp_static;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int64_t mm = (int64_t)m * m;
-  for (int64_t e = tid; e < mm; e += nt) a[e] = (Tm)S[e];
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int ld = m + 1;
+  const Tm eps = sizeof(Tm) == 4 ? (Tm)1.2e-7 : (Tm)2.3e-16;
+  for (int k = warp; k < m; k += nw)
+    for (int i = lane; i < m; i += 32)
+      a[i + k * ld] = (Tm)(S[i + k * m] - (dev && i == k ? 1.0 : 0.0));
   if (tid == 0) bad = 0;
   __syncthreads();
-  // A pivot that has lost all but m rounding errors of its original diagonal
-  // entry marks a (numerically) singular S.
-  const Tm eps = sizeof(Tm) == 4 ? (Tm)1.2e-7 : (Tm)2.3e-16;
   for (int j = 0; j < m; ++j) {
     if (tid == 0) {
-      Tm d = a[j + (int64_t)j * m];
-      const Tm floor_j = (Tm)(4 * m) * eps * (Tm)fabs(S[j + (int64_t)j * m]);
-      if (!(d > floor_j)) {
-        bad = 1;
-        d = (Tm)1;
+      Tm d = a[j + j * ld];
+      if (dev) {
+        if (!(d > (Tm)-0.999)) {  // pivot 1 + d not positive: singular S
+          bad = 1;
+          d = (Tm)0;
+        }
+        a[j + j * ld] = d / ((Tm)1 + sqrt((Tm)1 + d));
+      } else {
+        // a pivot that has lost all but 4m roundings of its original
+        // diagonal entry marks a (numerically) singular S
+        const Tm floor_j = (Tm)(4 * m) * eps * (Tm)fabs(S[j + j * m]);
+        if (!(d > floor_j)) {
+          bad = 1;
+          d = (Tm)1;
+        }
+        a[j + j * ld] = sqrt(d);
       }
-      a[j + (int64_t)j * m] = sqrt(d);
     }
     __syncthreads();
-    const Tm ljj = a[j + (int64_t)j * m];
-    for (int i = j + 1 + tid; i < m; i += nt) a[i + (int64_t)j * m] /= ljj;
+    const Tm ljj = (dev ? (Tm)1 : (Tm)0) + a[j + j * ld];
+    for (int i = j + 1 + tid; i < m; i += nt) a[i + j * ld] /= ljj;
     __syncthreads();
-    const int n2 = m - j - 1;
-    const int64_t cnt = (int64_t)n2 * n2;
-    for (int64_t e = tid; e < cnt; e += nt) {
-      const int ii = (int)(e % n2), kk = (int)(e / n2);
-      if (kk <= ii) {
-        const int i = j + 1 + ii, k = j + 1 + kk;
-        a[i + (int64_t)k * m] -= a[i + (int64_t)j * m] * a[k + (int64_t)j * m];
-      }
+    // trailing update of the lower triangle: a warp per column, lanes down
+    for (int k = j + 1 + warp; k < m; k += nw) {
+      const Tm lkj = a[k + j * ld];
+      for (int i = k + lane; i < m; i += 32) a[i + k * ld] -= a[i + j * ld] * lkj;
     }
     __syncthreads();
   }
   for (int j = m - 1; j >= 0; --j) {
-    if (tid == 0) a[j + (int64_t)j * m] = (Tm)1 / a[j + (int64_t)j * m];
-    for (int i = j + 1 + tid; i < m; i += nt) tmp[i] = a[i + (int64_t)j * m];
+    if (tid == 0) {
+      const Tm f = a[j + j * ld];
+      a[j + j * ld] = dev ? -f / ((Tm)1 + f) : (Tm)1 / f;
+    }
+    for (int i = j + 1 + tid; i < m; i += nt) tmp[i] = a[i + j * ld];
     __syncthreads();
-    const Tm ajj = -a[j + (int64_t)j * m];
-    for (int i = j + 1 + tid; i < m; i += nt) {
+    const Tm scale = dev ? -((Tm)1 + a[j + j * ld]) : -a[j + j * ld];
+    // row i of the already inverted trailing block times the column below
+    // the pivot: one warp per row, lanes along k
+    for (int i = j + 1 + warp; i < m; i += nw) {
       Tm y = 0;
-      for (int k = j + 1; k <= i; ++k) y += a[i + (int64_t)k * m] * tmp[k];
-      a[i + (int64_t)j * m] = y * ajj;
+      for (int k = j + 1 + lane; k <= i; k += 32) y += a[i + k * ld] * tmp[k];
+      y = warp_sum(y);
+      if (lane == 0) a[i + j * ld] = scale * ((dev ? tmp[i] : (Tm)0) + y);
     }
     __syncthreads();
   }
   const int isbad = bad;
-  for (int64_t e = tid; e < mm; e += nt) {
-    const int i = (int)(e % m), k = (int)(e / m);
-    double v;
-    if (isbad)
-      v = (i == k) ? 1.0 : 0.0;
-    else
-      v = (i >= k) ? (double)a[e] : 0.0;
-    Linv[e] = v;                   // Linv(i, k)
-    R[k + (int64_t)i * m] = v;     // R(k, i) = Linv(i, k)
+  for (int k = warp; k < m; k += nw) {
+    for (int i = lane; i < m; i += 32) {
+      double v;
+      if (isbad)
+        v = (i == k) ? 1.0 : 0.0;
+      else
+        v = (dev && i == k ? 1.0 : 0.0) + (i >= k ? (double)a[i + k * ld] : 0.0);
+      Linv[i + k * m] = v;  // Linv(i, k)
+      R[k + i * m] = v;     // R(k, i) = Linv(i, k)
+    }
   }
   if (tid == 0 && isbad && sc) sc->status |= 1;
 }
@@ -217,22 +243,23 @@ __global__ void __launch_bounds__(1024)
   __shared__ double red[2 * 32];
   __shared__ int done;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int64_t mm = (int64_t)m * m;
-  for (int64_t e = tid; e < mm; e += nt)
-    Zw[e] = (e % m == e / m) ? 1.0 : 0.0;
+  const int lane = tid & 31, nw = nt >> 5;
+  for (int c = tid >> 5; c < m; c += nw)
+    for (int r = lane; r < m; r += 32) Zw[r + c * m] = (r == c) ? 1.0 : 0.0;
   const int M = m + (m & 1);
   const int np = M / 2;
   int sweeps = 0;
   __syncthreads();
   for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
     double v[2] = {0.0, 0.0};
-    for (int64_t e = tid; e < mm; e += nt) {
-      const double x = A[e];
-      if (e % m == e / m)
-        v[1] += x * x;
-      else
-        v[0] += x * x;
-    }
+    for (int c = tid >> 5; c < m; c += nw)
+      for (int r = lane; r < m; r += 32) {
+        const double x = A[r + c * m];
+        if (r == c)
+          v[1] += x * x;
+        else
+          v[0] += x * x;
+      }
     block_sum<2>(v, red);
     if (tid == 0) done = (v[0] <= 1e-30 * (v[0] + v[1])) || sweep == max_sweeps;
     __syncthreads();
@@ -267,33 +294,36 @@ __global__ void __launch_bounds__(1024)
         qq[k] = min(q, m - 1);
       }
       __syncthreads();
-      const int64_t cnt = (int64_t)np * m;
-      for (int64_t e = tid; e < cnt; e += nt) {  // A <- A J
-        const int k = (int)(e / m), i = (int)(e % m);
+      for (int k = tid >> 5; k < np; k += nw) {  // A <- A J
         const double s = sn[k];
         if (s == 0.0) continue;
         const double c = cs[k];
-        double* ap = A + (int64_t)pp[k] * m;
-        double* aq = A + (int64_t)qq[k] * m;
-        const double x = ap[i], y = aq[i];
-        ap[i] = c * x - s * y;
-        aq[i] = s * x + c * y;
+        double* ap = A + pp[k] * m;
+        double* aq = A + qq[k] * m;
+        for (int i = lane; i < m; i += 32) {
+          const double x = ap[i], y = aq[i];
+          ap[i] = c * x - s * y;
+          aq[i] = s * x + c * y;
+        }
       }
       __syncthreads();
-      for (int64_t e = tid; e < cnt; e += nt) {  // A <- J^T A, Z <- Z J
-        const int k = (int)(e / m), jc = (int)(e % m);
+      for (int k = tid >> 5; k < np; k += nw) {  // A <- J^T A, Z <- Z J
         const double s = sn[k];
         if (s == 0.0) continue;
         const double c = cs[k];
         const int p = pp[k], q = qq[k];
-        const double x = A[p + (int64_t)jc * m], y = A[q + (int64_t)jc * m];
-        A[p + (int64_t)jc * m] = c * x - s * y;
-        A[q + (int64_t)jc * m] = s * x + c * y;
-        double* zp = Zw + (int64_t)p * m;
-        double* zq = Zw + (int64_t)q * m;
-        const double u = zp[jc], t = zq[jc];
-        zp[jc] = c * u - s * t;
-        zq[jc] = s * u + c * t;
+        for (int jc = lane; jc < m; jc += 32) {
+          const double x = A[p + jc * m], y = A[q + jc * m];
+          A[p + jc * m] = c * x - s * y;
+          A[q + jc * m] = s * x + c * y;
+        }
+        double* zp = Zw + p * m;
+        double* zq = Zw + q * m;
+        for (int jc = lane; jc < m; jc += 32) {
+          const double u = zp[jc], t = zq[jc];
+          zp[jc] = c * u - s * t;
+          zq[jc] = s * u + c * t;
+        }
       }
       __syncthreads();
     }
@@ -315,9 +345,13 @@ __global__ void __launch_bounds__(1024)
 }  // namespace
 
 void mm_gemm(int m, const double* A, bool trA, const double* B, bool trB,
-             double* Cm, double alpha, double beta, cudaStream_t s) {
+             double* Cm, double alpha, double beta, cudaStream_t s,
+             bool fp32) {
   dim3 grid(ceil_div(m, 16), ceil_div(m, 16));
-  k_mm_gemm<<<grid, 256, 0, s>>>(m, A, trA, B, trB, Cm, alpha, beta);
+  if (fp32)
+    k_mm_gemm<float><<<grid, 256, 0, s>>>(m, A, trA, B, trB, Cm, alpha, beta);
+  else
+    k_mm_gemm<double><<<grid, 256, 0, s>>>(m, A, trA, B, trB, Cm, alpha, beta);
   TRM_CHECK_LAUNCH();
 }
 
@@ -340,21 +374,38 @@ void line_step(int m, const double* A0, const double* Bm, const double* Q,
   TRM_CHECK_LAUNCH();
 }
 
-template <typename Tm>
-void chol_inv(int m, const double* S, double* Linv, double* R, IterScalars* sc,
-              double* gwork, cudaStream_t s) {
+template <typename Tm, bool dev>
+static void chol_launch(int m, const double* S, double* Linv, double* R,
+                        IterScalars* sc, double* gwork, cudaStream_t s) {
   if (m > 1024) throw Error(-1, "chol_inv: m > 1024");
-  const size_t bytes = (size_t)m * m * sizeof(Tm);
+  const size_t bytes = (size_t)m * (m + 1) * sizeof(Tm);
   const bool smem = bytes <= 200 * 1024;
   if (smem) {
-    TRM_CUDA(cudaFuncSetAttribute(k_chol_inv<Tm>,
+    TRM_CUDA(cudaFuncSetAttribute(k_chol_inv<Tm, dev>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)bytes));
   }
-  k_chol_inv<Tm><<<1, 1024, smem ? bytes : 0, s>>>(
+  k_chol_inv<Tm, dev><<<1, 1024, smem ? bytes : 0, s>>>(
       m, S, Linv, R, sc, reinterpret_cast<Tm*>(gwork), smem ? 1 : 0);
   TRM_CHECK_LAUNCH();
 }
+
+template <typename Tm>
+void chol_inv(int m, const double* S, double* Linv, double* R, IterScalars* sc,
+              double* gwork, cudaStream_t s) {
+  chol_launch<Tm, false>(m, S, Linv, R, sc, gwork, s);
+}
+
+template <typename Tm>
+void chol_inv_dev(int m, const double* S, double* Linv, double* R,
+                  IterScalars* sc, double* gwork, cudaStream_t s) {
+  chol_launch<Tm, true>(m, S, Linv, R, sc, gwork, s);
+}
+
+template void chol_inv_dev<float>(int, const double*, double*, double*,
+                                  IterScalars*, double*, cudaStream_t);
+template void chol_inv_dev<double>(int, const double*, double*, double*,
+                                   IterScalars*, double*, cudaStream_t);
 
 void sym_eig(int m, const double* A, double* w, double* Z, double* work,
              int* info, cudaStream_t s) {

@@ -348,7 +348,7 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   bx.cols = m_;
   bx.count = 1;
   TRM_PROF(kgr, 2 * m2N, 2 * es * nm,
-           gram<T>(N_, m_, C, bx, Hp_, part_, part_cap_, s_));        // (6)
+           gram<T>(N_, m_, C, bx, Hp_, part_, part_cap_, s_, &sc_->status));        // (6)
   if (sizeof(T) == 4) zero_diag(m_, Hp_, s_);
   TRM_PROF(kgd, 2 * m2N, 5 * es * nm,
            gradient<T>(N_, m_, C, X, Hp_, G, Gp, P, minv, sc_, part_,
@@ -361,7 +361,7 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   bp.cols = m_;
   bp.count = 1;
   TRM_PROF(kgr, 2 * m2N, 2 * es * nm,
-           gram<T>(N_, m_, C, bp, Bm_, part_, part_cap_, s_));        // C^T P
+           gram<T>(N_, m_, C, bp, Bm_, part_, part_cap_, s_, &sc_->status));        // C^T P
   Blocks<T> b3;
   b3.p[0] = P;
   b3.p[1] = HP;
@@ -369,15 +369,19 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   b3.cols = m_;
   b3.count = 3;
   TRM_PROF(kgr, 6 * m2N, 4 * es * nm,
-           gram<T>(N_, m_, P, b3, PG_, part_, part_cap_, s_));        // P^T[P HP G]
+           gram<T>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status));        // P^T[P HP G]
   const double m3 = md * md * md;
   prof.begin(KC_SMALL, s_);
   make_A0(m_, Hp_, HD_, A0_, s_);
-  mm_gemm(m_, A0_, false, Bm_, false, T1_, 1.0, 0.0, s_);
-  mm_gemm(m_, Bm_, false, A0_, false, T2_, 1.0, 0.0, s_);
+  const bool f32 = sizeof(Tm) == 4;
+  mm_gemm(m_, A0_, false, Bm_, false, T1_, 1.0, 0.0, s_, f32);
+  mm_gemm(m_, Bm_, false, A0_, false, T2_, 1.0, 0.0, s_, f32);
   line_step<Tm>(m_, A0_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, T1_, T2_, S_, sc_,
                 s_);
-  chol_inv<Tm>(m_, S_, Linv_, R_, sc_, mmw_, s_);           // Fig. ONFIG
+  if (f32)
+    chol_inv_dev<Tm>(m_, S_, Linv_, R_, sc_, mmw_, s_);     // Fig. ONFIG
+  else
+    chol_inv<Tm>(m_, S_, Linv_, R_, sc_, mmw_, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(krt, m2N, 3 * es * nm,
            (rotate<T, T>(N_, m_, C, P, R_, Cn, sc_, s_)));    // (C+aP)L^-T
@@ -412,11 +416,11 @@ void Solver::iter_mp2() {
   bx.cols = m_;
   bx.count = 1;
   TRM_PROF(KC_GRAM32, 2 * m2N, 8 * nm,
-           gram<float>(N_, m_, C32_, bx, Hp_, part_, part_cap_, s_)); // (6)
+           gram<float>(N_, m_, C32_, bx, Hp_, part_, part_cap_, s_, &sc_->status)); // (6)
   zero_diag(m_, Hp_, s_);
   TRM_PROF(KC_GRAD32, 2 * m2N, 20 * nm,
            gradient<float>(N_, m_, C32_, X32_, Hp_, G, Gp, P, minv, sc_,
-                           part_, part_cap_, s_));                    // (7)
+                           part_, part_cap_, s_));            // (7)
   TRM_PROF(KC_ROWOPS, 2 * nm, 12 * nm,
            update_p<float>(N_, m_, G, P, minv, sc_, s_));
   TRM_PROF(KC_SPMM32, f32, b32, apply_h(op_, P, HP, m_, s_));
@@ -425,7 +429,7 @@ void Solver::iter_mp2() {
   bp.cols = m_;
   bp.count = 1;
   TRM_PROF(KC_GRAM32, 2 * m2N, 8 * nm,
-           gram<float>(N_, m_, C32_, bp, Bm_, part_, part_cap_, s_));
+           gram<float>(N_, m_, C32_, bp, Bm_, part_, part_cap_, s_, &sc_->status));
   Blocks<float> b3;
   b3.p[0] = P;
   b3.p[1] = HP;
@@ -433,14 +437,14 @@ void Solver::iter_mp2() {
   b3.cols = m_;
   b3.count = 3;
   TRM_PROF(KC_GRAM32, 6 * m2N, 16 * nm,
-           gram<float>(N_, m_, P, b3, PG_, part_, part_cap_, s_));
+           gram<float>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status));
   prof.begin(KC_SMALL, s_);
   make_A0(m_, Hp_, HD_, A0_, s_);
-  mm_gemm(m_, A0_, false, Bm_, false, T1_, 1.0, 0.0, s_);
-  mm_gemm(m_, Bm_, false, A0_, false, T2_, 1.0, 0.0, s_);
-  line_step<double>(m_, A0_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, T1_, T2_, S_,
-                    sc_, s_);
-  chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_);
+  mm_gemm(m_, A0_, false, Bm_, false, T1_, 1.0, 0.0, s_, true);
+  mm_gemm(m_, Bm_, false, A0_, false, T2_, 1.0, 0.0, s_, true);
+  line_step<float>(m_, A0_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, T1_, T2_, S_,
+                   sc_, s_);
+  chol_inv_dev<float>(m_, S_, Linv_, R_, sc_, mmw_, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(KC_ROT32, m2N, 20 * nm,
            rotate_split(N_, m_, C64_, P, R_, C64n_, sc_, s_));
@@ -456,7 +460,7 @@ void Solver::orth_fp64(double*& C, double*& Cn) {
   b.count = 1;
   const double nm = (double)N_ * m_, m2N = nm * m_;
   TRM_PROF(KC_GRAM64, 2 * m2N, 16 * nm,
-           gram<double>(N_, m_, C, b, S_, part_, part_cap_, s_));
+           gram<double>(N_, m_, C, b, S_, part_, part_cap_, s_, &sc_->status));
   TRM_PROF(KC_SMALL, 2.0 * m_ * m_ * m_ / 3, 0.0,
            chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_));
   TRM_PROF(KC_ROT64, m2N, 16 * nm,
@@ -470,7 +474,7 @@ void Solver::orth_uniform(T*& C, T*& Cn) {
   b.p[0] = C;
   b.cols = m_;
   b.count = 1;
-  gram<T>(N_, m_, C, b, S_, part_, part_cap_, s_);
+  gram<T>(N_, m_, C, b, S_, part_, part_cap_, s_, &sc_->status);
   chol_inv<T>(m_, S_, Linv_, R_, sc_, mmw_, s_);
   rotate<T, T>(N_, m_, C, static_cast<const T*>(nullptr), R_, Cn, nullptr,
                s_);
@@ -484,7 +488,7 @@ void Solver::rr_rotate_fp64() {
   b.p[0] = X64_;
   b.cols = m_;
   b.count = 1;
-  gram<double>(N_, m_, C64_, b, Hp_, part_, part_cap_, s_);
+  gram<double>(N_, m_, C64_, b, Hp_, part_, part_cap_, s_, &sc_->status);
   make_A0(m_, Hp_, nullptr, A0_, s_);
   TRM_PROF(KC_EIG, 0.0, 0.0, sym_eig(m_, A0_, eigw_, Z_, mmw_, info_, s_));
   const double nm = (double)N_ * m_;
@@ -502,12 +506,12 @@ void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
   bx.p[0] = X64_;
   bx.cols = m_;
   bx.count = 1;
-  gram<double>(N_, m_, C, bx, Hp_, part_, part_cap_, s_);
+  gram<double>(N_, m_, C, bx, Hp_, part_, part_cap_, s_, &sc_->status);
   Blocks<double> bc;
   bc.p[0] = C;
   bc.cols = m_;
   bc.count = 1;
-  gram<double>(N_, m_, C, bc, S_, part_, part_cap_, s_);
+  gram<double>(N_, m_, C, bc, S_, part_, part_cap_, s_, &sc_->status);
   chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_);
   mm_gemm(m_, Linv_, false, Hp_, false, T1_, 1.0, 0.0, s_);
   mm_gemm(m_, T1_, false, Linv_, true, T2_, 1.0, 0.0, s_);
@@ -556,6 +560,11 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
   int status = TRM_OK;
   double r0 = -1.0, best = INFINITY;
   int best_at = 0;
+  // Full SP has reached its floor when the energy (summed in FP64 from FP32
+  // products, resolution ~1e-7 |E|) stops making new minima.
+  double E_min = INFINITY;
+  int E_min_at = 0;
+  const int sp_floor_window = 30;
   int since_orth = 0, since_rr = 0, rescues = 0;
   // MP2 keeps C orthonormal between exact FP64 re-orthonormalizations only
   // to the FP32 accuracy of its overlap update, an error proportional to the
@@ -625,6 +634,11 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
                    std::to_string(i);
       break;
     }
+    if (v.status & 2) {  // a bounded device wait gave up
+      status = TRM_ETIMEOUT;
+      last_error = "a tensor-core pipeline wait timed out";
+      break;
+    }
     if (v.status & 1) {  // overlap not positive definite: re-orthonormalise
       drain();
       if (++rescues > 5) {
@@ -650,9 +664,14 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
         break;
       }
     }
+    if (v.E < E_min - 1e-7 * std::fabs(v.E)) {
+      E_min = v.E;
+      E_min_at = i;
+    }
     if (phase == PH_SP) {
       const bool small = v.rms <= opt_.switch_tol[0] * r0;
-      const bool stalled = i - best_at > stall_window;
+      const bool stalled = i - best_at > stall_window ||
+                           (prec != TRM_FULL_SP && i - E_min_at > sp_floor_window);
       if (prec == TRM_FULL_SP) {
         if (stalled) {
           status = TRM_ENOCONV;
@@ -780,7 +799,7 @@ void Solver::energy_gradient(const double* C, double* E, double* HD,
     b.p[0] = X64_;
     b.cols = m_;
     b.count = 1;
-    gram<double>(N_, m_, C, b, Hp_, part_, part_cap_, s_);
+    gram<double>(N_, m_, C, b, Hp_, part_, part_cap_, s_, &sc_->status);
     if (zdiag) zero_diag(m_, Hp_, s_);
     gradient<double>(N_, m_, C, X64_, Hp_, static_cast<double*>(G), nullptr,
                      nullptr, nullptr, sc_, part_, part_cap_, s_);
@@ -790,7 +809,7 @@ void Solver::energy_gradient(const double* C, double* E, double* HD,
     b.p[0] = X32_;
     b.cols = m_;
     b.count = 1;
-    gram<float>(N_, m_, C32_, b, Hp_, part_, part_cap_, s_);
+    gram<float>(N_, m_, C32_, b, Hp_, part_, part_cap_, s_, &sc_->status);
     if (zdiag) zero_diag(m_, Hp_, s_);
     gradient<float>(N_, m_, C32_, X32_, Hp_, static_cast<float*>(G), nullptr,
                     nullptr, nullptr, sc_, part_, part_cap_, s_);
