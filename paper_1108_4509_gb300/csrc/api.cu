@@ -279,7 +279,8 @@ trm_status trm_orthonormalize(int64_t N, int m, double* C, void* stream) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t mm = (size_t)m * m;
     const size_t cap = trm::gram_partials_doubles(N, m, m);
-    const size_t bytes = (cap + 4 * mm + m + (size_t)N * m) * sizeof(double) +
+    const size_t cw = trm::chol_work_elems(m);
+    const size_t bytes = (cap + 3 * mm + cw + (size_t)N * m) * sizeof(double) +
                          sizeof(trm::IterScalars);
     char* w = nullptr;
     TRM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&w), bytes, s));
@@ -287,8 +288,8 @@ trm_status trm_orthonormalize(int64_t N, int m, double* C, void* stream) {
     double* S = part + cap;
     double* Linv = S + mm;
     double* R = Linv + mm;
-    double* gw = R + mm;        // m (m + 1): padded factorisation workspace
-    double* Cn = gw + mm + m;
+    double* gw = R + mm;        // padded factorisation workspace
+    double* Cn = gw + cw;
     auto* sc = reinterpret_cast<trm::IterScalars*>(Cn + (size_t)N * m);
     int status = 0;
     try {

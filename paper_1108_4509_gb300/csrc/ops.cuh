@@ -140,14 +140,21 @@ void mm_gemm(int m, const double* A, bool trA, const double* B, bool trB,
 // A0 = sym(H') + diag(H_D)
 void make_A0(int m, const double* Hp, const double* HD, double* A0,
              cudaStream_t s);
-// line model: alpha from the projections (T1 = A0 B, T2 = B A0); writes
-// S = I + a (B + B^T) + a^2 Q and the step into sc
+// The line step along P and the factor of the new overlap: the line-model
+// terms from H' (diag zeroed), H_D, B = C^T P, Q = P^T P, P^T H P and
+// W = P^T G give alpha (into sc); then S = I + a (B + B^T) + a^2 Q is
+// factorised (in deviation form when dev) into Linv and R = L^{-T}.
+// part: >= 4 * ceil(m/32)^2 doubles; gwork: chol_work_elems(m) doubles.
 template <typename Tm>
-void line_step(int m, const double* A0, const double* Bm, const double* Q,
-               const double* HPP, const double* W, const double* T1,
-               const double* T2, double* S, IterScalars* sc, cudaStream_t s);
+void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
+                 const double* Q, const double* HPP, const double* W,
+                 double* Linv, double* R, IterScalars* sc, double* gwork,
+                 double* part, bool dev, cudaStream_t s);
+// Elements (of the arithmetic type) of the factorisation workspace gwork.
+size_t chol_work_elems(int m);
 // S = L L^T (lower); writes Linv = L^{-1} and R = L^{-T}. Non-PD sets
-// sc->status bit 1 and returns identities. gwork: m*m doubles.
+// sc->status bit 1 and returns identities. gwork: chol_work_elems(m)
+// doubles (used when the working copy does not fit in shared memory).
 template <typename Tm>
 void chol_inv(int m, const double* S, double* Linv, double* R,
               IterScalars* sc, double* gwork, cudaStream_t s);

@@ -67,37 +67,288 @@ __global__ void k_make_A0(int m, const double* __restrict__ Hp,
 // with B = C^T P, Q = P^T P, W = P^T G. Every term is formed from small
 // quantities, so E(a) - E(0) = tr(S(a)^{-1} (a D1 + a^2 D2)) keeps its
 // relative accuracy close to convergence. To second order
-//   E(a) - E(0) = a tr(D1) + a^2 (tr(D2) - tr(S1 D1)),
-// and the step is the minimiser of that parabola, bounded so that the RMS
-// column change a ||P||_F / sqrt(m) stays below 1.
+//   E(a) - E(0) = a tr(D1) + a^2 (tr(D2) - tr(S1 D1)).
+// ---------------------------------------------------------------------------
+
+// ---------------------------------------------------------------------------
+// Cholesky S = L L^T and L^{-1}, blocked in 32-column panels, one CTA of 1024
+// threads. Writes Linv (lower) and R = L^{-T} (upper).
+//
+// m is padded to mp, a multiple of 32, with the identity, which changes
+// neither factor. Per panel p: (a) one warp factors the diagonal block
+// column by column; (b) every row below solves x L_pp^T = a (registers);
+// (c) all threads update the lower trailing triangle with 4 x 4 register
+// tiles. The inverse: (d) warp p inverts diagonal block p; (e) row-block by
+// row-block, X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj through a 32 x mp
+// temporary. The working copy has leading dimension mp + 1.
+//
+// S is read from memory, or (Bm != null) formed on the fly as
+// S = I + a (B + B^T) + a^2 Q with a = sc->alpha (the line step's overlap).
+//
+// With dev = true the factorisation runs in deviation form for S = I + E:
+// L = I + F and L^{-1} = I + Y with the identity kept exact and only the
+// small E, F, Y held in Tm. Pivot: d = E_cc - sum_k F_ck^2 and
+// f_cc = d / (1 + sqrt(1 + d)); off the diagonal L and F coincide; inverse
+// diagonal y_cc = -f_cc / (1 + f_cc). When S - I is small, FP32 arithmetic
+// here yields L to FP64 accuracy relative to I.
+// ---------------------------------------------------------------------------
+template <typename Tm, bool dev>
+__global__ void __launch_bounds__(512)
+    k_chol_inv(int m, const double* __restrict__ S, const double* __restrict__ Bm,
+               const double* __restrict__ Q, double* __restrict__ Linv,
+               double* __restrict__ R, IterScalars* sc, Tm* gwork,
+               int use_smem) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int mp = (m + 31) & ~31, ld = mp + 1, P = mp >> 5;
+  Tm* a = use_smem ? reinterpret_cast<Tm*>(smraw) : gwork;
+  Tm* tb = a + (size_t)mp * ld;  // 32 x mp, leading dimension 33
+  const Tm one = dev ? (Tm)1 : (Tm)0;
+  const Tm eps = sizeof(Tm) == 4 ? (Tm)1.2e-7 : (Tm)2.3e-16;
+  const double al = Bm ? sc->alpha : 0.0;
+  for (int k = warp; k < mp; k += nw)
+    for (int i = k + lane; i < mp; i += 32) {
+      double v;
+      if (i < m && k < m) {
+        if (Bm)
+          v = al * (Bm[i + k * m] + Bm[k + i * m]) +
+              al * al * 0.5 * (Q[i + k * m] + Q[k + i * m]) +
+              (!dev && i == k ? 1.0 : 0.0);
+        else
+          v = S[i + k * m] - (dev && i == k ? 1.0 : 0.0);
+      } else {
+        v = (!dev && i == k) ? 1.0 : 0.0;
+      }
+      a[i + k * ld] = (Tm)v;
+    }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+
+  for (int p = 0; p < P; ++p) {
+    const int c0 = 32 * p;
+    // (a) diagonal block: lane r holds row c0 + r in registers; pivots and
+    // column entries move between lanes by shuffles
+    if (warp == 0) {
+      const int r = c0 + lane;
+      Tm v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = a[r + (c0 + k) * ld];
+      bool b = false;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int cc = c0 + c;
+        Tm d = __shfl_sync(0xffffffffu, v[c], c);
+        Tm piv;
+        if (dev) {
+          if (!(d > (Tm)-0.999)) {  // pivot 1 + d not positive: singular S
+            b = true;
+            d = (Tm)0;
+          }
+          piv = d / ((Tm)1 + sqrt((Tm)1 + d));
+        } else {
+          // a pivot that has lost all but 4m roundings of its original
+          // diagonal entry marks a (numerically) singular S
+          const double sjj = (Bm || cc >= m) ? 1.0 : fabs(S[cc + cc * m]);
+          if (!(d > (Tm)(4 * m) * eps * (Tm)sjj)) {
+            b = true;
+            d = (Tm)1;
+          }
+          piv = sqrt(d);
+        }
+        const Tm inv = (Tm)1 / (one + piv);
+        if (lane == c) v[c] = piv;
+        if (lane > c) v[c] *= inv;
+#pragma unroll
+        for (int k = c + 1; k < 32; ++k) {
+          const Tm lkc = __shfl_sync(0xffffffffu, v[c], k);
+          if (lane >= k) v[k] -= v[c] * lkc;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 32; ++k) a[r + (c0 + k) * ld] = v[k];
+      if (lane == 0 && b) bad = 1;
+    }
+    __syncthreads();
+    // (b) rows below the block: x L_pp^T = a
+    for (int r = c0 + 32 + tid; r < mp; r += nt) {
+      Tm x[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) x[c] = a[r + (c0 + c) * ld];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        Tm sum = x[c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) sum -= x[k] * a[(c0 + c) + (c0 + k) * ld];
+        x[c] = sum / (one + a[(c0 + c) + (c0 + c) * ld]);
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) a[r + (c0 + c) * ld] = x[c];
+    }
+    __syncthreads();
+    // (c) lower trailing triangle, 4 x 4 tiles
+    const int base = c0 + 32;
+    const int T = (mp - base) >> 2;
+    const int ntile = T * (T + 1) / 2;
+    for (int t = tid; t < ntile; t += nt) {
+      int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+      while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+      while (ti * (ti + 1) / 2 > t) --ti;
+      const int tj = t - ti * (ti + 1) / 2;
+      const int r0 = base + 4 * ti, s0 = base + 4 * tj;
+      Tm acc[4][4] = {};
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        Tm lr[4], ls[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          lr[u] = a[(r0 + u) + (c0 + k) * ld];
+          ls[u] = a[(s0 + u) + (c0 + k) * ld];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] += lr[u] * ls[v];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (r0 + u >= s0 + v) a[(r0 + u) + (s0 + v) * ld] -= acc[u][v];
+    }
+    __syncthreads();
+  }
+
+  // (d) inverse of each diagonal block, one warp per block
+  for (int pb = warp; pb < P; pb += nw) {
+    const int c0 = 32 * pb;
+    const int r = c0 + lane;
+    for (int c = 31; c >= 0; --c) {
+      const int cc = c0 + c;
+      const Tm f = a[cc + cc * ld];
+      const Tm yd = dev ? -f / ((Tm)1 + f) : (Tm)1 / f;
+      const Tm scale = dev ? -((Tm)1 + yd) : -yd;
+      const Tm xr = lane > c ? a[r + cc * ld] : (Tm)0;
+      Tm sum = 0;
+      for (int k = c + 1; k < 32; ++k) {
+        const Tm xk = __shfl_sync(0xffffffffu, xr, k);
+        if (k <= lane) sum += a[r + (c0 + k) * ld] * xk;
+      }
+      __syncwarp();
+      if (lane == c) a[cc + cc * ld] = yd;
+      if (lane > c) a[r + cc * ld] = scale * ((dev ? xr : (Tm)0) + sum);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // (e) off-diagonal blocks, row-block by row-block
+  for (int i = 1; i < P; ++i) {
+    const int ri = 32 * i;
+    const int cnt = 32 * ri;
+    for (int e = tid; e < cnt; e += nt) {  // T = sum_k L_ik X_kj
+      const int r = e & 31, c = e >> 5;
+      Tm sum = dev ? a[(ri + r) + c * ld] : (Tm)0;  // identity part of X_jj
+      for (int col = c; col < ri; ++col) sum += a[(ri + r) + col * ld] * a[col + c * ld];
+      tb[r + c * 33] = sum;
+    }
+    __syncthreads();
+    for (int e = tid; e < cnt; e += nt) {  // X_ij = -X_ii T
+      const int r = e & 31, c = e >> 5;
+      Tm sum = dev ? tb[r + c * 33] : (Tm)0;
+      for (int q = 0; q <= r; ++q) sum += a[(ri + r) + (ri + q) * ld] * tb[q + c * 33];
+      a[(ri + r) + c * ld] = -sum;
+    }
+    __syncthreads();
+  }
+  const int isbad = bad;
+  for (int k = warp; k < m; k += nw) {
+    for (int i = lane; i < m; i += 32) {
+      double v;
+      if (isbad)
+        v = (i == k) ? 1.0 : 0.0;
+      else
+        v = (dev && i == k ? 1.0 : 0.0) + (i >= k ? (double)a[i + k * ld] : 0.0);
+      Linv[i + k * m] = v;  // Linv(i, k)
+      R[k + i * m] = v;     // R(k, i) = Linv(i, k)
+    }
+  }
+  if (tid == 0 && isbad && sc) sc->status |= 1;
+}
+
+// ---------------------------------------------------------------------------
+// Line-model terms over 32 x 32 tiles of the (i, j) index space, one CTA of
+// 1024 threads per tile, partial sums to part[tile * 4 + q]:
+//   q = 0: tr(D1) = -tr(W)
+//   q = 1: tr(D2) = tr(P^T H P) - sum_ij Q_ij A0_ij
+//   q = 2: tr(S1 D1) = sum_ij A0_ij (B B^T - B^T B)_ij
+//                      - 1/2 sum_ij S1_ij (W_ij + W_ji)
+//   q = 3: tr(Q)
+// with A0 = sym(H') + diag(H_D), S1 = B + B^T; tr(S1 (A0 B - B A0)) reduces
+// to tr(A0 (B B^T - B^T B)) by cyclic invariance, so no m x m product is
+// stored.
 // ---------------------------------------------------------------------------
 template <typename Tm>
 __global__ void __launch_bounds__(1024)
-    k_line_step(int m, const double* __restrict__ A0,
-                const double* __restrict__ Bm, const double* __restrict__ Q,
-                const double* __restrict__ HPP, const double* __restrict__ W,
-                const double* __restrict__ T1, const double* __restrict__ T2,
-                double* __restrict__ S, IterScalars* sc) {
+    k_line_terms(int m, const double* __restrict__ Hp,
+                 const double* __restrict__ HD, const double* __restrict__ Bm,
+                 const double* __restrict__ Q, const double* __restrict__ HPP,
+                 const double* __restrict__ W, double* __restrict__ part) {
+  __shared__ Tm t0[32][33], t1[32][33], t2[32][33], t3[32][33];
   __shared__ double red[4 * 32];
-  __shared__ double alpha_sh;
-  Tm trD1 = 0, trD2 = 0, trS1D1 = 0, trQ = 0;
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = threadIdx.x >> 5; j < m; j += nw)
-  for (int i = lane; i < m; i += 32) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int I0 = blockIdx.x * 32, J0 = blockIdx.y * 32;
+  const int i = I0 + tx, j = J0 + ty;
+  Tm M = 0;
+  for (int k0 = 0; k0 < m; k0 += 32) {
+    t0[tx][ty] = (I0 + tx < m && k0 + ty < m) ? (Tm)Bm[(I0 + tx) + (k0 + ty) * m] : (Tm)0;
+    t1[tx][ty] = (J0 + tx < m && k0 + ty < m) ? (Tm)Bm[(J0 + tx) + (k0 + ty) * m] : (Tm)0;
+    t2[tx][ty] = (k0 + tx < m && I0 + ty < m) ? (Tm)Bm[(k0 + tx) + (I0 + ty) * m] : (Tm)0;
+    t3[tx][ty] = (k0 + tx < m && J0 + ty < m) ? (Tm)Bm[(k0 + tx) + (J0 + ty) * m] : (Tm)0;
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk)
+      M += t0[tx][kk] * t1[ty][kk] - t2[kk][tx] * t3[kk][ty];
+    __syncthreads();
+  }
+  // transposed tiles (J, I) of H', B, W for the (j, i) entries
+  t0[tx][ty] = (J0 + tx < m && I0 + ty < m) ? (Tm)Hp[(J0 + tx) + (I0 + ty) * m] : (Tm)0;
+  t1[tx][ty] = (J0 + tx < m && I0 + ty < m) ? (Tm)Bm[(J0 + tx) + (I0 + ty) * m] : (Tm)0;
+  t2[tx][ty] = (J0 + tx < m && I0 + ty < m) ? (Tm)W[(J0 + tx) + (I0 + ty) * m] : (Tm)0;
+  __syncthreads();
+  Tm v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+  if (i < m && j < m) {
     const int e = i + j * m;
-    const int et = j + i * m;  // (j, i)
-    const Tm s1 = (Tm)Bm[e] + (Tm)Bm[et];   // S1_ij
-    // D1_ji = T1_ji - T2_ji - (W_ji + W_ij)/2
-    const Tm d1ji = (Tm)T1[et] - (Tm)T2[et] - (Tm)0.5 * ((Tm)W[et] + (Tm)W[e]);
-    trS1D1 += s1 * d1ji;
-    trD2 -= (Tm)Q[e] * (Tm)A0[e];
+    const Tm a0 = (Tm)0.5 * ((Tm)Hp[e] + t0[ty][tx]) + (i == j ? (Tm)HD[i] : (Tm)0);
+    const Tm s1 = (Tm)Bm[e] + t1[ty][tx];
+    const Tm wij = (Tm)W[e], wji = t2[ty][tx];
+    v2 = a0 * M - (Tm)0.5 * s1 * (wij + wji);
+    v1 = -(Tm)Q[e] * a0;
     if (i == j) {
-      trD1 -= (Tm)W[e];
-      trD2 += (Tm)HPP[e];
-      trQ += (Tm)Q[e];
+      v0 = -wij;
+      v1 += (Tm)HPP[e];
+      v3 = (Tm)Q[e];
     }
   }
-  double v[4] = {(double)trD1, (double)trD2, (double)trS1D1, (double)trQ};
+  double v[4] = {(double)v0, (double)v1, (double)v2, (double)v3};
+  block_sum<4>(v, red);
+  if (threadIdx.x == 0) {
+    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) part[b * 4 + q] = v[q];
+  }
+}
+
+// The step along P: minimiser of the parabola a tr(D1) + a^2 (tr(D2) -
+// tr(S1 D1)), bounded so that the RMS column change a ||P||_F / sqrt(m)
+// stays below 1; a restart is requested when P is not a descent direction.
+__global__ void k_line_alpha(int m, const double* __restrict__ part, int nparts,
+                             IterScalars* sc) {
+  __shared__ double red[4 * 32];
+  double v[4] = {0, 0, 0, 0};
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] += part[(size_t)p * 4 + q];
   block_sum<4>(v, red);
   if (threadIdx.x == 0) {
     const double g0 = v[0];
@@ -118,133 +369,33 @@ __global__ void __launch_bounds__(1024)
     sc->alpha_prev = alpha > 0.0 ? alpha : sc->alpha_prev;
     sc->c2 = c2;
     sc->dE = alpha * g0 + alpha * alpha * c2;
-    alpha_sh = alpha;
   }
-  __syncthreads();
-  const double a = alpha_sh;
-  for (int j = threadIdx.x >> 5; j < m; j += nw)
-  for (int i = lane; i < m; i += 32) {
-    const int e = i + j * m;
-    const int et = j + i * m;
-    const double s1 = Bm[e] + Bm[et];
-    const double q = 0.5 * (Q[e] + Q[et]);
-    S[e] = (i == j ? 1.0 : 0.0) + a * s1 + a * a * q;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Cholesky S = L L^T (right-looking, lower) and L^{-1} in place (backward
-// column sweep: col j of L^{-1} below the diagonal is -(L22^{-1} l) / l_jj).
-// Writes Linv (lower) and R = L^{-T} (upper). One CTA of 1024 threads; the
-// working copy has leading dimension m + 1 so that a warp walking along a
-// row touches 32 distinct banks.
-//
-// With dev = true the matrix is S = I + E and the factorisation runs in
-// deviation form: L = I + F and L^{-1} = I + Y with the identity kept exact
-// and only the small E, F, Y held in Tm. Pivot j: d = E_jj - sum_k F_jk^2,
-// f_jj = d / (1 + sqrt(1 + d)); below it F_ij = (E_ij - sum_k F_ik F_jk) /
-// (1 + f_jj). Inverse: y_jj = -f_jj / (1 + f_jj), and the column below is
-// -(1 + y_jj) (x + Y22 x) with x = F[j+1:, j]. When S - I is small, FP32
-// arithmetic here yields L to FP64 accuracy relative to I.
-// ---------------------------------------------------------------------------
-template <typename Tm, bool dev>
-__global__ void __launch_bounds__(1024)
-    k_chol_inv(int m, const double* __restrict__ S, double* __restrict__ Linv,
-               double* __restrict__ R, IterScalars* sc, Tm* gwork,
-               int use_smem) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ int bad;
-  __shared__ Tm tmp[1024];
-  Tm* a = use_smem ? reinterpret_cast<Tm*>(smraw) : gwork;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const int ld = m + 1;
-  const Tm eps = sizeof(Tm) == 4 ? (Tm)1.2e-7 : (Tm)2.3e-16;
-  for (int k = warp; k < m; k += nw)
-    for (int i = lane; i < m; i += 32)
-      a[i + k * ld] = (Tm)(S[i + k * m] - (dev && i == k ? 1.0 : 0.0));
-  if (tid == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    if (tid == 0) {
-      Tm d = a[j + j * ld];
-      if (dev) {
-        if (!(d > (Tm)-0.999)) {  // pivot 1 + d not positive: singular S
-          bad = 1;
-          d = (Tm)0;
-        }
-        a[j + j * ld] = d / ((Tm)1 + sqrt((Tm)1 + d));
-      } else {
-        // a pivot that has lost all but 4m roundings of its original
-        // diagonal entry marks a (numerically) singular S
-        const Tm floor_j = (Tm)(4 * m) * eps * (Tm)fabs(S[j + j * m]);
-        if (!(d > floor_j)) {
-          bad = 1;
-          d = (Tm)1;
-        }
-        a[j + j * ld] = sqrt(d);
-      }
-    }
-    __syncthreads();
-    const Tm ljj = (dev ? (Tm)1 : (Tm)0) + a[j + j * ld];
-    for (int i = j + 1 + tid; i < m; i += nt) a[i + j * ld] /= ljj;
-    __syncthreads();
-    // trailing update of the lower triangle: a warp per column, lanes down
-    for (int k = j + 1 + warp; k < m; k += nw) {
-      const Tm lkj = a[k + j * ld];
-      for (int i = k + lane; i < m; i += 32) a[i + k * ld] -= a[i + j * ld] * lkj;
-    }
-    __syncthreads();
-  }
-  for (int j = m - 1; j >= 0; --j) {
-    if (tid == 0) {
-      const Tm f = a[j + j * ld];
-      a[j + j * ld] = dev ? -f / ((Tm)1 + f) : (Tm)1 / f;
-    }
-    for (int i = j + 1 + tid; i < m; i += nt) tmp[i] = a[i + j * ld];
-    __syncthreads();
-    const Tm scale = dev ? -((Tm)1 + a[j + j * ld]) : -a[j + j * ld];
-    // row i of the already inverted trailing block times the column below
-    // the pivot: one warp per row, lanes along k
-    for (int i = j + 1 + warp; i < m; i += nw) {
-      Tm y = 0;
-      for (int k = j + 1 + lane; k <= i; k += 32) y += a[i + k * ld] * tmp[k];
-      y = warp_sum(y);
-      if (lane == 0) a[i + j * ld] = scale * ((dev ? tmp[i] : (Tm)0) + y);
-    }
-    __syncthreads();
-  }
-  const int isbad = bad;
-  for (int k = warp; k < m; k += nw) {
-    for (int i = lane; i < m; i += 32) {
-      double v;
-      if (isbad)
-        v = (i == k) ? 1.0 : 0.0;
-      else
-        v = (dev && i == k ? 1.0 : 0.0) + (i >= k ? (double)a[i + k * ld] : 0.0);
-      Linv[i + k * m] = v;  // Linv(i, k)
-      R[k + i * m] = v;     // R(k, i) = Linv(i, k)
-    }
-  }
-  if (tid == 0 && isbad && sc) sc->status |= 1;
 }
 
 // ---------------------------------------------------------------------------
 // Cyclic Jacobi with the round-robin ordering: in each round m/2 disjoint
-// (p, q) pairs are annihilated at once (columns, then rows, then Z).
-// A (work, overwritten) and Zw are in global memory; one CTA.
+// (p, q) pairs are annihilated at once (columns, then rows, then Z). One CTA;
+// A lives in shared memory (leading dimension m + 1) when it fits, else in
+// the global work copy; Z accumulates in global memory, where its column
+// updates are contiguous.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-    k_jacobi(int m, double* __restrict__ A, double* __restrict__ Zw,
+    k_jacobi(int m, double* __restrict__ Ag, double* __restrict__ Zw,
              double* __restrict__ w, double* __restrict__ Z, int* info,
-             int max_sweeps) {
+             int max_sweeps, int use_smem) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double cs[512], sn[512];
   __shared__ int pp[512], qq[512];
   __shared__ double red[2 * 32];
   __shared__ int done;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, nw = nt >> 5;
-  for (int c = tid >> 5; c < m; c += nw)
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int ld = use_smem ? m + 1 : m;
+  double* A = use_smem ? reinterpret_cast<double*>(smraw) : Ag;
+  if (use_smem)
+    for (int c = warp; c < m; c += nw)
+      for (int r = lane; r < m; r += 32) A[r + c * ld] = Ag[r + c * m];
+  for (int c = warp; c < m; c += nw)
     for (int r = lane; r < m; r += 32) Zw[r + c * m] = (r == c) ? 1.0 : 0.0;
   const int M = m + (m & 1);
   const int np = M / 2;
@@ -252,9 +403,9 @@ __global__ void __launch_bounds__(1024)
   __syncthreads();
   for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
     double v[2] = {0.0, 0.0};
-    for (int c = tid >> 5; c < m; c += nw)
+    for (int c = warp; c < m; c += nw)
       for (int r = lane; r < m; r += 32) {
-        const double x = A[r + c * m];
+        const double x = A[r + c * ld];
         if (r == c)
           v[1] += x * x;
         else
@@ -273,9 +424,9 @@ __global__ void __launch_bounds__(1024)
         const int p = min(a0, b0), q = max(a0, b0);
         double c = 1.0, s = 0.0;
         if (q < m) {
-          const double apq = A[p + (int64_t)q * m];
-          const double app = A[p + (int64_t)p * m];
-          const double aqq = A[q + (int64_t)q * m];
+          const double apq = A[p + q * ld];
+          const double app = A[p + p * ld];
+          const double aqq = A[q + q * ld];
           if (fabs(apq) > 1e-300 &&
               fabs(apq) > 1e-18 * (fabs(app) + fabs(aqq))) {
             const double th = (aqq - app) / (2.0 * apq);
@@ -294,35 +445,58 @@ __global__ void __launch_bounds__(1024)
         qq[k] = min(q, m - 1);
       }
       __syncthreads();
-      for (int k = tid >> 5; k < np; k += nw) {  // A <- A J
+      for (int k = warp; k < np; k += nw) {  // A <- A J (columns p, q)
         const double s = sn[k];
         if (s == 0.0) continue;
         const double c = cs[k];
-        double* ap = A + pp[k] * m;
-        double* aq = A + qq[k] * m;
-        for (int i = lane; i < m; i += 32) {
-          const double x = ap[i], y = aq[i];
-          ap[i] = c * x - s * y;
-          aq[i] = s * x + c * y;
+        double* ap = A + pp[k] * ld;
+        double* aq = A + qq[k] * ld;
+        for (int i0 = lane; i0 < m; i0 += 128) {
+          double x[4], y[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + 32 * u;
+            x[u] = i < m ? ap[i] : 0.0;
+            y[u] = i < m ? aq[i] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + 32 * u;
+            if (i < m) {
+              ap[i] = c * x[u] - s * y[u];
+              aq[i] = s * x[u] + c * y[u];
+            }
+          }
         }
       }
       __syncthreads();
-      for (int k = tid >> 5; k < np; k += nw) {  // A <- J^T A, Z <- Z J
+      for (int k = warp; k < np; k += nw) {  // A <- J^T A (rows), Z <- Z J
         const double s = sn[k];
         if (s == 0.0) continue;
         const double c = cs[k];
         const int p = pp[k], q = qq[k];
-        for (int jc = lane; jc < m; jc += 32) {
-          const double x = A[p + jc * m], y = A[q + jc * m];
-          A[p + jc * m] = c * x - s * y;
-          A[q + jc * m] = s * x + c * y;
-        }
         double* zp = Zw + p * m;
         double* zq = Zw + q * m;
-        for (int jc = lane; jc < m; jc += 32) {
-          const double u = zp[jc], t = zq[jc];
-          zp[jc] = c * u - s * t;
-          zq[jc] = s * u + c * t;
+        for (int j0 = lane; j0 < m; j0 += 128) {
+          double x[4], y[4], u_[4], t_[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int jc = j0 + 32 * u;
+            x[u] = jc < m ? A[p + jc * ld] : 0.0;
+            y[u] = jc < m ? A[q + jc * ld] : 0.0;
+            u_[u] = jc < m ? zp[jc] : 0.0;
+            t_[u] = jc < m ? zq[jc] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int jc = j0 + 32 * u;
+            if (jc < m) {
+              A[p + jc * ld] = c * x[u] - s * y[u];
+              A[q + jc * ld] = s * x[u] + c * y[u];
+              zp[jc] = c * u_[u] - s * t_[u];
+              zq[jc] = s * u_[u] + c * t_[u];
+            }
+          }
         }
       }
       __syncthreads();
@@ -330,14 +504,14 @@ __global__ void __launch_bounds__(1024)
   }
   // ascending order (stable on ties)
   for (int i = tid; i < m; i += nt) {
-    const double wi = A[i + (int64_t)i * m];
+    const double wi = A[i + i * ld];
     int rank = 0;
     for (int j = 0; j < m; ++j) {
-      const double wj = A[j + (int64_t)j * m];
+      const double wj = A[j + j * ld];
       rank += (wj < wi) || (wj == wi && j < i);
     }
     w[rank] = wi;
-    for (int r = 0; r < m; ++r) Z[r + (int64_t)rank * m] = Zw[r + (int64_t)i * m];
+    for (int r = 0; r < m; ++r) Z[r + rank * m] = Zw[r + i * m];
   }
   if (tid == 0 && info) *info = done ? sweeps : -1;
 }
@@ -366,46 +540,77 @@ void make_A0(int m, const double* Hp, const double* HD, double* A0,
   TRM_CHECK_LAUNCH();
 }
 
-template <typename Tm>
-void line_step(int m, const double* A0, const double* Bm, const double* Q,
-               const double* HPP, const double* W, const double* T1,
-               const double* T2, double* S, IterScalars* sc, cudaStream_t s) {
-  k_line_step<Tm><<<1, 1024, 0, s>>>(m, A0, Bm, Q, HPP, W, T1, T2, S, sc);
-  TRM_CHECK_LAUNCH();
+
+// elements of the padded working copy plus the inverse's temporary
+size_t chol_work_elems(int m) {
+  const size_t mp = (size_t)((m + 31) & ~31);
+  return mp * (mp + 1) + 33 * mp;
 }
 
 template <typename Tm, bool dev>
-static void chol_launch(int m, const double* S, double* Linv, double* R,
+static void chol_launch(int m, const double* S, const double* Bm,
+                        const double* Q, double* Linv, double* R,
                         IterScalars* sc, double* gwork, cudaStream_t s) {
   if (m > 1024) throw Error(-1, "chol_inv: m > 1024");
-  const size_t bytes = (size_t)m * (m + 1) * sizeof(Tm);
+  const size_t bytes = chol_work_elems(m) * sizeof(Tm);
   const bool smem = bytes <= 200 * 1024;
   if (smem) {
-    TRM_CUDA(cudaFuncSetAttribute(k_chol_inv<Tm, dev>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)bytes));
+    static int done[64] = {};
+    int dv = 0;
+    cudaGetDevice(&dv);
+    if (dv < 0 || dv >= 64 || !done[dv]) {
+      TRM_CUDA(cudaFuncSetAttribute(k_chol_inv<Tm, dev>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
+      if (dv >= 0 && dv < 64) done[dv] = 1;
+    }
   }
-  k_chol_inv<Tm, dev><<<1, 1024, smem ? bytes : 0, s>>>(
-      m, S, Linv, R, sc, reinterpret_cast<Tm*>(gwork), smem ? 1 : 0);
+  k_chol_inv<Tm, dev><<<1, 512, smem ? bytes : 0, s>>>(
+      m, S, Bm, Q, Linv, R, sc, reinterpret_cast<Tm*>(gwork), smem ? 1 : 0);
   TRM_CHECK_LAUNCH();
 }
 
 template <typename Tm>
 void chol_inv(int m, const double* S, double* Linv, double* R, IterScalars* sc,
               double* gwork, cudaStream_t s) {
-  chol_launch<Tm, false>(m, S, Linv, R, sc, gwork, s);
+  chol_launch<Tm, false>(m, S, nullptr, nullptr, Linv, R, sc, gwork, s);
 }
 
 template <typename Tm>
 void chol_inv_dev(int m, const double* S, double* Linv, double* R,
                   IterScalars* sc, double* gwork, cudaStream_t s) {
-  chol_launch<Tm, true>(m, S, Linv, R, sc, gwork, s);
+  chol_launch<Tm, true>(m, S, nullptr, nullptr, Linv, R, sc, gwork, s);
+}
+
+template <typename Tm>
+void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
+                 const double* Q, const double* HPP, const double* W,
+                 double* Linv, double* R, IterScalars* sc, double* gwork,
+                 double* part, bool dev, cudaStream_t s) {
+  const int t = ceil_div(m, 32);
+  k_line_terms<Tm><<<dim3(t, t), 1024, 0, s>>>(m, Hp, HD, Bm, Q, HPP, W, part);
+  TRM_CHECK_LAUNCH();
+  k_line_alpha<<<1, 256, 0, s>>>(m, part, t * t, sc);
+  TRM_CHECK_LAUNCH();
+  if (dev)
+    chol_launch<Tm, true>(m, nullptr, Bm, Q, Linv, R, sc, gwork, s);
+  else
+    chol_launch<Tm, false>(m, nullptr, Bm, Q, Linv, R, sc, gwork, s);
 }
 
 template void chol_inv_dev<float>(int, const double*, double*, double*,
                                   IterScalars*, double*, cudaStream_t);
 template void chol_inv_dev<double>(int, const double*, double*, double*,
                                    IterScalars*, double*, cudaStream_t);
+template void line_factor<float>(int, const double*, const double*,
+                                 const double*, const double*, const double*,
+                                 const double*, double*, double*, IterScalars*,
+                                 double*, double*, bool, cudaStream_t);
+template void line_factor<double>(int, const double*, const double*,
+                                  const double*, const double*, const double*,
+                                  const double*, double*, double*,
+                                  IterScalars*, double*, double*, bool,
+                                  cudaStream_t);
 
 void sym_eig(int m, const double* A, double* w, double* Z, double* work,
              int* info, cudaStream_t s) {
@@ -414,18 +619,17 @@ void sym_eig(int m, const double* A, double* w, double* Z, double* work,
   double* Zw = work + (size_t)m * m;
   TRM_CUDA(cudaMemcpyAsync(Aw, A, sizeof(double) * m * m,
                            cudaMemcpyDeviceToDevice, s));
-  k_jacobi<<<1, 1024, 0, s>>>(m, Aw, Zw, w, Z, info, 40);
+  const size_t bytes = (size_t)m * (m + 1) * sizeof(double);
+  const bool smem = bytes <= 200 * 1024;
+  if (smem)
+    TRM_CUDA(cudaFuncSetAttribute(k_jacobi,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+  k_jacobi<<<1, 1024, smem ? bytes : 0, s>>>(m, Aw, Zw, w, Z, info, 40,
+                                             smem ? 1 : 0);
   TRM_CHECK_LAUNCH();
 }
 
-template void line_step<float>(int, const double*, const double*,
-                               const double*, const double*, const double*,
-                               const double*, const double*, double*,
-                               IterScalars*, cudaStream_t);
-template void line_step<double>(int, const double*, const double*,
-                                const double*, const double*, const double*,
-                                const double*, const double*, double*,
-                                IterScalars*, cudaStream_t);
 template void chol_inv<float>(int, const double*, double*, double*,
                               IterScalars*, double*, cudaStream_t);
 template void chol_inv<double>(int, const double*, double*, double*,

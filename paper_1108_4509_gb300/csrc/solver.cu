@@ -168,7 +168,7 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   Linv_ = d(mm);
   R_ = d(mm);
   Z_ = d(mm);
-  mmw_ = d(2 * mm);
+  mmw_ = d(std::max(2 * mm, chol_work_elems(m)));
   eigw_ = d(m);
   lam_ = d(m);
   res_ = d(m);
@@ -372,16 +372,8 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
            gram<T>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status));        // P^T[P HP G]
   const double m3 = md * md * md;
   prof.begin(KC_SMALL, s_);
-  make_A0(m_, Hp_, HD_, A0_, s_);
-  const bool f32 = sizeof(Tm) == 4;
-  mm_gemm(m_, A0_, false, Bm_, false, T1_, 1.0, 0.0, s_, f32);
-  mm_gemm(m_, Bm_, false, A0_, false, T2_, 1.0, 0.0, s_, f32);
-  line_step<Tm>(m_, A0_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, T1_, T2_, S_, sc_,
-                s_);
-  if (f32)
-    chol_inv_dev<Tm>(m_, S_, Linv_, R_, sc_, mmw_, s_);     // Fig. ONFIG
-  else
-    chol_inv<Tm>(m_, S_, Linv_, R_, sc_, mmw_, s_);
+  line_factor<Tm>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, Linv_, R_,
+                  sc_, mmw_, T1_, sizeof(Tm) == 4, s_);     // alpha, Fig. ONFIG
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(krt, m2N, 3 * es * nm,
            (rotate<T, T>(N_, m_, C, P, R_, Cn, sc_, s_)));    // (C+aP)L^-T
@@ -439,12 +431,8 @@ void Solver::iter_mp2() {
   TRM_PROF(KC_GRAM32, 6 * m2N, 16 * nm,
            gram<float>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status));
   prof.begin(KC_SMALL, s_);
-  make_A0(m_, Hp_, HD_, A0_, s_);
-  mm_gemm(m_, A0_, false, Bm_, false, T1_, 1.0, 0.0, s_, true);
-  mm_gemm(m_, Bm_, false, A0_, false, T2_, 1.0, 0.0, s_, true);
-  line_step<float>(m_, A0_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, T1_, T2_, S_,
-                   sc_, s_);
-  chol_inv_dev<float>(m_, S_, Linv_, R_, sc_, mmw_, s_);
+  line_factor<float>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, Linv_, R_,
+                     sc_, mmw_, T1_, true, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(KC_ROT32, m2N, 20 * nm,
            rotate_split(N_, m_, C64_, P, R_, C64n_, sc_, s_));
