@@ -55,6 +55,10 @@ def parse():
                     help="also time one solve of the all-FP64 path")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="budget of the oracle CPU sample")
+    ap.add_argument("--clocks", type=int, default=1,
+                    help="sample nvidia-smi clocks during the timed region "
+                         "(0 under a profiler, which should see no other "
+                         "GPU client)")
     return ap.parse_args()
 
 
@@ -316,7 +320,8 @@ def main():
     torch.cuda.synchronize()
     trm.trm_profile(h, True)
     sampler = ClockSampler(torch.cuda.current_device())
-    sampler.start()
+    if args.clocks:
+        sampler.start()
     launches0 = trm.trm_launch_count()
     times, errs, iters, statuses = [], [], [], []
     if dist:

@@ -465,10 +465,26 @@ void xprime(int64_t N, int m, const T* C, T* X, const double* HD, float* C32,
   TRM_CHECK_LAUNCH();
 }
 
+static bool aligned16(const void* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
 template <typename T>
 void gradient(int64_t N, int m, const T* C, const T* Xp, const double* Hp,
               T* G, const T* Gprev, const T* Pprev, const T* minv,
-              IterScalars* sc, double* partials, size_t cap, cudaStream_t s) {
+              IterScalars* sc, double* partials, size_t cap, cudaStream_t s,
+              const TcWork* tw) {
+  if constexpr (sizeof(T) == 4) {
+    if (mul_tc_eligible(N, m, m, tw) && aligned16(C)) {
+      if ((size_t)mul_tc_parts(N, m) * 4 > cap)
+        throw Error(-2, "gradient: partials buffer too small");
+      const int nparts = mul_tc_grad(N, m, C, Hp, Xp, G, Gprev, Pprev, minv,
+                                     partials, *tw, s);
+      k_cg_scalars<<<1, 1024, 0, s>>>(partials, nparts, m, sc);
+      TRM_CHECK_LAUNCH();
+      return;
+    }
+  }
   dim3 grid(ceil_div(N, GT), ceil_div(m, GT));
   const size_t nparts = (size_t)grid.x * grid.y;
   if (nparts * 4 > cap) throw Error(-2, "gradient: partials buffer too small");
@@ -488,7 +504,14 @@ void update_p(int64_t N, int m, const T* G, T* P, const T* minv,
 
 template <typename T, typename TP>
 void rotate(int64_t N, int m, const T* C, const TP* P, const double* R, T* Cn,
-            const IterScalars* sc, cudaStream_t s) {
+            const IterScalars* sc, cudaStream_t s, const TcWork* tw) {
+  if constexpr (sizeof(T) == 4 && sizeof(TP) == 4) {
+    if (mul_tc_eligible(N, m, m, tw) && aligned16(C) &&
+        (P == nullptr || (sc && aligned16(P)))) {
+      mul_tc_store(N, m, m, C, P, sc, R, Cn, *tw, s);
+      return;
+    }
+  }
   dim3 grid(ceil_div(N, GT), ceil_div(m, GT));
   k_rotate<T, TP><<<grid, 256, 0, s>>>(N, m, C, P, R, Cn, sc);
   TRM_CHECK_LAUNCH();
@@ -496,7 +519,11 @@ void rotate(int64_t N, int m, const T* C, const TP* P, const double* R, T* Cn,
 
 void rotate_split(int64_t N, int m, const double* C, const float* P,
                   const double* R, double* Cn, const IterScalars* sc,
-                  cudaStream_t s) {
+                  cudaStream_t s, const float* C32, const TcWork* tw) {
+  if (C32 && mul_tc_eligible(N, m, m, tw) && aligned16(C32) && aligned16(P)) {
+    mul_tc_split64(N, m, C32, P, C, sc, R, Cn, *tw, s);
+    return;
+  }
   dim3 grid(ceil_div(N, GT), ceil_div(m, GT));
   k_rotate_split<<<grid, 256, 0, s>>>(N, m, C, P, R, Cn, sc);
   TRM_CHECK_LAUNCH();
@@ -555,7 +582,7 @@ void random_block(int64_t N, int m, uint64_t seed, double* C, cudaStream_t s) {
                           float*, cudaStream_t);                             \
   template void gradient<T>(int64_t, int, const T*, const T*, const double*, \
                             T*, const T*, const T*, const T*, IterScalars*,  \
-                            double*, size_t, cudaStream_t);                  \
+                            double*, size_t, cudaStream_t, const TcWork*);   \
   template void update_p<T>(int64_t, int, const T*, T*, const T*,            \
                             const IterScalars*, cudaStream_t);
 TRM_INST(float)
@@ -563,9 +590,10 @@ TRM_INST(double)
 #undef TRM_INST
 template void rotate<float, float>(int64_t, int, const float*, const float*,
                                    const double*, float*, const IterScalars*,
-                                   cudaStream_t);
+                                   cudaStream_t, const TcWork*);
 template void rotate<double, double>(int64_t, int, const double*,
                                      const double*, const double*, double*,
-                                     const IterScalars*, cudaStream_t);
+                                     const IterScalars*, cudaStream_t,
+                                     const TcWork*);
 
 }  // namespace trm

@@ -1,0 +1,493 @@
+// Products of a tall FP32 block with a small matrix, Y M (Y: N x k, M: k x n),
+// on the 5th-generation tensor cores: the O(N m^2) products of the gradient
+// G = -2 (X' - C H') (Fig. EGFIG step (7)) and of the update
+// (C + alpha P) L^{-T} (Fig. TMFIG with the orthonormalisation of Fig. ONFIG).
+//
+// Precision: as in the Gram kernel, each FP32 value of Y is split in shared
+// memory into two TF32 terms (hi = rna_tf32(y), lo = rna_tf32(y - hi)), M is
+// split the same way from FP64 by k_split_small, and hi.hi + hi.lo + lo.hi is
+// accumulated in FP32 in tensor memory (FP32-class accuracy, ~2^-22 relative
+// per term).
+//
+// Layout: Y is column-major (rows contiguous), so a TMA box of 32 rows x 32
+// columns with the 128-byte swizzle holds 32 lines of 32 rows each (the
+// contraction index k is the strided one). The TF32 MMA reads both operands
+// K-major, so the converter warps transpose while they split: they read Y
+// (and P) from the staging ring and write hi and lo as 128 rows of 128 bytes
+// (32 k values), the layout of the Gram kernel's operands. M (hi and lo, k
+// contiguous) is loaded K-major by TMA directly.
+//
+// Rings: staging (TMA -> converters; raw Y and P tiles), operand (converters
+// and TMA -> MMA; hi, lo and the M tiles), accumulator (MMA -> epilogue; two
+// 128-column TMEM buffers, so the epilogue of one tile overlaps the next).
+// Persistent CTAs (one per SM) walk (128-row, 128-column) tiles. Warp roles
+// (512 threads): warp 0 TMA for Y/P, warp 1 TMEM allocation and MMA issue
+// (one thread), warp 2 TMA for M, warps 4-11 form Y = C (+ alpha P), split
+// and transpose, warps 12-15 read the accumulator and run the fused
+// epilogue. Every wait is bounded (bit 2 of *err).
+#include "ops.cuh"
+#include "tc.cuh"
+
+namespace trm {
+
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128;  // rows per tile (MMA M)
+constexpr int NC = 128;  // output columns per tile (MMA N)
+constexpr int BK = 32;   // columns of Y per stage
+constexpr int RS = 3;    // staging stages
+constexpr int CS = 2;    // operand stages
+constexpr int THREADS = 512;
+constexpr int CONV0 = 4, NCONV = 8, EPI0 = 12;
+
+enum Mode { kStore = 0, kGrad = 1, kSplit64 = 2 };
+
+struct MulSmem {
+  float raw[RS][BM * BK];   // Y tile as loaded (32 lines of 32 rows each)
+  float rawp[RS][BM * BK];  // P tile as loaded
+  float ah[CS][BM * BK];    // Y hi, K-major (128 rows of 32 k values)
+  float al[CS][BM * BK];    // Y lo
+  float bh[CS][NC * BK];    // M hi, K-major
+  float bl[CS][NC * BK];    // M lo
+  uint64_t raw_full[RS], raw_empty[RS];
+  uint64_t conv_done[CS], b_full[CS], op_empty[CS];
+  uint64_t accfull[2], accempty[2], mmadone;
+  uint32_t tmem_base;
+  int failed;
+  double red[4][4];
+};
+
+struct MulArgs {
+  int64_t N;
+  int k, n;        // Y: N x k, M: k x n
+  int ntr, nch;    // row tiles, column chunks of 128
+  int has_p;       // Y = A + alpha P
+  const IterScalars* sc;
+  float* out;      // kStore: Y M; kGrad: G (N x n, ld N)
+  const float* xp; // kGrad
+  const float* gprev;
+  const float* pprev;
+  const float* minv;
+  double* part;    // kGrad: 4 sums per CTA
+  const double* c64;  // kSplit64: Cn = (C64 + alpha P) diag(R) + Y M
+  const float* p32;
+  const double* R;
+  double* out64;
+  int* err;
+};
+
+// Converter thread (row i, half h) reads the 16 values of row i in the
+// column groups q = 2j + h (j = 0..3) of a staged tile: element (i, k) of a
+// staged 32 x 32 box sits in line k at 16-byte chunk ((i % 32) / 4) ^ (k % 8).
+__device__ __forceinline__ float staged(const float* t, int i, int k) {
+  return t[(i >> 5) * 1024 + k * 32 + (((((i & 31) >> 2) ^ (k & 7))) << 2) +
+           (i & 3)];
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_mul_tc(const __grid_constant__ CUtensorMap mapA,
+             const __grid_constant__ CUtensorMap mapP,
+             const __grid_constant__ CUtensorMap mapBh,
+             const __grid_constant__ CUtensorMap mapBl, MulArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  MulSmem* sm = reinterpret_cast<MulSmem*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = args.ntr * args.nch;
+  const int nk = (args.k + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RS; ++s) {
+      mbar_init(&sm->raw_full[s], 1);
+      mbar_init(&sm->raw_empty[s], NCONV * 32);
+    }
+    for (int s = 0; s < CS; ++s) {
+      mbar_init(&sm->conv_done[s], NCONV * 32);
+      mbar_init(&sm->b_full[s], 1);
+      mbar_init(&sm->op_empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm->accfull[b], 1);
+      mbar_init(&sm->accempty[b], 128);
+    }
+    mbar_init(&sm->mmadone, 1);
+    sm->failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(&sm->tmem_base, 2 * NC);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sm->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA: Y (and P) into the staging ring ----------------
+    if (lane == 0) {
+      const uint32_t bytes = (uint32_t)(BM * BK * 4 * (args.has_p ? 2 : 1));
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int r0 = (t % args.ntr) * BM;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % RS;
+          if (it >= RS &&
+              !mbar_wait(&sm->raw_empty[s], ((it / RS) - 1) & 1, args.err,
+                         &sm->failed)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&sm->raw_full[s], bytes);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            tma_load_2d(sm->raw[s] + c * 1024, &mapA, r0 + 32 * c, kb * BK,
+                        &sm->raw_full[s]);
+            if (args.has_p)
+              tma_load_2d(sm->rawp[s] + c * 1024, &mapP, r0 + 32 * c,
+                          kb * BK, &sm->raw_full[s]);
+          }
+        }
+      }
+      // the copies in flight must land before the CTA may exit
+      for (int j = it > RS ? it - RS : 0; j < it; ++j)
+        mbar_wait_own(&sm->raw_full[j % RS], (j / RS) & 1, args.err);
+    }
+  } else if (warp == 2) {
+    // ---------------- TMA: M hi/lo into the operand ring ----------------
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int c0 = (t / args.ntr) * NC;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % CS;
+          if (it >= CS &&
+              !mbar_wait(&sm->op_empty[s], ((it / CS) - 1) & 1, args.err,
+                         &sm->failed)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&sm->b_full[s], 2 * NC * BK * 4);
+          tma_load_2d(sm->bh[s], &mapBh, kb * BK, c0, &sm->b_full[s]);
+          tma_load_2d(sm->bl[s], &mapBl, kb * BK, c0, &sm->b_full[s]);
+        }
+      }
+      for (int j = it > CS ? it - CS : 0; j < it; ++j)
+        mbar_wait_own(&sm->b_full[j % CS], (j / CS) & 1, args.err);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(BM, NC, false, false);
+      int it = 0, tl = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+        const int b = tl & 1;
+        if (tl >= 2 && !mbar_wait(&sm->accempty[b], ((tl / 2) - 1) & 1,
+                                  args.err, &sm->failed)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * NC);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % CS;
+          const uint32_t par = (it / CS) & 1;
+          if (!mbar_wait(&sm->conv_done[s], par, args.err, &sm->failed) ||
+              !mbar_wait(&sm->b_full[s], par, args.err, &sm->failed)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t aH = smem_u32(sm->ah[s]), aL = smem_u32(sm->al[s]);
+          const uint32_t bH = smem_u32(sm->bh[s]), bL = smem_u32(sm->bl[s]);
+          const uint32_t pa[3] = {aH, aH, aL};
+          const uint32_t pb[3] = {bH, bL, bH};
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk)  // K = 8 per MMA (32 bytes)
+              mma_tf32(d, smem_desc(pa[p] + kk * 32, 16, 1024),
+                       smem_desc(pb[p] + kk * 32, 16, 1024), idesc,
+                       (kb > 0 || p > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&sm->op_empty[s]);
+        }
+        if (ok) mma_commit(&sm->accfull[b]);
+      }
+      // every MMA of this thread completes before the TMEM is released
+      mma_commit(&sm->mmadone);
+      mbar_wait_own(&sm->mmadone, 0, args.err);
+    }
+  } else if (warp >= CONV0 && warp < EPI0) {
+    // ------------- form Y, split it and write it K-major -------------
+    const int t = threadIdx.x - CONV0 * 32;  // 0..255
+    const int i = t >> 1, h = t & 1;         // row of the tile, half
+    const bool axpy = args.has_p != 0;
+    const float alpha = (axpy && args.sc) ? (float)args.sc->alpha : 0.f;
+    int it = 0;
+    bool ok = true;
+    for (int tt = blockIdx.x; tt < ntiles && ok; tt += gridDim.x) {
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int rs = it % RS, cs = it % CS;
+        if (!mbar_wait(&sm->raw_full[rs], (it / RS) & 1, args.err,
+                       &sm->failed)) {
+          ok = false;
+          break;
+        }
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = 4 * (2 * j + h) + e;
+            float y = staged(sm->raw[rs], i, k);
+            if (axpy) y = fmaf(alpha, staged(sm->rawp[rs], i, k), y);
+            v[4 * j + e] = y;
+          }
+        // The staged tile is overwritten next by TMA (async proxy): order
+        // these generic-proxy reads before that write.
+        fence_proxy_async();
+        mbar_arrive(&sm->raw_empty[rs]);
+        if (it >= CS && !mbar_wait(&sm->op_empty[cs], ((it / CS) - 1) & 1,
+                                   args.err, &sm->failed)) {
+          ok = false;
+          break;
+        }
+        float4* hi = reinterpret_cast<float4*>(sm->ah[cs] + i * 32);
+        float4* lo = reinterpret_cast<float4*>(sm->al[cs] + i * 32);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int q = (2 * j + h) ^ (i & 7);  // 128-byte swizzle
+          float4 a, o;
+          a.x = tf32_rna(v[4 * j + 0]); o.x = tf32_rna(v[4 * j + 0] - a.x);
+          a.y = tf32_rna(v[4 * j + 1]); o.y = tf32_rna(v[4 * j + 1] - a.y);
+          a.z = tf32_rna(v[4 * j + 2]); o.z = tf32_rna(v[4 * j + 2] - a.z);
+          a.w = tf32_rna(v[4 * j + 3]); o.w = tf32_rna(v[4 * j + 3] - a.w);
+          hi[q] = a;
+          lo[q] = o;
+        }
+        fence_proxy_async();
+        mbar_arrive(&sm->conv_done[cs]);
+      }
+    }
+  } else if (warp >= EPI0) {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;  // TMEM lane quarter
+    const int rr = 32 * q + lane;
+    const int64_t N = args.N;
+    double s_gg = 0, s_gmg = 0, s_pmg = 0, s_gpp = 0;
+    double alpha64 = 0.0;
+    if (MODE == kSplit64 && args.sc) alpha64 = args.sc->alpha;
+    int tl = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+      const int b = tl & 1;
+      // warp-uniform outcome: the TMEM loads below are .sync.aligned
+      const bool got =
+          mbar_wait(&sm->accfull[b], (tl / 2) & 1, args.err, &sm->failed);
+      if (!__all_sync(0xffffffffu, got)) break;
+      fence_after();
+      const int64_t row = (int64_t)(t % args.ntr) * BM + rr;
+      const int c0 = (t / args.ntr) * NC;
+      const bool rin = row < N;
+      float mi = 1.f;
+      if (MODE == kGrad && rin && args.minv) mi = args.minv[row];
+#pragma unroll 1
+      for (int cb = 0; cb < NC; cb += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * NC + cb), r);
+        if (!rin) continue;
+        if (MODE == kStore) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int col = c0 + cb + e;
+            if (col < args.n)
+              args.out[row + (int64_t)col * N] = __uint_as_float(r[e]);
+          }
+        } else if (MODE == kGrad) {
+          // the 16 columns' operands are staged in registers first, so the
+          // loads are all in flight before the stores
+          float xv[16], gv[16], pv[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int col = c0 + cb + e;
+            const int64_t idx = row + (int64_t)col * N;
+            const bool in = col < args.n;
+            xv[e] = in ? args.xp[idx] : 0.f;
+            gv[e] = (in && args.gprev) ? args.gprev[idx] : 0.f;
+            pv[e] = (in && args.pprev) ? args.pprev[idx] : 0.f;
+          }
+          float gg = 0.f, gmg = 0.f, pmg = 0.f, gpp = 0.f;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int col = c0 + cb + e;
+            if (col < args.n) {
+              const float g = -2.f * (xv[e] - __uint_as_float(r[e]));
+              args.out[row + (int64_t)col * N] = g;
+              const float mg = mi * g;
+              gg = fmaf(g, g, gg);
+              gmg = fmaf(g, mg, gmg);
+              pmg = fmaf(gv[e], mg, pmg);
+              gpp = fmaf(g, pv[e], gpp);
+            }
+          }
+          s_gg += gg;
+          s_gmg += gmg;
+          s_pmg += pmg;
+          s_gpp += gpp;
+        } else {
+#pragma unroll
+          for (int h = 0; h < 16; h += 8) {
+            double cv[8];
+            float pv[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int col = c0 + cb + h + e;
+              const int64_t idx = row + (int64_t)col * N;
+              const bool in = col < args.n;
+              cv[e] = in ? args.c64[idx] : 0.0;
+              pv[e] = in ? args.p32[idx] : 0.f;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int col = c0 + cb + h + e;
+              if (col < args.n) {
+                const double y = fma(alpha64, (double)pv[e], cv[e]);
+                args.out64[row + (int64_t)col * N] =
+                    fma(y, args.R[col + (int64_t)col * args.k],
+                        (double)__uint_as_float(r[h + e]));
+              }
+            }
+          }
+        }
+      }
+      fence_before();
+      mbar_arrive(&sm->accempty[b]);
+    }
+    if (MODE == kGrad) {
+      double v[4] = {s_gg, s_gmg, s_pmg, s_gpp};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = warp_sum(v[j]);
+      if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sm->red[warp - EPI0][j] = v[j];
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (threadIdx.x == EPI0 * 32) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          args.part[(size_t)blockIdx.x * 4 + j] =
+              ((sm->red[0][j] + sm->red[1][j]) + sm->red[2][j]) + sm->red[3][j];
+      }
+    }
+  }
+  __syncwarp();
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    fence_after();
+    tmem_dealloc(tmem, 2 * NC);
+  }
+}
+
+// hi + lo = M (FP64 k x n, ld k) to ~2^-22 relative, as TF32 values stored in
+// FP32 with leading dimension ldm; zero_diag leaves the diagonal out.
+__global__ void k_split_small(int k, int n, int ldm, const double* __restrict__ M,
+                              float* __restrict__ hi, float* __restrict__ lo,
+                              int zero_diag) {
+  const int total = ldm * n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += gridDim.x * blockDim.x) {
+    const int i = e % ldm, j = e / ldm;
+    double x = 0.0;
+    if (i < k && !(zero_diag && i == j)) x = M[i + (size_t)j * k];
+    const float h = tf32_rna((float)x);
+    hi[e] = h;
+    lo[e] = tf32_rna((float)(x - (double)h));
+  }
+}
+
+int ldm_of(int k) { return (k + 3) & ~3; }
+
+template <int MODE>
+void launch(const MulArgs& a0, const float* A, const float* P,
+            const double* M, int zero_diag, float* ws, cudaStream_t s,
+            int* grid_out) {
+  MulArgs a = a0;
+  const int ldm = ldm_of(a.k);
+  float* hi = ws;
+  float* lo = ws + (size_t)ldm * a.n;
+  k_split_small<<<ceil_div((int64_t)ldm * a.n, 256), 256, 0, s>>>(
+      a.k, a.n, ldm, M, hi, lo, zero_diag);
+  TRM_CHECK_LAUNCH();
+  CUtensorMap mA = f32_map(A, a.N, a.k, a.N, 32, BK);
+  CUtensorMap mP = f32_map(P ? P : A, a.N, a.k, a.N, 32, BK);
+  CUtensorMap mBh = f32_map(hi, a.k, a.n, ldm, BK, NC);
+  CUtensorMap mBl = f32_map(lo, a.k, a.n, ldm, BK, NC);
+  a.ntr = (int)ceil_div(a.N, (int64_t)BM);
+  a.nch = ceil_div(a.n, NC);
+  a.has_p = P ? 1 : 0;
+  const int tiles = a.ntr * a.nch;
+  const int grid = tiles < sm_count() ? tiles : sm_count();
+  const size_t smem = sizeof(MulSmem) + 1024;
+  static int attr_dev = -1;
+  int dev = 0;
+  TRM_CUDA(cudaGetDevice(&dev));
+  if (attr_dev != dev) {
+    TRM_CUDA(cudaFuncSetAttribute(k_mul_tc<MODE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    attr_dev = dev;
+  }
+  k_mul_tc<MODE><<<grid, THREADS, smem, s>>>(mA, mP, mBh, mBl, a);
+  TRM_CHECK_LAUNCH();
+  if (grid_out) *grid_out = grid;
+}
+
+}  // namespace
+
+bool mul_tc_eligible(int64_t N, int k, int n, const TcWork* tw) {
+  if (!tw || !tw->msplit || !tw->err) return false;
+  if (N % 4 != 0 || N < BM || k < 32 || n < 32) return false;
+  if (tw->msplit_floats < mul_tc_work_floats(k, n)) return false;
+  return encode_fn() != nullptr;
+}
+
+size_t mul_tc_work_floats(int k, int n) { return 2 * (size_t)ldm_of(k) * n; }
+
+int mul_tc_parts(int64_t N, int n) {
+  const int64_t tiles = (int64_t)ceil_div(N, (int64_t)BM) * ceil_div(n, NC);
+  return (int)(tiles < sm_count() ? tiles : sm_count());
+}
+
+void mul_tc_store(int64_t N, int k, int n, const float* A, const float* P,
+                  const IterScalars* sc, const double* M, float* out,
+                  const TcWork& tw, cudaStream_t s) {
+  MulArgs a{};
+  a.N = N; a.k = k; a.n = n; a.sc = sc; a.out = out; a.err = tw.err;
+  launch<kStore>(a, A, P, M, 0, tw.msplit, s, nullptr);
+}
+
+int mul_tc_grad(int64_t N, int m, const float* C, const double* Hp,
+                const float* Xp, float* G, const float* Gprev,
+                const float* Pprev, const float* minv, double* part,
+                const TcWork& tw, cudaStream_t s) {
+  MulArgs a{};
+  a.N = N; a.k = m; a.n = m; a.out = G; a.xp = Xp; a.gprev = Gprev;
+  a.pprev = Pprev; a.minv = minv; a.part = part; a.err = tw.err;
+  int grid = 0;
+  launch<kGrad>(a, C, nullptr, Hp, 0, tw.msplit, s, &grid);
+  return grid;
+}
+
+void mul_tc_split64(int64_t N, int m, const float* C32, const float* P,
+                    const double* C64, const IterScalars* sc, const double* R,
+                    double* Cn, const TcWork& tw, cudaStream_t s) {
+  MulArgs a{};
+  a.N = N; a.k = m; a.n = m; a.sc = sc; a.c64 = C64; a.p32 = P; a.R = R;
+  a.out64 = Cn; a.err = tw.err;
+  launch<kSplit64>(a, C32, P, R, 1, tw.msplit, s, nullptr);
+}
+
+}  // namespace trm

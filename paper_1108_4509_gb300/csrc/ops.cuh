@@ -68,8 +68,8 @@ void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
           int* err = nullptr);
 void sum_splits(const double* part, int splits, size_t count, double* out,
                 cudaStream_t s);
-// tcgen05 Gram of FP32 blocks (three-term BF16 split, FP32 accumulation in
-// tensor memory): needs N % 4 == 0, m >= 64, at most 3 B segments whose
+// tcgen05 Gram of FP32 blocks (two-term TF32 split, three products, FP32
+// accumulation in tensor memory): needs N % 4 == 0, m >= 64, at most 3 B segments whose
 // widths are multiples of 128 when there are several.
 bool gram_tc_eligible(int64_t N, int m, const Blocks<float>& B);
 void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
@@ -94,13 +94,43 @@ void energy_diag(int64_t N, int m, const T* C, const T* X, double* HD,
 template <typename T>
 void xprime(int64_t N, int m, const T* C, T* X, const double* HD,
             float* C32, float* Xp32, cudaStream_t s);
+// Workspace of the tensor-core block products Y M: the TF32 split of the
+// small matrix M (mul_tc_work_floats floats) and the device error word of the
+// bounded waits. A null TcWork (or member) selects the SIMT kernels.
+struct TcWork {
+  float* msplit = nullptr;
+  size_t msplit_floats = 0;
+  int* err = nullptr;
+};
+size_t mul_tc_work_floats(int k, int n);
+// Y: N x k FP32 block, M: k x n; N % 4 == 0, N >= 128, k, n >= 32, 16-byte
+// aligned blocks (checked by the callers).
+bool mul_tc_eligible(int64_t N, int k, int n, const TcWork* tw);
+// number of partial-sum records mul_tc_grad writes
+int mul_tc_parts(int64_t N, int n);
+// out = (A + alpha P) M (P may be null; alpha = sc->alpha)
+void mul_tc_store(int64_t N, int k, int n, const float* A, const float* P,
+                  const IterScalars* sc, const double* M, float* out,
+                  const TcWork& tw, cudaStream_t s);
+// G = -2 (X' - C H') with the four Polak-Ribiere partial sums per CTA in
+// part; returns the number of records
+int mul_tc_grad(int64_t N, int m, const float* C, const double* Hp,
+                const float* Xp, float* G, const float* Gprev,
+                const float* Pprev, const float* minv, double* part,
+                const TcWork& tw, cudaStream_t s);
+// Cn = (C64 + alpha P) diag(R) + (C32 + alpha P) (R - diag(R))
+void mul_tc_split64(int64_t N, int m, const float* C32, const float* P,
+                    const double* C64, const IterScalars* sc, const double* R,
+                    double* Cn, const TcWork& tw, cudaStream_t s);
+
 // G = -2 (X' - C H') with the Polak-Ribiere partial sums; G_prev/P_prev may
 // be null (first iteration). Then the device scalar update of gamma, r.
+// FP32 blocks use the tensor cores when tw allows.
 template <typename T>
 void gradient(int64_t N, int m, const T* C, const T* Xp, const double* Hp,
               T* G, const T* Gprev, const T* Pprev, const T* minv,
               IterScalars* sc, double* partials, size_t partials_cap,
-              cudaStream_t s);
+              cudaStream_t s, const TcWork* tw = nullptr);
 // P = M G + gamma P (gamma from sc)
 template <typename T>
 void update_p(int64_t N, int m, const T* G, T* P, const T* minv,
@@ -109,11 +139,15 @@ void update_p(int64_t N, int m, const T* G, T* P, const T* minv,
 // when P is null)
 template <typename T, typename TP>
 void rotate(int64_t N, int m, const T* C, const TP* P, const double* R,
-            T* Cn, const IterScalars* sc, cudaStream_t s);
-// MP1 (ii): Cn = Y L_D + fl32(Y) L', Y = C + alpha P; R = L^{-T} FP64
+            T* Cn, const IterScalars* sc, cudaStream_t s,
+            const TcWork* tw = nullptr);
+// MP1 (ii): Cn = Y L_D + fl32(Y) L', Y = C + alpha P; R = L^{-T} FP64.
+// With C32 = fl32(C) and tw, fl32(Y) is formed as C32 + alpha P in FP32 and
+// the product runs on the tensor cores.
 void rotate_split(int64_t N, int m, const double* C, const float* P,
                   const double* R, double* Cn, const IterScalars* sc,
-                  cudaStream_t s);
+                  cudaStream_t s, const float* C32 = nullptr,
+                  const TcWork* tw = nullptr);
 // Y = A M for A: N x k (FP64), M: k x n FP64
 void mult(int64_t N, int k, int n, const double* A, const double* M,
           double* Y, cudaStream_t s);

@@ -181,6 +181,9 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   part_ = d(part_cap_);
   sc_ = static_cast<IterScalars*>(mem_.alloc(sizeof(IterScalars)));
   TRM_CUDA(cudaMemsetAsync(sc_, 0, sizeof(IterScalars), s_));
+  tw_.msplit_floats = mul_tc_work_floats(m, m);
+  tw_.msplit = f(tw_.msplit_floats);
+  tw_.err = &sc_->status;
   diag64_ = d(N);
   diag32_ = f(N);
   minv64_ = d(N);
@@ -352,7 +355,7 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   if (sizeof(T) == 4) zero_diag(m_, Hp_, s_);
   TRM_PROF(kgd, 2 * m2N, 5 * es * nm,
            gradient<T>(N_, m_, C, X, Hp_, G, Gp, P, minv, sc_, part_,
-                       part_cap_, s_));                               // (7)
+                       part_cap_, s_, &tw_));                         // (7)
   TRM_PROF(KC_ROWOPS, 2 * nm, 3 * es * nm,
            update_p<T>(N_, m_, G, P, minv, sc_, s_));                 // P
   TRM_PROF(ksp, sfl, sby, apply_h(op_, P, HP, m_, s_));              // H P
@@ -376,7 +379,7 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
                   sc_, mmw_, T1_, sizeof(Tm) == 4, s_);     // alpha, Fig. ONFIG
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(krt, m2N, 3 * es * nm,
-           (rotate<T, T>(N_, m_, C, P, R_, Cn, sc_, s_)));    // (C+aP)L^-T
+           (rotate<T, T>(N_, m_, C, P, R_, Cn, sc_, s_, &tw_)));  // (C+aP)L^-T
   std::swap(C, Cn);
   std::swap(G, Gp);
 }
@@ -412,7 +415,7 @@ void Solver::iter_mp2() {
   zero_diag(m_, Hp_, s_);
   TRM_PROF(KC_GRAD32, 2 * m2N, 20 * nm,
            gradient<float>(N_, m_, C32_, X32_, Hp_, G, Gp, P, minv, sc_,
-                           part_, part_cap_, s_));            // (7)
+                           part_, part_cap_, s_, &tw_));      // (7)
   TRM_PROF(KC_ROWOPS, 2 * nm, 12 * nm,
            update_p<float>(N_, m_, G, P, minv, sc_, s_));
   TRM_PROF(KC_SPMM32, f32, b32, apply_h(op_, P, HP, m_, s_));
@@ -435,7 +438,7 @@ void Solver::iter_mp2() {
                      sc_, mmw_, T1_, true, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(KC_ROT32, m2N, 20 * nm,
-           rotate_split(N_, m_, C64_, P, R_, C64n_, sc_, s_));
+           rotate_split(N_, m_, C64_, P, R_, C64n_, sc_, s_, C32_, &tw_));
   std::swap(C64_, C64n_);
   std::swap(Gb_[0], Gb_[1]);
 }
@@ -465,7 +468,7 @@ void Solver::orth_uniform(T*& C, T*& Cn) {
   gram<T>(N_, m_, C, b, S_, part_, part_cap_, s_, &sc_->status);
   chol_inv<T>(m_, S_, Linv_, R_, sc_, mmw_, s_);
   rotate<T, T>(N_, m_, C, static_cast<const T*>(nullptr), R_, Cn, nullptr,
-               s_);
+               s_, &tw_);
   std::swap(C, Cn);
 }
 
@@ -800,7 +803,7 @@ void Solver::energy_gradient(const double* C, double* E, double* HD,
     gram<float>(N_, m_, C32_, b, Hp_, part_, part_cap_, s_, &sc_->status);
     if (zdiag) zero_diag(m_, Hp_, s_);
     gradient<float>(N_, m_, C32_, X32_, Hp_, static_cast<float*>(G), nullptr,
-                    nullptr, nullptr, sc_, part_, part_cap_, s_);
+                    nullptr, nullptr, sc_, part_, part_cap_, s_, &tw_);
   } else {
     throw Error(-1, "energy_gradient: G_dtype must be TRM_F32 or TRM_F64");
   }
@@ -811,6 +814,7 @@ void Solver::energy_gradient(const double* C, double* E, double* HD,
                              cudaMemcpyDeviceToDevice, s_));
   IterScalars v;
   read_scalars(&v);
+  if (v.status & 2) throw Error(-6, "a bounded device wait gave up");
   if (E) *E = v.E;
 }
 
@@ -865,6 +869,7 @@ void Solver::iterate(int mode, int restart, double* E, double* rms,
   if (E) *E = v.E;
   if (rms) *rms = v.rms;
   if (alpha) *alpha = v.alpha;
+  if (v.status & 2) throw Error(-6, "a bounded device wait gave up");
   if (v.status & 1) throw Error(-3, "overlap matrix not positive definite");
 }
 

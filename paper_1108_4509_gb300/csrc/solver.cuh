@@ -119,6 +119,7 @@ class Solver {
   double* part_;
   size_t part_cap_;
   IterScalars* sc_;
+  TcWork tw_;  // tensor-core product workspace (error word in sc_->status)
   IterScalars* ring_ = nullptr;  // pinned host ring of per-iteration scalars
   std::vector<cudaEvent_t> ev_;
   int state_ = 0;  // 0: C64 current, 1: C32 current

@@ -152,11 +152,13 @@ def test_max_iter_reports_enoconv_with_result(trm):
     assert np.max(np.abs(C.T @ C - np.eye(m))) < 1e-10
 
 
-def test_device_output_and_repeatability(trm):
+@pytest.mark.parametrize("m", [7, 40])
+def test_device_output_and_repeatability(trm, m):
     """C written to a device buffer; two solves from the same seed give the
-    same bytes (fixed reduction orders)."""
+    same bytes (fixed reduction orders; m = 40 runs the tensor-core
+    products)."""
     torch = gu.torch_mod()
-    shape, m = (16, 12, 12), 7
+    shape = (16, 12, 12)
     N = int(np.prod(shape))
     V = ti.gaussian_wells(shape, 5, seed=4)
     opt = trm.trm_default_options(stream=gu.stream(), precision=trm.TRM_MIXED,

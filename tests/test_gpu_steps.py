@@ -204,8 +204,13 @@ def test_orthonormalize_rank_deficient_reports_enotpd(trm):
 # ---------------------------------------------------------------------------
 # a2-a4: Fig. EGFIG Algorithm-2 (FP64, and MP2 with FP32 steps (6), (7))
 # ---------------------------------------------------------------------------
+# (N % 4 == 0, m >= 32 takes the tensor-core product for the FP32 gradient:
+# N = 1848 leaves a 56-row tail tile, m = 40 a partial column block, m = 130
+# the 256-column tile with two K-blocks past 128.)
 @pytest.mark.parametrize("shape,order,m", [((16, 12, 10), 4, 17),
-                                           ((13, 11, 9), 2, 70)])
+                                           ((13, 11, 9), 2, 70),
+                                           ((14, 12, 11), 4, 40),
+                                           ((12, 12, 12), 2, 130)])
 def test_energy_gradient(trm, shape, order, m):
     torch = gu.torch_mod()
     V = ti.gaussian_wells(shape, 3, seed=5)
@@ -272,9 +277,10 @@ def test_rayleigh_ritz(trm):
 # ---------------------------------------------------------------------------
 # a5, a7: one step of Fig. TMFIG (FP64, full SP and MP2)
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [10, 40])
 @pytest.mark.parametrize("mode", ["fp64", "sp", "mp2"])
-def test_iterate_one_step(trm, mode):
-    shape, order, m = (14, 12, 11), 4, 10
+def test_iterate_one_step(trm, mode, m):
+    shape, order = (14, 12, 11), 4
     V = ti.gaussian_wells(shape, 4, seed=6)
     H = op.grid_hamiltonian(shape, order, 1.0, V)
     N = H.shape[0]
@@ -312,5 +318,36 @@ def test_iterate_one_step(trm, mode):
         E1_trace = float(np.trace(C1.T @ op.apply_h(H, C1)))
         assert E2 == pytest.approx(E1_trace, rel=max(tol, 1e-12))
         assert E2 < E0
+    finally:
+        trm.trm_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# Repeatability of the step at the benchmark size (N = 48^3, m = 128): the
+# tensor-core pipelines run one persistent CTA per SM over 864 row tiles, so
+# an ordering bug between their stages shows up here as differing bytes.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["sp", "mp2"])
+def test_iterate_repeatable_full_size(trm, mode):
+    torch = gu.torch_mod()
+    w = ti.workload("grid48_o4_w64_m128", seed=1)
+    N, m = w.N, w.m
+    nx, ny, nz = w.shape
+    opt = trm.trm_default_options(stream=gu.stream(), precond=1)
+    h = trm.trm_create_stencil(nx, ny, nz, w.order, w.h, w.potential(), m,
+                               1e-8, opt)
+    md = {"sp": trm.TRM_FULL_SP, "mp2": trm.TRM_MP2}[mode]
+    try:
+        cd = gu.to_dev(otrm.orthonormalize(ti.random_block(N, m, seed=2)))
+        outs = []
+        for _ in range(3):
+            trm.trm_set_block(h, cd.data_ptr())
+            scal = [trm.trm_iterate(h, md, restart=(k == 0)) for k in range(3)]
+            out = gu.empty(N, m, np.float64)
+            trm.trm_get_block(h, out.data_ptr())
+            outs.append((scal, gu.from_dev(out)))
+        for scal, C in outs[1:]:
+            assert scal == outs[0][0]
+            assert np.array_equal(C, outs[0][1])
     finally:
         trm.trm_destroy(h)
