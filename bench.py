@@ -10,7 +10,7 @@ reference; a step that misses 1e-10 relative error is reported.
 
 Printed JSON keys beyond the base contract: roofline (dominant kernel class,
 timed live with CUDA events around each of its launches in the timed region),
-spmm (the H-application GB/s), fp64_path (the same solve with every operation
+classes (the same for every kernel class), fp64_path (the same solve with every operation
 in FP64), e2e (the solve through the C ABI from host buffers, copies
 included), clocks (nvidia-smi sampled during the timed region), cpu_baseline
 (the FP64 oracle on the host cores, a bounded sample scaled to a solve).
@@ -37,9 +37,15 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Fallback peaks when the measured file is absent (one earlier GB300 run).
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # Peaks derived from unit counts and the 2070 MHz maximum SM clock:
-# FP32 SIMT = 152 SMs x 128 FMA/clk x 2; FP64 = the 1.25 TFLOP/s nominal.
+# FP32 SIMT = 152 SMs x 128 FMA lanes x 2 flops; FP64 = 152 SMs x 2 FMA
+# lanes x 2 flops (1.26 TFLOP/s, the nominal 1.25).
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_TFLOPS = 1.25
+FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Kernel classes whose bound is HBM traffic (algorithmic bytes); the others
+# are bound by FP64 (or FP32 SIMT) arithmetic. The FP32 product classes run
+# on the tensor cores, where the TF32 MMAs take a few percent of the time the
+# operands take to stream, so traffic bounds them.
+HBM_CLASSES = ("spmm_f32", "gram_f32", "grad_f32", "rotate_f32", "rowops")
 METRIC = "time-to-E_G at 1e-10 rel err (mixed precision)"
 
 
@@ -207,43 +213,81 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# DRAM traffic of a kernel class from its committed ncu summary (profiles/),
+# per launch; None when there is none or the kernel source has changed since
+# the capture (the summary records the source file and its sha256 prefix).
+# ---------------------------------------------------------------------------
+PROFILE_OF_CLASS = {
+    "spmm_f64": "k_stencil_v4_f64_grid48_m128.md",
+    "grad_f32": "k_mul_tc_grad_grid48_m128.md",
+    "gram_f32": "k_gram_tc_line_grams_grid48_m128.md",
+}
+
+
+def traffic_from_profile(cls):
+    import hashlib
+    import re
+    name = PROFILE_OF_CLASS.get(cls)
+    if not name:
+        return None
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+    except OSError:
+        return None
+    m = re.search(r"Kernel source at capture: `([^`]+)` sha256 ([0-9a-f]+)", text)
+    if not m:
+        return None
+    try:
+        src = open(os.path.join(ROOT, m.group(1)), "rb").read()
+    except OSError:
+        return None
+    if not hashlib.sha256(src).hexdigest().startswith(m.group(2)):
+        return None
+    total = 0.0
+    for metric in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        mm = re.search(r"`%s` \| ([0-9.]+) (\w+)" % re.escape(metric), text)
+        if not mm:
+            return None
+        scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}[mm.group(2)]
+        total += float(mm.group(1)) * scale
+    return {"bytes_per_launch": total, "source": "profiles/" + name}
+
+
+# ---------------------------------------------------------------------------
 # roofline of the dominant kernel class
 # ---------------------------------------------------------------------------
 def roofline(prof, peaks, src):
     classes = {k: v for k, v in prof.items() if v["launches"] > 0 and v["ms"] > 0}
     if not classes:
         return None, None
-    name = max(classes, key=lambda k: classes[k]["ms"])
-    c = classes[name]
-    per_launch_s = c["ms"] / 1e3 / c["launches"]
 
     def entry(cname, cc):
         pl = cc["ms"] / 1e3 / cc["launches"]
-        if cname.startswith("spmm"):
+        if cname in HBM_CLASSES and cc["bytes"] > 0:
             ach = cc["bytes"] / cc["launches"] / pl / 1e9
-            return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
-                    "peak_source": src}
-        ach = cc["flops"] / cc["launches"] / pl / 1e12
-        if cname.endswith("f64") or cname in ("small_mm", "eig"):
-            pk, ps = FP64_TFLOPS, "nominal FP64 (1.25 TFLOP/s)"
+            e = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                 "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                 "peak_source": src + " (copy bandwidth)"}
         else:
-            pk, ps = FP32_SIMT_TFLOPS, "derived FP32 SIMT (152 SMs x 128 FMA x 2070 MHz)"
-        return {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk, "peak_source": ps}
+            ach = cc["flops"] / cc["launches"] / pl / 1e12
+            if cname.endswith("f64") or cname in ("small_mm", "eig"):
+                pk, ps = FP64_TFLOPS, "derived FP64 (152 SMs x 2 FMA x 2070 MHz)"
+            else:
+                pk, ps = FP32_SIMT_TFLOPS, "derived FP32 SIMT (152 SMs x 128 FMA x 2070 MHz)"
+            e = {"bound": "alu", "achieved": ach, "peak": pk,
+                 "unit": "TFLOP/s", "frac": ach / pk, "peak_source": ps}
+        e.update({"launches": cc["launches"], "avg_launch_ms": pl * 1e3})
+        return e
 
-    r = entry(name, c)
-    r.update({"kernel": name, "launches": c["launches"],
-              "avg_launch_ms": per_launch_s * 1e3, "traffic": None,
-              "share_of_timed": c["ms"] / sum(v["ms"] for v in classes.values())})
-    sp = None
-    for k in ("spmm_f32", "spmm_f64"):
-        if k in classes:
-            e = entry(k, classes[k])
-            e.update({"kernel": k, "launches": classes[k]["launches"]})
-            sp = sp or {}
-            sp[k] = e
-    return r, sp
+    name = max(classes, key=lambda k: classes[k]["ms"])
+    r = entry(name, classes[name])
+    tr = traffic_from_profile(name)
+    r.update({"kernel": name,
+              "traffic": tr["bytes_per_launch"] if tr else None,
+              "traffic_source": tr["source"] if tr else None,
+              "share_of_timed": classes[name]["ms"] / sum(v["ms"] for v in classes.values())})
+    every = {k: entry(k, v) for k, v in classes.items()}
+    return r, every
 
 
 # ---------------------------------------------------------------------------
@@ -355,7 +399,7 @@ def main():
     peaks_file = load_json(PEAKS)
     peaks = peaks_file if peaks_file else FALLBACK
     src = "measured" if peaks_file else "fallback"
-    roof, spmm = roofline(prof, peaks, src)
+    roof, per_class = roofline(prof, peaks, src)
 
     # all-FP64 path, one solve (not part of the timed region)
     fp64 = None
@@ -414,7 +458,7 @@ def main():
                "iterations": iters, "status": statuses,
                "rel_err_E_G": errs,
                "E_G_ok": all(e is not None and e <= 1e-10 for e in errs),
-               "roofline": roof, "spmm": spmm,
+               "roofline": roof, "classes": per_class,
                "profile_ms_per_solve": {
                    k: round(v["ms"] / args.steps, 3) for k, v in prof.items()
                    if v["launches"]},

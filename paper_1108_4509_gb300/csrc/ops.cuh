@@ -177,7 +177,7 @@ void make_A0(int m, const double* Hp, const double* HD, double* A0,
 // The line step along P and the factor of the new overlap: the line-model
 // terms from H' (diag zeroed), H_D, B = C^T P, Q = P^T P, P^T H P and
 // W = P^T G give alpha (into sc); then S = I + a (B + B^T) + a^2 Q is
-// factorised (in deviation form when dev) into Linv and R = L^{-T}.
+// factorised (in deviation form when dev) into Linv (may be null) and R = L^{-T}.
 // part: >= 4 * ceil(m/32)^2 doubles; gwork: chol_work_elems(m) doubles.
 template <typename Tm>
 void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
@@ -186,7 +186,7 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
                  double* part, bool dev, cudaStream_t s);
 // Elements (of the arithmetic type) of the factorisation workspace gwork.
 size_t chol_work_elems(int m);
-// S = L L^T (lower); writes Linv = L^{-1} and R = L^{-T}. Non-PD sets
+// S = L L^T (lower); writes Linv = L^{-1} (unless null) and R = L^{-T}. Non-PD sets
 // sc->status bit 1 and returns identities. gwork: chol_work_elems(m)
 // doubles (used when the working copy does not fit in shared memory).
 template <typename Tm>

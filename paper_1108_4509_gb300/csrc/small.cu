@@ -71,16 +71,18 @@ __global__ void k_make_A0(int m, const double* __restrict__ Hp,
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
-// Cholesky S = L L^T and L^{-1}, blocked in 32-column panels, one CTA of 1024
-// threads. Writes Linv (lower) and R = L^{-T} (upper).
+// Cholesky S = L L^T and L^{-1}, blocked in 32-column panels, one CTA (512
+// threads in FP32, 256 in FP64). Writes Linv (lower) and R = L^{-T} (upper).
 //
 // m is padded to mp, a multiple of 32, with the identity, which changes
 // neither factor. Per panel p: (a) one warp factors the diagonal block
-// column by column; (b) every row below solves x L_pp^T = a (registers);
+// column by column, rows in registers, pivots by shuffles; (b) every row
+// below solves x L_pp^T = a (registers, reciprocal pivots from (a));
 // (c) all threads update the lower trailing triangle with 4 x 4 register
-// tiles. The inverse: (d) warp p inverts diagonal block p; (e) row-block by
-// row-block, X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj through a 32 x mp
-// temporary. The working copy has leading dimension mp + 1.
+// tiles. The inverse: (d) warp p inverts diagonal block p in registers;
+// (e) row-block by row-block, X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj through
+// a 32 x mp temporary. The working copy has leading dimension mp + 1. Linv
+// may be null (only R is written then).
 //
 // S is read from memory, or (Bm != null) formed on the fly as
 // S = I + a (B + B^T) + a^2 Q with a = sc->alpha (the line step's overlap).
@@ -92,14 +94,46 @@ __global__ void k_make_A0(int m, const double* __restrict__ Hp,
 // diagonal y_cc = -f_cc / (1 + f_cc). When S - I is small, FP32 arithmetic
 // here yields L to FP64 accuracy relative to I.
 // ---------------------------------------------------------------------------
+// Square root and reciprocal of the pivot chain by Newton's method from the
+// hardware approximations (rsqrt, reciprocal): one step in FP32, two from
+// the FP32 seed in FP64. Arguments are positive normal numbers (the pivot
+// tests come first); the results are within a few ulp, and the chain stays
+// free of the slow-path calls of the IEEE operations.
+__device__ __forceinline__ float piv_sqrt(float t) {
+  const float r = rsqrtf(t);
+  const float s = t * r;
+  return fmaf(0.5f * r, fmaf(-s, s, t), s);
+}
+__device__ __forceinline__ float piv_rcp(float t) {
+  const float r = __fdividef(1.0f, t);
+  return fmaf(r, fmaf(-t, r, 1.0f), r);
+}
+__device__ __forceinline__ double piv_rcp(double t) {
+  double r = (double)__fdividef(1.0f, (float)t);
+  r = fma(r, fma(-t, r, 1.0), r);
+  return fma(r, fma(-t, r, 1.0), r);
+}
+__device__ __forceinline__ double piv_sqrt(double t) {
+  double r = (double)rsqrtf((float)t);
+  r = r * fma(-0.5 * t * r, r, 1.5);
+  r = r * fma(-0.5 * t * r, r, 1.5);
+  const double s = t * r;
+  return fma(0.5 * r, fma(-s, s, t), s);
+}
+
+// FP32: 512 threads; FP64 (twice the registers per row): 256.
+template <typename Tm>
+constexpr int chol_threads() { return sizeof(Tm) == 4 ? 512 : 256; }
+
 template <typename Tm, bool dev>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(chol_threads<Tm>())
     k_chol_inv(int m, const double* __restrict__ S, const double* __restrict__ Bm,
                const double* __restrict__ Q, double* __restrict__ Linv,
                double* __restrict__ R, IterScalars* sc, Tm* gwork,
                int use_smem) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
+  __shared__ Tm rdiag[32];  // 1 / L_cc of the current panel
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int mp = (m + 31) & ~31, ld = mp + 1, P = mp >> 5;
@@ -107,22 +141,32 @@ __global__ void __launch_bounds__(512)
   Tm* tb = a + (size_t)mp * ld;  // 32 x mp, leading dimension 33
   const Tm one = dev ? (Tm)1 : (Tm)0;
   const Tm eps = sizeof(Tm) == 4 ? (Tm)1.2e-7 : (Tm)2.3e-16;
-  const double al = Bm ? sc->alpha : 0.0;
-  for (int k = warp; k < mp; k += nw)
-    for (int i = k + lane; i < mp; i += 32) {
-      double v;
-      if (i < m && k < m) {
-        if (Bm)
-          v = al * (Bm[i + k * m] + Bm[k + i * m]) +
-              al * al * 0.5 * (Q[i + k * m] + Q[k + i * m]) +
-              (!dev && i == k ? 1.0 : 0.0);
-        else
+  if (Bm) {
+    // half of a (B + B^T) + a^2/2 (Q + Q^T) from each triangle, read in
+    // column order, then the lower triangle adds its mirror
+    const double al = sc->alpha;
+    for (int k = warp; k < mp; k += nw)
+      for (int i = lane; i < mp; i += 32)
+        a[i + k * ld] =
+            (i < m && k < m)
+                ? (Tm)(al * Bm[i + k * m] + 0.5 * al * al * Q[i + k * m])
+                : (Tm)0;
+    __syncthreads();
+    for (int k = warp; k < mp; k += nw)
+      for (int i = k + lane; i < mp; i += 32)
+        a[i + k * ld] = a[i + k * ld] + a[k + i * ld] +
+                        ((!dev && i == k) ? (Tm)1 : (Tm)0);
+  } else {
+    for (int k = warp; k < mp; k += nw)
+      for (int i = k + lane; i < mp; i += 32) {
+        double v;
+        if (i < m && k < m)
           v = S[i + k * m] - (dev && i == k ? 1.0 : 0.0);
-      } else {
-        v = (!dev && i == k) ? 1.0 : 0.0;
+        else
+          v = (!dev && i == k) ? 1.0 : 0.0;
+        a[i + k * ld] = (Tm)v;
       }
-      a[i + k * ld] = (Tm)v;
-    }
+  }
   if (tid == 0) bad = 0;
   __syncthreads();
 
@@ -138,32 +182,38 @@ __global__ void __launch_bounds__(512)
       bool b = false;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        const int cc = c0 + c;
         Tm d = __shfl_sync(0xffffffffu, v[c], c);
-        Tm piv;
+        Tm piv, rl;  // L_cc - one and 1 / L_cc
         if (dev) {
           if (!(d > (Tm)-0.999)) {  // pivot 1 + d not positive: singular S
             b = true;
             d = (Tm)0;
           }
-          piv = d / ((Tm)1 + sqrt((Tm)1 + d));
+          piv = d * piv_rcp((Tm)1 + piv_sqrt((Tm)1 + d));
+          rl = piv_rcp((Tm)1 + piv);
         } else {
           // a pivot that has lost all but 4m roundings of its original
           // diagonal entry marks a (numerically) singular S
+          const int cc = c0 + c;
           const double sjj = (Bm || cc >= m) ? 1.0 : fabs(S[cc + cc * m]);
           if (!(d > (Tm)(4 * m) * eps * (Tm)sjj)) {
             b = true;
             d = (Tm)1;
           }
-          piv = sqrt(d);
+          piv = piv_sqrt(d);
+          rl = piv_rcp(piv);
         }
-        const Tm inv = (Tm)1 / (one + piv);
         if (lane == c) v[c] = piv;
-        if (lane > c) v[c] *= inv;
+        if (lane > c) v[c] *= rl;
+        if (lane == 0) rdiag[c] = rl;
+        // constant trip count (k > c folds away once c is unrolled), so the
+        // row stays in registers
 #pragma unroll
-        for (int k = c + 1; k < 32; ++k) {
-          const Tm lkc = __shfl_sync(0xffffffffu, v[c], k);
-          if (lane >= k) v[k] -= v[c] * lkc;
+        for (int k = 1; k < 32; ++k) {
+          if (k > c) {
+            const Tm lkc = __shfl_sync(0xffffffffu, v[c], k);
+            if (lane >= k) v[k] -= v[c] * lkc;
+          }
         }
       }
 #pragma unroll
@@ -178,10 +228,13 @@ __global__ void __launch_bounds__(512)
       for (int c = 0; c < 32; ++c) x[c] = a[r + (c0 + c) * ld];
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        Tm sum = x[c];
+        Tm s0 = x[c], s1 = 0;
 #pragma unroll
-        for (int k = 0; k < c; ++k) sum -= x[k] * a[(c0 + c) + (c0 + k) * ld];
-        x[c] = sum / (one + a[(c0 + c) + (c0 + c) * ld]);
+        for (int k = 0; k < 31; k += 2) {
+          if (k < c) s0 -= x[k] * a[(c0 + c) + (c0 + k) * ld];
+          if (k + 1 < c) s1 -= x[k + 1] * a[(c0 + c) + (c0 + k + 1) * ld];
+        }
+        x[c] = (s0 + s1) * rdiag[c];
       }
 #pragma unroll
       for (int c = 0; c < 32; ++c) a[r + (c0 + c) * ld] = x[c];
@@ -220,59 +273,120 @@ __global__ void __launch_bounds__(512)
     __syncthreads();
   }
 
-  // (d) inverse of each diagonal block, one warp per block
+  // (d) inverse of each diagonal block, one warp per block, rows in
+  // registers: for c descending, lane r > c forms
+  // X_rc = -(1/L_cc) sum_{k=c+1..r} X_rk L_kc, where X_rk (k > c) is already
+  // in its register and L_kc is still in lane k's register c.
   for (int pb = warp; pb < P; pb += nw) {
     const int c0 = 32 * pb;
     const int r = c0 + lane;
+    Tm v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = k <= lane ? a[r + (c0 + k) * ld] : (Tm)0;
+#pragma unroll
     for (int c = 31; c >= 0; --c) {
-      const int cc = c0 + c;
-      const Tm f = a[cc + cc * ld];
-      const Tm yd = dev ? -f / ((Tm)1 + f) : (Tm)1 / f;
-      const Tm scale = dev ? -((Tm)1 + yd) : -yd;
-      const Tm xr = lane > c ? a[r + cc * ld] : (Tm)0;
-      Tm sum = 0;
-      for (int k = c + 1; k < 32; ++k) {
-        const Tm xk = __shfl_sync(0xffffffffu, xr, k);
-        if (k <= lane) sum += a[r + (c0 + k) * ld] * xk;
+      const Tm lcc = __shfl_sync(0xffffffffu, v[c], c);
+      const Tm rc = piv_rcp(one + lcc);
+      Tm s0 = 0, s1 = 0;
+#pragma unroll
+      for (int k = 1; k < 32; ++k) {
+        if (k > c) {
+          const Tm lkc = __shfl_sync(0xffffffffu, v[c], k);
+          if (lane >= k) {
+            if ((k - c) & 1) s0 += v[k] * lkc;
+            else s1 += v[k] * lkc;
+          }
+        }
       }
-      __syncwarp();
-      if (lane == c) a[cc + cc * ld] = yd;
-      if (lane > c) a[r + cc * ld] = scale * ((dev ? xr : (Tm)0) + sum);
-      __syncwarp();
+      if (lane == c) v[c] = dev ? -lcc * rc : rc;
+      else if (lane > c) v[c] = -rc * ((dev ? v[c] : (Tm)0) + s0 + s1);
     }
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if (k <= lane) a[r + (c0 + k) * ld] = v[k];
   }
   __syncthreads();
-  // (e) off-diagonal blocks, row-block by row-block
+  // (e) off-diagonal blocks, row-block by row-block: T = L_{i,0:i} X_{0:i,0:i}
+  // (32 x ri, through tb), then X_{i,0:i} = -X_ii T; 4 x 4 register tiles.
+  // Only the lower triangle of the working copy is read.
   for (int i = 1; i < P; ++i) {
     const int ri = 32 * i;
-    const int cnt = 32 * ri;
-    for (int e = tid; e < cnt; e += nt) {  // T = sum_k L_ik X_kj
-      const int r = e & 31, c = e >> 5;
-      Tm sum = dev ? a[(ri + r) + c * ld] : (Tm)0;  // identity part of X_jj
-      for (int col = c; col < ri; ++col) sum += a[(ri + r) + col * ld] * a[col + c * ld];
-      tb[r + c * 33] = sum;
+    const int nblk = 2 * ri;  // 8 row groups x ri/4 column groups
+    for (int bq = tid; bq < nblk; bq += nt) {
+      const int r0 = 4 * (bq & 7), cb = 4 * (bq >> 3);
+      Tm acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)  // identity part of X (deviation form)
+          acc[u][v] = dev ? a[(ri + r0 + u) + (cb + v) * ld] : (Tm)0;
+      for (int col = cb; col < ri; ++col) {
+        Tm lr[4], xc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) lr[u] = a[(ri + r0 + u) + col * ld];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          xc[v] = col >= cb + v ? a[col + (cb + v) * ld] : (Tm)0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] += lr[u] * xc[v];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tb[(r0 + u) + (cb + v) * 33] = acc[u][v];
     }
     __syncthreads();
-    for (int e = tid; e < cnt; e += nt) {  // X_ij = -X_ii T
-      const int r = e & 31, c = e >> 5;
-      Tm sum = dev ? tb[r + c * 33] : (Tm)0;
-      for (int q = 0; q <= r; ++q) sum += a[(ri + r) + (ri + q) * ld] * tb[q + c * 33];
-      a[(ri + r) + c * ld] = -sum;
+    for (int bq = tid; bq < nblk; bq += nt) {
+      const int r0 = 4 * (bq & 7), cb = 4 * (bq >> 3);
+      Tm acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          acc[u][v] = dev ? tb[(r0 + u) + (cb + v) * 33] : (Tm)0;
+      for (int q = 0; q <= r0 + 3; ++q) {
+        Tm xr[4], tv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          xr[u] = q <= r0 + u ? a[(ri + r0 + u) + (ri + q) * ld] : (Tm)0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tv[v] = tb[q + (cb + v) * 33];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] += xr[u] * tv[v];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) a[(ri + r0 + u) + (cb + v) * ld] = -acc[u][v];
     }
     __syncthreads();
   }
   const int isbad = bad;
-  for (int k = warp; k < m; k += nw) {
-    for (int i = lane; i < m; i += 32) {
+  // Linv(i, k) column by column, then R(k, i) = Linv(i, k) column by column
+  if (Linv)
+    for (int k = warp; k < m; k += nw)
+      for (int i = lane; i < m; i += 32) {
+        double v;
+        if (isbad)
+          v = (i == k) ? 1.0 : 0.0;
+        else
+          v = (dev && i == k ? 1.0 : 0.0) +
+              (i >= k ? (double)a[i + k * ld] : 0.0);
+        Linv[i + k * m] = v;
+      }
+  for (int i = warp; i < m; i += nw)
+    for (int k = lane; k < m; k += 32) {
       double v;
       if (isbad)
         v = (i == k) ? 1.0 : 0.0;
       else
         v = (dev && i == k ? 1.0 : 0.0) + (i >= k ? (double)a[i + k * ld] : 0.0);
-      Linv[i + k * m] = v;  // Linv(i, k)
-      R[k + i * m] = v;     // R(k, i) = Linv(i, k)
+      R[k + i * m] = v;
     }
-  }
   if (tid == 0 && isbad && sc) sc->status |= 1;
 }
 
@@ -565,7 +679,7 @@ static void chol_launch(int m, const double* S, const double* Bm,
       if (dv >= 0 && dv < 64) done[dv] = 1;
     }
   }
-  k_chol_inv<Tm, dev><<<1, 512, smem ? bytes : 0, s>>>(
+  k_chol_inv<Tm, dev><<<1, chol_threads<Tm>(), smem ? bytes : 0, s>>>(
       m, S, Bm, Q, Linv, R, sc, reinterpret_cast<Tm*>(gwork), smem ? 1 : 0);
   TRM_CHECK_LAUNCH();
 }

@@ -375,7 +375,7 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
            gram<T>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status));        // P^T[P HP G]
   const double m3 = md * md * md;
   prof.begin(KC_SMALL, s_);
-  line_factor<Tm>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, Linv_, R_,
+  line_factor<Tm>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, nullptr, R_,
                   sc_, mmw_, T1_, sizeof(Tm) == 4, s_);     // alpha, Fig. ONFIG
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(krt, m2N, 3 * es * nm,
@@ -434,7 +434,7 @@ void Solver::iter_mp2() {
   TRM_PROF(KC_GRAM32, 6 * m2N, 16 * nm,
            gram<float>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status));
   prof.begin(KC_SMALL, s_);
-  line_factor<float>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, Linv_, R_,
+  line_factor<float>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, nullptr, R_,
                      sc_, mmw_, T1_, true, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(KC_ROT32, m2N, 20 * nm,
@@ -564,6 +564,11 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
   // reorth_every iterations), and rotate to the Ritz basis whenever it has
   // dropped 1000-fold (or after rr_every iterations), as Sec. 3 suggests.
   double r_orth = INFINITY, r_rr = INFINITY;
+  // Full SP re-orthonormalizes (FP32) every sp_reorth iterations: its overlap
+  // update drifts by about one FP32 rounding per step, and without the reset
+  // that drift, times |lambda|, becomes the floor of the SP residual.
+  const int sp_reorth = 20;
+  int since_sp = 0;
   double E_last = NAN;
   // A phase has stalled when its best residual has not dropped by 30 % for
   // this many iterations (slow but steady CG on a small gap still passes).
@@ -660,6 +665,10 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
       E_min_at = i;
     }
     if (phase == PH_SP) {
+      if (++since_sp >= sp_reorth) {
+        orth_uniform<float>(C32_, C32n_);
+        since_sp = 0;
+      }
       const bool small = v.rms <= opt_.switch_tol[0] * r0;
       const bool stalled = i - best_at > stall_window ||
                            (prec != TRM_FULL_SP && i - E_min_at > sp_floor_window);

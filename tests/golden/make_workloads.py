@@ -4,13 +4,16 @@ gap assumption of Sec. 2.1), with the reference E_G = sum of the m lowest
 eigenvalues and the gap, all from the oracle (Lanczos on the oracle's own
 Kronecker-sum H, dense for N <= 3000).
 
+With --lambdas it stores the m lowest eigenvalues themselves (for the
+per-eigenvalue parity checks) for the recorded seeds.
+
 With --oracle-iterations it also runs the oracle's trace minimization
 (diagonal preconditioner, random C0 of seed 1) on each accepted workload and
 records the first iteration at which the RMS residual is <= 1e-8 and
 <= 1e-10, and the oracle's own E_G.
 
 Run from the repository root:
-    python tests/golden/make_workloads.py [--oracle-iterations] [names]
+    python tests/golden/make_workloads.py [--lambdas] [--oracle-iterations] [names]
 """
 import json
 import os
@@ -39,11 +42,19 @@ def scan(name, max_seed=20):
         rec = {"seed": seed, "N": w.N, "m": w.m, "gap": gap,
                "E_G": float(np.sum(lam[:w.m])),
                "lambda_m": float(lam[w.m - 1]), "lambda_m1": float(lam[w.m]),
-               "lambda_1": float(lam[0]), "seconds": round(time.time() - t, 1)}
+               "lambda_1": float(lam[0]), "seconds": round(time.time() - t, 1),
+               "lambdas": [float(x) for x in lam[:w.m]]}
         print(name, rec, flush=True)
         if gap >= MIN_GAP:
             return rec
     raise RuntimeError(f"no seed below {max_seed} passes the gap rule for {name}")
+
+
+def lambdas(name, seed):
+    w = ti.workload(name, seed=seed)
+    H = op.grid_hamiltonian(w.shape, w.order, w.h, w.potential())
+    lam = op.lowest_eigenvalues(H, w.m + 4)
+    return {"lambdas": [float(x) for x in lam[:w.m]]}
 
 
 def oracle_iterations(name, seed):
@@ -74,6 +85,7 @@ def save(data):
 
 def main(argv):
     its = "--oracle-iterations" in argv
+    lams = "--lambdas" in argv
     names = [a for a in argv if not a.startswith("--")] or [
         "grid16_o2_w8_m16", "grid48_o4_w64_m128"]
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
@@ -82,6 +94,9 @@ def main(argv):
     for name in names:
         if name not in data:
             data[name] = scan(name)
+            save(data)
+        if lams:
+            data[name].update(lambdas(name, data[name]["seed"]))
             save(data)
         if its:
             data[name].update(oracle_iterations(name, data[name]["seed"]))
