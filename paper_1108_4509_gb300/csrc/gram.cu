@@ -112,21 +112,28 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-__global__ void k_sum_splits(const double* __restrict__ part, int splits,
-                             size_t count, double* __restrict__ out) {
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= count) return;
-  // four running sums over k = 0, 1, 2, 3 (mod 4), added in a fixed order
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int k = 0;
-  for (; k + 4 <= splits; k += 4) {
-    s0 += part[(size_t)k * count + e];
-    s1 += part[(size_t)(k + 1) * count + e];
-    s2 += part[(size_t)(k + 2) * count + e];
-    s3 += part[(size_t)(k + 3) * count + e];
+// out[e] = sum over splits of part[k * count + e]. A CTA owns 32 consecutive
+// outputs; its 8 warps take the splits k = g (mod 8) (coalesced rows of the
+// partials) and the 8 sums are added in a fixed order.
+__global__ void __launch_bounds__(256)
+    k_sum_splits(const double* __restrict__ part, int splits, size_t count,
+                 double* __restrict__ out) {
+  __shared__ double red[8][33];
+  const int el = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const size_t e = (size_t)blockIdx.x * 32 + el;
+  double s = 0.0;
+  if (e < count) {
+#pragma unroll 4
+    for (int k = g; k < splits; k += 8) s += part[(size_t)k * count + e];
   }
-  for (; k < splits; ++k) s0 += part[(size_t)k * count + e];
-  out[e] = (s0 + s1) + (s2 + s3);
+  red[g][el] = s;
+  __syncthreads();
+  if (g == 0 && e < count) {
+    double t = red[0][el];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) t += red[q][el];
+    out[e] = t;
+  }
 }
 
 void plan(int64_t N, int m, int n, int* splits, int64_t* rows) {
@@ -154,7 +161,7 @@ size_t gram_partials_doubles(int64_t N, int m, int n) {
 
 void sum_splits(const double* part, int splits, size_t count, double* out,
                 cudaStream_t s) {
-  k_sum_splits<<<ceil_div(count, 256), 256, 0, s>>>(part, splits, count, out);
+  k_sum_splits<<<ceil_div(count, 32), 256, 0, s>>>(part, splits, count, out);
   TRM_CHECK_LAUNCH();
 }
 
@@ -179,8 +186,8 @@ void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
   k_gram<T><<<grid, 256, 0, s>>>(N, m, A, B, rows, tiles_m, partials);
   TRM_CHECK_LAUNCH();
   const size_t count = (size_t)m * n;
-  k_sum_splits<<<ceil_div(count, 256), 256, 0, s>>>(partials, splits, count,
-                                                    out);
+  k_sum_splits<<<ceil_div(count, 32), 256, 0, s>>>(partials, splits, count,
+                                                   out);
   TRM_CHECK_LAUNCH();
 }
 
@@ -206,8 +213,8 @@ void gram_in_scratch(int64_t N, int m, const T* A, const Blocks<T>& B,
   k_gram<T><<<grid, 256, 0, s>>>(N, m, A, B, rows, tiles_m, scratch);
   TRM_CHECK_LAUNCH();
   const size_t count = (size_t)m * n;
-  k_sum_splits<<<ceil_div(count, 256), 256, 0, s>>>(scratch, splits, count,
-                                                    out);
+  k_sum_splits<<<ceil_div(count, 32), 256, 0, s>>>(scratch, splits, count,
+                                                   out);
   TRM_CHECK_LAUNCH();
 }
 

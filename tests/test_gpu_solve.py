@@ -177,3 +177,30 @@ def test_device_output_and_repeatability(trm, m):
         assert np.array_equal(outs[0][2], outs[1][2])
     finally:
         trm.trm_destroy(h)
+
+
+def test_grid48_full_size_vs_oracle_reference(trm):
+    """The benchmark workload at full size (48^3 grid, 13-point stencil, 64
+    wells, m = 128, diagonal preconditioner), mixed precision to r <= 1e-10,
+    launched as bench.py launches it. Against the oracle's Lanczos values
+    (tests/golden/workloads.json, written by make_workloads.py from oracle/
+    only): E_G to 1e-10 relative and every lambda_j to 1e-9. C^T C = I to
+    1e-12. The largest principal angle to the exact invariant subspace is
+    bounded (Davis-Kahan) by ||H C - C diag(lambda)||_F / (lambda_{m+1} -
+    lambda_m), with the residual formed on the CPU by the oracle's H."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "workloads.json")))["grid48_o4_w64_m128"]
+    w = ti.workload("grid48_o4_w64_m128", seed=g["seed"])
+    V = w.potential()
+    lam, eg, C, st, status = _solve(trm, w.shape, w.order, w.h, V, w.m, 1e-10,
+                                    precision=trm.TRM_MIXED, precond=1,
+                                    seed=w.seed + 100)
+    assert status == 0, st
+    _check(lam, eg, C, np.array(g["lambdas"]))
+    assert np.max(np.abs(C.T @ C - np.eye(w.m))) <= 1e-12
+    H = op.grid_hamiltonian(w.shape, w.order, w.h, V)
+    R = op.apply_h(H, C) - C * lam
+    gap = g["lambda_m1"] - lam[-1]
+    assert np.linalg.norm(R) / gap <= ANGLE_TOL, np.linalg.norm(R) / gap
