@@ -54,7 +54,7 @@ __global__ void k_colsum(const double* __restrict__ part, int chunks, int m,
 template <typename T>
 __global__ void k_xprime(int64_t N, const T* __restrict__ C, T* __restrict__ X,
                          const double* __restrict__ HD, float* C32,
-                         float* Xp32) {
+                         float* Xp32, int write_x) {
   const int j = blockIdx.y;
   const T h = (T)HD[j];
   const int64_t off = (int64_t)j * N;
@@ -62,7 +62,7 @@ __global__ void k_xprime(int64_t N, const T* __restrict__ C, T* __restrict__ X,
        i += (int64_t)gridDim.x * blockDim.x) {
     const T c = C[off + i];
     const T x = X[off + i] - c * h;
-    X[off + i] = x;
+    if (write_x) X[off + i] = x;
     if (C32) C32[off + i] = (float)c;
     if (Xp32) Xp32[off + i] = (float)x;
   }
@@ -458,10 +458,17 @@ void energy_diag(int64_t N, int m, const T* C, const T* X, double* HD,
   TRM_CHECK_LAUNCH();
 }
 
+void energy_from_dots(const double* dots, int chunks, int m, double* HD,
+                      IterScalars* sc, cudaStream_t s) {
+  k_colsum<<<1, 1024, 0, s>>>(dots, chunks, m, HD, sc ? &sc->E : nullptr, 0);
+  TRM_CHECK_LAUNCH();
+}
+
 template <typename T>
 void xprime(int64_t N, int m, const T* C, T* X, const double* HD, float* C32,
-            float* Xp32, cudaStream_t s) {
-  k_xprime<T><<<dim3(elem_grid_x(N), m), 256, 0, s>>>(N, C, X, HD, C32, Xp32);
+            float* Xp32, cudaStream_t s, bool write_x) {
+  k_xprime<T><<<dim3(elem_grid_x(N), m), 256, 0, s>>>(N, C, X, HD, C32, Xp32,
+                                                      write_x ? 1 : 0);
   TRM_CHECK_LAUNCH();
 }
 
@@ -579,7 +586,7 @@ void random_block(int64_t N, int m, uint64_t seed, double* C, cudaStream_t s) {
   template void energy_diag<T>(int64_t, int, const T*, const T*, double*,    \
                                IterScalars*, double*, cudaStream_t);         \
   template void xprime<T>(int64_t, int, const T*, T*, const double*, float*, \
-                          float*, cudaStream_t);                             \
+                          float*, cudaStream_t, bool);                       \
   template void gradient<T>(int64_t, int, const T*, const T*, const double*, \
                             T*, const T*, const T*, const T*, IterScalars*,  \
                             double*, size_t, cudaStream_t, const TcWork*);   \

@@ -37,6 +37,14 @@ void apply_h(const Operator& op, const float* X, float* Y, int ncols,
              cudaStream_t s);
 void apply_h(const Operator& op, const double* X, double* Y, int ncols,
              cudaStream_t s);
+// FP32 Y = H X with the column dot products sum_i X_ic Y_ic of each CTA in
+// dots[chunk * ncols + c] (apply_h_dots_doubles entries); returns the number
+// of chunks (energy_from_dots adds them up). (In FP64 the products would
+// load the FP64 pipe the stencil is already bound by; energy_diag reads the
+// two blocks instead.)
+int apply_h_dots(const Operator& op, const float* X, float* Y, int ncols,
+                 double* dots, cudaStream_t s);
+size_t apply_h_dots_doubles(const Operator& op, int ncols);
 
 // diag[i] = t*w0*ndim + V[i] for a stencil operator
 void stencil_diag(const StencilOp& st, double t_w0_ndim, const double* V,
@@ -90,10 +98,14 @@ void gram_in_scratch(int64_t N, int m, const T* A, const Blocks<T>& B,
 template <typename T>
 void energy_diag(int64_t N, int m, const T* C, const T* X, double* HD,
                  IterScalars* sc, double* partials, cudaStream_t s);
-// X' = X - C diag(H_D), in place on X; optional FP32 copies (MP2 phase)
+// H_D[j] = sum over chunks of dots (from apply_h_dots), E into sc->E
+void energy_from_dots(const double* dots, int chunks, int m, double* HD,
+                      IterScalars* sc, cudaStream_t s);
+// X' = X - C diag(H_D), in place on X unless write_x is false; optional
+// FP32 copies (MP2 phase)
 template <typename T>
 void xprime(int64_t N, int m, const T* C, T* X, const double* HD,
-            float* C32, float* Xp32, cudaStream_t s);
+            float* C32, float* Xp32, cudaStream_t s, bool write_x = true);
 // Workspace of the tensor-core block products Y M: the TF32 split of the
 // small matrix M (mul_tc_work_floats floats) and the device error word of the
 // bounded waits. A null TcWork (or member) selects the SIMT kernels.

@@ -177,7 +177,7 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   part_cap_ = std::max<size_t>(
       {gram_partials_doubles(N, m, 3 * m), gram_partials_doubles(N, m, m),
        (size_t)4 * ceil_div(N, 64) * ceil_div(m, 64), 3 * chunks * m + m,
-       (size_t)4096});
+       (size_t)ceil_div(N, 256) * m, (size_t)4096});
   part_ = d(part_cap_);
   sc_ = static_cast<IterScalars*>(mem_.alloc(sizeof(IterScalars)));
   TRM_CUDA(cudaMemsetAsync(sc_, 0, sizeof(IterScalars), s_));
@@ -341,9 +341,16 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   const int krt = sizeof(T) == 4 ? KC_ROT32 : KC_ROT64;
   double sfl, sby;
   spmm_cost(op_, m_, (int)es, &sfl, &sby);
-  TRM_PROF(ksp, sfl, sby, apply_h(op_, C, X, m_, s_));               // Alg-2 (1)
-  TRM_PROF(KC_ROWOPS, 2 * nm, 2 * es * nm,
-           energy_diag<T>(N_, m_, C, X, HD_, sc_, part_, s_));        // (2), (3)
+  if constexpr (sizeof(T) == 4) {  // (1) with the column dots of (2) fused in
+    int chunks = 0;
+    TRM_PROF(ksp, sfl, sby, chunks = apply_h_dots(op_, C, X, m_, part_, s_));
+    TRM_PROF(KC_ROWOPS, 2.0 * m_ * chunks, 8.0 * m_ * chunks,
+             energy_from_dots(part_, chunks, m_, HD_, sc_, s_));      // (2), (3)
+  } else {
+    TRM_PROF(ksp, sfl, sby, apply_h(op_, C, X, m_, s_));             // (1)
+    TRM_PROF(KC_ROWOPS, 2 * nm, 2 * es * nm,
+             energy_diag<T>(N_, m_, C, X, HD_, sc_, part_, s_));      // (2), (3)
+  }
   TRM_PROF(KC_ROWOPS, 2 * nm, 3 * es * nm,
            xprime<T>(N_, m_, C, X, HD_, nullptr, nullptr, s_));       // (5)
   Blocks<T> bx;
@@ -404,8 +411,9 @@ void Solver::iter_mp2() {
   TRM_PROF(KC_SPMM64, f64, b64, apply_h(op_, C64_, X64_, m_, s_));   // (1) FP64
   TRM_PROF(KC_ROWOPS, 2 * nm, 16 * nm,
            energy_diag<double>(N_, m_, C64_, X64_, HD_, sc_, part_, s_));
-  TRM_PROF(KC_ROWOPS, 2 * nm, 32 * nm,
-           xprime<double>(N_, m_, C64_, X64_, HD_, C32_, X32_, s_));  // (5)
+  // (5): only the FP32 copies of C and X' are used in this step
+  TRM_PROF(KC_ROWOPS, 2 * nm, 24 * nm,
+           xprime<double>(N_, m_, C64_, X64_, HD_, C32_, X32_, s_, false));
   Blocks<float> bx;
   bx.p[0] = X32_;
   bx.cols = m_;
@@ -804,7 +812,7 @@ void Solver::energy_gradient(const double* C, double* E, double* HD,
     gradient<double>(N_, m_, C, X64_, Hp_, static_cast<double*>(G), nullptr,
                      nullptr, nullptr, sc_, part_, part_cap_, s_);
   } else if (G_dtype == TRM_F32) {
-    xprime<double>(N_, m_, C, X64_, HD_, C32_, X32_, s_);
+    xprime<double>(N_, m_, C, X64_, HD_, C32_, X32_, s_, false);
     Blocks<float> b;
     b.p[0] = X32_;
     b.cols = m_;

@@ -49,15 +49,42 @@ __device__ __forceinline__ const double* diag_ptr<double>(const double* d64,
   return d64;
 }
 
+// Columns per CTA (grid.y walks column groups).
+constexpr int kCpb = 4;
+
+// Column dot products sum_i X_ic Y_ic fused into H X (Fig. EGFIG steps
+// (2), (3) read exactly the block pair this kernel holds): every warp adds
+// its lanes' products per column into red[q][warp]; after the column loop
+// the CTA's 8 warp sums are added in a fixed order and written to
+// dots[blockIdx.x * ncols + c].
+template <typename T>
+__device__ __forceinline__ void warp_dot(T d, double (*red)[8], int q) {
+  d = warp_sum(d);
+  if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = (double)d;
+}
+__device__ __forceinline__ void write_dots(double (*red)[8], double* dots,
+                                           int cb, int ncols) {
+  __syncthreads();
+  if (threadIdx.x < kCpb && cb + (int)threadIdx.x < ncols) {
+    double t = red[threadIdx.x][0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) t += red[threadIdx.x][w];
+    dots[(size_t)blockIdx.x * ncols + cb + threadIdx.x] = t;
+  }
+}
+
 // Four x points per thread; requires nx % 4 == 0.
-template <typename T, int R>
+template <typename T, int R, bool DOTS>
 __global__ void __launch_bounds__(256)
     k_stencil_v4(StencilOp st, int64_t N, const double* __restrict__ d64,
                  const float* __restrict__ d32, const T* __restrict__ X,
-                 T* __restrict__ Y, int ncols, int cols_per_block) {
+                 T* __restrict__ Y, int ncols, double* __restrict__ dots) {
   const int64_t nv = N >> 2;
-  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nv) return;
+  const int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = v0 < nv;
+  if (!DOTS && !valid) return;  // with DOTS every thread joins the sums
+  const int64_t v = valid ? v0 : 0;
+  __shared__ double red[kCpb][8];
   const int nxv = st.nx >> 2;
   const int xv = (int)(v % nxv);
   const int64_t yz = v / nxv;
@@ -72,9 +99,14 @@ __global__ void __launch_bounds__(256)
   const bool zm2 = z >= 2, zp2 = z + 2 < st.nz;
   const V4<T> d = ld4(diag_ptr<T>(d64, d32) + i0);
   const T c1 = (T)st.c1, c2 = (T)st.c2;
-  const int cb = blockIdx.y * cols_per_block;
-  const int ce = min(ncols, cb + cols_per_block);
-  for (int c = cb; c < ce; ++c) {
+  const int cb = blockIdx.y * kCpb;
+  for (int q = 0; q < kCpb; ++q) {
+    const int c = cb + q;
+    if (c >= ncols) break;
+    if (DOTS && !valid) {
+      warp_dot((T)0, red, q);
+      continue;
+    }
     const T* x = X + (int64_t)c * N + i0;
     const V4<T> xc = ld4(x);
     V4<T> xlv = {{0, 0, 0, 0}}, xrv = {{0, 0, 0, 0}};
@@ -106,17 +138,25 @@ __global__ void __launch_bounds__(256)
       out.v[k] = acc;
     }
     st4(Y + (int64_t)c * N + i0, out);
+    if (DOTS)
+      warp_dot(xc.v[0] * out.v[0] + xc.v[1] * out.v[1] +
+                   xc.v[2] * out.v[2] + xc.v[3] * out.v[3],
+               red, q);
   }
+  if (DOTS) write_dots(red, dots, cb, ncols);
 }
 
 // One point per thread, any nx.
-template <typename T, int R>
+template <typename T, int R, bool DOTS>
 __global__ void __launch_bounds__(256)
     k_stencil_1(StencilOp st, int64_t N, const double* __restrict__ d64,
                 const float* __restrict__ d32, const T* __restrict__ X,
-                T* __restrict__ Y, int ncols, int cols_per_block) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+                T* __restrict__ Y, int ncols, double* __restrict__ dots) {
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i0 < N;
+  if (!DOTS && !valid) return;
+  const int64_t i = valid ? i0 : 0;
+  __shared__ double red[kCpb][8];
   const int x = (int)(i % st.nx);
   const int64_t yz = i / st.nx;
   const int y = (int)(yz % st.ny);
@@ -124,9 +164,14 @@ __global__ void __launch_bounds__(256)
   const int64_t sy = st.nx, sz = (int64_t)st.nx * st.ny;
   const T d = diag_ptr<T>(d64, d32)[i];
   const T c1 = (T)st.c1, c2 = (T)st.c2;
-  const int cb = blockIdx.y * cols_per_block;
-  const int ce = min(ncols, cb + cols_per_block);
-  for (int c = cb; c < ce; ++c) {
+  const int cb = blockIdx.y * kCpb;
+  for (int q = 0; q < kCpb; ++q) {
+    const int c = cb + q;
+    if (c >= ncols) break;
+    if (DOTS && !valid) {
+      warp_dot((T)0, red, q);
+      continue;
+    }
     const T* xp = X + (int64_t)c * N + i;
     T s1 = 0, s2 = 0;
     if (x >= 1) s1 += xp[-1];
@@ -146,23 +191,27 @@ __global__ void __launch_bounds__(256)
       acc += c2 * s2;
     }
     Y[(int64_t)c * N + i] = acc;
+    if (DOTS) warp_dot(xp[0] * acc, red, q);
   }
+  if (DOTS) write_dots(red, dots, cb, ncols);
 }
 
 constexpr int kCsrCache = 16;
 
-template <typename T, typename TV>
+template <typename T, typename TV, bool DOTS>
 __global__ void __launch_bounds__(256)
     k_csr(int64_t N, const int32_t* __restrict__ rowptr,
           const int32_t* __restrict__ cols, const TV* __restrict__ vals,
           const T* __restrict__ X, T* __restrict__ Y, int ncols,
-          int cols_per_block) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= N) return;
-  const int b = rowptr[r], e = rowptr[r + 1];
+          double* __restrict__ dots) {
+  const int64_t r0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = r0 < N;
+  if (!DOTS && !valid) return;
+  const int64_t r = valid ? r0 : 0;
+  __shared__ double red[kCpb][8];
+  const int b = valid ? rowptr[r] : 0, e = valid ? rowptr[r + 1] : 0;
   const int nnz = e - b;
-  const int cb = blockIdx.y * cols_per_block;
-  const int ce = min(ncols, cb + cols_per_block);
+  const int cb = blockIdx.y * kCpb;
   if (nnz <= kCsrCache) {
     int ci[kCsrCache];
     T cv[kCsrCache];
@@ -171,63 +220,76 @@ __global__ void __launch_bounds__(256)
       ci[k] = k < nnz ? cols[b + k] : 0;
       cv[k] = k < nnz ? (T)vals[b + k] : (T)0;
     }
-    for (int c = cb; c < ce; ++c) {
-      const T* x = X + (int64_t)c * N;
-      T acc = 0;
+    for (int q = 0; q < kCpb; ++q) {
+      const int c = cb + q;
+      if (c >= ncols) break;
+      T d = 0;
+      if (valid) {
+        const T* x = X + (int64_t)c * N;
+        T acc = 0;
 #pragma unroll
-      for (int k = 0; k < kCsrCache; ++k)
-        if (k < nnz) acc += cv[k] * __ldg(x + ci[k]);
-      Y[(int64_t)c * N + r] = acc;
+        for (int k = 0; k < kCsrCache; ++k)
+          if (k < nnz) acc += cv[k] * __ldg(x + ci[k]);
+        Y[(int64_t)c * N + r] = acc;
+        d = x[r] * acc;
+      }
+      if (DOTS) warp_dot(d, red, q);
     }
   } else {
-    for (int c = cb; c < ce; ++c) {
-      const T* x = X + (int64_t)c * N;
-      T acc = 0;
-      for (int k = b; k < e; ++k) acc += (T)vals[k] * __ldg(x + cols[k]);
-      Y[(int64_t)c * N + r] = acc;
+    for (int q = 0; q < kCpb; ++q) {
+      const int c = cb + q;
+      if (c >= ncols) break;
+      T d = 0;
+      if (valid) {
+        const T* x = X + (int64_t)c * N;
+        T acc = 0;
+        for (int k = b; k < e; ++k) acc += (T)vals[k] * __ldg(x + cols[k]);
+        Y[(int64_t)c * N + r] = acc;
+        d = x[r] * acc;
+      }
+      if (DOTS) warp_dot(d, red, q);
     }
   }
+  if (DOTS) write_dots(red, dots, cb, ncols);
 }
 
-template <typename T>
-void apply_impl(const Operator& op, const T* X, T* Y, int ncols,
-                cudaStream_t s) {
-  if (ncols <= 0) return;
+template <typename T, bool DOTS>
+int launch_apply(const Operator& op, const T* X, T* Y, int ncols, double* dots,
+                 cudaStream_t s) {
   const int threads = 256;
-  const int cpb = 4;
-  const int gy = ceil_div(ncols, cpb);
+  const int gy = ceil_div(ncols, kCpb);
   if (gy > 65535) throw Error(-1, "too many columns for one launch");
+  dim3 grid;
   if (op.kind == 0) {
     const StencilOp& st = op.st;
     if (st.nx % 4 == 0) {
-      dim3 grid(ceil_div(op.N / 4, threads), gy);
+      grid = dim3(ceil_div(op.N / 4, threads), gy);
       if (st.radius == 1)
-        k_stencil_v4<T, 1><<<grid, threads, 0, s>>>(st, op.N, op.diag64,
-                                                    op.diag32, X, Y, ncols, cpb);
+        k_stencil_v4<T, 1, DOTS><<<grid, threads, 0, s>>>(
+            st, op.N, op.diag64, op.diag32, X, Y, ncols, dots);
       else
-        k_stencil_v4<T, 2><<<grid, threads, 0, s>>>(st, op.N, op.diag64,
-                                                    op.diag32, X, Y, ncols, cpb);
+        k_stencil_v4<T, 2, DOTS><<<grid, threads, 0, s>>>(
+            st, op.N, op.diag64, op.diag32, X, Y, ncols, dots);
     } else {
-      dim3 grid(ceil_div(op.N, threads), gy);
+      grid = dim3(ceil_div(op.N, threads), gy);
       if (st.radius == 1)
-        k_stencil_1<T, 1><<<grid, threads, 0, s>>>(st, op.N, op.diag64,
-                                                   op.diag32, X, Y, ncols, cpb);
+        k_stencil_1<T, 1, DOTS><<<grid, threads, 0, s>>>(
+            st, op.N, op.diag64, op.diag32, X, Y, ncols, dots);
       else
-        k_stencil_1<T, 2><<<grid, threads, 0, s>>>(st, op.N, op.diag64,
-                                                   op.diag32, X, Y, ncols, cpb);
+        k_stencil_1<T, 2, DOTS><<<grid, threads, 0, s>>>(
+            st, op.N, op.diag64, op.diag32, X, Y, ncols, dots);
     }
   } else {
-    dim3 grid(ceil_div(op.N, threads), gy);
+    grid = dim3(ceil_div(op.N, threads), gy);
     if (op.csr.vals64)
-      k_csr<T, double><<<grid, threads, 0, s>>>(op.N, op.csr.rowptr,
-                                                op.csr.cols, op.csr.vals64, X,
-                                                Y, ncols, cpb);
+      k_csr<T, double, DOTS><<<grid, threads, 0, s>>>(
+          op.N, op.csr.rowptr, op.csr.cols, op.csr.vals64, X, Y, ncols, dots);
     else
-      k_csr<T, float><<<grid, threads, 0, s>>>(op.N, op.csr.rowptr,
-                                               op.csr.cols, op.csr.vals32, X, Y,
-                                               ncols, cpb);
+      k_csr<T, float, DOTS><<<grid, threads, 0, s>>>(
+          op.N, op.csr.rowptr, op.csr.cols, op.csr.vals32, X, Y, ncols, dots);
   }
   TRM_CHECK_LAUNCH();
+  return (int)grid.x;
 }
 
 __global__ void k_stencil_diag(int64_t N, double base,
@@ -293,11 +355,19 @@ __global__ void k_precond(const double* __restrict__ d, int64_t n,
 
 void apply_h(const Operator& op, const float* X, float* Y, int ncols,
              cudaStream_t s) {
-  apply_impl<float>(op, X, Y, ncols, s);
+  if (ncols > 0) launch_apply<float, false>(op, X, Y, ncols, nullptr, s);
 }
 void apply_h(const Operator& op, const double* X, double* Y, int ncols,
              cudaStream_t s) {
-  apply_impl<double>(op, X, Y, ncols, s);
+  if (ncols > 0) launch_apply<double, false>(op, X, Y, ncols, nullptr, s);
+}
+int apply_h_dots(const Operator& op, const float* X, float* Y, int ncols,
+                 double* dots, cudaStream_t s) {
+  return ncols > 0 ? launch_apply<float, true>(op, X, Y, ncols, dots, s) : 0;
+}
+size_t apply_h_dots_doubles(const Operator& op, int ncols) {
+  const int64_t pts = (op.kind == 0 && op.st.nx % 4 == 0) ? op.N / 4 : op.N;
+  return (size_t)ceil_div(pts, 256) * ncols;
 }
 
 void stencil_diag(const StencilOp&, double base, const double* V,
