@@ -22,9 +22,11 @@
 // 128-column TMEM buffers, so the epilogue of one tile overlaps the next).
 // Persistent CTAs (one per SM) walk (128-row, 128-column) tiles. Warp roles
 // (512 threads): warp 0 TMA for Y/P, warp 1 TMEM allocation and MMA issue
-// (one thread), warp 2 TMA for M, warps 4-11 form Y = C (+ alpha P), split
-// and transpose, warps 12-15 read the accumulator and run the fused
-// epilogue. Every wait is bounded (bit 2 of *err).
+// (one thread), warp 2 TMA for M, warps 4-7 form Y = C (+ alpha P), split
+// and transpose (one row per thread), warps 8-15 read the accumulator and run
+// the fused epilogue (two warps per TMEM lane quarter, one column half each:
+// the epilogue streams most of the kernel's bytes with plain loads, so it
+// gets the warps). Every wait is bounded (bit 2 of *err).
 #include "ops.cuh"
 #include "tc.cuh"
 
@@ -40,7 +42,7 @@ constexpr int BK = 32;   // columns of Y per stage
 constexpr int RS = 3;    // staging stages
 constexpr int CS = 2;    // operand stages
 constexpr int THREADS = 512;
-constexpr int CONV0 = 4, NCONV = 8, EPI0 = 12;
+constexpr int CONV0 = 4, NCONV = 4, EPI0 = 8, NEPI = 8;
 
 enum Mode { kStore = 0, kGrad = 1, kSplit64 = 2 };
 
@@ -56,7 +58,7 @@ struct MulSmem {
   uint64_t accfull[2], accempty[2], mmadone;
   uint32_t tmem_base;
   int failed;
-  double red[4][4];
+  double red[NEPI][4];
 };
 
 struct MulArgs {
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm->accfull[b], 1);
-      mbar_init(&sm->accempty[b], 128);
+      mbar_init(&sm->accempty[b], NEPI * 32);
     }
     mbar_init(&sm->mmadone, 1);
     sm->failed = 0;
@@ -222,8 +224,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp >= CONV0 && warp < EPI0) {
     // ------------- form Y, split it and write it K-major -------------
-    const int t = threadIdx.x - CONV0 * 32;  // 0..255
-    const int i = t >> 1, h = t & 1;         // row of the tile, half
+    const int i = threadIdx.x - CONV0 * 32;  // 0..127: row of the tile
     const bool axpy = args.has_p != 0;
     const float alpha = (axpy && args.sc) ? (float)args.sc->alpha : 0.f;
     int it = 0;
@@ -236,16 +237,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           ok = false;
           break;
         }
-        float v[16];
+        float v[32];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int k = 4 * (2 * j + h) + e;
-            float y = staged(sm->raw[rs], i, k);
-            if (axpy) y = fmaf(alpha, staged(sm->rawp[rs], i, k), y);
-            v[4 * j + e] = y;
-          }
+        for (int k = 0; k < 32; ++k) {
+          float y = staged(sm->raw[rs], i, k);
+          if (axpy) y = fmaf(alpha, staged(sm->rawp[rs], i, k), y);
+          v[k] = y;
+        }
         // The staged tile is overwritten next by TMA (async proxy): order
         // these generic-proxy reads before that write.
         fence_proxy_async();
@@ -258,8 +256,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         float4* hi = reinterpret_cast<float4*>(sm->ah[cs] + i * 32);
         float4* lo = reinterpret_cast<float4*>(sm->al[cs] + i * 32);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int q = (2 * j + h) ^ (i & 7);  // 128-byte swizzle
+        for (int j = 0; j < 8; ++j) {
+          const int q = j ^ (i & 7);  // 128-byte swizzle
           float4 a, o;
           a.x = tf32_rna(v[4 * j + 0]); o.x = tf32_rna(v[4 * j + 0] - a.x);
           a.y = tf32_rna(v[4 * j + 1]); o.y = tf32_rna(v[4 * j + 1] - a.y);
@@ -274,7 +272,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp >= EPI0) {
     // ---------------- epilogue ----------------
-    const int q = warp & 3;  // TMEM lane quarter
+    const int q = warp & 3;                  // TMEM lane quarter
+    const int cbeg = ((warp - EPI0) >> 2) * (NC / 2);  // column half
     const int rr = 32 * q + lane;
     const int64_t N = args.N;
     double s_gg = 0, s_gmg = 0, s_pmg = 0, s_gpp = 0;
@@ -294,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       float mi = 1.f;
       if (MODE == kGrad && rin && args.minv) mi = args.minv[row];
 #pragma unroll 1
-      for (int cb = 0; cb < NC; cb += 16) {
+      for (int cb = cbeg; cb < cbeg + NC / 2; cb += 16) {
         uint32_t r[16];
         tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * NC + cb), r);
         if (!rin) continue;
@@ -372,12 +371,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (lane == 0)
 #pragma unroll
         for (int j = 0; j < 4; ++j) sm->red[warp - EPI0][j] = v[j];
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(NEPI * 32) : "memory");
       if (threadIdx.x == EPI0 * 32) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          args.part[(size_t)blockIdx.x * 4 + j] =
-              ((sm->red[0][j] + sm->red[1][j]) + sm->red[2][j]) + sm->red[3][j];
+        for (int j = 0; j < 4; ++j) {
+          double t = sm->red[0][j];
+#pragma unroll
+          for (int w = 1; w < NEPI; ++w) t += sm->red[w][j];
+          args.part[(size_t)blockIdx.x * 4 + j] = t;
+        }
       }
     }
   }
