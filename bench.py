@@ -44,8 +44,10 @@ FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Kernel classes whose bound is HBM traffic (algorithmic bytes); the others
 # are bound by FP64 (or FP32 SIMT) arithmetic. The FP32 product classes run
 # on the tensor cores, where the TF32 MMAs take a few percent of the time the
-# operands take to stream, so traffic bounds them.
-HBM_CLASSES = ("spmm_f32", "gram_f32", "grad_f32", "rotate_f32", "rowops")
+# operands take to stream, so traffic bounds them; spmm_f64 is the MP2 stencil
+# in double-float (FP32 pairs, 8 bytes per element like FP64).
+HBM_CLASSES = ("spmm_f32", "spmm_f64", "gram_f32", "grad_f32", "rotate_f32",
+               "rowops")
 METRIC = "time-to-E_G at 1e-10 rel err (mixed precision)"
 
 
@@ -218,7 +220,6 @@ class ClockSampler:
 # the capture (the summary records the source file and its sha256 prefix).
 # ---------------------------------------------------------------------------
 PROFILE_OF_CLASS = {
-    "spmm_f64": "k_stencil_v4_f64_grid48_m128.md",
     "grad_f32": "k_mul_tc_grad_grid48_m128.md",
     "gram_f32": "k_gram_tc_line_grams_grid48_m128.md",
 }

@@ -3,6 +3,7 @@
 // the direction update of Fig. TMFIG; the rotation C (+ alpha P) L^{-T} of
 // Fig. ONFIG step (4), including the split form C L_D + C L' of Sec. 2.2
 // (MP1 (ii)); column residual norms; the random initial block.
+#include "dfmath.cuh"
 #include "ops.cuh"
 
 namespace trm {
@@ -294,6 +295,52 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same split update with C and Cn as FP32 pairs: the FP32 operand is
+// Ch + alpha P, and Y diag(R) is formed in double-float.
+__global__ void __launch_bounds__(256)
+    k_rotate_split_df(int64_t N, int m, const float* __restrict__ Ch,
+                      const float* __restrict__ Cl,
+                      const float* __restrict__ P, const double* __restrict__ R,
+                      float* __restrict__ Cnh, float* __restrict__ Cnl,
+                      const IterScalars* __restrict__ sc) {
+  __shared__ __align__(16) float As[GK][GLD];
+  __shared__ __align__(16) float Ms[GK][GLD];
+  const int64_t r0 = (int64_t)blockIdx.x * GT;
+  const int c0 = blockIdx.y * GT;
+  const float alpha = (float)sc->alpha;
+  const F2 alpha2 = df_of(sc->alpha);
+  float acc[4][4] = {};
+  auto loadA = [&](int r, int k) -> float {
+    const int64_t row = r0 + r;
+    if (row >= N) return 0.f;
+    const int64_t idx = row + (int64_t)k * N;
+    return fmaf(alpha, P[idx], Ch[idx]);
+  };
+  auto loadM = [&](int k, int c) -> float {
+    const int col = c0 + c;
+    return (col < m && k != col) ? (float)R[k + (int64_t)col * m] : 0.f;
+  };
+  const int kend = min(m, c0 + GT);
+  tile_product<float>(0, kend, loadA, loadM, acc, As, Ms);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int64_t row = r0 + tx * 4 + x;
+    if (row >= N) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int col = c0 + ty * 4 + y;
+      if (col >= m) continue;
+      const int64_t idx = row + (int64_t)col * N;
+      const F2 yv = df_add(F2{Ch[idx], Cl[idx]}, df_mul(alpha2, F2{P[idx], 0.f}));
+      const F2 t = df_add(df_mul(yv, df_of(R[col + (int64_t)col * m])),
+                          F2{acc[x][y], 0.f});
+      Cnh[idx] = t.h;
+      Cnl[idx] = t.l;
+    }
+  }
+}
+
 // Y = A M, A: N x k FP64, M: k x n FP64
 __global__ void __launch_bounds__(256)
     k_mult(int64_t N, int k, int n, const double* __restrict__ A,
@@ -533,6 +580,18 @@ void rotate_split(int64_t N, int m, const double* C, const float* P,
   }
   dim3 grid(ceil_div(N, GT), ceil_div(m, GT));
   k_rotate_split<<<grid, 256, 0, s>>>(N, m, C, P, R, Cn, sc);
+  TRM_CHECK_LAUNCH();
+}
+
+void rotate_split_df(int64_t N, int m, const float* Ch, const float* Cl,
+                     const float* P, const double* R, float* Cnh, float* Cnl,
+                     const IterScalars* sc, cudaStream_t s, const TcWork* tw) {
+  if (mul_tc_eligible(N, m, m, tw) && aligned16(Ch) && aligned16(P)) {
+    mul_tc_splitdf(N, m, Ch, Cl, P, sc, R, Cnh, Cnl, *tw, s);
+    return;
+  }
+  dim3 grid(ceil_div(N, GT), ceil_div(m, GT));
+  k_rotate_split_df<<<grid, 256, 0, s>>>(N, m, Ch, Cl, P, R, Cnh, Cnl, sc);
   TRM_CHECK_LAUNCH();
 }
 

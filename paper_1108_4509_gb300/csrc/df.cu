@@ -1,0 +1,224 @@
+// Double-float ("FP32 pair") arithmetic for the FP64-accuracy steps of the
+// MP2 phase (Sec. 2.2: H C, the energy terms H_D and X' = X - C diag(H_D)).
+//
+// GB300 runs FP64 at 1/64 of its FP32 rate, and the FP64 stencil was bound
+// by that pipe. Here a value is held as hi + lo with hi = fl32(v) and
+// lo = fl32(v - hi) (|lo| <= ulp(hi)/2, about 48 significant bits), and
+// sums and products use the error-free transformations of Knuth (TwoSum)
+// and Dekker/Kahan (TwoProduct with a fused multiply-add), so the results
+// carry a relative error of a few units of 2^-48 of the magnitudes involved
+// — far below what E_G at 1e-10 and residuals at 1e-10 need — while every
+// operation runs on the FP32 pipe. No FP64 instruction is executed per
+// element, except once per thread when an FP64 scalar is split.
+#include "dfmath.cuh"
+#include "ops.cuh"
+
+namespace trm {
+
+namespace {
+
+// Neighbour-sum accumulator: the hi parts are added exactly (TwoSum), the
+// lo parts and the rounding errors plainly; normalised once at the end.
+struct Acc {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(float vh, float vl) {
+    const F2 t = two_sum(h, vh);
+    h = t.h;
+    l += t.l + vl;
+  }
+  __device__ __forceinline__ F2 get() const { return quick_two_sum(h, l); }
+};
+
+__global__ void k_split_df(int64_t n, const double* __restrict__ x,
+                           float* __restrict__ hi, float* __restrict__ lo) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const F2 v = df_of(x[i]);
+    hi[i] = v.h;
+    lo[i] = v.l;
+  }
+}
+
+__global__ void k_join_df(int64_t n, const float* __restrict__ hi,
+                          const float* __restrict__ lo,
+                          double* __restrict__ x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (double)hi[i] + (double)lo[i];
+}
+
+constexpr int kCols = 4;  // columns per CTA (grid.y walks column groups)
+
+// X = H C for the stencil operator, one grid point per thread.
+template <int R>
+__global__ void __launch_bounds__(256)
+    k_stencil_df(StencilOp st, int64_t N, const float* __restrict__ dh,
+                 const float* __restrict__ dl, const float* __restrict__ Ch,
+                 const float* __restrict__ Cl, float* __restrict__ Xh,
+                 float* __restrict__ Xl, int ncols) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int x = (int)(i % st.nx);
+  const int64_t yz = i / st.nx;
+  const int y = (int)(yz % st.ny);
+  const int z = (int)(yz / st.ny);
+  const int64_t sy = st.nx, sz = (int64_t)st.nx * st.ny;
+  const F2 d = {dh[i], dl[i]};
+  const F2 c1 = {st.c1h, st.c1l}, c2 = {st.c2h, st.c2l};
+  // neighbours present at this point (Dirichlet: absent ones are 0)
+  const bool xm1 = x >= 1, xp1 = x + 1 < st.nx, ym1 = y >= 1,
+             yp1 = y + 1 < st.ny, zm1 = z >= 1, zp1 = z + 1 < st.nz;
+  const bool xm2 = x >= 2, xp2 = x + 2 < st.nx, ym2 = y >= 2,
+             yp2 = y + 2 < st.ny, zm2 = z >= 2, zp2 = z + 2 < st.nz;
+  const int cb = blockIdx.y * kCols;
+  for (int q = 0; q < kCols; ++q) {
+    const int c = cb + q;
+    if (c >= ncols) break;
+    const int64_t base = (int64_t)c * N + i;
+    const float* ph = Ch + base;
+    const float* pl = Cl + base;
+    Acc s1, s2;
+    if (xm1) s1.add(__ldg(ph - 1), __ldg(pl - 1));
+    if (xp1) s1.add(__ldg(ph + 1), __ldg(pl + 1));
+    if (ym1) s1.add(__ldg(ph - sy), __ldg(pl - sy));
+    if (yp1) s1.add(__ldg(ph + sy), __ldg(pl + sy));
+    if (zm1) s1.add(__ldg(ph - sz), __ldg(pl - sz));
+    if (zp1) s1.add(__ldg(ph + sz), __ldg(pl + sz));
+    if (R == 2) {
+      if (xm2) s2.add(__ldg(ph - 2), __ldg(pl - 2));
+      if (xp2) s2.add(__ldg(ph + 2), __ldg(pl + 2));
+      if (ym2) s2.add(__ldg(ph - 2 * sy), __ldg(pl - 2 * sy));
+      if (yp2) s2.add(__ldg(ph + 2 * sy), __ldg(pl + 2 * sy));
+      if (zm2) s2.add(__ldg(ph - 2 * sz), __ldg(pl - 2 * sz));
+      if (zp2) s2.add(__ldg(ph + 2 * sz), __ldg(pl + 2 * sz));
+    }
+    F2 r = df_mul(d, F2{__ldg(ph), __ldg(pl)});
+    r = df_add(r, df_mul(c1, s1.get()));
+    if (R == 2) r = df_add(r, df_mul(c2, s2.get()));
+    Xh[base] = r.h;
+    Xl[base] = r.l;
+  }
+}
+
+// X = H C for a CSR operator (values split into hi + lo at creation).
+__global__ void __launch_bounds__(256)
+    k_csr_df(int64_t N, const int32_t* __restrict__ rowptr,
+             const int32_t* __restrict__ cols, const float* __restrict__ vh,
+             const float* __restrict__ vl, const float* __restrict__ Ch,
+             const float* __restrict__ Cl, float* __restrict__ Xh,
+             float* __restrict__ Xl, int ncols) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const int b = rowptr[r], e = rowptr[r + 1];
+  const int cb = blockIdx.y * kCols;
+  for (int q = 0; q < kCols; ++q) {
+    const int c = cb + q;
+    if (c >= ncols) break;
+    const int64_t off = (int64_t)c * N;
+    F2 acc = {0.f, 0.f};
+    for (int k = b; k < e; ++k) {
+      const int64_t j = off + cols[k];
+      acc = df_add(acc, df_mul(F2{vh[k], vl[k]}, F2{__ldg(Ch + j), __ldg(Cl + j)}));
+    }
+    Xh[off + r] = acc.h;
+    Xl[off + r] = acc.l;
+  }
+}
+
+constexpr int kRowChunk = 4096;  // rows per partial of the column dots
+
+// dots[chunk * m + j] = sum_{i in chunk} C_ij X_ij
+__global__ void __launch_bounds__(256)
+    k_coldot_df(int64_t N, int m, const float* __restrict__ Ch,
+                const float* __restrict__ Cl, const float* __restrict__ Xh,
+                const float* __restrict__ Xl, double* __restrict__ dots) {
+  __shared__ double red[32];
+  const int j = blockIdx.y;
+  const int64_t rb = (int64_t)blockIdx.x * kRowChunk;
+  const int64_t re = min(N, rb + kRowChunk);
+  const int64_t off = (int64_t)j * N;
+  F2 acc = {0.f, 0.f};
+  for (int64_t i = rb + threadIdx.x; i < re; i += blockDim.x)
+    acc = df_add(acc, df_mul(F2{Ch[off + i], Cl[off + i]},
+                             F2{Xh[off + i], Xl[off + i]}));
+  double v[1] = {to_double(acc)};
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0) dots[(size_t)blockIdx.x * m + j] = v[0];
+}
+
+// X32 = fl32(X - C diag(H_D))
+__global__ void k_xprime_df(int64_t N, const float* __restrict__ Ch,
+                            const float* __restrict__ Cl,
+                            const float* __restrict__ Xh,
+                            const float* __restrict__ Xl,
+                            const double* __restrict__ HD,
+                            float* __restrict__ X32) {
+  const int j = blockIdx.y;
+  const F2 h = df_of(-HD[j]);
+  const int64_t off = (int64_t)j * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const F2 t = df_mul(F2{Ch[off + i], Cl[off + i]}, h);
+    X32[off + i] = df_add(F2{Xh[off + i], Xl[off + i]}, t).h;
+  }
+}
+
+int grid_1d(int64_t n) {
+  const int64_t g = (n + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 8 * 4096 ? 8 * 4096 : g));
+}
+
+}  // namespace
+
+void split_df(const double* x, float* hi, float* lo, int64_t n,
+              cudaStream_t s) {
+  k_split_df<<<grid_1d(n), 256, 0, s>>>(n, x, hi, lo);
+  TRM_CHECK_LAUNCH();
+}
+
+void join_df(const float* hi, const float* lo, double* x, int64_t n,
+             cudaStream_t s) {
+  k_join_df<<<grid_1d(n), 256, 0, s>>>(n, hi, lo, x);
+  TRM_CHECK_LAUNCH();
+}
+
+void apply_h_df(const Operator& op, const float* Ch, const float* Cl,
+                float* Xh, float* Xl, int ncols, cudaStream_t s) {
+  if (ncols <= 0) return;
+  const int gy = ceil_div(ncols, kCols);
+  if (gy > 65535) throw Error(-1, "too many columns for one launch");
+  dim3 grid(ceil_div(op.N, 256), gy);
+  if (op.kind == 0) {
+    if (op.st.radius == 1)
+      k_stencil_df<1><<<grid, 256, 0, s>>>(op.st, op.N, op.diag32, op.diaglo,
+                                           Ch, Cl, Xh, Xl, ncols);
+    else
+      k_stencil_df<2><<<grid, 256, 0, s>>>(op.st, op.N, op.diag32, op.diaglo,
+                                           Ch, Cl, Xh, Xl, ncols);
+  } else {
+    k_csr_df<<<grid, 256, 0, s>>>(op.N, op.csr.rowptr, op.csr.cols,
+                                  op.csr.valshi, op.csr.valslo, Ch, Cl, Xh,
+                                  Xl, ncols);
+  }
+  TRM_CHECK_LAUNCH();
+}
+
+void energy_diag_df(int64_t N, int m, const float* Ch, const float* Cl,
+                    const float* Xh, const float* Xl, double* HD,
+                    IterScalars* sc, double* partials, cudaStream_t s) {
+  const int chunks = ceil_div(N, kRowChunk);
+  k_coldot_df<<<dim3(chunks, m), 256, 0, s>>>(N, m, Ch, Cl, Xh, Xl, partials);
+  TRM_CHECK_LAUNCH();
+  energy_from_dots(partials, chunks, m, HD, sc, s);
+}
+
+void xprime_df(int64_t N, int m, const float* Ch, const float* Cl,
+               const float* Xh, const float* Xl, const double* HD, float* X32,
+               cudaStream_t s) {
+  int gx = ceil_div(N, 256 * 4);
+  gx = gx < 1 ? 1 : (gx > 4096 ? 4096 : gx);
+  k_xprime_df<<<dim3(gx, m), 256, 0, s>>>(N, Ch, Cl, Xh, Xl, HD, X32);
+  TRM_CHECK_LAUNCH();
+}
+
+}  // namespace trm

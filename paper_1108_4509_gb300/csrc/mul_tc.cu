@@ -27,6 +27,7 @@
 // the fused epilogue (two warps per TMEM lane quarter, one column half each:
 // the epilogue streams most of the kernel's bytes with plain loads, so it
 // gets the warps). Every wait is bounded (bit 2 of *err).
+#include "dfmath.cuh"
 #include "ops.cuh"
 #include "tc.cuh"
 
@@ -44,7 +45,7 @@ constexpr int CS = 2;    // operand stages
 constexpr int THREADS = 512;
 constexpr int CONV0 = 4, NCONV = 4, EPI0 = 8, NEPI = 8;
 
-enum Mode { kStore = 0, kGrad = 1, kSplit64 = 2 };
+enum Mode { kStore = 0, kGrad = 1, kSplit64 = 2, kSplitDf = 3 };
 
 struct MulSmem {
   float raw[RS][BM * BK];   // Y tile as loaded (32 lines of 32 rows each)
@@ -77,6 +78,11 @@ struct MulArgs {
   const float* p32;
   const double* R;
   double* out64;
+  const float* ch;     // kSplitDf: C as FP32 pairs, Cn written as pairs
+  const float* cl;
+  float* outh;
+  float* outl;
+  const float* rdiag;  // kSplitDf: diag(R) as pairs (hi[0..n), lo[n..2n))
   int* err;
 };
 
@@ -279,6 +285,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     double s_gg = 0, s_gmg = 0, s_pmg = 0, s_gpp = 0;
     double alpha64 = 0.0;
     if (MODE == kSplit64 && args.sc) alpha64 = args.sc->alpha;
+    F2 alpha2 = {0.f, 0.f};
+    if (MODE == kSplitDf && args.sc) alpha2 = df_of(args.sc->alpha);
     int tl = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       const int b = tl & 1;
@@ -335,6 +343,34 @@ __global__ void __launch_bounds__(THREADS, 1)
           s_gmg += gmg;
           s_pmg += pmg;
           s_gpp += gpp;
+        } else if (MODE == kSplitDf) {
+#pragma unroll
+          for (int h = 0; h < 16; h += 8) {
+            float hv[8], lv[8], pv[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int col = c0 + cb + h + e;
+              const int64_t idx = row + (int64_t)col * N;
+              const bool in = col < args.n;
+              hv[e] = in ? args.ch[idx] : 0.f;
+              lv[e] = in ? args.cl[idx] : 0.f;
+              pv[e] = in ? args.p32[idx] : 0.f;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int col = c0 + cb + h + e;
+              if (col < args.n) {
+                const F2 y = df_add(F2{hv[e], lv[e]},
+                                    df_mul(alpha2, F2{pv[e], 0.f}));
+                const F2 rd = {args.rdiag[col], args.rdiag[args.n + col]};
+                const F2 t = df_add(df_mul(y, rd),
+                                    F2{__uint_as_float(r[h + e]), 0.f});
+                const int64_t idx = row + (int64_t)col * N;
+                args.outh[idx] = t.h;
+                args.outl[idx] = t.l;
+              }
+            }
+          }
         } else {
 #pragma unroll
           for (int h = 0; h < 16; h += 8) {
@@ -397,7 +433,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 // FP32 with leading dimension ldm; zero_diag leaves the diagonal out.
 __global__ void k_split_small(int k, int n, int ldm, const double* __restrict__ M,
                               float* __restrict__ hi, float* __restrict__ lo,
-                              int zero_diag) {
+                              int zero_diag, float* __restrict__ diag2) {
   const int total = ldm * n;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += gridDim.x * blockDim.x) {
@@ -407,6 +443,11 @@ __global__ void k_split_small(int k, int n, int ldm, const double* __restrict__ 
     const float h = tf32_rna((float)x);
     hi[e] = h;
     lo[e] = tf32_rna((float)(x - (double)h));
+    if (diag2 && i == j && i < k) {  // the left-out diagonal as FP32 pairs
+      const F2 d = df_of(M[i + (size_t)j * k]);
+      diag2[j] = d.h;
+      diag2[n + j] = d.l;
+    }
   }
 }
 
@@ -420,8 +461,10 @@ void launch(const MulArgs& a0, const float* A, const float* P,
   const int ldm = ldm_of(a.k);
   float* hi = ws;
   float* lo = ws + (size_t)ldm * a.n;
+  float* diag2 = MODE == kSplitDf ? lo + (size_t)ldm * a.n : nullptr;
+  if (diag2) a.rdiag = diag2;
   k_split_small<<<ceil_div((int64_t)ldm * a.n, 256), 256, 0, s>>>(
-      a.k, a.n, ldm, M, hi, lo, zero_diag);
+      a.k, a.n, ldm, M, hi, lo, zero_diag, diag2);
   TRM_CHECK_LAUNCH();
   CUtensorMap mA = f32_map(A, a.N, a.k, a.N, 32, BK);
   CUtensorMap mP = f32_map(P ? P : A, a.N, a.k, a.N, 32, BK);
@@ -456,7 +499,9 @@ bool mul_tc_eligible(int64_t N, int k, int n, const TcWork* tw) {
   return encode_fn() != nullptr;
 }
 
-size_t mul_tc_work_floats(int k, int n) { return 2 * (size_t)ldm_of(k) * n; }
+size_t mul_tc_work_floats(int k, int n) {
+  return 2 * (size_t)ldm_of(k) * n + 2 * (size_t)n;
+}
 
 int mul_tc_parts(int64_t N, int n) {
   const int64_t tiles = (int64_t)ceil_div(N, (int64_t)BM) * ceil_div(n, NC);
@@ -481,6 +526,15 @@ int mul_tc_grad(int64_t N, int m, const float* C, const double* Hp,
   int grid = 0;
   launch<kGrad>(a, C, nullptr, Hp, 0, tw.msplit, s, &grid);
   return grid;
+}
+
+void mul_tc_splitdf(int64_t N, int m, const float* Ch, const float* Cl,
+                    const float* P, const IterScalars* sc, const double* R,
+                    float* Cnh, float* Cnl, const TcWork& tw, cudaStream_t s) {
+  MulArgs a{};
+  a.N = N; a.k = m; a.n = m; a.sc = sc; a.ch = Ch; a.cl = Cl; a.p32 = P;
+  a.R = R; a.outh = Cnh; a.outl = Cnl; a.err = tw.err;
+  launch<kSplitDf>(a, Ch, P, R, 1, tw.msplit, s, nullptr);
 }
 
 void mul_tc_split64(int64_t N, int m, const float* C32, const float* P,

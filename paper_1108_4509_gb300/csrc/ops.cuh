@@ -12,6 +12,7 @@ struct StencilOp {
   int nx = 1, ny = 1, nz = 1;
   int radius = 1;            // 1: 3-point rule per axis, 2: 5-point rule
   double c1 = 0.0, c2 = 0.0; // coefficients of the +-1 and +-2 neighbours
+  float c1h = 0.f, c1l = 0.f, c2h = 0.f, c2l = 0.f;  // the same as FP32 pairs
 };
 
 struct CsrOp {
@@ -19,6 +20,8 @@ struct CsrOp {
   const int32_t* cols = nullptr;
   const float* vals32 = nullptr;
   const double* vals64 = nullptr;
+  const float* valshi = nullptr;  // values as FP32 pairs (hi + lo)
+  const float* valslo = nullptr;
   int max_row_nnz = 0;
 };
 
@@ -28,7 +31,8 @@ struct Operator {
   StencilOp st;
   CsrOp csr;
   const double* diag64 = nullptr;  // H_ii
-  const float* diag32 = nullptr;
+  const float* diag32 = nullptr;   // fl32(H_ii), the hi part of the pair
+  const float* diaglo = nullptr;   // H_ii - fl32(H_ii)
   const double* minv64 = nullptr;  // diagonal preconditioner M_ii
   const float* minv32 = nullptr;
 };
@@ -45,6 +49,26 @@ void apply_h(const Operator& op, const double* X, double* Y, int ncols,
 int apply_h_dots(const Operator& op, const float* X, float* Y, int ncols,
                  double* dots, cudaStream_t s);
 size_t apply_h_dots_doubles(const Operator& op, int ncols);
+
+// ---------------------------------------------------------------------------
+// Double-float (FP32 pair, ~48-bit) arithmetic for the FP64-accuracy steps
+// of MP2; a block is two arrays (hi, lo) of N x m floats.
+// ---------------------------------------------------------------------------
+void split_df(const double* x, float* hi, float* lo, int64_t n,
+              cudaStream_t s);
+void join_df(const float* hi, const float* lo, double* x, int64_t n,
+             cudaStream_t s);
+// X = H C in double-float (needs Operator::diaglo, and valshi/valslo for CSR)
+void apply_h_df(const Operator& op, const float* Ch, const float* Cl,
+                float* Xh, float* Xl, int ncols, cudaStream_t s);
+// H_D[j] = sum_i C_ij X_ij, E = sum_j H_D[j] into sc->E
+void energy_diag_df(int64_t N, int m, const float* Ch, const float* Cl,
+                    const float* Xh, const float* Xl, double* HD,
+                    IterScalars* sc, double* partials, cudaStream_t s);
+// X32 = fl32(X - C diag(H_D))
+void xprime_df(int64_t N, int m, const float* Ch, const float* Cl,
+               const float* Xh, const float* Xl, const double* HD, float* X32,
+               cudaStream_t s);
 
 // diag[i] = t*w0*ndim + V[i] for a stencil operator
 void stencil_diag(const StencilOp& st, double t_w0_ndim, const double* V,
@@ -134,6 +158,11 @@ int mul_tc_grad(int64_t N, int m, const float* C, const double* Hp,
 void mul_tc_split64(int64_t N, int m, const float* C32, const float* P,
                     const double* C64, const IterScalars* sc, const double* R,
                     double* Cn, const TcWork& tw, cudaStream_t s);
+// The same with C and Cn as FP32 pairs (C32 = Ch): Y = C + alpha P and
+// Y diag(R) in double-float, plus the tensor-core product
+void mul_tc_splitdf(int64_t N, int m, const float* Ch, const float* Cl,
+                    const float* P, const IterScalars* sc, const double* R,
+                    float* Cnh, float* Cnl, const TcWork& tw, cudaStream_t s);
 
 // G = -2 (X' - C H') with the Polak-Ribiere partial sums; G_prev/P_prev may
 // be null (first iteration). Then the device scalar update of gamma, r.
@@ -160,6 +189,12 @@ void rotate_split(int64_t N, int m, const double* C, const float* P,
                   const double* R, double* Cn, const IterScalars* sc,
                   cudaStream_t s, const float* C32 = nullptr,
                   const TcWork* tw = nullptr);
+// The split update with C and Cn as FP32 pairs (hi, lo): the FP32 operand
+// is Ch + alpha P, Y diag(R) is formed in double-float
+void rotate_split_df(int64_t N, int m, const float* Ch, const float* Cl,
+                     const float* P, const double* R, float* Cnh, float* Cnl,
+                     const IterScalars* sc, cudaStream_t s,
+                     const TcWork* tw = nullptr);
 // Y = A M for A: N x k (FP64), M: k x n FP64
 void mult(int64_t N, int k, int n, const double* A, const double* M,
           double* Y, cudaStream_t s);

@@ -71,8 +71,8 @@ __global__ void k_make_A0(int m, const double* __restrict__ Hp,
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
-// Cholesky S = L L^T and L^{-1}, blocked in 32-column panels, one CTA (512
-// threads in FP32, 256 in FP64). Writes Linv (lower) and R = L^{-T} (upper).
+// Cholesky S = L L^T and L^{-1}, blocked in 32-column panels, one CTA of 256
+// threads. Writes Linv (lower) and R = L^{-T} (upper).
 //
 // m is padded to mp, a multiple of 32, with the identity, which changes
 // neither factor. Per panel p: (a) one warp factors the diagonal block
@@ -121,9 +121,11 @@ __device__ __forceinline__ double piv_sqrt(double t) {
   return fma(0.5 * r, fma(-s, s, t), s);
 }
 
-// FP32: 512 threads; FP64 (twice the registers per row): 256.
+// 256 threads: the register-resident rows of the diagonal-block steps need
+// more than the 128 registers a 512-thread CTA allows (they spilled, and
+// the sequential pivot chain paid for it); the parallel phases lose less.
 template <typename Tm>
-constexpr int chol_threads() { return sizeof(Tm) == 4 ? 512 : 256; }
+constexpr int chol_threads() { return 256; }
 
 template <typename Tm, bool dev>
 __global__ void __launch_bounds__(chol_threads<Tm>())

@@ -151,6 +151,9 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   C32_ = f(nm);
   C32n_ = f(nm);
   X32_ = f(nm);
+  Cdf_ = f(2 * nm);  // MP2 blocks as FP32 pairs: hi at [0, nm), lo after
+  Cdfn_ = f(2 * nm);
+  Xdf_ = f(2 * nm);
   Gb_[0] = d(nm);
   Gb_[1] = d(nm);
   Pb_ = d(nm);
@@ -186,6 +189,7 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   tw_.err = &sc_->status;
   diag64_ = d(N);
   diag32_ = f(N);
+  diaglo_ = f(N);
   minv64_ = d(N);
   minv32_ = f(N);
   TRM_CUDA(cudaHostAlloc(&ring_, sizeof(IterScalars) * kRing,
@@ -221,6 +225,10 @@ void Solver::init_stencil(int nx, int ny, int nz, int order, double h,
   op_.st.radius = order == 2 ? 1 : 2;
   op_.st.c1 = t * w1;
   op_.st.c2 = t * w2;
+  op_.st.c1h = (float)op_.st.c1;
+  op_.st.c1l = (float)(op_.st.c1 - (double)op_.st.c1h);
+  op_.st.c2h = (float)op_.st.c2;
+  op_.st.c2l = (float)(op_.st.c2 - (double)op_.st.c2h);
   double* Vd = nullptr;
   if (V_host) {
     Vd = static_cast<double*>(mem_.alloc((size_t)N_ * 8));
@@ -228,8 +236,10 @@ void Solver::init_stencil(int nx, int ny, int nz, int order, double h,
                              cudaMemcpyHostToDevice, s_));
   }
   stencil_diag(op_.st, t * w0 * ndim, Vd, diag64_, diag32_, N_, s_);
+  split_df(diag64_, diag32_, diaglo_, N_, s_);
   op_.diag64 = diag64_;
   op_.diag32 = diag32_;
+  op_.diaglo = diaglo_;
   if (opt_.precond) {
     diag_preconditioner(diag64_, N_, minv64_, minv32_, part_, s_);
     op_.minv64 = minv64_;
@@ -259,15 +269,26 @@ void Solver::init_csr(const int32_t* rowptr, const int32_t* cols,
     TRM_CUDA(cudaMemcpyAsync(v, vals, (size_t)nnz * 8, cudaMemcpyHostToDevice,
                              s_));
     op_.csr.vals64 = v;
+    auto* vh = static_cast<float*>(mem_.alloc((size_t)nnz * 4));
+    auto* vl = static_cast<float*>(mem_.alloc((size_t)nnz * 4));
+    split_df(v, vh, vl, nnz, s_);
+    op_.csr.valshi = vh;
+    op_.csr.valslo = vl;
   } else {
     auto* v = static_cast<float*>(mem_.alloc((size_t)nnz * 4));
     TRM_CUDA(cudaMemcpyAsync(v, vals, (size_t)nnz * 4, cudaMemcpyHostToDevice,
                              s_));
     op_.csr.vals32 = v;
+    auto* vl = static_cast<float*>(mem_.alloc((size_t)nnz * 4));
+    TRM_CUDA(cudaMemsetAsync(vl, 0, (size_t)nnz * 4, s_));
+    op_.csr.valshi = v;
+    op_.csr.valslo = vl;
   }
   csr_diag(op_, diag64_, diag32_, s_);
+  split_df(diag64_, diag32_, diaglo_, N_, s_);
   op_.diag64 = diag64_;
   op_.diag32 = diag32_;
+  op_.diaglo = diaglo_;
   if (opt_.precond) {
     diag_preconditioner(diag64_, N_, minv64_, minv32_, part_, s_);
     op_.minv64 = minv64_;
@@ -392,9 +413,12 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
 }
 
 // ---------------------------------------------------------------------------
-// MP2 (Sec. 2.2): steps (1), (2), (3), (5) and E in FP64; H' and G from FP32
-// products (diag(H') = 0); G, P, HP stored FP32; m x m work in FP64; the
-// rotation split as C L_D (FP64) + C L' (FP32), C kept in FP64.
+// MP2 (Sec. 2.2): steps (1), (2), (3), (5) and E at FP64-class accuracy, in
+// double-float (C and X = HC held as FP32 pairs, ~48 bits: GB300's FP64
+// pipe is 1/64 of its FP32 rate); H' and G from FP32 products (diag(H') =
+// 0) with C32 = the hi half of C; G, P, HP stored FP32; m x m work in FP32
+// deviation form; the rotation split as C L_D (double-float) + C L' (FP32,
+// tensor cores).
 // ---------------------------------------------------------------------------
 void Solver::iter_mp2() {
   float* G = static_cast<float*>(Gb_[0]);
@@ -403,52 +427,68 @@ void Solver::iter_mp2() {
   float* HP = static_cast<float*>(HPb_);
   const float* minv = opt_.precond ? minv32_ : nullptr;
   const size_t mm = (size_t)m_ * m_;
+  const size_t nm = (size_t)N_ * m_;
   const double Nd = (double)N_, md = m_;
-  const double nm = Nd * md, m2N = nm * md, m3 = md * md * md;
+  const double dnm = Nd * md, m2N = dnm * md, m3 = md * md * md;
+  float* Ch = Cdf_;
+  float* Cl = Cdf_ + nm;
+  float* Xh = Xdf_;
+  float* Xl = Xdf_ + nm;
   double f64, b64, f32, b32;
   spmm_cost(op_, m_, 8, &f64, &b64);
   spmm_cost(op_, m_, 4, &f32, &b32);
-  TRM_PROF(KC_SPMM64, f64, b64, apply_h(op_, C64_, X64_, m_, s_));   // (1) FP64
-  TRM_PROF(KC_ROWOPS, 2 * nm, 16 * nm,
-           energy_diag<double>(N_, m_, C64_, X64_, HD_, sc_, part_, s_));
-  // (5): only the FP32 copies of C and X' are used in this step
-  TRM_PROF(KC_ROWOPS, 2 * nm, 24 * nm,
-           xprime<double>(N_, m_, C64_, X64_, HD_, C32_, X32_, s_, false));
+  TRM_PROF(KC_SPMM64, f64, b64, apply_h_df(op_, Ch, Cl, Xh, Xl, m_, s_));  // (1)
+  TRM_PROF(KC_ROWOPS, 2 * dnm, 16 * dnm,
+           energy_diag_df(N_, m_, Ch, Cl, Xh, Xl, HD_, sc_, part_, s_));  // (2), (3)
+  TRM_PROF(KC_ROWOPS, 2 * dnm, 20 * dnm,
+           xprime_df(N_, m_, Ch, Cl, Xh, Xl, HD_, X32_, s_));  // (5) FP32 X'
   Blocks<float> bx;
   bx.p[0] = X32_;
   bx.cols = m_;
   bx.count = 1;
-  TRM_PROF(KC_GRAM32, 2 * m2N, 8 * nm,
-           gram<float>(N_, m_, C32_, bx, Hp_, part_, part_cap_, s_, &sc_->status)); // (6)
+  TRM_PROF(KC_GRAM32, 2 * m2N, 8 * dnm,
+           gram<float>(N_, m_, Ch, bx, Hp_, part_, part_cap_, s_, &sc_->status)); // (6)
   zero_diag(m_, Hp_, s_);
-  TRM_PROF(KC_GRAD32, 2 * m2N, 20 * nm,
-           gradient<float>(N_, m_, C32_, X32_, Hp_, G, Gp, P, minv, sc_,
+  TRM_PROF(KC_GRAD32, 2 * m2N, 20 * dnm,
+           gradient<float>(N_, m_, Ch, X32_, Hp_, G, Gp, P, minv, sc_,
                            part_, part_cap_, s_, &tw_));      // (7)
-  TRM_PROF(KC_ROWOPS, 2 * nm, 12 * nm,
+  TRM_PROF(KC_ROWOPS, 2 * dnm, 12 * dnm,
            update_p<float>(N_, m_, G, P, minv, sc_, s_));
   TRM_PROF(KC_SPMM32, f32, b32, apply_h(op_, P, HP, m_, s_));
   Blocks<float> bp;
   bp.p[0] = P;
   bp.cols = m_;
   bp.count = 1;
-  TRM_PROF(KC_GRAM32, 2 * m2N, 8 * nm,
-           gram<float>(N_, m_, C32_, bp, Bm_, part_, part_cap_, s_, &sc_->status));
+  TRM_PROF(KC_GRAM32, 2 * m2N, 8 * dnm,
+           gram<float>(N_, m_, Ch, bp, Bm_, part_, part_cap_, s_, &sc_->status));
   Blocks<float> b3;
   b3.p[0] = P;
   b3.p[1] = HP;
   b3.p[2] = G;
   b3.cols = m_;
   b3.count = 3;
-  TRM_PROF(KC_GRAM32, 6 * m2N, 16 * nm,
+  TRM_PROF(KC_GRAM32, 6 * m2N, 16 * dnm,
            gram<float>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status));
   prof.begin(KC_SMALL, s_);
   line_factor<float>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, nullptr, R_,
                      sc_, mmw_, T1_, true, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
-  TRM_PROF(KC_ROT32, m2N, 20 * nm,
-           rotate_split(N_, m_, C64_, P, R_, C64n_, sc_, s_, C32_, &tw_));
-  std::swap(C64_, C64n_);
+  TRM_PROF(KC_ROT32, m2N, 24 * dnm,
+           rotate_split_df(N_, m_, Ch, Cl, P, R_, Cdfn_, Cdfn_ + nm, sc_, s_,
+                           &tw_));
+  std::swap(Cdf_, Cdfn_);
   std::swap(Gb_[0], Gb_[1]);
+}
+
+// The MP2 blocks between FP64 and FP32 pairs (at re-orthonormalizations,
+// Rayleigh-Ritz rotations and phase changes).
+void Solver::c64_to_df() {
+  const size_t nm = (size_t)N_ * m_;
+  split_df(C64_, Cdf_, Cdf_ + nm, (int64_t)nm, s_);
+}
+void Solver::df_to_c64() {
+  const size_t nm = (size_t)N_ * m_;
+  join_df(Cdf_, Cdf_ + nm, C64_, (int64_t)nm, s_);
 }
 
 // Fig. ONFIG in FP64: S = C^T C, S = L L^T, C <- C L^{-T}.
@@ -548,6 +588,7 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
     orth_uniform<float>(C32_, C32n_);
   } else {
     orth_fp64(C64_, C64n_);
+    if (phase == PH_MP2) c64_to_df();
   }
   set_restart();
 
@@ -650,10 +691,15 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
         last_error = "overlap matrix not positive definite";
         break;
       }
-      if (phase == PH_SP)
+      if (phase == PH_SP) {
         orth_uniform<float>(C32_, C32n_);
-      else
+      } else if (phase == PH_MP2) {
+        df_to_c64();
         orth_fp64(C64_, C64n_);
+        c64_to_df();
+      } else {
+        orth_fp64(C64_, C64n_);
+      }
       set_restart();
       continue;
     }
@@ -691,6 +737,7 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
         to_f64(C32_, C64_, (int64_t)nm, s_);
         orth_fp64(C64_, C64n_);
         rr_rotate_fp64();
+        c64_to_df();
         set_restart();
         phase = PH_MP2;
         best = INFINITY;
@@ -708,8 +755,10 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
           last_error = "stagnated above the tolerance";
           break;
         }
+        if (phase == PH_MP2) df_to_c64();
         orth_fp64(C64_, C64n_);
         rr_rotate_fp64();
+        if (phase == PH_MP2) c64_to_df();
         set_restart();
         best = INFINITY;
         best_at = enq;
@@ -724,16 +773,18 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
         const bool ro = v.rms < 1e-2 * r_orth ||
                         (opt_.reorth_every > 0 && since_orth >= opt_.reorth_every);
         if (rr || ro) {
+          df_to_c64();
           orth_fp64(C64_, C64n_);
           ++n_reorth;
           since_orth = 0;
           r_orth = v.rms;
-        }
-        if (rr) {
-          rr_rotate_fp64();
-          set_restart();
-          since_rr = 0;
-          r_rr = v.rms;
+          if (rr) {
+            rr_rotate_fp64();
+            set_restart();
+            since_rr = 0;
+            r_rr = v.rms;
+          }
+          c64_to_df();
         }
       }
     }
@@ -741,6 +792,7 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
   drain();
   if (prof.on) prof.resolve();
   if (phase == PH_SP) to_f64(C32_, C64_, (int64_t)nm, s_);
+  if (phase == PH_MP2) df_to_c64();
   double* Cfin = C64n_;
   double* Xfin = static_cast<double*>(Gb_[0]);
   final_rr(C64_, Cfin, Xfin);
@@ -877,7 +929,9 @@ void Solver::iterate(int mode, int restart, double* E, double* rms,
     Gb_[1] = Gp;
     to_f64(C32_, C64_, (int64_t)nm, s_);
   } else if (mode == TRM_MP2) {
+    c64_to_df();
     iter_mp2();
+    df_to_c64();
   } else {
     throw Error(-1, "iterate: mode must be TRM_FP64, TRM_FULL_SP or TRM_MP2");
   }

@@ -86,6 +86,8 @@ class Solver {
   template <typename T, typename Tm>
   void iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP);
   void iter_mp2();
+  void c64_to_df();
+  void df_to_c64();
   void orth_fp64(double*& C, double*& Cn);
   template <typename T>
   void orth_uniform(T*& C, T*& Cn);
@@ -106,11 +108,13 @@ class Solver {
   // operator data
   double* diag64_ = nullptr;
   float* diag32_ = nullptr;
+  float* diaglo_ = nullptr;
   double* minv64_ = nullptr;
   float* minv32_ = nullptr;
   // blocks (G, P, HP sized for FP64 and reused as FP32)
   double *C64_ = nullptr, *C64n_ = nullptr, *X64_ = nullptr;
   float *C32_ = nullptr, *C32n_ = nullptr, *X32_ = nullptr;
+  float *Cdf_ = nullptr, *Cdfn_ = nullptr, *Xdf_ = nullptr;  // FP32 pairs
   void *Gb_[2] = {nullptr, nullptr}, *Pb_ = nullptr, *HPb_ = nullptr;
   // m x m (FP64)
   double *HD_, *Hp_, *A0_, *Bm_, *PG_, *T1_, *T2_, *S_, *Linv_, *R_, *mmw_,
