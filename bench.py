@@ -292,6 +292,19 @@ def roofline(prof, peaks, src):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank: one independent solve per rank (replicas, weak scaling); the
+# job's time per step is the slowest rank's
+# ---------------------------------------------------------------------------
+def job_seconds(t_local, dist=None, device="cpu"):
+    if dist is None:
+        return float(t_local)
+    import torch
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -391,11 +404,7 @@ def main():
     clocks = sampler.stop()
     prof = trm.trm_profile_read(h)
     trm.trm_profile(h, False)
-    t_step = statistics.mean(times)
-    if dist:
-        t = torch.tensor([t_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = job_seconds(statistics.mean(times), dist, "cuda")
 
     peaks_file = load_json(PEAKS)
     peaks = peaks_file if peaks_file else FALLBACK
