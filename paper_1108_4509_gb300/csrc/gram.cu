@@ -6,6 +6,7 @@
 // 64 x 64 output tile t, summing in the input precision, and writes the tile
 // as FP64 partials; a second kernel adds the partials of all splits in a fixed
 // order, so the result is bitwise reproducible.
+#include "dfmath.cuh"
 #include "ops.cuh"
 
 namespace trm {
@@ -136,6 +137,33 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same for partials stored as FP32 pairs (hi at [2 k count, ...), lo
+// after it): the sums run in double-float on the FP32 pipe and each output
+// is converted to FP64 once.
+__global__ void __launch_bounds__(256)
+    k_sum_splits_pairs(const float* __restrict__ part, int splits,
+                       size_t count, double* __restrict__ out) {
+  __shared__ float rh[8][33], rl[8][33];
+  const int el = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const size_t e = (size_t)blockIdx.x * 32 + el;
+  F2 acc = {0.f, 0.f};
+  if (e < count) {
+#pragma unroll 4
+    for (int k = g; k < splits; k += 8)
+      acc = df_add(acc, F2{part[2 * (size_t)k * count + e],
+                           part[(2 * (size_t)k + 1) * count + e]});
+  }
+  rh[g][el] = acc.h;
+  rl[g][el] = acc.l;
+  __syncthreads();
+  if (g == 0 && e < count) {
+    F2 t = {rh[0][el], rl[0][el]};
+#pragma unroll
+    for (int q = 1; q < 8; ++q) t = df_add(t, F2{rh[q][el], rl[q][el]});
+    out[e] = (double)t.h + (double)t.l;
+  }
+}
+
 void plan(int64_t N, int m, int n, int* splits, int64_t* rows) {
   const int tiles = ceil_div(m, TM) * ceil_div(n, TN);
   const int target = 4 * sm_count();
@@ -157,6 +185,13 @@ size_t gram_partials_doubles(int64_t N, int m, int n) {
   int64_t r;
   plan(N, m, n, &s, &r);
   return (size_t)s * m * n;
+}
+
+void sum_splits_pairs(const float* part, int splits, size_t count,
+                      double* out, cudaStream_t s) {
+  k_sum_splits_pairs<<<ceil_div(count, 32), 256, 0, s>>>(part, splits, count,
+                                                         out);
+  TRM_CHECK_LAUNCH();
 }
 
 void sum_splits(const double* part, int splits, size_t count, double* out,

@@ -12,21 +12,35 @@
 // (hi overwrites x, lo goes to a twin buffer) and no tile is copied.
 //
 // One CTA owns a 128 x 128 output tile and a slice of the N rows (split-K);
-// its partial tile is written in FP64 and the slices are added in a fixed
-// order by k_sum_splits, as in the SIMT path.
+// its partial tile is written as double-float pairs and the slices are added
+// in a fixed order by k_sum_splits_pairs (FP64 results).
 //
-// Warp roles (320 threads): warp 0 issues the TMA loads (one box of A and one
+// The tensor core accumulates in FP32 but does not round to nearest: every
+// MMA step drops up to an ulp of the running sum, so the error grows with
+// the number of steps (measured: 6.7e-4 relative after 98304 rows). The MMA
+// therefore accumulates chunks of KC stages (KC * 32 rows) into one of two
+// TMEM buffers, and accumulator warps fold each finished chunk into a
+// double-float (hi, lo) running sum kept in the other half of TMEM; the bias
+// is bounded by KC * 12 steps of 2^-23 of the chunk sums. Row slices of at
+// most kSingleChunk stages (3072 rows, all of the 48^3 case) are one chunk:
+// the bias is then at most 96 * 12 steps and nothing is folded.
+//
+// Warp roles (576 threads): warp 0 issues the TMA loads (one box of A and one
 // of B per 32-row stage, three stages in flight); warp 1 allocates tensor
-// memory and issues the MMAs from one thread; warps 2-9 split the stage in
-// place (half a line of A and of B each), then read the accumulator back
-// (warp w owns TMEM lanes 32 (w % 4) .. +31 and one 64-column half). Every mbarrier wait is bounded: on timeout the kernel
-// sets bit 2 of *err and falls through to its clean-up.
+// memory and issues the MMAs from one thread; warps 2-9 split each stage in
+// place (half a line of A and of B each); warps 10-17 fold the finished
+// chunks and write the partial as FP32 pairs (warp w owns TMEM lanes
+// 32 (w % 4) .. +31 and one 64-column half). No FP64 instruction runs here
+// (GB300's FP64 pipe is 1/64 of its FP32 rate). Every mbarrier wait is
+// bounded: on timeout the kernel sets bit 2 of *err and falls through to its
+// clean-up.
 #include <cuda.h>
 
 #include <algorithm>
 #include <mutex>
 #include <unordered_map>
 
+#include "dfmath.cuh"
 #include "ops.cuh"
 #include "tc.cuh"
 
@@ -40,13 +54,16 @@ constexpr int BM = 128;        // output rows per CTA (columns of A)
 constexpr int BN = 128;        // output columns per CTA (columns of B)
 constexpr int BK = 32;         // block rows per stage (one 128-byte box)
 constexpr int STAGES = 3;
-constexpr int THREADS = 320;  // 10 warps
+constexpr int THREADS = 576;  // 18 warps
+constexpr int KC = 4;         // stages per accumulation chunk
+constexpr int kSingleChunk = 96;  // row slices this short are one chunk
 
 struct TcSmem {
   // [stage][A hi, B hi, A lo, B lo][128 columns x 32 rows], 128-byte swizzle:
   // 16-byte chunk q of column c sits at chunk q ^ (c % 8).
   float tile[STAGES][4][BM * BK];
-  uint64_t full[STAGES], conv[STAGES], empty[STAGES], accdone;
+  uint64_t full[STAGES], conv[STAGES], empty[STAGES];
+  uint64_t accfull[2], accempty[2], mmadone;
   uint32_t tmem_base;
   int failed;
 };
@@ -95,13 +112,17 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&sm->conv[s], 256);
       mbar_init(&sm->empty[s], 1);
     }
-    mbar_init(&sm->accdone, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm->accfull[b], 1);
+      mbar_init(&sm->accempty[b], 256);  // the eight fold warps
+    }
+    mbar_init(&sm->mmadone, 1);
     sm->failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
-    tmem_alloc(&sm->tmem_base, BN);
-  }
+  // TMEM: chunk buffers at columns 0 and BN, the double-float sum's hi at
+  // 2 BN and lo at 3 BN
+  if (warp == 1) tmem_alloc(&sm->tmem_base, 4 * BN);
   fence_before();
   __syncthreads();
   fence_after();
@@ -131,13 +152,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       bool ok = true;
+      const int kcl = nk <= kSingleChunk ? nk : KC;  // stages per chunk
       for (int k = 0; k < nk && ok; ++k) {
         const int s = k % STAGES;
+        const int kc = k % kcl, c = k / kcl, b = c & 1;
+        if (kc == 0 && c >= 2 &&
+            !mbar_wait(&sm->accempty[b], ((c / 2) - 1) & 1, args.err,
+                       &sm->failed)) {
+          ok = false;
+          break;
+        }
         if (!mbar_wait(&sm->conv[s], (k / STAGES) & 1, args.err, &sm->failed)) {
           ok = false;
           break;
         }
         fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * BN);
         const uint32_t aH = smem_u32(sm->tile[s][0]);
         const uint32_t bH = smem_u32(sm->tile[s][1]);
         const uint32_t aL = smem_u32(sm->tile[s][2]);
@@ -148,50 +178,100 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int p = 0; p < 3; ++p) {
 #pragma unroll
           for (int kk = 0; kk < BK / 8; ++kk)  // K = 8 per TF32 MMA (32 bytes)
-            mma_tf32(tmem, kdesc(pa[p] + kk * 32), kdesc(pb[p] + kk * 32),
-                     kIdesc, (k > 0 || p > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(d, kdesc(pa[p] + kk * 32), kdesc(pb[p] + kk * 32),
+                     kIdesc, (kc > 0 || p > 0 || kk > 0) ? 1u : 0u);
         }
         mma_commit(&sm->empty[s]);  // stage reusable once these MMAs are done
+        if (kc == kcl - 1 || k == nk - 1) mma_commit(&sm->accfull[b]);
       }
-      mma_commit(&sm->accdone);
+      // every MMA of this thread completes before the TMEM is released
+      mma_commit(&sm->mmadone);
+      mbar_wait_own(&sm->mmadone, 0, args.err);
     }
-  } else {
-    // ---------------- in-place split, then epilogue ----------------
+  } else if (warp < 10) {
+    // ---------------- in-place split ----------------
     const int t = threadIdx.x - 64;  // 0..255: half a line of A and of B
-    const int c = t >> 1, half = t & 1;
-    bool ok = true;
-    for (int k = 0; k < nk && ok; ++k) {
+    const int c_line = t >> 1, half = t & 1;
+    for (int k = 0; k < nk; ++k) {
       const int s = k % STAGES;
-      if (!mbar_wait(&sm->full[s], (k / STAGES) & 1, args.err, &sm->failed)) {
-        ok = false;
+      if (!mbar_wait(&sm->full[s], (k / STAGES) & 1, args.err, &sm->failed))
         break;
-      }
-      split_half(sm->tile[s][0], sm->tile[s][2], c, half, false, 0.f);
-      split_half(sm->tile[s][1], sm->tile[s][3], c, half, false, 0.f);
+      split_half(sm->tile[s][0], sm->tile[s][2], c_line, half, false, 0.f);
+      split_half(sm->tile[s][1], sm->tile[s][3], c_line, half, false, 0.f);
       fence_proxy_async();
       mbar_arrive(&sm->conv[s]);
     }
-    const bool acc_ok =
-        ok && nk > 0 && mbar_wait(&sm->accdone, 0, args.err, &sm->failed);
-    __syncwarp();  // the TMEM loads below are .sync.aligned
-    fence_after();
-    const int q = warp & 3;          // TMEM lane quarter of this warp
-    const int g = (warp - 2) >> 2;   // column half of the tile
+  } else {
+    // ------- fold the chunks into the double-float sum, then write -------
+    const int q = warp & 3;            // TMEM lane quarter of this warp
+    const int g = (warp - 10) >> 2;    // column half of the tile
+    const uint32_t lrow = (uint32_t)(32 * q) << 16;
+    const int kcl = nk <= kSingleChunk ? nk : KC;
+    const int nch = nk > 0 ? (nk + kcl - 1) / kcl : 0;
     const int row = i0 + 32 * q + lane;
-    double* out = args.part + (size_t)split * args.m * args.n;
+    // partials as FP32 pairs: split s holds hi at [2 s count, (2 s + 1)
+    // count) and lo after it (no FP64 instruction in this kernel)
+    const size_t count = (size_t)args.m * args.n;
+    float* out_hi = reinterpret_cast<float*>(args.part) + 2 * (size_t)split * count;
+    float* out_lo = out_hi + count;
+    bool ok = nch > 0;
+    for (int c = 0; c < nch && ok; ++c) {
+      const int b = c & 1;
+      const bool last = c == nch - 1;
+      const bool got =
+          mbar_wait(&sm->accfull[b], (c / 2) & 1, args.err, &sm->failed);
+      if (!__all_sync(0xffffffffu, got)) {  // the TMEM ops are .sync.aligned
+        ok = false;
+        break;
+      }
+      fence_after();
 #pragma unroll 1
-    for (int cb = 64 * g; cb < 64 * g + 64; cb += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + cb, r);
-      if (row < args.m) {
+      for (int cb = 64 * g; cb < 64 * g + 64; cb += 16) {
+        uint32_t x[16], hi[16], lo[16];
+        tmem_ld16_async(tmem + lrow + (uint32_t)(b * BN + cb), x);
+        if (c > 0) {
+          tmem_ld16_async(tmem + lrow + (uint32_t)(2 * BN + cb), hi);
+          tmem_ld16_async(tmem + lrow + (uint32_t)(3 * BN + cb), lo);
+        }
+        tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          const int col = j0 + cb + e;
-          if (col < args.n)
-            out[row + (size_t)col * args.m] =
-                acc_ok ? (double)__uint_as_float(r[e]) : 0.0;
+        for (int e = 0; e < 16; ++e) {
+          F2 v = {__uint_as_float(x[e]), 0.f};
+          if (c > 0)
+            v = df_add(F2{__uint_as_float(hi[e]), __uint_as_float(lo[e])}, v);
+          hi[e] = __float_as_uint(v.h);
+          lo[e] = __float_as_uint(v.l);
+        }
+        if (last) {  // the partial of this row slice, as FP32 pairs
+          if (row < args.m) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int col = j0 + cb + e;
+              if (col < args.n) {
+                const size_t idx = row + (size_t)col * args.m;
+                out_hi[idx] = __uint_as_float(hi[e]);
+                out_lo[idx] = __uint_as_float(lo[e]);
+              }
+            }
+          }
+        } else {
+          tmem_st16(tmem + lrow + (uint32_t)(2 * BN + cb), hi);
+          tmem_st16(tmem + lrow + (uint32_t)(3 * BN + cb), lo);
         }
       }
+      if (!last) {
+        tmem_wait_st();
+        fence_before();
+        mbar_arrive(&sm->accempty[b]);
+      }
+    }
+    __syncwarp();
+    if (!ok && row < args.m) {  // a wait gave up: zero partial, error set
+      for (int cb = 64 * g; cb < 64 * g + 64; ++cb)
+        if (j0 + cb < args.n) {
+          out_hi[row + (size_t)(j0 + cb) * args.m] = 0.f;
+          out_lo[row + (size_t)(j0 + cb) * args.m] = 0.f;
+        }
     }
   }
   __syncwarp();  // lanes that skipped a single-thread role wait for it here
@@ -200,7 +280,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 1) {
     __syncwarp();
     fence_after();
-    tmem_dealloc(tmem, BN);
+    tmem_dealloc(tmem, 4 * BN);
   }
 }
 
@@ -254,7 +334,8 @@ void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
   k_gram_tc<<<grid, THREADS, smem, s>>>(mA, mB[0], mB[1], mB[2], a);
   TRM_CHECK_LAUNCH();
   const size_t count = (size_t)m * n;
-  sum_splits(partials, splits, count, out, s);
+  sum_splits_pairs(reinterpret_cast<const float*>(partials), splits, count,
+                   out, s);
 }
 
 }  // namespace trm

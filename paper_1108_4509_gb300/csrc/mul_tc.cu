@@ -282,7 +282,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int cbeg = ((warp - EPI0) >> 2) * (NC / 2);  // column half
     const int rr = 32 * q + lane;
     const int64_t N = args.N;
-    double s_gg = 0, s_gmg = 0, s_pmg = 0, s_gpp = 0;
+    // Polak-Ribiere sums as double-float pairs (no FP64 instruction per
+    // batch: GB300's FP64 pipe is 1/64 of its FP32 rate)
+    F2 s_sum[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     double alpha64 = 0.0;
     if (MODE == kSplit64 && args.sc) alpha64 = args.sc->alpha;
     F2 alpha2 = {0.f, 0.f};
@@ -339,10 +341,10 @@ __global__ void __launch_bounds__(THREADS, 1)
               gpp = fmaf(g, pv[e], gpp);
             }
           }
-          s_gg += gg;
-          s_gmg += gmg;
-          s_pmg += pmg;
-          s_gpp += gpp;
+          s_sum[0] = df_add(s_sum[0], F2{gg, 0.f});
+          s_sum[1] = df_add(s_sum[1], F2{gmg, 0.f});
+          s_sum[2] = df_add(s_sum[2], F2{pmg, 0.f});
+          s_sum[3] = df_add(s_sum[3], F2{gpp, 0.f});
         } else if (MODE == kSplitDf) {
 #pragma unroll
           for (int h = 0; h < 16; h += 8) {
@@ -401,12 +403,17 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_arrive(&sm->accempty[b]);
     }
     if (MODE == kGrad) {
-      double v[4] = {s_gg, s_gmg, s_pmg, s_gpp};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = warp_sum(v[j]);
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          s_sum[j] = df_add(s_sum[j],
+                            F2{__shfl_xor_sync(0xffffffffu, s_sum[j].h, o),
+                               __shfl_xor_sync(0xffffffffu, s_sum[j].l, o)});
       if (lane == 0)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) sm->red[warp - EPI0][j] = v[j];
+        for (int j = 0; j < 4; ++j)
+          sm->red[warp - EPI0][j] = (double)s_sum[j].h + (double)s_sum[j].l;
       asm volatile("bar.sync 1, %0;" ::"n"(NEPI * 32) : "memory");
       if (threadIdx.x == EPI0 * 32) {
 #pragma unroll

@@ -100,6 +100,9 @@ void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
           int* err = nullptr);
 void sum_splits(const double* part, int splits, size_t count, double* out,
                 cudaStream_t s);
+// the same for partials stored as FP32 pairs (hi, then lo, per split)
+void sum_splits_pairs(const float* part, int splits, size_t count,
+                      double* out, cudaStream_t s);
 // tcgen05 Gram of FP32 blocks (two-term TF32 split, three products, FP32
 // accumulation in tensor memory): needs N % 4 == 0, m >= 64, at most 3 B segments whose
 // widths are multiples of 128 when there are several.

@@ -82,3 +82,9 @@ def test_grid_csr_13_point_coefficients():
         assert abs(row[r - off] + 2.0 / 3.0) < 1e-15
         assert abs(row[r + 2 * off] - 1.0 / 24.0) < 1e-15
         assert abs(row[r - 2 * off] - 1.0 / 24.0) < 1e-15
+
+
+def test_random_block_column_matches_block():
+    B = ti.random_block(1000, 5, 7)
+    for j in range(5):
+        assert np.array_equal(B[:, j], ti.random_block_column(1000, j, 7))

@@ -69,6 +69,12 @@ def random_block(N: int, m: int, seed: int) -> np.ndarray:
     return vals.reshape((m, N)).T.copy(order="F")
 
 
+def random_block_column(N: int, j: int, seed: int) -> np.ndarray:
+    """Column j of random_block(N, m, seed) alone (same counters i + N*j)."""
+    idx = np.arange(N, dtype=np.uint64) + np.uint64(N) * np.uint64(j)
+    return uniform01(seed, idx) - 0.5
+
+
 def gaussian_wells(shape, nwells: int, seed: int, h: float = 1.0,
                    depth=(-2.0, -0.5), width: float = 1.5) -> np.ndarray:
     """Sum of `nwells` Gaussian wells sampled on a grid, FP64, x fastest.
