@@ -16,6 +16,11 @@ included), clocks (nvidia-smi sampled during the timed region), cpu_baseline
 (the FP64 oracle on the host cores, a bounded sample scaled to a solve).
 
 --impl reference times the oracle itself (the CPU program), bounded samples.
+
+--serving T replaces the solve benchmark with a serving run: T seconds of
+seeded Poisson arrivals of stencil problems (grids 12^3 to 40^3, orders 2 and
+4, 4 to 64 Gaussian wells, m = 8 to 96) submitted to the request server; the
+same arrival trace is then replayed with one solve at a time for comparison.
 """
 from __future__ import annotations
 
@@ -63,6 +68,14 @@ def parse():
                     help="also time one solve of the all-FP64 path")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="budget of the oracle CPU sample")
+    ap.add_argument("--serving", type=float, default=0.0,
+                    help="instead of the solve benchmark: seconds of seeded "
+                         "Poisson arrivals of mixed problems through the "
+                         "request server; prints latency p50/p99 and solves/s")
+    ap.add_argument("--rate", type=float, default=20.0,
+                    help="serving: mean arrivals per second")
+    ap.add_argument("--max-live", type=int, default=8,
+                    help="serving: concurrent solves")
     ap.add_argument("--clocks", type=int, default=1,
                     help="sample nvidia-smi clocks during the timed region "
                          "(0 under a profiler, which should see no other "
@@ -336,8 +349,95 @@ def run_reference(args):
     return 0
 
 
+def serving_trace(seconds, rate, seed=2024):
+    """Seeded arrival times and problems of the serving run."""
+    import numpy as np
+    import trm_inputs as ti
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            return out
+        n = int(rng.integers(12, 41))
+        order = int(rng.choice([2, 4]))
+        wells = int(rng.integers(4, 65))
+        m = int(rng.integers(8, 97))
+        V = ti.gaussian_wells((n, n, n), wells, seed=int(rng.integers(1 << 30)))
+        out.append((t, (n, n, n), order, V, m))
+
+
+def serve(trm, trace, max_live, tol, budget):
+    """Replays the trace through a server; returns the per-request results
+    and the wall time from the first arrival to the last completion."""
+    srv = trm.trm_server_create(budget, max_live)
+    tickets = []
+    t0 = time.perf_counter()
+    try:
+        for i, (ta, shape, order, V, m) in enumerate(trace):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            opt = trm.trm_default_options(precision=trm.TRM_MIXED, precond=1,
+                                          seed=1000 + i)
+            tickets.append(trm.trm_server_submit(srv, shape, order, 1.0, V, m,
+                                                 tol, opt))
+        res = [trm.trm_server_wait(srv, tk, tr[4])
+               for tk, tr in zip(tickets, trace)]
+        wall = time.perf_counter() - t0 - trace[0][0]
+    finally:
+        trm.trm_server_destroy(srv)
+    return res, wall
+
+
+def run_serving(args):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1108_4509_gb300 as trm
+    trace = serving_trace(args.serving, args.rate)
+    budget = int(0.5 * torch.cuda.mem_get_info()[0])
+    # warm-up: one small solve through a server (module load, attributes)
+    serve(trm, trace[:2], 2, args.tol, budget)
+    sampler = ClockSampler(0)
+    if args.clocks:
+        sampler.start()
+    launches0 = trm.trm_launch_count()
+    res, wall = serve(trm, trace, args.max_live, args.tol, budget)
+    launches = trm.trm_launch_count() - launches0
+    clocks = sampler.stop()
+    seq, wall1 = serve(trm, trace, 1, args.tol, budget)
+    lat = np.array([r[4] for r in res])
+    lat1 = np.array([r[4] for r in seq])
+    same = all(np.array_equal(a[0], b[0]) and a[1] == b[1]
+               for a, b in zip(res, seq))
+    out = {"metric": "serving latency p50/p99 and throughput (mixed precision)",
+           "value": len(trace) / wall, "unit": "solves/s", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "Poisson arrivals of stencil problems",
+                      "rate_per_s": args.rate, "seconds": args.serving,
+                      "requests": len(trace), "grid": "12^3..40^3",
+                      "order": [2, 4], "wells": "4..64", "m": "8..96",
+                      "tol": args.tol, "max_live": args.max_live},
+           "latency_s": {"p50": float(np.percentile(lat, 50)),
+                         "p99": float(np.percentile(lat, 99)),
+                         "max": float(lat.max())},
+           "one_at_a_time": {"solves_per_s": len(trace) / wall1,
+                             "p50": float(np.percentile(lat1, 50)),
+                             "p99": float(np.percentile(lat1, 99))},
+           "status": sorted({int(r[3]) for r in res}),
+           "same_bytes_as_one_at_a_time": bool(same),
+           "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
+    if args.serving > 0:
+        return run_serving(args)
     if args.impl == "reference":
         return run_reference(args)
     import numpy as np

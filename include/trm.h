@@ -88,7 +88,7 @@ typedef struct {
   double max_residual;      /* final FP64 max_j ||H c_j - lambda_j c_j|| */
   double E_last;            /* energy of the last iterate (FP64 trace) */
   double seconds;           /* host wall time of trm_solve */
-  long long launches;       /* library kernel launches in the process so far */
+  long long launches;       /* library kernel launches this solve issued */
 } trm_stats;
 
 /* Per-class kernel timing of one handle (see trm_profile). */
@@ -257,6 +257,56 @@ trm_status trm_gram_noalloc(int64_t N, int m, int n, int dtype, const void* A,
  * given seed: entry (i, j) = u(seed, i + N j) - 0.5 (Sec. 3: random C0). */
 trm_status trm_random_block(int64_t N, int m, uint64_t seed, double* C,
                             void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request server that solves eigenproblems of different sizes as
+ * they arrive (no counterpart in the paper; it serves many independent
+ * trace minimizations on one GPU). A request is admitted in arrival order
+ * while the device footprints of the live solves fit device_bytes and fewer
+ * than max_live solves run; every live solve has its own CUDA stream and host
+ * thread, so solves overlap on the device. Each result is the one trm_solve
+ * returns for the same problem and options on its own handle: the same
+ * bytes alone and in the mix.
+ * ------------------------------------------------------------------------ */
+typedef struct trm_server_ctx* trm_server;
+
+/* A stencil problem (as trm_create_stencil): V is a host array of
+ * nx*ny*nz FP64 values (or NULL), copied at submission; opt.stream is
+ * ignored (the server owns the streams); opt may be all defaults
+ * (trm_default_options). */
+typedef struct {
+  int nx, ny, nz, order;
+  double h;
+  const double* V;
+  int m;
+  double tol;
+  trm_options opt;
+} trm_problem;
+
+/* Device bytes a solve of an N x m problem allocates (the admission
+ * estimate); 0 for invalid sizes. */
+size_t trm_footprint_bytes(int64_t N, int m);
+
+/* Start a server on the current device. device_bytes: admission budget;
+ * max_live: most concurrent solves. TRM_EINVAL if either is 0. */
+trm_status trm_server_create(trm_server* out, size_t device_bytes,
+                             int max_live);
+
+/* Queue a problem; never blocks. *ticket identifies it for trm_server_wait.
+ * TRM_EINVAL for invalid sizes, TRM_ENOMEM when its footprint alone exceeds
+ * the budget. */
+trm_status trm_server_submit(trm_server s, const trm_problem* p,
+                             int64_t* ticket);
+
+/* Block until the ticket's solve is done; writes lambda[m] (host), *E_G,
+ * *stats and *latency (seconds from submission to completion; any output
+ * may be NULL) and releases the ticket. Returns the solve's status (as
+ * trm_solve); details in trm_last_global_error(). */
+trm_status trm_server_wait(trm_server s, int64_t ticket, double* lambda,
+                           double* E_G, trm_stats* stats, double* latency);
+
+/* Finish every queued and live solve, then free the server. */
+trm_status trm_server_destroy(trm_server s);
 
 #ifdef __cplusplus
 }

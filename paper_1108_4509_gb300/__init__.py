@@ -64,6 +64,12 @@ class trm_kernel_stats(ct.Structure):
                 ("bytes", ct.c_double)]
 
 
+class trm_problem(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+                ("order", ct.c_int), ("h", ct.c_double), ("V", ct.c_void_p),
+                ("m", ct.c_int), ("tol", ct.c_double), ("opt", trm_options)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(
         f"{LIB_PATH} is missing: build the CUDA library first "
@@ -102,6 +108,13 @@ _SIGS = {
     "trm_profile": (_i, [_h, _i]),
     "trm_profile_read": (_i, [_h, ct.POINTER(trm_kernel_stats), _i]),
     "trm_launch_count": (ct.c_longlong, []),
+    "trm_footprint_bytes": (ct.c_size_t, [_i64, _i]),
+    "trm_server_create": (_i, [ct.POINTER(_h), ct.c_size_t, _i]),
+    "trm_server_submit": (_i, [_h, ct.POINTER(trm_problem),
+                               ct.POINTER(ct.c_int64)]),
+    "trm_server_wait": (_i, [_h, ct.c_int64, _p, _p, ct.POINTER(trm_stats),
+                             _p]),
+    "trm_server_destroy": (_i, [_h]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -349,3 +362,48 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Serving: concurrent solves of problems submitted as they arrive
+# ---------------------------------------------------------------------------
+def trm_footprint_bytes(N, m):
+    return int(lib.trm_footprint_bytes(N, m))
+
+
+def trm_server_create(device_bytes, max_live):
+    h = _h()
+    _check(lib.trm_server_create(ct.byref(h), device_bytes, max_live))
+    return h
+
+
+def trm_server_submit(server, shape, order, h, V, m, tol, opt=None):
+    """Queue a stencil problem; returns its ticket. V (host, nx*ny*nz FP64
+    or None) is copied before this returns."""
+    nx, ny, nz = (tuple(shape) + (1, 1))[:3]
+    Varr, Vp = _host(V, np.float64)
+    if Varr is not None and Varr.size != nx * ny * nz:
+        raise ValueError("V must have nx*ny*nz entries")
+    p = trm_problem(nx=nx, ny=ny, nz=nz, order=order, h=h, V=Vp, m=m,
+                    tol=tol, opt=opt if opt is not None else trm_default_options())
+    t = ct.c_int64()
+    _check(lib.trm_server_submit(server, ct.byref(p), ct.byref(t)))
+    return t.value
+
+
+def trm_server_wait(server, ticket, m):
+    """Block until the ticket's solve is done: (lambda, E_G, stats, status,
+    latency_seconds); the status is trm_solve's (not raised)."""
+    lam = np.zeros(m)
+    eg = ct.c_double()
+    st = trm_stats()
+    lat = ct.c_double()
+    status = lib.trm_server_wait(server, ticket,
+                                 lam.ctypes.data_as(ct.c_void_p),
+                                 ct.cast(ct.byref(eg), ct.c_void_p),
+                                 ct.byref(st), ct.cast(ct.byref(lat), ct.c_void_p))
+    return lam, eg.value, st.as_dict(), status, lat.value
+
+
+def trm_server_destroy(server):
+    return _check(lib.trm_server_destroy(server))

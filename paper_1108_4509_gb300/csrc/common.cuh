@@ -39,6 +39,7 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 int sm_count();
 // Kernel launches issued by the library so far in this process.
 long long launch_count();
+long long thread_launch_count();  // launches by the calling host thread
 // Message returned by trm_last_global_error() on this host thread.
 void set_global_error(const std::string& msg);
 

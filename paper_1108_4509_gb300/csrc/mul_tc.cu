@@ -27,6 +27,8 @@
 // the fused epilogue (two warps per TMEM lane quarter, one column half each:
 // the epilogue streams most of the kernel's bytes with plain loads, so it
 // gets the warps). Every wait is bounded (bit 2 of *err).
+#include <atomic>
+
 #include "dfmath.cuh"
 #include "ops.cuh"
 #include "tc.cuh"
@@ -483,14 +485,14 @@ void launch(const MulArgs& a0, const float* A, const float* P,
   const int tiles = a.ntr * a.nch;
   const int grid = tiles < sm_count() ? tiles : sm_count();
   const size_t smem = sizeof(MulSmem) + 1024;
-  static int attr_dev = -1;
+  static std::atomic<int> attr_dev{-1};  // launches may come from several threads
   int dev = 0;
   TRM_CUDA(cudaGetDevice(&dev));
-  if (attr_dev != dev) {
+  if (attr_dev.load(std::memory_order_relaxed) != dev) {
     TRM_CUDA(cudaFuncSetAttribute(k_mul_tc<MODE>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-    attr_dev = dev;
+    attr_dev.store(dev, std::memory_order_relaxed);
   }
   k_mul_tc<MODE><<<grid, THREADS, smem, s>>>(mA, mP, mBh, mBl, a);
   TRM_CHECK_LAUNCH();

@@ -4,6 +4,8 @@
 // (Sec. 2.1: "diagonalization of H ... will give the explicit eigenvalues").
 // All matrices are column-major with leading dimension m and stored as FP64;
 // the template parameter Tm is the arithmetic type.
+#include <atomic>
+
 #include "ops.cuh"
 
 namespace trm {
@@ -671,14 +673,14 @@ static void chol_launch(int m, const double* S, const double* Bm,
   const size_t bytes = chol_work_elems(m) * sizeof(Tm);
   const bool smem = bytes <= 200 * 1024;
   if (smem) {
-    static int done[64] = {};
+    static std::atomic<int> done[64] = {};  // per device; any thread may launch
     int dv = 0;
     cudaGetDevice(&dv);
-    if (dv < 0 || dv >= 64 || !done[dv]) {
+    if (dv < 0 || dv >= 64 || !done[dv].load(std::memory_order_relaxed)) {
       TRM_CUDA(cudaFuncSetAttribute(k_chol_inv<Tm, dev>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     200 * 1024));
-      if (dv >= 0 && dv < 64) done[dv] = 1;
+      if (dv >= 0 && dv < 64) done[dv].store(1, std::memory_order_relaxed);
     }
   }
   k_chol_inv<Tm, dev><<<1, chol_threads<Tm>(), smem ? bytes : 0, s>>>(

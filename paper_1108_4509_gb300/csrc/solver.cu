@@ -40,22 +40,29 @@ double neumaier_sum(const double* x, int n) {
 }  // namespace
 
 int sm_count() {
-  static int n = 0;
+  static std::atomic<int> cached{0};  // solves may run on several threads
+  int n = cached.load(std::memory_order_relaxed);
   if (n == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (n <= 0) n = 1;
+    cached.store(n, std::memory_order_relaxed);
   }
   return n;
 }
 
 namespace {
 std::atomic<long long> g_launches{0};
+thread_local long long t_launches = 0;  // launches issued by this host thread
 }  // namespace
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+long long thread_launch_count() { return t_launches; }
 
 const char* const kClassNames[KC_COUNT] = {
     "spmm_f32", "spmm_f64", "gram_f32", "gram_f64", "grad_f32", "grad_f64",
@@ -138,6 +145,28 @@ void* DevArena::alloc(size_t bytes) {
   return p;
 }
 
+// Doubles of the shared partial-sum buffer: the largest of the split-K Gram
+// partials, the gradient's per-CTA sums and the column reductions.
+size_t Solver::part_capacity(int64_t N, int m) {
+  const size_t chunks = (size_t)ceil_div(N, 4096);
+  return std::max<size_t>(
+      {gram_partials_doubles(N, m, 3 * m), gram_partials_doubles(N, m, m),
+       (size_t)4 * ceil_div(N, 64) * ceil_div(m, 64), 3 * chunks * m + m,
+       (size_t)ceil_div(N, 256) * m, (size_t)4096});
+}
+
+// Device bytes the constructor (and a stencil's potential) allocates; used
+// to admit requests by footprint.
+size_t Solver::footprint(int64_t N, int m) {
+  const size_t nm = (size_t)N * m, mm = (size_t)m * m;
+  size_t b = nm * (3 * 8 + 3 * 4 + 3 * 8 + 4 * 8);  // blocks
+  b += mm * 8 * 13 + std::max(2 * mm, chol_work_elems(m)) * 8 + 4 * m * 8;
+  b += part_capacity(N, m) * 8 + sizeof(IterScalars) + 16;
+  b += mul_tc_work_floats(m, m) * 4;
+  b += (size_t)N * (8 + 4 + 4 + 8 + 4 + 8);  // diagonals, M, V
+  return b + (64u << 10);                    // allocation granularity
+}
+
 Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
     : N_(N), m_(m), tol_(tol), opt_(opt) {
   s_ = reinterpret_cast<cudaStream_t>(opt.stream);
@@ -176,11 +205,7 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   lam_ = d(m);
   res_ = d(m);
   info_ = static_cast<int*>(mem_.alloc(16));
-  const size_t chunks = (size_t)ceil_div(N, 4096);
-  part_cap_ = std::max<size_t>(
-      {gram_partials_doubles(N, m, 3 * m), gram_partials_doubles(N, m, m),
-       (size_t)4 * ceil_div(N, 64) * ceil_div(m, 64), 3 * chunks * m + m,
-       (size_t)ceil_div(N, 256) * m, (size_t)4096});
+  part_cap_ = part_capacity(N, m);
   part_ = d(part_cap_);
   sc_ = static_cast<IterScalars*>(mem_.alloc(sizeof(IterScalars)));
   TRM_CUDA(cudaMemsetAsync(sc_, 0, sizeof(IterScalars), s_));
@@ -569,6 +594,7 @@ void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
 int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
                   const double* C0_host, trm_stats* stats) {
   const auto t_start = std::chrono::steady_clock::now();
+  const long long launches0 = thread_launch_count();
   const size_t nm = (size_t)N_ * m_;
   if (C0_host)
     TRM_CUDA(cudaMemcpyAsync(C64_, C0_host, nm * 8, cudaMemcpyHostToDevice,
@@ -823,7 +849,7 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
     stats->rms_residual = std::sqrt(ss / m_);
     stats->max_residual = mx;
     stats->E_last = E_last;
-    stats->launches = launch_count();
+    stats->launches = thread_launch_count() - launches0;
     stats->seconds = std::chrono::duration<double>(
                          std::chrono::steady_clock::now() - t_start)
                          .count();

@@ -58,6 +58,9 @@ class Solver {
  public:
   Solver(int64_t N, int m, double tol, const trm_options& opt);
   ~Solver();
+  static size_t footprint(int64_t N, int m);
+  static size_t part_capacity(int64_t N, int m);
+  size_t device_bytes() const { return mem_.bytes(); }
 
   void init_stencil(int nx, int ny, int nz, int order, double h,
                     const double* V_host);

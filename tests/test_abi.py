@@ -72,3 +72,13 @@ def test_invalid_arguments_rejected_on_host(trm):
         trm.trm_create_csr(3, np.array([0, 1, 2, 3]), np.array([0, 5, 2]),
                            np.ones(3), 1, 1e-8)
     assert e.value.status == -1
+
+
+def test_footprint_estimate(trm):
+    """The admission estimate grows with N m and covers the N x m blocks the
+    solver keeps (92 bytes per entry across FP64, FP32 and pair copies)."""
+    a = trm.trm_footprint_bytes(4096, 16)
+    b = trm.trm_footprint_bytes(110592, 128)
+    assert 92 * 4096 * 16 < a < b
+    assert 92 * 110592 * 128 <= b < 130 * 110592 * 128
+    assert trm.trm_footprint_bytes(1, 1) == 0
