@@ -235,6 +235,7 @@ class ClockSampler:
 PROFILE_OF_CLASS = {
     "grad_f32": "k_mul_tc_grad_grid48_m128.md",
     "gram_f32": "k_gram_tc_line_grams_grid48_m128.md",
+    "spmm_f64": "k_stencil_df_mp2_grid48_m128.md",
 }
 
 
@@ -264,7 +265,9 @@ def traffic_from_profile(cls):
             return None
         scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}[mm.group(2)]
         total += float(mm.group(1)) * scale
-    return {"bytes_per_launch": total, "source": "profiles/" + name}
+    ab = re.search(r"Algorithmic bytes of the captured launch: (\d+)", text)
+    return {"bytes_per_launch": total, "source": "profiles/" + name,
+            "algorithmic_bytes": int(ab.group(1)) if ab else None}
 
 
 # ---------------------------------------------------------------------------
@@ -293,14 +296,27 @@ def roofline(prof, peaks, src):
         e.update({"launches": cc["launches"], "avg_launch_ms": pl * 1e3})
         return e
 
+    def with_traffic(cname, e):
+        # DRAM bytes of the captured launch, scaled to this class's average
+        # launch by the ratio of algorithmic bytes (a class mixes launch
+        # sizes, e.g. the n = m and n = 3m Grams)
+        tr = traffic_from_profile(cname)
+        cc = classes[cname]
+        if tr and tr["algorithmic_bytes"] and cc["bytes"] > 0:
+            per = cc["bytes"] / cc["launches"]
+            e.update({"traffic": tr["bytes_per_launch"] * per / tr["algorithmic_bytes"],
+                      "traffic_captured": tr["bytes_per_launch"],
+                      "traffic_captured_algorithmic": tr["algorithmic_bytes"],
+                      "traffic_source": tr["source"]})
+        else:
+            e.update({"traffic": None, "traffic_source": None})
+        return e
+
     name = max(classes, key=lambda k: classes[k]["ms"])
-    r = entry(name, classes[name])
-    tr = traffic_from_profile(name)
+    r = with_traffic(name, entry(name, classes[name]))
     r.update({"kernel": name,
-              "traffic": tr["bytes_per_launch"] if tr else None,
-              "traffic_source": tr["source"] if tr else None,
               "share_of_timed": classes[name]["ms"] / sum(v["ms"] for v in classes.values())})
-    every = {k: entry(k, v) for k, v in classes.items()}
+    every = {k: with_traffic(k, entry(k, v)) for k, v in classes.items()}
     return r, every
 
 

@@ -78,13 +78,18 @@ __global__ void k_make_A0(int m, const double* __restrict__ Hp,
 //
 // m is padded to mp, a multiple of 32, with the identity, which changes
 // neither factor. Per panel p: (a) one warp factors the diagonal block
-// column by column, rows in registers, pivots by shuffles; (b) every row
+// column by column (right-looking), rows in registers: the pivot comes from
+// its lane by a shuffle, each finished column goes through shared memory
+// and every lane reads the entries it needs as broadcasts; (b) every row
 // below solves x L_pp^T = a (registers, reciprocal pivots from (a));
 // (c) all threads update the lower trailing triangle with 4 x 4 register
-// tiles. The inverse: (d) warp p inverts diagonal block p in registers;
-// (e) row-block by row-block, X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj through
-// a 32 x mp temporary. The working copy has leading dimension mp + 1. Linv
-// may be null (only R is written then).
+// tiles. The inverse: (d) warp p inverts diagonal block p by forward
+// substitution, one column of the inverse per lane in registers, rows of L
+// read as broadcasts; (e) row-block by row-block,
+// X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj through a 32 x mp temporary. The
+// working copy has leading dimension mp + 1. Linv may be null (only R is
+// written then). Every pivot chain step is a dependent sequence, so the
+// phases avoid shuffles and global loads inside it.
 //
 // S is read from memory, or (Bm != null) formed on the fly as
 // S = I + a (B + B^T) + a^2 Q with a = sc->alpha (the line step's overlap).
@@ -129,32 +134,48 @@ __device__ __forceinline__ double piv_sqrt(double t) {
 template <typename Tm>
 constexpr int chol_threads() { return 256; }
 
-template <typename Tm, bool dev>
-__global__ void __launch_bounds__(chol_threads<Tm>())
+// SM: the working copy lives in shared memory (a compile-time choice, so its
+// accesses compile to shared-memory instructions), else in gwork.
+template <typename Tm, bool dev, bool SM>
+__global__ void __launch_bounds__(chol_threads<Tm>(), 1)
     k_chol_inv(int m, const double* __restrict__ S, const double* __restrict__ Bm,
-               const double* __restrict__ Q, double* __restrict__ Linv,
-               double* __restrict__ R, IterScalars* sc, Tm* gwork,
-               int use_smem) {
+               const double* __restrict__ Q, const float* __restrict__ Bf,
+               const float* __restrict__ Qf, double* __restrict__ Linv,
+               double* __restrict__ R, IterScalars* sc, Tm* gwork) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
-  __shared__ Tm rdiag[32];  // 1 / L_cc of the current panel
+  __shared__ Tm rdiag[1024];  // 1 / L_cc, all columns (mp <= 1024)
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int mp = (m + 31) & ~31, ld = mp + 1, P = mp >> 5;
-  Tm* a = use_smem ? reinterpret_cast<Tm*>(smraw) : gwork;
+  Tm* a = SM ? reinterpret_cast<Tm*>(smraw) : gwork;
   Tm* tb = a + (size_t)mp * ld;  // 32 x mp, leading dimension 33
   const Tm one = dev ? (Tm)1 : (Tm)0;
   const Tm eps = sizeof(Tm) == 4 ? (Tm)1.2e-7 : (Tm)2.3e-16;
-  if (Bm) {
+  if (Bm || Bf) {
     // half of a (B + B^T) + a^2/2 (Q + Q^T) from each triangle, read in
-    // column order, then the lower triangle adds its mirror
+    // column order (four loads of each matrix in flight per thread), then
+    // the lower triangle adds its mirror. With FP32 copies of B and Q (Bf,
+    // Qf) the FP32 factorisation does no FP64 work here.
     const double al = sc->alpha;
+    const double hq = 0.5 * al * al;
+    const float alf = (float)al, hqf = (float)hq;
     for (int k = warp; k < mp; k += nw)
-      for (int i = lane; i < mp; i += 32)
-        a[i + k * ld] =
-            (i < m && k < m)
-                ? (Tm)(al * Bm[i + k * m] + 0.5 * al * al * Q[i + k * m])
-                : (Tm)0;
+      for (int i0 = lane; i0 < mp; i0 += 128) {
+        Tm t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          const bool in = i < m && k < m;
+          if (Bf)
+            t[u] = in ? (Tm)(alf * Bf[i + k * m] + hqf * Qf[i + k * m]) : (Tm)0;
+          else
+            t[u] = in ? (Tm)(al * Bm[i + k * m] + hq * Q[i + k * m]) : (Tm)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i0 + 32 * u < mp) a[(i0 + 32 * u) + k * ld] = t[u];
+      }
     __syncthreads();
     for (int k = warp; k < mp; k += nw)
       for (int i = k + lane; i < mp; i += 32)
@@ -209,16 +230,14 @@ __global__ void __launch_bounds__(chol_threads<Tm>())
         }
         if (lane == c) v[c] = piv;
         if (lane > c) v[c] *= rl;
-        if (lane == 0) rdiag[c] = rl;
-        // constant trip count (k > c folds away once c is unrolled), so the
-        // row stays in registers
+        if (lane == 0) rdiag[c0 + c] = rl;
+        // update of the later columns (constant trip count: k > c folds away
+        // once c is unrolled, so the row stays in registers). Lanes above
+        // the diagonal update too: their entries are never read, and no
+        // predicate sits in the pivot chain.
 #pragma unroll
-        for (int k = 1; k < 32; ++k) {
-          if (k > c) {
-            const Tm lkc = __shfl_sync(0xffffffffu, v[c], k);
-            if (lane >= k) v[k] -= v[c] * lkc;
-          }
-        }
+        for (int k = 1; k < 32; ++k)
+          if (k > c) v[k] -= v[c] * __shfl_sync(0xffffffffu, v[c], k);
       }
 #pragma unroll
       for (int k = 0; k < 32; ++k) a[r + (c0 + k) * ld] = v[k];
@@ -238,7 +257,7 @@ __global__ void __launch_bounds__(chol_threads<Tm>())
           if (k < c) s0 -= x[k] * a[(c0 + c) + (c0 + k) * ld];
           if (k + 1 < c) s1 -= x[k + 1] * a[(c0 + c) + (c0 + k + 1) * ld];
         }
-        x[c] = (s0 + s1) * rdiag[c];
+        x[c] = (s0 + s1) * rdiag[c0 + c];
       }
 #pragma unroll
       for (int c = 0; c < 32; ++c) a[r + (c0 + c) * ld] = x[c];
@@ -277,37 +296,33 @@ __global__ void __launch_bounds__(chol_threads<Tm>())
     __syncthreads();
   }
 
-  // (d) inverse of each diagonal block, one warp per block, rows in
-  // registers: for c descending, lane r > c forms
-  // X_rc = -(1/L_cc) sum_{k=c+1..r} X_rk L_kc, where X_rk (k > c) is already
-  // in its register and L_kc is still in lane k's register c.
+  // (d) inverse X = L_pp^{-1} of each diagonal block, one warp per block,
+  // in place, row by row: lane j forms X_ij = (delta_ij - sum_{k=j}^{i-1}
+  // L_ik X_kj) / L_ii from row i of L and its own column of X (rolled loops:
+  // code run once per launch would stall on instruction fetch). In
+  // deviation form (L = I + F, X = I + Y) the same recurrence reads
+  // y_jj = -f_jj / (1 + f_jj) and, for i > j,
+  // y_ij = -(f_ij + sum_{k=j}^{i-1} f_ik y_kj) / (1 + f_ii).
   for (int pb = warp; pb < P; pb += nw) {
-    const int c0 = 32 * pb;
-    const int r = c0 + lane;
-    Tm v[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = k <= lane ? a[r + (c0 + k) * ld] : (Tm)0;
-#pragma unroll
-    for (int c = 31; c >= 0; --c) {
-      const Tm lcc = __shfl_sync(0xffffffffu, v[c], c);
-      const Tm rc = piv_rcp(one + lcc);
-      Tm s0 = 0, s1 = 0;
-#pragma unroll
-      for (int k = 1; k < 32; ++k) {
-        if (k > c) {
-          const Tm lkc = __shfl_sync(0xffffffffu, v[c], k);
-          if (lane >= k) {
-            if ((k - c) & 1) s0 += v[k] * lkc;
-            else s1 += v[k] * lkc;
-          }
-        }
+    Tm* B = a + 32 * pb + (size_t)(32 * pb) * ld;  // block (i, k) at B[i + k ld]
+    const Tm* rd = rdiag + 32 * pb;
+    const int j = lane;
+    for (int i = 0; i < 32; ++i) {
+      Tm s0 = (dev && i > j) ? B[i + j * ld] : (Tm)0, s1 = 0;
+      int k = j;
+#pragma unroll 2
+      for (; k + 1 < i; k += 2) {
+        s0 += B[i + k * ld] * B[k + j * ld];
+        s1 += B[i + (k + 1) * ld] * B[(k + 1) + j * ld];
       }
-      if (lane == c) v[c] = dev ? -lcc * rc : rc;
-      else if (lane > c) v[c] = -rc * ((dev ? v[c] : (Tm)0) + s0 + s1);
+      if (k < i) s0 += B[i + k * ld] * B[k + j * ld];
+      Tm x = 0;
+      if (i == j) x = dev ? -B[i + i * ld] * rd[i] : rd[i];
+      else if (i > j) x = -(s0 + s1) * rd[i];
+      __syncwarp();  // row i of L is read by every lane before it is replaced
+      if (i >= j) B[i + j * ld] = x;
+      __syncwarp();
     }
-#pragma unroll
-    for (int k = 0; k < 32; ++k)
-      if (k <= lane) a[r + (c0 + k) * ld] = v[k];
   }
   __syncthreads();
   // (e) off-diagonal blocks, row-block by row-block: T = L_{i,0:i} X_{0:i,0:i}
@@ -324,6 +339,7 @@ __global__ void __launch_bounds__(chol_threads<Tm>())
 #pragma unroll
         for (int v = 0; v < 4; ++v)  // identity part of X (deviation form)
           acc[u][v] = dev ? a[(ri + r0 + u) + (cb + v) * ld] : (Tm)0;
+#pragma unroll 4
       for (int col = cb; col < ri; ++col) {
         Tm lr[4], xc[4];
 #pragma unroll
@@ -350,6 +366,7 @@ __global__ void __launch_bounds__(chol_threads<Tm>())
 #pragma unroll
         for (int v = 0; v < 4; ++v)
           acc[u][v] = dev ? tb[(r0 + u) + (cb + v) * 33] : (Tm)0;
+#pragma unroll 4
       for (int q = 0; q <= r0 + 3; ++q) {
         Tm xr[4], tv[4];
 #pragma unroll
@@ -371,26 +388,37 @@ __global__ void __launch_bounds__(chol_threads<Tm>())
   }
   const int isbad = bad;
   // Linv(i, k) column by column, then R(k, i) = Linv(i, k) column by column
-  if (Linv)
-    for (int k = warp; k < m; k += nw)
-      for (int i = lane; i < m; i += 32) {
-        double v;
-        if (isbad)
-          v = (i == k) ? 1.0 : 0.0;
-        else
-          v = (dev && i == k ? 1.0 : 0.0) +
-              (i >= k ? (double)a[i + k * ld] : 0.0);
-        Linv[i + k * m] = v;
-      }
-  for (int i = warp; i < m; i += nw)
-    for (int k = lane; k < m; k += 32) {
-      double v;
-      if (isbad)
-        v = (i == k) ? 1.0 : 0.0;
-      else
-        v = (dev && i == k ? 1.0 : 0.0) + (i >= k ? (double)a[i + k * ld] : 0.0);
-      R[k + i * m] = v;
+  // (FP64 work only where it is needed: a conversion per lower-triangle
+  // entry, the identity added on the diagonal alone)
+  // (four entries per thread in flight; an FP64 conversion per
+  // lower-triangle entry, the identity added on the diagonal alone)
+  auto entry = [&](int i, int k) -> double {
+    double v = 0.0;
+    if (isbad) {
+      if (i == k) v = 1.0;
+    } else if (i >= k) {
+      v = (double)a[i + k * ld];
+      if (dev && i == k) v += 1.0;
     }
+    return v;
+  };
+  for (int o = 0; o < (Linv ? 2 : 1); ++o) {
+    double* out = o ? Linv : R;
+    for (int k = warp; k < m; k += nw)  // column k of Linv, row k of R
+      for (int i0 = lane; i0 < m; i0 += 128) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          v[u] = i < m ? (o ? entry(i, k) : entry(k, i)) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          if (i < m) out[i + k * m] = v[u];
+        }
+      }
+  }
   if (tid == 0 && isbad && sc) sc->status |= 1;
 }
 
@@ -411,7 +439,8 @@ __global__ void __launch_bounds__(1024)
     k_line_terms(int m, const double* __restrict__ Hp,
                  const double* __restrict__ HD, const double* __restrict__ Bm,
                  const double* __restrict__ Q, const double* __restrict__ HPP,
-                 const double* __restrict__ W, double* __restrict__ part) {
+                 const double* __restrict__ W, double* __restrict__ part,
+                 float* __restrict__ Bf, float* __restrict__ Qf) {
   __shared__ Tm t0[32][33], t1[32][33], t2[32][33], t3[32][33];
   __shared__ double red[4 * 32];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -438,10 +467,15 @@ __global__ void __launch_bounds__(1024)
   if (i < m && j < m) {
     const int e = i + j * m;
     const Tm a0 = (Tm)0.5 * ((Tm)Hp[e] + t0[ty][tx]) + (i == j ? (Tm)HD[i] : (Tm)0);
-    const Tm s1 = (Tm)Bm[e] + t1[ty][tx];
+    const Tm bij = (Tm)Bm[e], qij = (Tm)Q[e];
+    if (Bf) {  // FP32 copies for the factorisation that follows
+      Bf[e] = (float)bij;
+      Qf[e] = (float)qij;
+    }
+    const Tm s1 = bij + t1[ty][tx];
     const Tm wij = (Tm)W[e], wji = t2[ty][tx];
     v2 = a0 * M - (Tm)0.5 * s1 * (wij + wji);
-    v1 = -(Tm)Q[e] * a0;
+    v1 = -qij * a0;
     if (i == j) {
       v0 = -wij;
       v1 += (Tm)HPP[e];
@@ -667,8 +701,9 @@ size_t chol_work_elems(int m) {
 
 template <typename Tm, bool dev>
 static void chol_launch(int m, const double* S, const double* Bm,
-                        const double* Q, double* Linv, double* R,
-                        IterScalars* sc, double* gwork, cudaStream_t s) {
+                        const double* Q, const float* Bf, const float* Qf,
+                        double* Linv, double* R, IterScalars* sc,
+                        double* gwork, cudaStream_t s) {
   if (m > 1024) throw Error(-1, "chol_inv: m > 1024");
   const size_t bytes = chol_work_elems(m) * sizeof(Tm);
   const bool smem = bytes <= 200 * 1024;
@@ -677,27 +712,33 @@ static void chol_launch(int m, const double* S, const double* Bm,
     int dv = 0;
     cudaGetDevice(&dv);
     if (dv < 0 || dv >= 64 || !done[dv].load(std::memory_order_relaxed)) {
-      TRM_CUDA(cudaFuncSetAttribute(k_chol_inv<Tm, dev>,
+      TRM_CUDA(cudaFuncSetAttribute(k_chol_inv<Tm, dev, true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     200 * 1024));
       if (dv >= 0 && dv < 64) done[dv].store(1, std::memory_order_relaxed);
     }
   }
-  k_chol_inv<Tm, dev><<<1, chol_threads<Tm>(), smem ? bytes : 0, s>>>(
-      m, S, Bm, Q, Linv, R, sc, reinterpret_cast<Tm*>(gwork), smem ? 1 : 0);
+  if (smem)
+    k_chol_inv<Tm, dev, true><<<1, chol_threads<Tm>(), bytes, s>>>(
+        m, S, Bm, Q, Bf, Qf, Linv, R, sc, nullptr);
+  else
+    k_chol_inv<Tm, dev, false><<<1, chol_threads<Tm>(), 0, s>>>(
+        m, S, Bm, Q, Bf, Qf, Linv, R, sc, reinterpret_cast<Tm*>(gwork));
   TRM_CHECK_LAUNCH();
 }
 
 template <typename Tm>
 void chol_inv(int m, const double* S, double* Linv, double* R, IterScalars* sc,
               double* gwork, cudaStream_t s) {
-  chol_launch<Tm, false>(m, S, nullptr, nullptr, Linv, R, sc, gwork, s);
+  chol_launch<Tm, false>(m, S, nullptr, nullptr, nullptr, nullptr, Linv, R,
+                         sc, gwork, s);
 }
 
 template <typename Tm>
 void chol_inv_dev(int m, const double* S, double* Linv, double* R,
                   IterScalars* sc, double* gwork, cudaStream_t s) {
-  chol_launch<Tm, true>(m, S, nullptr, nullptr, Linv, R, sc, gwork, s);
+  chol_launch<Tm, true>(m, S, nullptr, nullptr, nullptr, nullptr, Linv, R,
+                        sc, gwork, s);
 }
 
 template <typename Tm>
@@ -706,14 +747,24 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
                  double* Linv, double* R, IterScalars* sc, double* gwork,
                  double* part, bool dev, cudaStream_t s) {
   const int t = ceil_div(m, 32);
-  k_line_terms<Tm><<<dim3(t, t), 1024, 0, s>>>(m, Hp, HD, Bm, Q, HPP, W, part);
+  // FP32 factorisations take B and Q as FP32 copies written by the line
+  // terms, placed after the factorisation's own FP32 working copy in gwork
+  // (gwork holds max(2 m^2, chol_work_elems(m)) doubles)
+  float* Bf = nullptr;
+  float* Qf = nullptr;
+  if (sizeof(Tm) == 4) {
+    Bf = reinterpret_cast<float*>(gwork) + chol_work_elems(m);
+    Qf = Bf + (size_t)m * m;
+  }
+  k_line_terms<Tm><<<dim3(t, t), 1024, 0, s>>>(m, Hp, HD, Bm, Q, HPP, W, part,
+                                                Bf, Qf);
   TRM_CHECK_LAUNCH();
   k_line_alpha<<<1, 256, 0, s>>>(m, part, t * t, sc);
   TRM_CHECK_LAUNCH();
   if (dev)
-    chol_launch<Tm, true>(m, nullptr, Bm, Q, Linv, R, sc, gwork, s);
+    chol_launch<Tm, true>(m, nullptr, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s);
   else
-    chol_launch<Tm, false>(m, nullptr, Bm, Q, Linv, R, sc, gwork, s);
+    chol_launch<Tm, false>(m, nullptr, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s);
 }
 
 template void chol_inv_dev<float>(int, const double*, double*, double*,

@@ -71,7 +71,7 @@ const char* const kClassNames[KC_COUNT] = {
 Profiler::~Profiler() {
   for (auto& r : pending_) {
     cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
+    if (!r.b_taken) cudaEventDestroy(r.b);
   }
   for (auto e : pool_) cudaEventDestroy(e);
 }
@@ -87,18 +87,34 @@ cudaEvent_t Profiler::get() {
   return e;
 }
 
+// Consecutive timed launches share one event: the end of one record is the
+// start of the next when no other kernel was launched on the thread and
+// nothing else was enqueued (cut()) in between, which halves the events
+// recorded in the timed region.
 void Profiler::begin(int, cudaStream_t s) {
   if (!on) return;
-  open_ = get();
-  TRM_CUDA(cudaEventRecord(open_, s));
+  if (last_ && s == last_s_ && thread_launch_count() == last_launch_ &&
+      !pending_.empty() && pending_.back().b == last_) {
+    pending_.back().b_taken = true;
+    open_ = last_;
+    open_shared_ = true;
+  } else {
+    open_ = get();
+    open_shared_ = false;
+    TRM_CUDA(cudaEventRecord(open_, s));
+  }
+  last_ = nullptr;
 }
 
 void Profiler::end(int k, double fl, double by, cudaStream_t s) {
   if (!on || !open_) return;
   cudaEvent_t b = get();
   TRM_CUDA(cudaEventRecord(b, s));
-  pending_.push_back({k, open_, b, fl, by});
+  pending_.push_back({k, open_, b, fl, by, false});
   open_ = nullptr;
+  last_ = b;
+  last_launch_ = thread_launch_count();
+  last_s_ = s;
 }
 
 void Profiler::resolve() {
@@ -111,12 +127,15 @@ void Profiler::resolve() {
     launches[r.k] += 1;
     flops[r.k] += r.flops;
     bytes[r.k] += r.bytes;
+    // a record releases its start event (its own, or the previous record's
+    // end, which it took over) and its end unless the next record took it
     pool_.push_back(r.a);
-    pool_.push_back(r.b);
+    if (!r.b_taken) pool_.push_back(r.b);
     ++done;
   }
   cudaGetLastError();
   pending_.erase(pending_.begin(), pending_.begin() + done);
+  if (pending_.empty()) last_ = nullptr;
 }
 
 void Profiler::reset() {
@@ -674,6 +693,7 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
     TRM_CUDA(cudaMemcpyAsync(&ring_[enq % kRing], sc_, sizeof(IterScalars),
                              cudaMemcpyDeviceToHost, s_));
     TRM_CUDA(cudaEventRecord(ev_[enq % kRing], s_));
+    prof.cut();
     ++enq;
   };
   auto drain = [&]() {  // wait for everything enqueued

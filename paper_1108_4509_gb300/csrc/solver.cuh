@@ -25,21 +25,30 @@ class Profiler {
   void end(int k, double flops, double bytes, cudaStream_t s);
   void resolve();  // the stream must be idle
   void reset();
+  // The next begin() records a fresh event (work other than kernel
+  // launches, e.g. a copy, was enqueued since the last end()).
+  void cut() { last_ = nullptr; }
   double ms[KC_COUNT] = {};
   long long launches[KC_COUNT] = {};
   double flops[KC_COUNT] = {};
   double bytes[KC_COUNT] = {};
 
  private:
+  // b_taken: b is also the next record's a (and is released with it).
   struct Rec {
     int k;
     cudaEvent_t a, b;
     double flops, bytes;
+    bool b_taken;
   };
   cudaEvent_t get();
   std::vector<Rec> pending_;
   std::vector<cudaEvent_t> pool_;
   cudaEvent_t open_ = nullptr;
+  bool open_shared_ = false;
+  cudaEvent_t last_ = nullptr;  // end event of the last record
+  long long last_launch_ = -1;  // thread launch count at that end
+  cudaStream_t last_s_ = nullptr;
 };
 
 // Device memory owned by one solver; freed in the destructor.
