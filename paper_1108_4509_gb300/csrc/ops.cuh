@@ -250,8 +250,11 @@ void chol_inv_dev(int m, const double* S, double* Linv, double* R,
                   IterScalars* sc, double* gwork, cudaStream_t s);
 // set diagonal of an m x m matrix to zero
 void zero_diag(int m, double* A, cudaStream_t s);
-// symmetric eigenproblem A = Z diag(w) Z^T (cyclic Jacobi, FP64), w
-// ascending; work: 2*m*m doubles; info (device int): sweeps or -1
+// symmetric eigenproblem A = Z diag(w) Z^T to FP64 accuracy (FP32 cyclic
+// Jacobi, FP64 refinement of the eigenvectors, FP64 Jacobi on the refined
+// projection), w ascending; work: sym_eig_work_doubles(m); info (device
+// int): sweeps of the closing FP64 Jacobi, or -1
+size_t sym_eig_work_doubles(int m);
 void sym_eig(int m, const double* A, double* w, double* Z, double* work,
              int* info, cudaStream_t s);
 

@@ -529,42 +529,56 @@ __global__ void k_line_alpha(int m, const double* __restrict__ part, int nparts,
 // (p, q) pairs are annihilated at once (columns, then rows, then Z). One CTA;
 // A lives in shared memory (leading dimension m + 1) when it fits, else in
 // the global work copy; Z accumulates in global memory, where its column
-// updates are contiguous.
+// updates are contiguous. T is the arithmetic type. Z starts from Z0 (FP64,
+// may be null for the identity), so Z = Z0 J. A rotation is skipped when
+// |a_pq| <= rot_tol (|a_pp| + |a_qq|) + abs_c ||A||_F (the second term sits
+// above the rounding noise of the arithmetic type, so the sweeps end); they
+// stop when one applied no rotation or the off-diagonal part is below
+// conv_tol of the whole (squared Frobenius norms).
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(1024)
-    k_jacobi(int m, double* __restrict__ Ag, double* __restrict__ Zw,
+    k_jacobi(int m, const double* __restrict__ Ain, T* __restrict__ Ag,
+             T* __restrict__ Zw, const double* __restrict__ Z0,
              double* __restrict__ w, double* __restrict__ Z, int* info,
-             int max_sweeps, int use_smem) {
+             int max_sweeps, T rot_tol, T abs_c, T conv_tol, int use_smem) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ double cs[512], sn[512];
+  __shared__ T cs[512], sn[512];
   __shared__ int pp[512], qq[512];
   __shared__ double red[2 * 32];
-  __shared__ int done;
+  __shared__ int done, rotated;
+  __shared__ T abs_tol;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int ld = use_smem ? m + 1 : m;
-  double* A = use_smem ? reinterpret_cast<double*>(smraw) : Ag;
-  if (use_smem)
-    for (int c = warp; c < m; c += nw)
-      for (int r = lane; r < m; r += 32) A[r + c * ld] = Ag[r + c * m];
+  T* A = use_smem ? reinterpret_cast<T*>(smraw) : Ag;
   for (int c = warp; c < m; c += nw)
-    for (int r = lane; r < m; r += 32) Zw[r + c * m] = (r == c) ? 1.0 : 0.0;
+    for (int r = lane; r < m; r += 32) A[r + c * ld] = (T)Ain[r + c * m];
+  for (int c = warp; c < m; c += nw)
+    for (int r = lane; r < m; r += 32)
+      Zw[r + c * m] = Z0 ? (T)Z0[r + c * m] : (r == c ? (T)1 : (T)0);
   const int M = m + (m & 1);
   const int np = M / 2;
   int sweeps = 0;
+  if (tid == 0) rotated = 1;
   __syncthreads();
   for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
     double v[2] = {0.0, 0.0};
     for (int c = warp; c < m; c += nw)
       for (int r = lane; r < m; r += 32) {
-        const double x = A[r + c * ld];
+        const double x = (double)A[r + c * ld];
         if (r == c)
           v[1] += x * x;
         else
           v[0] += x * x;
       }
     block_sum<2>(v, red);
-    if (tid == 0) done = (v[0] <= 1e-30 * (v[0] + v[1])) || sweep == max_sweeps;
+    if (tid == 0) {
+      done = (v[0] <= (double)conv_tol * (v[0] + v[1])) || !rotated ||
+             sweep == max_sweeps;
+      if (sweep == 0) abs_tol = (T)((double)abs_c * sqrt(v[0] + v[1]));
+      rotated = 0;  // before the barrier: the rounds below may set it
+    }
     __syncthreads();
     if (done) break;
     sweeps = sweep + 1;
@@ -574,21 +588,22 @@ __global__ void __launch_bounds__(1024)
         const int kb = M - 1 - k;
         const int b0 = 1 + ((kb - 1 + r) % (M - 1));
         const int p = min(a0, b0), q = max(a0, b0);
-        double c = 1.0, s = 0.0;
+        T c = 1, s = 0;
         if (q < m) {
-          const double apq = A[p + q * ld];
-          const double app = A[p + p * ld];
-          const double aqq = A[q + q * ld];
-          if (fabs(apq) > 1e-300 &&
-              fabs(apq) > 1e-18 * (fabs(app) + fabs(aqq))) {
-            const double th = (aqq - app) / (2.0 * apq);
-            double t;
-            if (fabs(th) > 1e150)
-              t = 0.5 / th;
+          const T apq = A[p + q * ld];
+          const T app = A[p + p * ld];
+          const T aqq = A[q + q * ld];
+          if (apq != (T)0 &&
+              fabs(apq) > rot_tol * (fabs(app) + fabs(aqq)) + abs_tol) {
+            const T th = (aqq - app) / ((T)2 * apq);
+            T t;
+            if (fabs(th) > (T)1e18)
+              t = (T)0.5 / th;
             else
-              t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
+              t = (th >= (T)0 ? (T)1 : (T)-1) / (fabs(th) + sqrt(th * th + (T)1));
+            c = (T)1 / sqrt(t * t + (T)1);
             s = t * c;
+            rotated = 1;
           }
         }
         cs[k] = c;
@@ -598,18 +613,18 @@ __global__ void __launch_bounds__(1024)
       }
       __syncthreads();
       for (int k = warp; k < np; k += nw) {  // A <- A J (columns p, q)
-        const double s = sn[k];
-        if (s == 0.0) continue;
-        const double c = cs[k];
-        double* ap = A + pp[k] * ld;
-        double* aq = A + qq[k] * ld;
+        const T s = sn[k];
+        if (s == (T)0) continue;
+        const T c = cs[k];
+        T* ap = A + pp[k] * ld;
+        T* aq = A + qq[k] * ld;
         for (int i0 = lane; i0 < m; i0 += 128) {
-          double x[4], y[4];
+          T x[4], y[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int i = i0 + 32 * u;
-            x[u] = i < m ? ap[i] : 0.0;
-            y[u] = i < m ? aq[i] : 0.0;
+            x[u] = i < m ? ap[i] : (T)0;
+            y[u] = i < m ? aq[i] : (T)0;
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -623,21 +638,21 @@ __global__ void __launch_bounds__(1024)
       }
       __syncthreads();
       for (int k = warp; k < np; k += nw) {  // A <- J^T A (rows), Z <- Z J
-        const double s = sn[k];
-        if (s == 0.0) continue;
-        const double c = cs[k];
+        const T s = sn[k];
+        if (s == (T)0) continue;
+        const T c = cs[k];
         const int p = pp[k], q = qq[k];
-        double* zp = Zw + p * m;
-        double* zq = Zw + q * m;
+        T* zp = Zw + p * m;
+        T* zq = Zw + q * m;
         for (int j0 = lane; j0 < m; j0 += 128) {
-          double x[4], y[4], u_[4], t_[4];
+          T x[4], y[4], u_[4], t_[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int jc = j0 + 32 * u;
-            x[u] = jc < m ? A[p + jc * ld] : 0.0;
-            y[u] = jc < m ? A[q + jc * ld] : 0.0;
-            u_[u] = jc < m ? zp[jc] : 0.0;
-            t_[u] = jc < m ? zq[jc] : 0.0;
+            x[u] = jc < m ? A[p + jc * ld] : (T)0;
+            y[u] = jc < m ? A[q + jc * ld] : (T)0;
+            u_[u] = jc < m ? zp[jc] : (T)0;
+            t_[u] = jc < m ? zq[jc] : (T)0;
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -656,16 +671,67 @@ __global__ void __launch_bounds__(1024)
   }
   // ascending order (stable on ties)
   for (int i = tid; i < m; i += nt) {
-    const double wi = A[i + i * ld];
+    const T wi = A[i + i * ld];
     int rank = 0;
     for (int j = 0; j < m; ++j) {
-      const double wj = A[j + j * ld];
+      const T wj = A[j + j * ld];
       rank += (wj < wi) || (wj == wi && j < i);
     }
-    w[rank] = wi;
-    for (int r = 0; r < m; ++r) Z[r + rank * m] = Zw[r + i * m];
+    w[rank] = (double)wi;
+    for (int r = 0; r < m; ++r) Z[r + rank * m] = (double)Zw[r + i * m];
   }
   if (tid == 0 && info) *info = done ? sweeps : -1;
+}
+
+// ---------------------------------------------------------------------------
+// One correction of an approximate eigenvector matrix X of a symmetric A, by
+// the refinement of Ogita and Aishima (2018), derived to first order from
+// (I + E)^T (X^T X) (I + E) = I and (I + E)^T (X^T A X) (I + E) diagonal:
+// with R = I - X^T X and S = X^T A X,
+//   lambda_i = s_ii / (1 - r_ii),
+//   e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)  if the two are
+//          further apart than delta = 2 (||S - diag(lambda)|| + ||A|| ||R||),
+//   e_ij = r_ij / 2 otherwise, and also where the first-order step would
+//          exceed 0.01 (inside a cluster only orthonormality is restored;
+//          the closing FP64 Jacobi separates the cluster),
+// and X <- X + X E. Frobenius norms stand for the 2-norms (a larger delta)
+// and max |lambda_i| for ||A||. One CTA; G = X^T X, S = X^T A X in, E out.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+    k_refine_eig(int m, const double* __restrict__ G,
+                 const double* __restrict__ S, double* __restrict__ E) {
+  __shared__ double lam[1024];
+  __shared__ double red[2 * 32];
+  __shared__ unsigned long long amax;  // max |lambda| (bits of a double >= 0)
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) amax = 0ull;
+  __syncthreads();
+  for (int i = tid; i < m; i += nt) {
+    lam[i] = S[i + (size_t)i * m] / G[i + (size_t)i * m];
+    // non-negative doubles order like their bit patterns
+    atomicMax(&amax, (unsigned long long)__double_as_longlong(fabs(lam[i])));
+  }
+  __syncthreads();
+  double v[2] = {0.0, 0.0};  // ||S - D||^2, ||R||^2
+  for (size_t e = tid; e < (size_t)m * m; e += nt) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    const double r = (i == j ? 1.0 : 0.0) - G[e];
+    const double d = S[e] - (i == j ? lam[i] : 0.0);
+    v[0] += d * d;
+    v[1] += r * r;
+  }
+  block_sum<2>(v, red);
+  const double anorm = __longlong_as_double((long long)amax);
+  const double delta = 2.0 * (sqrt(v[0]) + anorm * sqrt(v[1]));
+  for (size_t e = tid; e < (size_t)m * m; e += nt) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    const double r = (i == j ? 1.0 : 0.0) - G[e];
+    const double dl = lam[j] - lam[i];
+    const double num = S[e] + lam[j] * r;
+    E[e] = (i != j && fabs(dl) > delta && fabs(num) <= 0.01 * fabs(dl))
+               ? num / dl
+               : 0.5 * r;
+  }
 }
 
 }  // namespace
@@ -781,22 +847,76 @@ template void line_factor<double>(int, const double*, const double*,
                                   IterScalars*, double*, double*, bool,
                                   cudaStream_t);
 
+template <typename T>
+static void jacobi_launch(int m, const double* A, const double* Z0, double* w,
+                          double* Z, T* Aw, T* Zw, int* info, int max_sweeps,
+                          T rot_tol, T abs_c, T conv_tol, cudaStream_t s) {
+  const size_t bytes = (size_t)m * (m + 1) * sizeof(T);
+  const bool smem = bytes <= 200 * 1024;
+  if (smem) {
+    static std::atomic<int> done[64] = {};  // per device; any thread may launch
+    int dv = 0;
+    cudaGetDevice(&dv);
+    if (dv < 0 || dv >= 64 || !done[dv].load(std::memory_order_relaxed)) {
+      TRM_CUDA(cudaFuncSetAttribute(k_jacobi<T>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
+      if (dv >= 0 && dv < 64) done[dv].store(1, std::memory_order_relaxed);
+    }
+  }
+  k_jacobi<T><<<1, 1024, smem ? bytes : 0, s>>>(m, A, Aw, Zw, Z0, w, Z, info,
+                                                max_sweeps, rot_tol, abs_c,
+                                                conv_tol, smem ? 1 : 0);
+  TRM_CHECK_LAUNCH();
+}
+
+size_t sym_eig_work_doubles(int m) { return (size_t)8 * m * m; }
+
+// FP32 Jacobi sweeps (the FP64 pipe is 1/64 of the FP32 one); then twice:
+// one FP64 refinement of the eigenvectors by matrix products on many CTAs,
+// and four Newton-Schulz steps X <- X (3 I - X^T X) / 2 (the refinement is
+// first order: where it splits close pairs it leaves X non-orthonormal by
+// the square of its step, and X^T A X would then not be similar to A; the
+// quadratically convergent steps bring that to FP64 rounding from up to
+// ~0.1); then FP64 Jacobi on X^T A X, nearly diagonal, which rotates
+// only the pairs still coupled above FP64 product noise (clusters) and
+// accumulates onto X.
 void sym_eig(int m, const double* A, double* w, double* Z, double* work,
              int* info, cudaStream_t s) {
   if (m > 1024) throw Error(-1, "sym_eig: m > 1024");
-  double* Aw = work;
-  double* Zw = work + (size_t)m * m;
-  TRM_CUDA(cudaMemcpyAsync(Aw, A, sizeof(double) * m * m,
-                           cudaMemcpyDeviceToDevice, s));
-  const size_t bytes = (size_t)m * (m + 1) * sizeof(double);
-  const bool smem = bytes <= 200 * 1024;
-  if (smem)
-    TRM_CUDA(cudaFuncSetAttribute(k_jacobi,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  200 * 1024));
-  k_jacobi<<<1, 1024, smem ? bytes : 0, s>>>(m, Aw, Zw, w, Z, info, 40,
-                                             smem ? 1 : 0);
-  TRM_CHECK_LAUNCH();
+  const size_t mm = (size_t)m * m;
+  double* X = work;
+  double* T = work + mm;
+  double* Sx = work + 2 * mm;
+  double* G = work + 3 * mm;
+  double* E = work + 4 * mm;
+  double* Xn = work + 5 * mm;
+  double* jw = work + 6 * mm;  // Jacobi work copies (2 m^2 of its type)
+  // FP32 sweeps until no coupling above 4e-7 of its pair's diagonal plus
+  // 1e-6 ||A||_F is left
+  jacobi_launch<float>(m, A, nullptr, w, X, reinterpret_cast<float*>(jw),
+                       reinterpret_cast<float*>(jw) + mm, info, 20, 4e-7f,
+                       1e-6f, 0.0f, s);
+  for (int it = 0; it < 2; ++it) {
+    mm_gemm(m, A, false, X, false, T, 1.0, 0.0, s, false);   // A X
+    mm_gemm(m, X, true, T, false, Sx, 1.0, 0.0, s, false);   // X^T A X
+    mm_gemm(m, X, true, X, false, G, 1.0, 0.0, s, false);    // X^T X
+    k_refine_eig<<<1, 1024, 0, s>>>(m, G, Sx, E);
+    TRM_CHECK_LAUNCH();
+    TRM_CUDA(cudaMemcpyAsync(Xn, X, mm * 8, cudaMemcpyDeviceToDevice, s));
+    mm_gemm(m, X, false, E, false, Xn, 1.0, 1.0, s, false);  // X + X E
+    std::swap(X, Xn);
+    for (int ns = 0; ns < 4; ++ns) {
+      mm_gemm(m, X, true, X, false, G, 1.0, 0.0, s, false);  // X^T X
+      TRM_CUDA(cudaMemcpyAsync(Xn, X, mm * 8, cudaMemcpyDeviceToDevice, s));
+      mm_gemm(m, X, false, G, false, Xn, -0.5, 1.5, s, false);  // 1.5 X - X G / 2
+      std::swap(X, Xn);
+    }
+  }
+  mm_gemm(m, A, false, X, false, T, 1.0, 0.0, s, false);
+  mm_gemm(m, X, true, T, false, Sx, 1.0, 0.0, s, false);
+  jacobi_launch<double>(m, Sx, X, w, Z, jw, jw + mm, info, 8, 1e-13, 1e-15,
+                        0.0, s);
 }
 
 template void chol_inv<float>(int, const double*, double*, double*,

@@ -180,6 +180,7 @@ size_t Solver::footprint(int64_t N, int m) {
   const size_t nm = (size_t)N * m, mm = (size_t)m * m;
   size_t b = nm * (3 * 8 + 3 * 4 + 3 * 8 + 4 * 8);  // blocks
   b += mm * 8 * 13 + std::max(2 * mm, chol_work_elems(m)) * 8 + 4 * m * 8;
+  b += sym_eig_work_doubles(m) * 8;
   b += part_capacity(N, m) * 8 + sizeof(IterScalars) + 16;
   b += mul_tc_work_floats(m, m) * 4;
   b += (size_t)N * (8 + 4 + 4 + 8 + 4 + 8);  // diagonals, M, V
@@ -220,6 +221,7 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   R_ = d(mm);
   Z_ = d(mm);
   mmw_ = d(std::max(2 * mm, chol_work_elems(m)));
+  eigws_ = d(sym_eig_work_doubles(m));
   eigw_ = d(m);
   lam_ = d(m);
   res_ = d(m);
@@ -573,7 +575,7 @@ void Solver::rr_rotate_fp64() {
   b.count = 1;
   gram<double>(N_, m_, C64_, b, Hp_, part_, part_cap_, s_, &sc_->status);
   make_A0(m_, Hp_, nullptr, A0_, s_);
-  TRM_PROF(KC_EIG, 0.0, 0.0, sym_eig(m_, A0_, eigw_, Z_, mmw_, info_, s_));
+  TRM_PROF(KC_EIG, 0.0, 0.0, sym_eig(m_, A0_, eigw_, Z_, eigws_, info_, s_));
   const double nm = (double)N_ * m_;
   TRM_PROF(KC_ROT64, 2 * nm * m_, 16 * nm,
            mult(N_, m_, m_, C64_, Z_, C64n_, s_));
@@ -599,7 +601,7 @@ void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
   mm_gemm(m_, Linv_, false, Hp_, false, T1_, 1.0, 0.0, s_);
   mm_gemm(m_, T1_, false, Linv_, true, T2_, 1.0, 0.0, s_);
   make_A0(m_, T2_, nullptr, A0_, s_);
-  sym_eig(m_, A0_, lam_, Z_, mmw_, info_, s_);
+  sym_eig(m_, A0_, lam_, Z_, eigws_, info_, s_);
   mm_gemm(m_, R_, false, Z_, false, T1_, 1.0, 0.0, s_);
   mult(N_, m_, m_, C, T1_, Cfin, s_);
   mult(N_, m_, m_, X64_, T1_, Xfin, s_);

@@ -130,6 +130,7 @@ class Solver {
   void *Gb_[2] = {nullptr, nullptr}, *Pb_ = nullptr, *HPb_ = nullptr;
   // m x m (FP64)
   double *HD_, *Hp_, *A0_, *Bm_, *PG_, *T1_, *T2_, *S_, *Linv_, *R_, *mmw_,
+      *eigws_,
       *eigw_, *Z_, *lam_, *res_;
   int* info_;
   double* part_;

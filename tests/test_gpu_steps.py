@@ -274,6 +274,33 @@ def test_rayleigh_ritz(trm):
         trm.trm_destroy(h)
 
 
+@pytest.mark.parametrize("n,m", [(20, 58), (30, 230)])
+def test_rayleigh_ritz_degenerate_spectrum(trm, n, m):
+    """The 2-D Laplacian's spectrum is full of exactly degenerate pairs and
+    tight clusters. Rayleigh-Ritz on a mixed, scaled basis of its m lowest
+    eigenvectors must return those eigenvalues (dense diagonalisation of the
+    oracle's H) to FP64 accuracy, with an orthonormal C. m = 230 takes the
+    eigensolver's global-memory paths."""
+    shape, order = (n, n, 1), 2
+    H = op.grid_hamiltonian(shape, order, 1.0, None)
+    N = H.shape[0]
+    w, Vd = np.linalg.eigh(H.toarray())
+    assert w[m] - w[m - 1] > 1e-6  # the block ends at a gap
+    assert np.min(np.diff(w[:m])) < 1e-12  # and holds degenerate pairs
+    Q = np.linalg.qr(ti.random_block(m, m, seed=3))[0]
+    Cin = Vd[:, :m] @ Q * 1.3
+    h = _handle(trm, shape, order, None, m)
+    try:
+        cd = gu.to_dev(Cin)
+        lam, res = trm.trm_rayleigh_ritz(h, cd.data_ptr(), m)
+        C = gu.from_dev(cd)
+        assert np.max(np.abs(lam - w[:m])) < 1e-12
+        assert np.max(np.abs(C.T @ C - np.eye(m))) < 1e-12
+        assert np.max(res) < 1e-10
+    finally:
+        trm.trm_destroy(h)
+
+
 # ---------------------------------------------------------------------------
 # a5, a7: one step of Fig. TMFIG (FP64, full SP and MP2)
 # ---------------------------------------------------------------------------
