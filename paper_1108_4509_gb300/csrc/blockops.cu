@@ -33,15 +33,36 @@ __global__ void __launch_bounds__(256)
 }
 
 // out[j] = sum_chunks part[chunk*m + j]; optional total into *tot (one CTA)
-__global__ void k_colsum(const double* __restrict__ part, int chunks, int m,
-                         double* __restrict__ out, double* tot, int do_sqrt) {
+// out[j] = sum_c part[c m + j] (then sqrt when do_sqrt), *tot = sum_j out[j];
+// one CTA of 1024 threads, m <= 1024: warp w takes the 32 columns of group
+// w % G (G = ceil(m / 32); loads coalesced across columns) and the chunks
+// c = w / G (mod 32 / G); the slices are added in a fixed order.
+__global__ void __launch_bounds__(1024)
+    k_colsum(const double* __restrict__ part, int chunks, int m,
+             double* __restrict__ out, double* tot, int do_sqrt) {
+  __shared__ double sl_sum[1024];  // [slice][column], S m <= 1024
   __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = (m + 31) >> 5, S = 32 / G;
+  const int cg = warp % G, sl = warp / G;
+  const int j = 32 * cg + lane;
+  if (sl < S && j < m) {
+    double s0 = 0.0, s1 = 0.0;
+    int c = sl;
+    for (; c + S < chunks; c += 2 * S) {
+      s0 += part[(size_t)c * m + j];
+      s1 += part[(size_t)(c + S) * m + j];
+    }
+    if (c < chunks) s0 += part[(size_t)c * m + j];
+    sl_sum[sl * m + j] = s0 + s1;
+  }
+  __syncthreads();
   double t = 0.0;
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < chunks; ++c) s += part[(size_t)c * m + j];
+  for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
+    double s = sl_sum[jj];
+    for (int q = 1; q < S; ++q) s += sl_sum[q * m + jj];
     if (do_sqrt) s = sqrt(s);
-    out[j] = s;
+    out[jj] = s;
     t += s;
   }
   double v[1] = {t};
@@ -181,25 +202,7 @@ __global__ void k_cg_scalars(const double* __restrict__ part, int nparts,
 #pragma unroll
     for (int q = 0; q < 4; ++q) v[q] += part[(size_t)p * 4 + q];
   block_sum<4>(v, red);
-  if (threadIdx.x == 0) {
-    const double gg = v[0], gMg = v[1], gpMg = v[2], gPp = v[3];
-    sc->gg = gg;
-    sc->gMg = gMg;
-    sc->gpMg = gpMg;
-    sc->gPp = gPp;
-    sc->rms = sqrt(gg) / (2.0 * sqrt((double)m));
-    // gamma = tr((G - G_prev)^T M G) / tr(G_prev^T M G_prev), or 0 on a
-    // restart; the previous blocks are not read then.
-    double gamma = 0.0;
-    if (!sc->restart && sc->a_prev > 0.0) {
-      gamma = (gMg - gpMg) / sc->a_prev;
-      if (!(gMg + gamma * gPp > 0.0)) gamma = 0.0;  // keep a descent direction
-    }
-    sc->gamma = gamma;
-    sc->slope0 = gamma != 0.0 ? -(gMg + gamma * gPp) : -gMg;
-    sc->a_prev = gMg;
-    sc->restart = 0;
-  }
+  if (threadIdx.x == 0) cg_scalars(v, m, sc);
 }
 
 // P = M G + gamma P
@@ -532,10 +535,9 @@ void gradient(int64_t N, int m, const T* C, const T* Xp, const double* Hp,
     if (mul_tc_eligible(N, m, m, tw) && aligned16(C)) {
       if ((size_t)mul_tc_parts(N, m) * 4 > cap)
         throw Error(-2, "gradient: partials buffer too small");
-      const int nparts = mul_tc_grad(N, m, C, Hp, Xp, G, Gprev, Pprev, minv,
-                                     partials, *tw, s);
-      k_cg_scalars<<<1, 1024, 0, s>>>(partials, nparts, m, sc);
-      TRM_CHECK_LAUNCH();
+      // the kernel's last CTA forms the CG scalars from the per-CTA sums
+      mul_tc_grad(N, m, C, Hp, Xp, G, Gprev, Pprev, minv, partials, sc, *tw,
+                  s);
       return;
     }
   }

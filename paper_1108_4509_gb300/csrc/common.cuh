@@ -100,7 +100,31 @@ struct IterScalars {
   int restart;     // 1: next P uses gamma = 0
   int status;      // bit flags: 1 = overlap not positive definite
   int iter;
-  int pad;
+  unsigned grad_done;  // CTAs of the tensor-core gradient that have finished
 };
+
+// The Polak-Ribiere scalars from the four gradient sums
+// v = {tr(G^T G), tr(G^T M G), tr(G_prev^T M G), tr(G^T P_prev)}: gamma =
+// tr((G - G_prev)^T M G) / tr(G_prev^T M G_prev), or 0 on a restart (the
+// previous blocks are not read then) or where P would not be a descent
+// direction; the RMS residual ||G||_F / (2 sqrt(m)).
+__device__ __forceinline__ void cg_scalars(const double (&v)[4], int m,
+                                           IterScalars* sc) {
+  const double gg = v[0], gMg = v[1], gpMg = v[2], gPp = v[3];
+  sc->gg = gg;
+  sc->gMg = gMg;
+  sc->gpMg = gpMg;
+  sc->gPp = gPp;
+  sc->rms = sqrt(gg) / (2.0 * sqrt((double)m));
+  double gamma = 0.0;
+  if (!sc->restart && sc->a_prev > 0.0) {
+    gamma = (gMg - gpMg) / sc->a_prev;
+    if (!(gMg + gamma * gPp > 0.0)) gamma = 0.0;  // keep a descent direction
+  }
+  sc->gamma = gamma;
+  sc->slope0 = gamma != 0.0 ? -(gMg + gamma * gPp) : -gMg;
+  sc->a_prev = gMg;
+  sc->restart = 0;
+}
 
 }  // namespace trm

@@ -62,6 +62,7 @@ struct MulSmem {
   uint32_t tmem_base;
   int failed;
   double red[NEPI][4];
+  int last;  // kGrad: this CTA finished last
 };
 
 struct MulArgs {
@@ -76,6 +77,7 @@ struct MulArgs {
   const float* pprev;
   const float* minv;
   double* part;    // kGrad: 4 sums per CTA
+  IterScalars* scw;  // kGrad: the CG scalars (formed by the last CTA)
   const double* c64;  // kSplit64: Cn = (C64 + alpha P) diag(R) + Y M
   const float* p32;
   const double* R;
@@ -425,6 +427,43 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int w = 1; w < NEPI; ++w) t += sm->red[w][j];
           args.part[(size_t)blockIdx.x * 4 + j] = t;
         }
+        // the last CTA to finish forms the CG scalars (the fence orders
+        // this CTA's sums before its count)
+        __threadfence();
+        const unsigned prev = atomicAdd(&args.scw->grad_done, 1u);
+        sm->last = prev == gridDim.x - 1;
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(NEPI * 32) : "memory");
+      if (sm->last) {
+        __threadfence();
+        // fixed order: thread t sums the CTAs t, t + 256, ..., then warps
+        // by shuffles, then the warps in order (whichever CTA is last)
+        const int t = threadIdx.x - EPI0 * 32;
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int c = t; c < (int)gridDim.x; c += NEPI * 32)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) v[j] += __ldcg(&args.part[(size_t)c * 4 + j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1)
+            v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+        asm volatile("bar.sync 1, %0;" ::"n"(NEPI * 32) : "memory");
+        if (lane == 0)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) sm->red[warp - EPI0][j] = v[j];
+        asm volatile("bar.sync 1, %0;" ::"n"(NEPI * 32) : "memory");
+        if (t == 0) {
+          double tot[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            tot[j] = sm->red[0][j];
+#pragma unroll
+            for (int w = 1; w < NEPI; ++w) tot[j] += sm->red[w][j];
+          }
+          cg_scalars(tot, args.k, args.scw);
+          args.scw->grad_done = 0u;  // ready for the next launch
+        }
       }
     }
   }
@@ -528,10 +567,10 @@ void mul_tc_store(int64_t N, int k, int n, const float* A, const float* P,
 int mul_tc_grad(int64_t N, int m, const float* C, const double* Hp,
                 const float* Xp, float* G, const float* Gprev,
                 const float* Pprev, const float* minv, double* part,
-                const TcWork& tw, cudaStream_t s) {
+                IterScalars* sc, const TcWork& tw, cudaStream_t s) {
   MulArgs a{};
   a.N = N; a.k = m; a.n = m; a.out = G; a.xp = Xp; a.gprev = Gprev;
-  a.pprev = Pprev; a.minv = minv; a.part = part; a.err = tw.err;
+  a.pprev = Pprev; a.minv = minv; a.part = part; a.scw = sc; a.err = tw.err;
   int grid = 0;
   launch<kGrad>(a, C, nullptr, Hp, 0, tw.msplit, s, &grid);
   return grid;

@@ -152,11 +152,12 @@ void mul_tc_store(int64_t N, int k, int n, const float* A, const float* P,
                   const IterScalars* sc, const double* M, float* out,
                   const TcWork& tw, cudaStream_t s);
 // G = -2 (X' - C H') with the four Polak-Ribiere partial sums per CTA in
-// part; returns the number of records
+// part; the last CTA to finish forms the CG scalars in sc (cg_scalars).
+// Returns the number of records.
 int mul_tc_grad(int64_t N, int m, const float* C, const double* Hp,
                 const float* Xp, float* G, const float* Gprev,
                 const float* Pprev, const float* minv, double* part,
-                const TcWork& tw, cudaStream_t s);
+                IterScalars* sc, const TcWork& tw, cudaStream_t s);
 // Cn = (C64 + alpha P) diag(R) + (C32 + alpha P) (R - diag(R))
 void mul_tc_split64(int64_t N, int m, const float* C32, const float* P,
                     const double* C64, const IterScalars* sc, const double* R,

@@ -72,6 +72,38 @@ __global__ void k_make_A0(int m, const double* __restrict__ Hp,
 //   E(a) - E(0) = a tr(D1) + a^2 (tr(D2) - tr(S1 D1)).
 // ---------------------------------------------------------------------------
 
+// The step along P: minimiser of the parabola a tr(D1) + a^2 (tr(D2) -
+// tr(S1 D1)), bounded so that the RMS column change a ||P||_F / sqrt(m)
+// stays below 1; a restart is requested when P is not a descent direction.
+__device__ void line_alpha_block(int m, const double* __restrict__ part,
+                                 int nparts, IterScalars* sc, double* red) {
+  double v[4] = {0, 0, 0, 0};
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] += part[(size_t)p * 4 + q];
+  block_sum<4>(v, red);
+  if (threadIdx.x == 0) {
+    const double g0 = v[0];
+    const double c2 = v[1] - v[2];
+    const double qn = v[3];
+    double alpha = 0.0;
+    const double cap = qn > 0.0 ? sqrt((double)m / qn) : 0.0;
+    if (g0 < 0.0 && qn > 0.0) {
+      if (c2 > 0.0)
+        alpha = -g0 / (2.0 * c2);
+      else
+        alpha = sc->alpha_prev > 0.0 ? 2.0 * sc->alpha_prev : 0.5 * cap;
+      if (alpha > cap) alpha = cap;
+    } else {
+      sc->restart = 1;  // not a descent direction: restart CG next time
+    }
+    sc->alpha = alpha;
+    sc->alpha_prev = alpha > 0.0 ? alpha : sc->alpha_prev;
+    sc->c2 = c2;
+    sc->dE = alpha * g0 + alpha * alpha * c2;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Cholesky S = L L^T and L^{-1}, blocked in 32-column panels, one CTA of 256
 // threads. Writes Linv (lower) and R = L^{-T} (upper).
@@ -141,7 +173,8 @@ __global__ void __launch_bounds__(chol_threads<Tm>(), 1)
     k_chol_inv(int m, const double* __restrict__ S, const double* __restrict__ Bm,
                const double* __restrict__ Q, const float* __restrict__ Bf,
                const float* __restrict__ Qf, double* __restrict__ Linv,
-               double* __restrict__ R, IterScalars* sc, Tm* gwork) {
+               double* __restrict__ R, IterScalars* sc, Tm* gwork,
+               const double* __restrict__ lpart, int nlpart) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
   __shared__ Tm rdiag[1024];  // 1 / L_cc, all columns (mp <= 1024)
@@ -152,6 +185,11 @@ __global__ void __launch_bounds__(chol_threads<Tm>(), 1)
   Tm* tb = a + (size_t)mp * ld;  // 32 x mp, leading dimension 33
   const Tm one = dev ? (Tm)1 : (Tm)0;
   const Tm eps = sizeof(Tm) == 4 ? (Tm)1.2e-7 : (Tm)2.3e-16;
+  if (lpart) {  // the line step first (it sets sc->alpha)
+    __shared__ double lred[4 * 32];
+    line_alpha_block(m, lpart, nlpart, sc, lred);
+    __syncthreads();
+  }
   if (Bm || Bf) {
     // half of a (B + B^T) + a^2/2 (Q + Q^T) from each triangle, read in
     // column order (four loads of each matrix in flight per thread), then
@@ -491,39 +529,6 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// The step along P: minimiser of the parabola a tr(D1) + a^2 (tr(D2) -
-// tr(S1 D1)), bounded so that the RMS column change a ||P||_F / sqrt(m)
-// stays below 1; a restart is requested when P is not a descent direction.
-__global__ void k_line_alpha(int m, const double* __restrict__ part, int nparts,
-                             IterScalars* sc) {
-  __shared__ double red[4 * 32];
-  double v[4] = {0, 0, 0, 0};
-  for (int p = threadIdx.x; p < nparts; p += blockDim.x)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] += part[(size_t)p * 4 + q];
-  block_sum<4>(v, red);
-  if (threadIdx.x == 0) {
-    const double g0 = v[0];
-    const double c2 = v[1] - v[2];
-    const double qn = v[3];
-    double alpha = 0.0;
-    const double cap = qn > 0.0 ? sqrt((double)m / qn) : 0.0;
-    if (g0 < 0.0 && qn > 0.0) {
-      if (c2 > 0.0)
-        alpha = -g0 / (2.0 * c2);
-      else
-        alpha = sc->alpha_prev > 0.0 ? 2.0 * sc->alpha_prev : 0.5 * cap;
-      if (alpha > cap) alpha = cap;
-    } else {
-      sc->restart = 1;  // not a descent direction: restart CG next time
-    }
-    sc->alpha = alpha;
-    sc->alpha_prev = alpha > 0.0 ? alpha : sc->alpha_prev;
-    sc->c2 = c2;
-    sc->dE = alpha * g0 + alpha * alpha * c2;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Cyclic Jacobi with the round-robin ordering: in each round m/2 disjoint
 // (p, q) pairs are annihilated at once (columns, then rows, then Z). One CTA;
@@ -769,7 +774,8 @@ template <typename Tm, bool dev>
 static void chol_launch(int m, const double* S, const double* Bm,
                         const double* Q, const float* Bf, const float* Qf,
                         double* Linv, double* R, IterScalars* sc,
-                        double* gwork, cudaStream_t s) {
+                        double* gwork, cudaStream_t s,
+                        const double* lpart = nullptr, int nlpart = 0) {
   if (m > 1024) throw Error(-1, "chol_inv: m > 1024");
   const size_t bytes = chol_work_elems(m) * sizeof(Tm);
   const bool smem = bytes <= 200 * 1024;
@@ -786,10 +792,11 @@ static void chol_launch(int m, const double* S, const double* Bm,
   }
   if (smem)
     k_chol_inv<Tm, dev, true><<<1, chol_threads<Tm>(), bytes, s>>>(
-        m, S, Bm, Q, Bf, Qf, Linv, R, sc, nullptr);
+        m, S, Bm, Q, Bf, Qf, Linv, R, sc, nullptr, lpart, nlpart);
   else
     k_chol_inv<Tm, dev, false><<<1, chol_threads<Tm>(), 0, s>>>(
-        m, S, Bm, Q, Bf, Qf, Linv, R, sc, reinterpret_cast<Tm*>(gwork));
+        m, S, Bm, Q, Bf, Qf, Linv, R, sc, reinterpret_cast<Tm*>(gwork), lpart,
+        nlpart);
   TRM_CHECK_LAUNCH();
 }
 
@@ -825,12 +832,13 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
   k_line_terms<Tm><<<dim3(t, t), 1024, 0, s>>>(m, Hp, HD, Bm, Q, HPP, W, part,
                                                 Bf, Qf);
   TRM_CHECK_LAUNCH();
-  k_line_alpha<<<1, 256, 0, s>>>(m, part, t * t, sc);
-  TRM_CHECK_LAUNCH();
+  // the factorisation kernel takes the line step from the partials first
   if (dev)
-    chol_launch<Tm, true>(m, nullptr, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s);
+    chol_launch<Tm, true>(m, nullptr, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s,
+                          part, t * t);
   else
-    chol_launch<Tm, false>(m, nullptr, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s);
+    chol_launch<Tm, false>(m, nullptr, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s,
+                           part, t * t);
 }
 
 template void chol_inv_dev<float>(int, const double*, double*, double*,
