@@ -78,6 +78,11 @@ typedef struct {
   int lag;              /* iterations the host may run ahead of the
                            convergence flags it has read; default 2 */
   void* stream;         /* cudaStream_t for all work; NULL = default stream */
+  int graphs;           /* 1 (default): after its first run, each kind of
+                           block iteration is captured once as a CUDA graph
+                           and replayed (fewer launch gaps; same kernels,
+                           same results); needs a non-NULL stream and is
+                           off while trm_profile is on. 0: plain launches */
 } trm_options;
 
 typedef struct {

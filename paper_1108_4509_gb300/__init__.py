@@ -40,7 +40,7 @@ class trm_options(ct.Structure):
                 ("max_iter", ct.c_int), ("seed", ct.c_uint64),
                 ("switch_tol", ct.c_double * 2), ("reorth_every", ct.c_int),
                 ("rr_every", ct.c_int), ("lag", ct.c_int),
-                ("stream", ct.c_void_p)]
+                ("stream", ct.c_void_p), ("graphs", ct.c_int)]
 
 
 class trm_stats(ct.Structure):

@@ -90,6 +90,7 @@ trm_status trm_default_options(trm_options* opt) {
   opt->reorth_every = 400;
   opt->rr_every = 0;
   opt->lag = 2;
+  opt->graphs = 1;
   opt->stream = nullptr;
   return TRM_OK;
 }

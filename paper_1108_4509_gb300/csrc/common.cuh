@@ -40,6 +40,10 @@ int sm_count();
 // Kernel launches issued by the library so far in this process.
 long long launch_count();
 long long thread_launch_count();  // launches by the calling host thread
+void count_launches(long long n);  // n kernels launched at once (a graph)
+// While sink is set, launches of the calling thread are counted into *sink
+// (kernels captured into a graph) instead of as launches.
+void capture_launches(long long* sink);
 // Message returned by trm_last_global_error() on this host thread.
 void set_global_error(const std::string& msg);
 

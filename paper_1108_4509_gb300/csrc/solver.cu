@@ -55,12 +55,22 @@ int sm_count() {
 namespace {
 std::atomic<long long> g_launches{0};
 thread_local long long t_launches = 0;  // launches issued by this host thread
+thread_local long long* t_capture = nullptr;  // kernels of a graph being captured
 }  // namespace
 
 void count_launch() {
+  if (t_capture) {  // captured into a graph: counted when the graph runs
+    ++*t_capture;
+    return;
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   ++t_launches;
 }
+void count_launches(long long n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
+void capture_launches(long long* sink) { t_capture = sink; }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 long long thread_launch_count() { return t_launches; }
 
@@ -248,6 +258,8 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
 Solver::~Solver() {
   if (s_) cudaStreamSynchronize(s_);
   else cudaDeviceSynchronize();
+  for (auto& g : graphs_)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (auto& e : ev_) cudaEventDestroy(e);
   if (ring_) cudaFreeHost(ring_);
 }
@@ -610,6 +622,78 @@ void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
 }
 
 // ---------------------------------------------------------------------------
+// Iteration graphs
+// ---------------------------------------------------------------------------
+void Solver::iter_state(void** st) const {
+  st[0] = C32_;
+  st[1] = C32n_;
+  st[2] = C64_;
+  st[3] = C64n_;
+  st[4] = Cdf_;
+  st[5] = Cdfn_;
+  st[6] = Gb_[0];
+  st[7] = Gb_[1];
+}
+
+void Solver::set_iter_state(void* const* st) {
+  C32_ = static_cast<float*>(st[0]);
+  C32n_ = static_cast<float*>(st[1]);
+  C64_ = static_cast<double*>(st[2]);
+  C64n_ = static_cast<double*>(st[3]);
+  Cdf_ = static_cast<float*>(st[4]);
+  Cdfn_ = static_cast<float*>(st[5]);
+  Gb_[0] = st[6];
+  Gb_[1] = st[7];
+}
+
+template <typename F>
+void Solver::run_iteration(int phase, F&& body) {
+  void* pre[kStatePtrs];
+  iter_state(pre);
+  int k = -1;
+  for (size_t i = 0; i < graphs_.size(); ++i)
+    if (graphs_[i].phase == phase &&
+        std::equal(pre, pre + kStatePtrs, graphs_[i].pre))
+      k = (int)i;
+  if (k < 0) {  // first run of this key: plain launches
+    IterGraph g{};
+    g.phase = phase;
+    std::copy(pre, pre + kStatePtrs, g.pre);
+    body();
+    iter_state(g.post);
+    graphs_.push_back(g);
+    return;
+  }
+  IterGraph& g = graphs_[k];
+  if (!g.exec) {  // second run: capture
+    long long nk = 0;
+    cudaGraph_t graph = nullptr;
+    TRM_CUDA(cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal));
+    capture_launches(&nk);
+    try {
+      body();
+    } catch (...) {
+      capture_launches(nullptr);
+      cudaStreamEndCapture(s_, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      throw;
+    }
+    capture_launches(nullptr);
+    TRM_CUDA(cudaStreamEndCapture(s_, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    TRM_CUDA(e);
+    g.kernels = nk;
+    iter_state(g.post);
+  } else {
+    set_iter_state(g.post);
+  }
+  TRM_CUDA(cudaGraphLaunch(g.exec, s_));
+  count_launches(g.kernels);
+}
+
+// ---------------------------------------------------------------------------
 // Fig. TMFIG with the precision ladder.
 // ---------------------------------------------------------------------------
 int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
@@ -671,26 +755,33 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
   const int stall_window = 250;
   const bool trace = std::getenv("TRM_TRACE") != nullptr;
 
+  const bool graphs = opt_.graphs && s_ != nullptr && !prof.on;
   auto enqueue_one = [&]() {
-    if (phase == PH_SP) {
-      float* G = static_cast<float*>(Gb_[0]);
-      float* Gp = static_cast<float*>(Gb_[1]);
-      iter_uniform<float, float>(C32_, C32n_, X32_, G, Gp,
-                                 static_cast<float*>(Pb_),
-                                 static_cast<float*>(HPb_));
-      Gb_[0] = G;
-      Gb_[1] = Gp;
-    } else if (phase == PH_FP64) {
-      double* G = static_cast<double*>(Gb_[0]);
-      double* Gp = static_cast<double*>(Gb_[1]);
-      iter_uniform<double, double>(C64_, C64n_, X64_, G, Gp,
-                                   static_cast<double*>(Pb_),
-                                   static_cast<double*>(HPb_));
-      Gb_[0] = G;
-      Gb_[1] = Gp;
-    } else {
-      iter_mp2();
-    }
+    auto body = [&]() {
+      if (phase == PH_SP) {
+        float* G = static_cast<float*>(Gb_[0]);
+        float* Gp = static_cast<float*>(Gb_[1]);
+        iter_uniform<float, float>(C32_, C32n_, X32_, G, Gp,
+                                   static_cast<float*>(Pb_),
+                                   static_cast<float*>(HPb_));
+        Gb_[0] = G;
+        Gb_[1] = Gp;
+      } else if (phase == PH_FP64) {
+        double* G = static_cast<double*>(Gb_[0]);
+        double* Gp = static_cast<double*>(Gb_[1]);
+        iter_uniform<double, double>(C64_, C64n_, X64_, G, Gp,
+                                     static_cast<double*>(Pb_),
+                                     static_cast<double*>(HPb_));
+        Gb_[0] = G;
+        Gb_[1] = Gp;
+      } else {
+        iter_mp2();
+      }
+    };
+    if (graphs)
+      run_iteration(phase, body);
+    else
+      body();
     n_phase[phase == PH_SP ? 0 : 1]++;
     TRM_CUDA(cudaMemcpyAsync(&ring_[enq % kRing], sc_, sizeof(IterScalars),
                              cudaMemcpyDeviceToHost, s_));

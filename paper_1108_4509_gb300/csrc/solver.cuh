@@ -98,6 +98,24 @@ class Solver {
   template <typename T, typename Tm>
   void iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP);
   void iter_mp2();
+  // CUDA graphs of block iterations. An iteration is a fixed kernel
+  // sequence given the phase and the block pointers it swaps, so a graph is
+  // keyed by both and remembers the pointers it leaves behind. The first
+  // run of a key is plain (one-time setup such as kernel attributes stays
+  // out of the capture), the second is captured, later ones replay it.
+  static constexpr int kStatePtrs = 8;
+  struct IterGraph {
+    int phase;
+    void* pre[kStatePtrs];
+    void* post[kStatePtrs];
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::vector<IterGraph> graphs_;
+  void iter_state(void** st) const;
+  void set_iter_state(void* const* st);
+  template <typename F>
+  void run_iteration(int phase, F&& body);
   void c64_to_df();
   void df_to_c64();
   void orth_fp64(double*& C, double*& Cn);

@@ -47,7 +47,10 @@ def test_status_strings(trm):
 def test_default_options(trm):
     o = trm.trm_default_options()
     assert o.precision == trm.TRM_MIXED and o.max_iter > 0 and o.lag >= 1
-    assert ct.sizeof(trm.trm_options) == 64
+    assert o.graphs == 1
+    # the C layout: 3 ints + pad, uint64, 2 doubles, 3 ints + pad, pointer,
+    # int + pad
+    assert ct.sizeof(trm.trm_options) == 72
 
 
 def test_invalid_arguments_rejected_on_host(trm):

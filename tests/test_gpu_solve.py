@@ -204,3 +204,29 @@ def test_grid48_full_size_vs_oracle_reference(trm):
     R = op.apply_h(H, C) - C * lam
     gap = g["lambda_m1"] - lam[-1]
     assert np.linalg.norm(R) / gap <= ANGLE_TOL, np.linalg.norm(R) / gap
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_graph_replay_same_bytes(trm, mode):
+    """On a side stream each kind of block iteration is captured once as a
+    CUDA graph and replayed; the solve must give the same bytes, iteration
+    counts and kernel counts as with plain launches, and agree with the
+    oracle's dense eigenvalues."""
+    torch = gu.torch_mod()
+    shape, order, m = (14, 13, 12), 4, 20
+    V = ti.gaussian_wells(shape, 6, seed=8)
+    H = op.grid_hamiltonian(shape, order, 1.0, V)
+    side = torch.cuda.Stream()
+    outs = []
+    for graphs in (0, 1):
+        with torch.cuda.stream(side):
+            outs.append(_solve(trm, shape, order, 1.0, V, m, 1e-10, seed=4,
+                               stream=side.cuda_stream, graphs=graphs,
+                               precision=getattr(trm, "TRM_" + mode)))
+        side.synchronize()
+    (lam0, eg0, C0, st0, s0), (lam1, eg1, C1, st1, s1) = outs
+    assert s0 == 0 and s1 == 0
+    assert np.array_equal(lam0, lam1) and eg0 == eg1 and np.array_equal(C0, C1)
+    assert st0["iterations"] == st1["iterations"]
+    assert st0["launches"] == st1["launches"]
+    _check(lam1, eg1, C1, op.lowest_eigenvalues(H, m))
