@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256)
 // partials) and the 8 sums are added in a fixed order.
 __global__ void __launch_bounds__(256)
     k_sum_splits(const double* __restrict__ part, int splits, size_t count,
-                 double* __restrict__ out) {
+                 double* __restrict__ out, float* __restrict__ out32) {
   __shared__ double red[8][33];
   const int el = threadIdx.x & 31, g = threadIdx.x >> 5;
   const size_t e = (size_t)blockIdx.x * 32 + el;
@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int q = 1; q < 8; ++q) t += red[q][el];
     out[e] = t;
+    if (out32) out32[e] = (float)t;
   }
 }
 
@@ -142,7 +143,8 @@ __global__ void __launch_bounds__(256)
 // is converted to FP64 once.
 __global__ void __launch_bounds__(256)
     k_sum_splits_pairs(const float* __restrict__ part, int splits,
-                       size_t count, double* __restrict__ out) {
+                       size_t count, double* __restrict__ out,
+                       float* __restrict__ out32) {
   __shared__ float rh[8][33], rl[8][33];
   const int el = threadIdx.x & 31, g = threadIdx.x >> 5;
   const size_t e = (size_t)blockIdx.x * 32 + el;
@@ -161,6 +163,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int q = 1; q < 8; ++q) t = df_add(t, F2{rh[q][el], rl[q][el]});
     out[e] = (double)t.h + (double)t.l;
+    if (out32) out32[e] = t.h;  // the sum rounded to FP32
   }
 }
 
@@ -188,26 +191,28 @@ size_t gram_partials_doubles(int64_t N, int m, int n) {
 }
 
 void sum_splits_pairs(const float* part, int splits, size_t count,
-                      double* out, cudaStream_t s) {
+                      double* out, cudaStream_t s, float* out32) {
   k_sum_splits_pairs<<<ceil_div(count, 32), 256, 0, s>>>(part, splits, count,
-                                                         out);
+                                                         out, out32);
   TRM_CHECK_LAUNCH();
 }
 
 void sum_splits(const double* part, int splits, size_t count, double* out,
                 cudaStream_t s) {
-  k_sum_splits<<<ceil_div(count, 32), 256, 0, s>>>(part, splits, count, out);
+  k_sum_splits<<<ceil_div(count, 32), 256, 0, s>>>(part, splits, count, out,
+                                                   nullptr);
   TRM_CHECK_LAUNCH();
 }
 
 template <typename T>
 void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
-          double* partials, size_t partials_cap, cudaStream_t s, int* err) {
+          double* partials, size_t partials_cap, cudaStream_t s, int* err,
+          float* out32) {
   const int n = B.total();
   if (m <= 0 || n <= 0) return;
   if constexpr (sizeof(T) == 4) {
     if (gram_tc_eligible(N, m, B)) {  // tensor cores, FP32-class accuracy
-      gram_tc(N, m, A, B, out, partials, partials_cap, err, s);
+      gram_tc(N, m, A, B, out, partials, partials_cap, err, s, out32);
       return;
     }
   }
@@ -222,7 +227,7 @@ void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
   TRM_CHECK_LAUNCH();
   const size_t count = (size_t)m * n;
   k_sum_splits<<<ceil_div(count, 32), 256, 0, s>>>(partials, splits, count,
-                                                   out);
+                                                   out, out32);
   TRM_CHECK_LAUNCH();
 }
 
@@ -249,7 +254,7 @@ void gram_in_scratch(int64_t N, int m, const T* A, const Blocks<T>& B,
   TRM_CHECK_LAUNCH();
   const size_t count = (size_t)m * n;
   k_sum_splits<<<ceil_div(count, 32), 256, 0, s>>>(scratch, splits, count,
-                                                   out);
+                                                   out, nullptr);
   TRM_CHECK_LAUNCH();
 }
 
@@ -261,8 +266,10 @@ template void gram_in_scratch<double>(int64_t, int, const double*,
                                       size_t, cudaStream_t);
 
 template void gram<float>(int64_t, int, const float*, const Blocks<float>&,
-                          double*, double*, size_t, cudaStream_t, int*);
+                          double*, double*, size_t, cudaStream_t, int*,
+                          float*);
 template void gram<double>(int64_t, int, const double*, const Blocks<double>&,
-                           double*, double*, size_t, cudaStream_t, int*);
+                           double*, double*, size_t, cudaStream_t, int*,
+                           float*);
 
 }  // namespace trm

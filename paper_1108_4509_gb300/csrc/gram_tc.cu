@@ -308,7 +308,7 @@ size_t gram_tc_partials_doubles(int64_t N, int m, int n) {
 
 void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
              double* out, double* partials, size_t cap, int* err,
-             cudaStream_t s) {
+             cudaStream_t s, float* out32) {
   const int n = B.total();
   const int tiles_m = ceil_div(m, BM);
   const int tiles = tiles_m * ceil_div(n, BN);
@@ -335,7 +335,7 @@ void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
   TRM_CHECK_LAUNCH();
   const size_t count = (size_t)m * n;
   sum_splits_pairs(reinterpret_cast<const float*>(partials), splits, count,
-                   out, s);
+                   out, s, out32);
 }
 
 }  // namespace trm

@@ -93,23 +93,24 @@ struct Blocks {
 
 size_t gram_partials_doubles(int64_t N, int m, int n);
 // FP32 inputs go to the tensor-core kernel when gram_tc_eligible; err (device
-// int, may be null) receives bit 2 if one of its bounded waits gave up.
+// int, may be null) receives bit 2 if one of its bounded waits gave up;
+// out32 (may be null) receives the result rounded to FP32 as well.
 template <typename T>
 void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
           double* partials, size_t partials_cap, cudaStream_t s,
-          int* err = nullptr);
+          int* err = nullptr, float* out32 = nullptr);
 void sum_splits(const double* part, int splits, size_t count, double* out,
                 cudaStream_t s);
 // the same for partials stored as FP32 pairs (hi, then lo, per split)
 void sum_splits_pairs(const float* part, int splits, size_t count,
-                      double* out, cudaStream_t s);
+                      double* out, cudaStream_t s, float* out32 = nullptr);
 // tcgen05 Gram of FP32 blocks (two-term TF32 split, three products, FP32
 // accumulation in tensor memory): needs N % 4 == 0, m >= 64, at most 3 B segments whose
 // widths are multiples of 128 when there are several.
 bool gram_tc_eligible(int64_t N, int m, const Blocks<float>& B);
 void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
              double* out, double* partials, size_t cap, int* err,
-             cudaStream_t s);
+             cudaStream_t s, float* out32 = nullptr);
 
 // Same product with the split partials in a caller-given scratch of
 // scratch_doubles doubles (fewer row slices when it is small); m*n must fit.
@@ -236,6 +237,11 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
                  const double* Q, const double* HPP, const double* W,
                  double* Linv, double* R, IterScalars* sc, double* gwork,
                  double* part, bool dev, cudaStream_t s);
+// line_factor<float> with the m x m inputs given in FP32 (Gram copies)
+void line_factor32(int m, const float* Hp, const double* HD, const float* Bm,
+                   const float* Q, const float* HPP, const float* W,
+                   double* Linv, double* R, IterScalars* sc, double* gwork,
+                   double* part, cudaStream_t s);
 // Elements (of the arithmetic type) of the factorisation workspace gwork.
 size_t chol_work_elems(int m);
 // S = L L^T (lower); writes Linv = L^{-1} (unless null) and R = L^{-T}. Non-PD sets
@@ -249,8 +255,9 @@ void chol_inv(int m, const double* S, double* Linv, double* R,
 template <typename Tm>
 void chol_inv_dev(int m, const double* S, double* Linv, double* R,
                   IterScalars* sc, double* gwork, cudaStream_t s);
-// set diagonal of an m x m matrix to zero
-void zero_diag(int m, double* A, cudaStream_t s);
+// set diagonal of an m x m matrix (and of its FP32 copy A32, may be null)
+// to zero
+void zero_diag(int m, double* A, cudaStream_t s, float* A32 = nullptr);
 // symmetric eigenproblem A = Z diag(w) Z^T to FP64 accuracy (FP32 cyclic
 // Jacobi, FP64 refinement of the eigenvectors, FP64 Jacobi on the refined
 // projection), w ascending; work: sym_eig_work_doubles(m); info (device

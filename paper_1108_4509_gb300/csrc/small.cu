@@ -45,9 +45,12 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-__global__ void k_zero_diag(int m, double* A) {
+__global__ void k_zero_diag(int m, double* A, float* A32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) A[i + (int64_t)i * m] = 0.0;
+  if (i < m) {
+    A[i + (int64_t)i * m] = 0.0;
+    if (A32) A32[i + (int64_t)i * m] = 0.f;
+  }
 }
 
 // A0 = sym(H') + diag(H_D): the projected matrix C^T H C when C^T C = I
@@ -472,12 +475,12 @@ __global__ void __launch_bounds__(chol_threads<Tm>(), 1)
 // to tr(A0 (B B^T - B^T B)) by cyclic invariance, so no m x m product is
 // stored.
 // ---------------------------------------------------------------------------
-template <typename Tm>
+template <typename Tm, typename Tin>
 __global__ void __launch_bounds__(1024)
-    k_line_terms(int m, const double* __restrict__ Hp,
-                 const double* __restrict__ HD, const double* __restrict__ Bm,
-                 const double* __restrict__ Q, const double* __restrict__ HPP,
-                 const double* __restrict__ W, double* __restrict__ part,
+    k_line_terms(int m, const Tin* __restrict__ Hp,
+                 const double* __restrict__ HD, const Tin* __restrict__ Bm,
+                 const Tin* __restrict__ Q, const Tin* __restrict__ HPP,
+                 const Tin* __restrict__ W, double* __restrict__ part,
                  float* __restrict__ Bf, float* __restrict__ Qf) {
   __shared__ Tm t0[32][33], t1[32][33], t2[32][33], t3[32][33];
   __shared__ double red[4 * 32];
@@ -752,8 +755,8 @@ void mm_gemm(int m, const double* A, bool trA, const double* B, bool trB,
   TRM_CHECK_LAUNCH();
 }
 
-void zero_diag(int m, double* A, cudaStream_t s) {
-  k_zero_diag<<<ceil_div(m, 256), 256, 0, s>>>(m, A);
+void zero_diag(int m, double* A, cudaStream_t s, float* A32) {
+  k_zero_diag<<<ceil_div(m, 256), 256, 0, s>>>(m, A, A32);
   TRM_CHECK_LAUNCH();
 }
 
@@ -829,8 +832,8 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
     Bf = reinterpret_cast<float*>(gwork) + chol_work_elems(m);
     Qf = Bf + (size_t)m * m;
   }
-  k_line_terms<Tm><<<dim3(t, t), 1024, 0, s>>>(m, Hp, HD, Bm, Q, HPP, W, part,
-                                                Bf, Qf);
+  k_line_terms<Tm, double><<<dim3(t, t), 1024, 0, s>>>(m, Hp, HD, Bm, Q, HPP,
+                                                        W, part, Bf, Qf);
   TRM_CHECK_LAUNCH();
   // the factorisation kernel takes the line step from the partials first
   if (dev)
@@ -839,6 +842,20 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
   else
     chol_launch<Tm, false>(m, nullptr, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s,
                            part, t * t);
+}
+
+// The FP32 path with the m x m inputs already in FP32 (copies the Gram sums
+// write): no FP64 conversion in the line terms or the factorisation.
+void line_factor32(int m, const float* Hp, const double* HD, const float* Bm,
+                   const float* Q, const float* HPP, const float* W,
+                   double* Linv, double* R, IterScalars* sc, double* gwork,
+                   double* part, cudaStream_t s) {
+  const int t = ceil_div(m, 32);
+  k_line_terms<float, float><<<dim3(t, t), 1024, 0, s>>>(
+      m, Hp, HD, Bm, Q, HPP, W, part, nullptr, nullptr);
+  TRM_CHECK_LAUNCH();
+  chol_launch<float, true>(m, nullptr, nullptr, nullptr, Bm, Q, Linv, R, sc,
+                           gwork, s, part, t * t);
 }
 
 template void chol_inv_dev<float>(int, const double*, double*, double*,

@@ -190,7 +190,7 @@ size_t Solver::footprint(int64_t N, int m) {
   const size_t nm = (size_t)N * m, mm = (size_t)m * m;
   size_t b = nm * (3 * 8 + 3 * 4 + 3 * 8 + 4 * 8);  // blocks
   b += mm * 8 * 13 + std::max(2 * mm, chol_work_elems(m)) * 8 + 4 * m * 8;
-  b += sym_eig_work_doubles(m) * 8;
+  b += sym_eig_work_doubles(m) * 8 + 5 * mm * 4;
   b += part_capacity(N, m) * 8 + sizeof(IterScalars) + 16;
   b += mul_tc_work_floats(m, m) * 4;
   b += (size_t)N * (8 + 4 + 4 + 8 + 4 + 8);  // diagonals, M, V
@@ -232,6 +232,9 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   Z_ = d(mm);
   mmw_ = d(std::max(2 * mm, chol_work_elems(m)));
   eigws_ = d(sym_eig_work_doubles(m));
+  Hp32_ = f(mm);
+  Bm32_ = f(mm);
+  PG32_ = f(3 * mm);
   eigw_ = d(m);
   lam_ = d(m);
   res_ = d(m);
@@ -436,9 +439,14 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   bx.p[0] = X;
   bx.cols = m_;
   bx.count = 1;
+  // FP32 phases also get FP32 copies of the m x m Gram results
+  float* const hp32 = sizeof(T) == 4 ? Hp32_ : nullptr;
+  float* const bm32 = sizeof(T) == 4 ? Bm32_ : nullptr;
+  float* const pg32 = sizeof(T) == 4 ? PG32_ : nullptr;
   TRM_PROF(kgr, 2 * m2N, 2 * es * nm,
-           gram<T>(N_, m_, C, bx, Hp_, part_, part_cap_, s_, &sc_->status));        // (6)
-  if (sizeof(T) == 4) zero_diag(m_, Hp_, s_);
+           gram<T>(N_, m_, C, bx, Hp_, part_, part_cap_, s_, &sc_->status,
+                   hp32));                                            // (6)
+  if (sizeof(T) == 4) zero_diag(m_, Hp_, s_, hp32);
   TRM_PROF(kgd, 2 * m2N, 5 * es * nm,
            gradient<T>(N_, m_, C, X, Hp_, G, Gp, P, minv, sc_, part_,
                        part_cap_, s_, &tw_));                         // (7)
@@ -450,7 +458,8 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   bp.cols = m_;
   bp.count = 1;
   TRM_PROF(kgr, 2 * m2N, 2 * es * nm,
-           gram<T>(N_, m_, C, bp, Bm_, part_, part_cap_, s_, &sc_->status));        // C^T P
+           gram<T>(N_, m_, C, bp, Bm_, part_, part_cap_, s_, &sc_->status,
+                   bm32));                                            // C^T P
   Blocks<T> b3;
   b3.p[0] = P;
   b3.p[1] = HP;
@@ -458,11 +467,16 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   b3.cols = m_;
   b3.count = 3;
   TRM_PROF(kgr, 6 * m2N, 4 * es * nm,
-           gram<T>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status));        // P^T[P HP G]
+           gram<T>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status,
+                   pg32));                                            // P^T[P HP G]
   const double m3 = md * md * md;
   prof.begin(KC_SMALL, s_);
-  line_factor<Tm>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, nullptr, R_,
-                  sc_, mmw_, T1_, sizeof(Tm) == 4, s_);     // alpha, Fig. ONFIG
+  if constexpr (sizeof(T) == 4 && sizeof(Tm) == 4)
+    line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, PG32_ + mm, PG32_ + 2 * mm,
+                  nullptr, R_, sc_, mmw_, T1_, s_);  // alpha, Fig. ONFIG
+  else
+    line_factor<Tm>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, nullptr,
+                    R_, sc_, mmw_, T1_, sizeof(Tm) == 4, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(krt, m2N, 3 * es * nm,
            (rotate<T, T>(N_, m_, C, P, R_, Cn, sc_, s_, &tw_)));  // (C+aP)L^-T
@@ -505,8 +519,9 @@ void Solver::iter_mp2() {
   bx.cols = m_;
   bx.count = 1;
   TRM_PROF(KC_GRAM32, 2 * m2N, 8 * dnm,
-           gram<float>(N_, m_, Ch, bx, Hp_, part_, part_cap_, s_, &sc_->status)); // (6)
-  zero_diag(m_, Hp_, s_);
+           gram<float>(N_, m_, Ch, bx, Hp_, part_, part_cap_, s_, &sc_->status,
+                       Hp32_));                                       // (6)
+  zero_diag(m_, Hp_, s_, Hp32_);
   TRM_PROF(KC_GRAD32, 2 * m2N, 20 * dnm,
            gradient<float>(N_, m_, Ch, X32_, Hp_, G, Gp, P, minv, sc_,
                            part_, part_cap_, s_, &tw_));      // (7)
@@ -518,7 +533,8 @@ void Solver::iter_mp2() {
   bp.cols = m_;
   bp.count = 1;
   TRM_PROF(KC_GRAM32, 2 * m2N, 8 * dnm,
-           gram<float>(N_, m_, Ch, bp, Bm_, part_, part_cap_, s_, &sc_->status));
+           gram<float>(N_, m_, Ch, bp, Bm_, part_, part_cap_, s_, &sc_->status,
+                       Bm32_));
   Blocks<float> b3;
   b3.p[0] = P;
   b3.p[1] = HP;
@@ -526,10 +542,11 @@ void Solver::iter_mp2() {
   b3.cols = m_;
   b3.count = 3;
   TRM_PROF(KC_GRAM32, 6 * m2N, 16 * dnm,
-           gram<float>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status));
+           gram<float>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status,
+                       PG32_));
   prof.begin(KC_SMALL, s_);
-  line_factor<float>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, nullptr, R_,
-                     sc_, mmw_, T1_, true, s_);
+  line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, PG32_ + mm, PG32_ + 2 * mm,
+                nullptr, R_, sc_, mmw_, T1_, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(KC_ROT32, m2N, 24 * dnm,
            rotate_split_df(N_, m_, Ch, Cl, P, R_, Cdfn_, Cdfn_ + nm, sc_, s_,

@@ -151,6 +151,8 @@ class Solver {
       *eigws_,
       *eigw_, *Z_, *lam_, *res_;
   int* info_;
+  // FP32 copies of H', B = C^T P and P^T [P HP G] (the Gram sums write them)
+  float *Hp32_ = nullptr, *Bm32_ = nullptr, *PG32_ = nullptr;
   double* part_;
   size_t part_cap_;
   IterScalars* sc_;
