@@ -100,6 +100,93 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same four grid points at a time (nx % 4 == 0): one thread owns points
+// x0..x0+3 of a row, loads the centre, the neighbouring quads along x and the
+// y/z neighbours as 16-byte (hi, lo) vectors, and takes the x neighbours
+// from registers, which cuts loads and boundary logic per point fourfold.
+template <int R>
+__global__ void __launch_bounds__(256)
+    k_stencil_df_v4(StencilOp st, int64_t N, const float* __restrict__ dh,
+                    const float* __restrict__ dl, const float* __restrict__ Ch,
+                    const float* __restrict__ Cl, float* __restrict__ Xh,
+                    float* __restrict__ Xl, int ncols) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= (N >> 2)) return;
+  const int nxv = st.nx >> 2;
+  const int xv = (int)(v % nxv);
+  const int64_t yz = v / nxv;
+  const int y = (int)(yz % st.ny);
+  const int z = (int)(yz / st.ny);
+  const int64_t i0 = v << 2;
+  const int64_t sy = st.nx, sz = (int64_t)st.nx * st.ny;
+  const bool xl = xv > 0, xr = xv + 1 < nxv;
+  const bool ym1 = y >= 1, yp1 = y + 1 < st.ny, zm1 = z >= 1,
+             zp1 = z + 1 < st.nz;
+  const bool ym2 = y >= 2, yp2 = y + 2 < st.ny, zm2 = z >= 2,
+             zp2 = z + 2 < st.nz;
+  const float4 d4h = *reinterpret_cast<const float4*>(dh + i0);
+  const float4 d4l = *reinterpret_cast<const float4*>(dl + i0);
+  const float dH[4] = {d4h.x, d4h.y, d4h.z, d4h.w};
+  const float dL[4] = {d4l.x, d4l.y, d4l.z, d4l.w};
+  const F2 c1 = {st.c1h, st.c1l}, c2 = {st.c2h, st.c2l};
+  auto ld = [](const float* p) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    return t;
+  };
+  auto add4 = [](Acc (&a)[4], const float4& h, const float4& l) {
+    a[0].add(h.x, l.x);
+    a[1].add(h.y, l.y);
+    a[2].add(h.z, l.z);
+    a[3].add(h.w, l.w);
+  };
+  const int cb = blockIdx.y * kCols;
+  for (int q = 0; q < kCols; ++q) {
+    const int c = cb + q;
+    if (c >= ncols) break;
+    const int64_t base = (int64_t)c * N + i0;
+    const float* ph = Ch + base;
+    const float* pl = Cl + base;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 ch = ld(ph), cl = ld(pl);
+    const float4 lh = xl ? ld(ph - 4) : zero, ll = xl ? ld(pl - 4) : zero;
+    const float4 rh = xr ? ld(ph + 4) : zero, rl = xr ? ld(pl + 4) : zero;
+    Acc s1[4], s2[4];
+    if (ym1) add4(s1, ld(ph - sy), ld(pl - sy));
+    if (yp1) add4(s1, ld(ph + sy), ld(pl + sy));
+    if (zm1) add4(s1, ld(ph - sz), ld(pl - sz));
+    if (zp1) add4(s1, ld(ph + sz), ld(pl + sz));
+    // x neighbours at distance 1: (l.w, c.x, c.y, c.z) and (c.y, c.z, c.w, r.x)
+    s1[0].add(lh.w, ll.w); s1[0].add(ch.y, cl.y);
+    s1[1].add(ch.x, cl.x); s1[1].add(ch.z, cl.z);
+    s1[2].add(ch.y, cl.y); s1[2].add(ch.w, cl.w);
+    s1[3].add(ch.z, cl.z); s1[3].add(rh.x, rl.x);
+    if (R == 2) {
+      if (ym2) add4(s2, ld(ph - 2 * sy), ld(pl - 2 * sy));
+      if (yp2) add4(s2, ld(ph + 2 * sy), ld(pl + 2 * sy));
+      if (zm2) add4(s2, ld(ph - 2 * sz), ld(pl - 2 * sz));
+      if (zp2) add4(s2, ld(ph + 2 * sz), ld(pl + 2 * sz));
+      // distance 2: (l.z, l.w, c.x, c.y) and (c.z, c.w, r.x, r.y)
+      s2[0].add(lh.z, ll.z); s2[0].add(ch.z, cl.z);
+      s2[1].add(lh.w, ll.w); s2[1].add(ch.w, cl.w);
+      s2[2].add(ch.x, cl.x); s2[2].add(rh.x, rl.x);
+      s2[3].add(ch.y, cl.y); s2[3].add(rh.y, rl.y);
+    }
+    const float cH[4] = {ch.x, ch.y, ch.z, ch.w};
+    const float cL[4] = {cl.x, cl.y, cl.z, cl.w};
+    float oh[4], ol[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      F2 r = df_mul(F2{dH[k], dL[k]}, F2{cH[k], cL[k]});
+      r = df_add(r, df_mul(c1, s1[k].get()));
+      if (R == 2) r = df_add(r, df_mul(c2, s2[k].get()));
+      oh[k] = r.h;
+      ol[k] = r.l;
+    }
+    *reinterpret_cast<float4*>(Xh + base) = make_float4(oh[0], oh[1], oh[2], oh[3]);
+    *reinterpret_cast<float4*>(Xl + base) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+  }
+}
+
 // X = H C for a CSR operator (values split into hi + lo at creation).
 __global__ void __launch_bounds__(256)
     k_csr_df(int64_t N, const int32_t* __restrict__ rowptr,
@@ -188,7 +275,20 @@ void apply_h_df(const Operator& op, const float* Ch, const float* Cl,
   const int gy = ceil_div(ncols, kCols);
   if (gy > 65535) throw Error(-1, "too many columns for one launch");
   dim3 grid(ceil_div(op.N, 256), gy);
-  if (op.kind == 0) {
+  const bool v4 = op.kind == 0 && op.st.nx % 4 == 0 && op.N % 4 == 0 &&
+                  ((reinterpret_cast<uintptr_t>(Ch) | reinterpret_cast<uintptr_t>(Cl) |
+                    reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl) |
+                    reinterpret_cast<uintptr_t>(op.diag32) |
+                    reinterpret_cast<uintptr_t>(op.diaglo)) & 15) == 0;
+  if (v4) {
+    dim3 g4(ceil_div(op.N / 4, 256), gy);
+    if (op.st.radius == 1)
+      k_stencil_df_v4<1><<<g4, 256, 0, s>>>(op.st, op.N, op.diag32, op.diaglo,
+                                            Ch, Cl, Xh, Xl, ncols);
+    else
+      k_stencil_df_v4<2><<<g4, 256, 0, s>>>(op.st, op.N, op.diag32, op.diaglo,
+                                            Ch, Cl, Xh, Xl, ncols);
+  } else if (op.kind == 0) {
     if (op.st.radius == 1)
       k_stencil_df<1><<<grid, 256, 0, s>>>(op.st, op.N, op.diag32, op.diaglo,
                                            Ch, Cl, Xh, Xl, ncols);
