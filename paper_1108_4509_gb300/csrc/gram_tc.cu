@@ -26,9 +26,12 @@
 // the bias is then at most 96 * 12 steps and nothing is folded.
 //
 // Warp roles (576 threads): warp 0 issues the TMA loads (one box of A and one
-// of B per 32-row stage, three stages in flight); warp 1 allocates tensor
-// memory and issues the MMAs from one thread; warps 2-9 split each stage in
-// place (half a line of A and of B each); warps 10-17 fold the finished
+// of B per 32-row stage into a ring of three raw stages); warp 1 allocates
+// tensor memory and issues the MMAs from one thread; warps 2-9 split each
+// raw stage into a ring of two operand stages (half a line of A and of B
+// each) and free the raw stage at once, so the loads run up to three stages
+// ahead of the split and are not held back by the MMAs (a DRAM round trip
+// under load is longer than one stage's MMAs); warps 10-17 fold the finished
 // chunks and write the partial as FP32 pairs (warp w owns TMEM lanes
 // 32 (w % 4) .. +31 and one 64-column half). No FP64 instruction runs here
 // (GB300's FP64 pipe is 1/64 of its FP32 rate). Every mbarrier wait is
@@ -53,20 +56,48 @@ using namespace tc;
 constexpr int BM = 128;        // output rows per CTA (columns of A)
 constexpr int BN = 128;        // output columns per CTA (columns of B)
 constexpr int BK = 32;         // block rows per stage (one 128-byte box)
-constexpr int STAGES = 3;
+constexpr int RSTAGES = 3;  // raw TMA stages
+constexpr int OSTAGES = 2;  // split operand stages
 constexpr int THREADS = 576;  // 18 warps
 constexpr int KC = 4;         // stages per accumulation chunk
 constexpr int kSingleChunk = 96;  // row slices this short are one chunk
 
 struct TcSmem {
-  // [stage][A hi, B hi, A lo, B lo][128 columns x 32 rows], 128-byte swizzle:
+  // [stage][A, B][128 columns x 32 rows] as loaded, and the split operands
+  // [stage][A hi, B hi, A lo, B lo] at the same offsets; 128-byte swizzle:
   // 16-byte chunk q of column c sits at chunk q ^ (c % 8).
-  float tile[STAGES][4][BM * BK];
-  uint64_t full[STAGES], conv[STAGES], empty[STAGES];
+  float raw[RSTAGES][2][BM * BK];
+  float op[OSTAGES][4][BM * BK];
+  uint64_t full[RSTAGES], rawfree[RSTAGES], opfull[OSTAGES], opfree[OSTAGES];
   uint64_t accfull[2], accempty[2], mmadone;
   uint32_t tmem_base;
   int failed;
 };
+
+// Split half of a 128-byte line (16 values) of a raw stage into TF32 hi and
+// lo terms at the same offsets of the operand buffers. Chunks are visited in
+// a bank-spread order.
+__device__ __forceinline__ void split_line_half(const float* raw, float* hi,
+                                                float* lo, int line,
+                                                int half) {
+  const float4* pr = reinterpret_cast<const float4*>(raw + line * 32);
+  float4* ph = reinterpret_cast<float4*>(hi + line * 32);
+  float4* pl = reinterpret_cast<float4*>(lo + line * 32);
+  float4 v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = pr[(half * 4 + j) ^ (line & 7)];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int q = (half * 4 + j) ^ (line & 7);
+    float4 h, o;
+    h.x = tf32_rna(v[j].x); o.x = tf32_rna(v[j].x - h.x);
+    h.y = tf32_rna(v[j].y); o.y = tf32_rna(v[j].y - h.y);
+    h.z = tf32_rna(v[j].z); o.z = tf32_rna(v[j].z - h.z);
+    h.w = tf32_rna(v[j].w); o.w = tf32_rna(v[j].w - h.w);
+    ph[q] = h;
+    pl[q] = o;
+  }
+}
 
 // K-major operand descriptor: 128-byte rows, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t kdesc(uint32_t saddr) {
@@ -107,10 +138,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   const CUtensorMap* mapB = seg == 0 ? &mapB0 : (seg == 1 ? &mapB1 : &mapB2);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < RSTAGES; ++s) {
       mbar_init(&sm->full[s], 1);
-      mbar_init(&sm->conv[s], 256);
-      mbar_init(&sm->empty[s], 1);
+      mbar_init(&sm->rawfree[s], 256);
+    }
+    for (int s = 0; s < OSTAGES; ++s) {
+      mbar_init(&sm->opfull[s], 256);
+      mbar_init(&sm->opfree[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm->accfull[b], 1);
@@ -133,20 +167,21 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       int issued = 0;
       for (int k = 0; k < nk; ++k) {
-        const int s = k % STAGES;
-        if (k >= STAGES && !mbar_wait(&sm->empty[s], ((k / STAGES) - 1) & 1,
-                                      args.err, &sm->failed))
+        const int s = k % RSTAGES;
+        if (k >= RSTAGES &&
+            !mbar_wait(&sm->rawfree[s], ((k / RSTAGES) - 1) & 1, args.err,
+                       &sm->failed))
           break;
         mbar_expect_tx(&sm->full[s], 2 * BM * BK * sizeof(float));
         const int x = (int)(rb + (int64_t)k * BK);
-        tma_load_2d(sm->tile[s][0], &mapA, x, i0, &sm->full[s]);
-        tma_load_2d(sm->tile[s][1], mapB, x, jb, &sm->full[s]);
+        tma_load_2d(sm->raw[s][0], &mapA, x, i0, &sm->full[s]);
+        tma_load_2d(sm->raw[s][1], mapB, x, jb, &sm->full[s]);
         ++issued;
       }
       // Before the CTA may exit, the copies it issued must have landed (they
       // already have unless a wait above gave up).
-      for (int k = issued > STAGES ? issued - STAGES : 0; k < issued; ++k)
-        mbar_wait_own(&sm->full[k % STAGES], (k / STAGES) & 1, args.err);
+      for (int k = issued > RSTAGES ? issued - RSTAGES : 0; k < issued; ++k)
+        mbar_wait_own(&sm->full[k % RSTAGES], (k / RSTAGES) & 1, args.err);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -154,7 +189,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       const int kcl = nk <= kSingleChunk ? nk : KC;  // stages per chunk
       for (int k = 0; k < nk && ok; ++k) {
-        const int s = k % STAGES;
+        const int s = k % OSTAGES;
         const int kc = k % kcl, c = k / kcl, b = c & 1;
         if (kc == 0 && c >= 2 &&
             !mbar_wait(&sm->accempty[b], ((c / 2) - 1) & 1, args.err,
@@ -162,16 +197,17 @@ __global__ void __launch_bounds__(THREADS, 1)
           ok = false;
           break;
         }
-        if (!mbar_wait(&sm->conv[s], (k / STAGES) & 1, args.err, &sm->failed)) {
+        if (!mbar_wait(&sm->opfull[s], (k / OSTAGES) & 1, args.err,
+                       &sm->failed)) {
           ok = false;
           break;
         }
         fence_after();
         const uint32_t d = tmem + (uint32_t)(b * BN);
-        const uint32_t aH = smem_u32(sm->tile[s][0]);
-        const uint32_t bH = smem_u32(sm->tile[s][1]);
-        const uint32_t aL = smem_u32(sm->tile[s][2]);
-        const uint32_t bL = smem_u32(sm->tile[s][3]);
+        const uint32_t aH = smem_u32(sm->op[s][0]);
+        const uint32_t bH = smem_u32(sm->op[s][1]);
+        const uint32_t aL = smem_u32(sm->op[s][2]);
+        const uint32_t bL = smem_u32(sm->op[s][3]);
         const uint32_t pa[3] = {aH, aH, aL};
         const uint32_t pb[3] = {bH, bL, bH};
 #pragma unroll
@@ -181,7 +217,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             mma_tf32(d, kdesc(pa[p] + kk * 32), kdesc(pb[p] + kk * 32),
                      kIdesc, (kc > 0 || p > 0 || kk > 0) ? 1u : 0u);
         }
-        mma_commit(&sm->empty[s]);  // stage reusable once these MMAs are done
+        mma_commit(&sm->opfree[s]);  // operands reusable once these MMAs are done
         if (kc == kcl - 1 || k == nk - 1) mma_commit(&sm->accfull[b]);
       }
       // every MMA of this thread completes before the TMEM is released
@@ -189,17 +225,24 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_wait_own(&sm->mmadone, 0, args.err);
     }
   } else if (warp < 10) {
-    // ---------------- in-place split ----------------
+    // ---------------- split: raw stage -> operand stage ----------------
     const int t = threadIdx.x - 64;  // 0..255: half a line of A and of B
     const int c_line = t >> 1, half = t & 1;
     for (int k = 0; k < nk; ++k) {
-      const int s = k % STAGES;
-      if (!mbar_wait(&sm->full[s], (k / STAGES) & 1, args.err, &sm->failed))
+      const int s = k % RSTAGES, o = k % OSTAGES;
+      if (!mbar_wait(&sm->full[s], (k / RSTAGES) & 1, args.err, &sm->failed))
         break;
-      split_half(sm->tile[s][0], sm->tile[s][2], c_line, half, false, 0.f);
-      split_half(sm->tile[s][1], sm->tile[s][3], c_line, half, false, 0.f);
+      if (k >= OSTAGES &&
+          !mbar_wait(&sm->opfree[o], ((k / OSTAGES) - 1) & 1, args.err,
+                     &sm->failed))
+        break;
+      split_line_half(sm->raw[s][0], sm->op[o][0], sm->op[o][2], c_line, half);
+      split_line_half(sm->raw[s][1], sm->op[o][1], sm->op[o][3], c_line, half);
+      // the raw reads before the next TMA write of this stage, the operand
+      // writes before the MMAs read them (both across the async proxy)
       fence_proxy_async();
-      mbar_arrive(&sm->conv[s]);
+      mbar_arrive(&sm->rawfree[s]);
+      mbar_arrive(&sm->opfull[o]);
     }
   } else {
     // ------- fold the chunks into the double-float sum, then write -------
