@@ -235,7 +235,8 @@ class ClockSampler:
 PROFILE_OF_CLASS = {
     "grad_f32": "k_mul_tc_grad_grid48_m128.md",
     "gram_f32": "k_gram_tc_line_grams_grid48_m128.md",
-    "spmm_f64": "k_stencil_df_mp2_grid48_m128.md",
+    "spmm_f64": "k_stencil_df_v4_mp2_grid48_m128.md",
+    "rotate_f32": "k_mul_tc_splitdf_mp2_grid48_m128.md",
 }
 
 
