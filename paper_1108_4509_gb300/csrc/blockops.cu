@@ -205,6 +205,42 @@ __global__ void k_cg_scalars(const double* __restrict__ part, int nparts,
   if (threadIdx.x == 0) cg_scalars(v, m, sc);
 }
 
+// FP32 blocks with N % 4 == 0: the same updates on 16-byte vectors.
+__device__ __forceinline__ float4 f4_fma(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z),
+                     fmaf(a, x.w, y.w));
+}
+__global__ void k_update_p4(int64_t N, const float4* __restrict__ G,
+                            float4* __restrict__ P,
+                            const float4* __restrict__ minv,
+                            const IterScalars* __restrict__ sc) {
+  const int j = blockIdx.y;
+  const float gamma = (float)sc->gamma;
+  const int64_t n4 = N >> 2, off = (int64_t)j * n4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float4 mg = G[off + i];
+    if (minv) {
+      const float4 w = minv[i];
+      mg = make_float4(w.x * mg.x, w.y * mg.y, w.z * mg.z, w.w * mg.w);
+    }
+    P[off + i] = gamma == 0.f ? mg : f4_fma(gamma, P[off + i], mg);
+  }
+}
+
+// X' = X - C diag(H_D), FP32, vectors of four (the FP32 copies are not
+// needed on this path)
+__global__ void k_xprime4(int64_t N, const float4* __restrict__ C,
+                          float4* __restrict__ X,
+                          const double* __restrict__ HD) {
+  const int j = blockIdx.y;
+  const float h = (float)HD[j];
+  const int64_t n4 = N >> 2, off = (int64_t)j * n4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x)
+    X[off + i] = f4_fma(-h, C[off + i], X[off + i]);
+}
+
 // P = M G + gamma P
 template <typename T>
 __global__ void k_update_p(int64_t N, const T* __restrict__ G, T* __restrict__ P,
@@ -517,6 +553,17 @@ void energy_from_dots(const double* dots, int chunks, int m, double* HD,
 template <typename T>
 void xprime(int64_t N, int m, const T* C, T* X, const double* HD, float* C32,
             float* Xp32, cudaStream_t s, bool write_x) {
+  if constexpr (sizeof(T) == 4) {
+    if (!C32 && !Xp32 && write_x && N % 4 == 0 &&
+        ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) &
+         15) == 0) {
+      k_xprime4<<<dim3(elem_grid_x(N), m), 256, 0, s>>>(
+          N, reinterpret_cast<const float4*>(C), reinterpret_cast<float4*>(X),
+          HD);
+      TRM_CHECK_LAUNCH();
+      return;
+    }
+  }
   k_xprime<T><<<dim3(elem_grid_x(N), m), 256, 0, s>>>(N, C, X, HD, C32, Xp32,
                                                       write_x ? 1 : 0);
   TRM_CHECK_LAUNCH();
@@ -554,6 +601,17 @@ void gradient(int64_t N, int m, const T* C, const T* Xp, const double* Hp,
 template <typename T>
 void update_p(int64_t N, int m, const T* G, T* P, const T* minv,
               const IterScalars* sc, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (N % 4 == 0 &&
+        ((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(P) |
+          reinterpret_cast<uintptr_t>(minv)) & 15) == 0) {
+      k_update_p4<<<dim3(elem_grid_x(N), m), 256, 0, s>>>(
+          N, reinterpret_cast<const float4*>(G), reinterpret_cast<float4*>(P),
+          reinterpret_cast<const float4*>(minv), sc);
+      TRM_CHECK_LAUNCH();
+      return;
+    }
+  }
   k_update_p<T><<<dim3(elem_grid_x(N), m), 256, 0, s>>>(N, G, P, minv, sc);
   TRM_CHECK_LAUNCH();
 }
