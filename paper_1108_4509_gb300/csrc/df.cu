@@ -214,20 +214,36 @@ __global__ void __launch_bounds__(256)
 
 constexpr int kRowChunk = 4096;  // rows per partial of the column dots
 
-// dots[chunk * m + j] = sum_{i in chunk} C_ij X_ij
+// dots[chunk * m + j] = sum_{i in chunk} C_ij X_ij (16-byte vectors when
+// N % 4 == 0 and the blocks are 16-byte aligned)
 __global__ void __launch_bounds__(256)
     k_coldot_df(int64_t N, int m, const float* __restrict__ Ch,
                 const float* __restrict__ Cl, const float* __restrict__ Xh,
-                const float* __restrict__ Xl, double* __restrict__ dots) {
+                const float* __restrict__ Xl, double* __restrict__ dots,
+                int vec) {
   __shared__ double red[32];
   const int j = blockIdx.y;
   const int64_t rb = (int64_t)blockIdx.x * kRowChunk;
   const int64_t re = min(N, rb + kRowChunk);
   const int64_t off = (int64_t)j * N;
   F2 acc = {0.f, 0.f};
-  for (int64_t i = rb + threadIdx.x; i < re; i += blockDim.x)
-    acc = df_add(acc, df_mul(F2{Ch[off + i], Cl[off + i]},
-                             F2{Xh[off + i], Xl[off + i]}));
+  if (vec) {
+    const float4* ch = reinterpret_cast<const float4*>(Ch + off);
+    const float4* cl = reinterpret_cast<const float4*>(Cl + off);
+    const float4* xh = reinterpret_cast<const float4*>(Xh + off);
+    const float4* xl = reinterpret_cast<const float4*>(Xl + off);
+    for (int64_t i = (rb >> 2) + threadIdx.x; i < (re >> 2); i += blockDim.x) {
+      const float4 a = ch[i], b = cl[i], c = xh[i], d = xl[i];
+      acc = df_add(acc, df_mul(F2{a.x, b.x}, F2{c.x, d.x}));
+      acc = df_add(acc, df_mul(F2{a.y, b.y}, F2{c.y, d.y}));
+      acc = df_add(acc, df_mul(F2{a.z, b.z}, F2{c.z, d.z}));
+      acc = df_add(acc, df_mul(F2{a.w, b.w}, F2{c.w, d.w}));
+    }
+  } else {
+    for (int64_t i = rb + threadIdx.x; i < re; i += blockDim.x)
+      acc = df_add(acc, df_mul(F2{Ch[off + i], Cl[off + i]},
+                               F2{Xh[off + i], Xl[off + i]}));
+  }
   double v[1] = {to_double(acc)};
   block_sum<1>(v, red);
   if (threadIdx.x == 0) dots[(size_t)blockIdx.x * m + j] = v[0];
@@ -247,6 +263,29 @@ __global__ void k_xprime_df(int64_t N, const float* __restrict__ Ch,
        i += (int64_t)gridDim.x * blockDim.x) {
     const F2 t = df_mul(F2{Ch[off + i], Cl[off + i]}, h);
     X32[off + i] = df_add(F2{Xh[off + i], Xl[off + i]}, t).h;
+  }
+}
+
+// The same on 16-byte vectors (N % 4 == 0, aligned blocks).
+__global__ void k_xprime_df4(int64_t N, const float4* __restrict__ Ch,
+                             const float4* __restrict__ Cl,
+                             const float4* __restrict__ Xh,
+                             const float4* __restrict__ Xl,
+                             const double* __restrict__ HD,
+                             float4* __restrict__ X32) {
+  const int j = blockIdx.y;
+  const F2 h = df_of(-HD[j]);
+  const int64_t n4 = N >> 2, off = (int64_t)j * n4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 a = Ch[off + i], b = Cl[off + i], c = Xh[off + i],
+                 d = Xl[off + i];
+    float4 o;
+    o.x = df_add(F2{c.x, d.x}, df_mul(F2{a.x, b.x}, h)).h;
+    o.y = df_add(F2{c.y, d.y}, df_mul(F2{a.y, b.y}, h)).h;
+    o.z = df_add(F2{c.z, d.z}, df_mul(F2{a.z, b.z}, h)).h;
+    o.w = df_add(F2{c.w, d.w}, df_mul(F2{a.w, b.w}, h)).h;
+    X32[off + i] = o;
   }
 }
 
@@ -307,7 +346,12 @@ void energy_diag_df(int64_t N, int m, const float* Ch, const float* Cl,
                     const float* Xh, const float* Xl, double* HD,
                     IterScalars* sc, double* partials, cudaStream_t s) {
   const int chunks = ceil_div(N, kRowChunk);
-  k_coldot_df<<<dim3(chunks, m), 256, 0, s>>>(N, m, Ch, Cl, Xh, Xl, partials);
+  const int vec = N % 4 == 0 &&
+                  ((reinterpret_cast<uintptr_t>(Ch) | reinterpret_cast<uintptr_t>(Cl) |
+                    reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl)) &
+                   15) == 0;
+  k_coldot_df<<<dim3(chunks, m), 256, 0, s>>>(N, m, Ch, Cl, Xh, Xl, partials,
+                                               vec);
   TRM_CHECK_LAUNCH();
   energy_from_dots(partials, chunks, m, HD, sc, s);
 }
@@ -317,6 +361,17 @@ void xprime_df(int64_t N, int m, const float* Ch, const float* Cl,
                cudaStream_t s) {
   int gx = ceil_div(N, 256 * 4);
   gx = gx < 1 ? 1 : (gx > 4096 ? 4096 : gx);
+  if (N % 4 == 0 &&
+      ((reinterpret_cast<uintptr_t>(Ch) | reinterpret_cast<uintptr_t>(Cl) |
+        reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl) |
+        reinterpret_cast<uintptr_t>(X32)) & 15) == 0) {
+    k_xprime_df4<<<dim3(gx, m), 256, 0, s>>>(
+        N, reinterpret_cast<const float4*>(Ch), reinterpret_cast<const float4*>(Cl),
+        reinterpret_cast<const float4*>(Xh), reinterpret_cast<const float4*>(Xl),
+        HD, reinterpret_cast<float4*>(X32));
+    TRM_CHECK_LAUNCH();
+    return;
+  }
   k_xprime_df<<<dim3(gx, m), 256, 0, s>>>(N, Ch, Cl, Xh, Xl, HD, X32);
   TRM_CHECK_LAUNCH();
 }
