@@ -112,10 +112,10 @@ __device__ void line_alpha_block(int m, const double* __restrict__ part,
 // threads. Writes Linv (lower) and R = L^{-T} (upper).
 //
 // m is padded to mp, a multiple of 32, with the identity, which changes
-// neither factor. Per panel p: (a) one warp factors the diagonal block
-// column by column (right-looking), rows in registers: the pivot comes from
-// its lane by a shuffle, each finished column goes through shared memory
-// and every lane reads the entries it needs as broadcasts; (b) every row
+// neither factor. Per panel p: (a) the eight warps factor the diagonal block
+// column by column (right-looking), four columns per warp in registers: the
+// owner of a column takes its pivot by a shuffle and publishes the column
+// through shared memory, and each warp updates its own columns; (b) every row
 // below solves x L_pp^T = a (registers, reciprocal pivots from (a));
 // (c) all threads update the lower trailing triangle with 4 x 4 register
 // tiles. The inverse: (d) warp p inverts diagonal block p by forward
@@ -238,50 +238,58 @@ __global__ void __launch_bounds__(chol_threads<Tm>(), 1)
 
   for (int p = 0; p < P; ++p) {
     const int c0 = 32 * p;
-    // (a) diagonal block: lane r holds row c0 + r in registers; pivots and
-    // column entries move between lanes by shuffles
-    if (warp == 0) {
+    // (a) diagonal block on all eight warps: warp w keeps columns w, w + 8,
+    // w + 16 and w + 24 of the block in registers (lane r = row c0 + r).
+    // For column c the owning warp forms the pivot and publishes the column
+    // through shared memory (two buffers, so one barrier per column); every
+    // warp then updates its own later columns. Lanes above the diagonal
+    // update too: those entries are never read.
+    {
+      __shared__ Tm colbuf[2][32];
       const int r = c0 + lane;
-      Tm v[32];
+      Tm v[4];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] = a[r + (c0 + k) * ld];
+      for (int q = 0; q < 4; ++q) v[q] = a[r + (c0 + warp + 8 * q) * ld];
       bool b = false;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        Tm d = __shfl_sync(0xffffffffu, v[c], c);
-        Tm piv, rl;  // L_cc - one and 1 / L_cc
-        if (dev) {
-          if (!(d > (Tm)-0.999)) {  // pivot 1 + d not positive: singular S
-            b = true;
-            d = (Tm)0;
+        const int q = c >> 3;
+        if (warp == (c & 7)) {
+          Tm d = __shfl_sync(0xffffffffu, v[q], c);
+          Tm piv, rl;  // L_cc - one and 1 / L_cc
+          if (dev) {
+            if (!(d > (Tm)-0.999)) {  // pivot 1 + d not positive: singular S
+              b = true;
+              d = (Tm)0;
+            }
+            piv = d * piv_rcp((Tm)1 + piv_sqrt((Tm)1 + d));
+            rl = piv_rcp((Tm)1 + piv);
+          } else {
+            // a pivot that has lost all but 4m roundings of its original
+            // diagonal entry marks a (numerically) singular S
+            const int cc = c0 + c;
+            const double sjj =
+                (Bm || Bf || cc >= m) ? 1.0 : fabs(S[cc + cc * m]);
+            if (!(d > (Tm)(4 * m) * eps * (Tm)sjj)) {
+              b = true;
+              d = (Tm)1;
+            }
+            piv = piv_sqrt(d);
+            rl = piv_rcp(piv);
           }
-          piv = d * piv_rcp((Tm)1 + piv_sqrt((Tm)1 + d));
-          rl = piv_rcp((Tm)1 + piv);
-        } else {
-          // a pivot that has lost all but 4m roundings of its original
-          // diagonal entry marks a (numerically) singular S
-          const int cc = c0 + c;
-          const double sjj = (Bm || cc >= m) ? 1.0 : fabs(S[cc + cc * m]);
-          if (!(d > (Tm)(4 * m) * eps * (Tm)sjj)) {
-            b = true;
-            d = (Tm)1;
-          }
-          piv = piv_sqrt(d);
-          rl = piv_rcp(piv);
+          if (lane == c) v[q] = piv;
+          if (lane > c) v[q] *= rl;
+          colbuf[c & 1][lane] = v[q];
+          if (lane == 0) rdiag[c0 + c] = rl;
         }
-        if (lane == c) v[c] = piv;
-        if (lane > c) v[c] *= rl;
-        if (lane == 0) rdiag[c0 + c] = rl;
-        // update of the later columns (constant trip count: k > c folds away
-        // once c is unrolled, so the row stays in registers). Lanes above
-        // the diagonal update too: their entries are never read, and no
-        // predicate sits in the pivot chain.
+        __syncthreads();
+        const Tm lrc = colbuf[c & 1][lane];
 #pragma unroll
-        for (int k = 1; k < 32; ++k)
-          if (k > c) v[k] -= v[c] * __shfl_sync(0xffffffffu, v[c], k);
+        for (int qq = 0; qq < 4; ++qq)
+          if (warp + 8 * qq > c) v[qq] -= lrc * colbuf[c & 1][warp + 8 * qq];
       }
 #pragma unroll
-      for (int k = 0; k < 32; ++k) a[r + (c0 + k) * ld] = v[k];
+      for (int q = 0; q < 4; ++q) a[r + (c0 + warp + 8 * q) * ld] = v[q];
       if (lane == 0 && b) bad = 1;
     }
     __syncthreads();
