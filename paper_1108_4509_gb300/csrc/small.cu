@@ -155,6 +155,17 @@ __device__ __forceinline__ double piv_rcp(double t) {
   r = fma(r, fma(-t, r, 1.0), r);
   return fma(r, fma(-t, r, 1.0), r);
 }
+// 1 / sqrt(t): the hardware reciprocal square root refined by Newton's step
+// r <- r (3 - t r^2) / 2, once in FP32, twice (from the FP32 seed) in FP64.
+__device__ __forceinline__ float piv_rsqrt(float t) {
+  const float r = rsqrtf(t);
+  return r * fmaf(-0.5f * t * r, r, 1.5f);
+}
+__device__ __forceinline__ double piv_rsqrt(double t) {
+  double r = (double)rsqrtf((float)t);
+  r = r * fma(-0.5 * t * r, r, 1.5);
+  return r * fma(-0.5 * t * r, r, 1.5);
+}
 __device__ __forceinline__ double piv_sqrt(double t) {
   double r = (double)rsqrtf((float)t);
   r = r * fma(-0.5 * t * r, r, 1.5);
@@ -256,14 +267,15 @@ __global__ void __launch_bounds__(chol_threads<Tm>(), 1)
         const int q = c >> 3;
         if (warp == (c & 7)) {
           Tm d = __shfl_sync(0xffffffffu, v[q], c);
-          Tm piv, rl;  // L_cc - one and 1 / L_cc
+          // 1 / L_cc is all the column needs: rsqrt(1 + d) (rsqrt(d)) on the
+          // pivot chain; L_cc itself is formed after the column is out
+          Tm rl;
           if (dev) {
             if (!(d > (Tm)-0.999)) {  // pivot 1 + d not positive: singular S
               b = true;
               d = (Tm)0;
             }
-            piv = d * piv_rcp((Tm)1 + piv_sqrt((Tm)1 + d));
-            rl = piv_rcp((Tm)1 + piv);
+            rl = piv_rsqrt((Tm)1 + d);
           } else {
             // a pivot that has lost all but 4m roundings of its original
             // diagonal entry marks a (numerically) singular S
@@ -274,13 +286,15 @@ __global__ void __launch_bounds__(chol_threads<Tm>(), 1)
               b = true;
               d = (Tm)1;
             }
-            piv = piv_sqrt(d);
-            rl = piv_rcp(piv);
+            rl = piv_rsqrt(d);
           }
-          if (lane == c) v[q] = piv;
           if (lane > c) v[q] *= rl;
-          colbuf[c & 1][lane] = v[q];
+          colbuf[c & 1][lane] = v[q];  // the diagonal entry is not read
           if (lane == 0) rdiag[c0 + c] = rl;
+          // L_cc (deviation form: L_cc - 1 = d / (1 + sqrt(1 + d)), with
+          // sqrt(1 + d) = (1 + d) rl, which keeps small d accurate)
+          if (lane == c)
+            v[q] = dev ? d * piv_rcp((Tm)1 + ((Tm)1 + d) * rl) : d * rl;
         }
         __syncthreads();
         const Tm lrc = colbuf[c & 1][lane];
