@@ -451,5 +451,53 @@ CUtensorMap f32_map(const float* p, int64_t rows, int64_t cols, int64_t ld,
   return map;
 }
 
+namespace {
+struct GridKey {
+  const void* p;
+  int nx, ny, nz, nc, by;
+  bool operator==(const GridKey& o) const {
+    return p == o.p && nx == o.nx && ny == o.ny && nz == o.nz && nc == o.nc &&
+           by == o.by;
+  }
+};
+struct GridKeyHash {
+  size_t operator()(const GridKey& k) const {
+    size_t h = std::hash<const void*>()(k.p);
+    for (int v : {k.nx, k.ny, k.nz, k.nc, k.by})
+      h = h * 1000003u ^ std::hash<int>()(v);
+    return h;
+  }
+};
+std::unordered_map<GridKey, CUtensorMap, GridKeyHash> g_grid_maps;
+}  // namespace
+
+CUtensorMap f32_grid_map(const float* p, int nx, int ny, int nz, int ncols,
+                         int box_y) {
+  std::lock_guard<std::mutex> lock(g_map_mu);
+  GridKey key{p, nx, ny, nz, ncols, box_y};
+  auto it = g_grid_maps.find(key);
+  if (it != g_grid_maps.end()) return it->second;
+  if (g_grid_maps.size() > 512) g_grid_maps.clear();
+  EncodeFn fn = encode_fn();
+  if (!fn) throw Error(-5, "cuTensorMapEncodeTiled is not available");
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz,
+                              (cuuint64_t)ncols};
+  const cuuint64_t plane = (cuuint64_t)nx * ny * sizeof(float);
+  const cuuint64_t strides[3] = {(cuuint64_t)nx * sizeof(float), plane,
+                                 plane * (cuuint64_t)nz};
+  const cuuint32_t box[4] = {(cuuint32_t)nx, (cuuint32_t)box_y, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                  const_cast<float*>(p), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw Error(-5, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  g_grid_maps.emplace(key, map);
+  return map;
+}
+
 }  // namespace tc
 }  // namespace trm

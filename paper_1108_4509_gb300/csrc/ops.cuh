@@ -35,6 +35,7 @@ struct Operator {
   const float* diaglo = nullptr;   // H_ii - fl32(H_ii)
   const double* minv64 = nullptr;  // diagonal preconditioner M_ii
   const float* minv32 = nullptr;
+  int* err = nullptr;  // device status word: bit 2 when a bounded wait gave up
 };
 
 void apply_h(const Operator& op, const float* X, float* Y, int ncols,

@@ -243,6 +243,7 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   part_ = d(part_cap_);
   sc_ = static_cast<IterScalars*>(mem_.alloc(sizeof(IterScalars)));
   TRM_CUDA(cudaMemsetAsync(sc_, 0, sizeof(IterScalars), s_));
+  op_.err = &sc_->status;
   tw_.msplit_floats = mul_tc_work_floats(m, m);
   tw_.msplit = f(tw_.msplit_floats);
   tw_.err = &sc_->status;

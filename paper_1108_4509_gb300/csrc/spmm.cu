@@ -7,7 +7,15 @@
 // vector load (x neighbours come from the vectors left and right of it).
 // CSR operators: one thread per row keeps the row's entries in registers and
 // walks the columns of its column group.
+#include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "dfmath.cuh"
 #include "ops.cuh"
+#include "tc.cuh"
 
 namespace trm {
 
@@ -253,9 +261,310 @@ __global__ void __launch_bounds__(256)
   if (DOTS) write_dots(red, dots, cb, ncols);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 stencil with the grid planes staged in shared memory by TMA (nx % 4
+// == 0, nx <= 256). A CTA owns rows y0 .. y0 + ty - 1 of one column and
+// marches along z. A ring of kPlanes staged planes holds, per plane, the rows
+// y0 - 2 .. y0 + ty + 1 (the halo), each loaded as one (nx x (ty + 4)) box of
+// the block's 4-D tensor map (x, y, z, column); rows and planes outside the
+// grid arrive as zeros, which is the Dirichlet boundary. All thirteen
+// neighbours are read from shared memory, so a value comes from DRAM once
+// (plus the halo rows) rather than once per neighbour through L1/L2. The z
+// range is cut into grid.z chunks (each reads two halo planes on either
+// side) so that about four CTAs per SM keep enough planes in flight. Thread
+// (qx, ry) computes the four points x = 4 qx .. 4 qx + 3 of row y0 + ry with
+// the same arithmetic, in the same order, as k_stencil_v4. With DOTS the
+// column dot X_c . Y_c is accumulated in double-float per thread and the
+// CTA's sum is written to dots[blockIdx.x * ncols + column].
+// ---------------------------------------------------------------------------
+constexpr int kPlanes = 8;
+constexpr int kHalo = 2;
+
+int plane_rows(int nx, int ny) {
+  const int nxq = nx / 4;
+  int ty = 256 / nxq;
+  if (ty > 256 - 2 * kHalo) ty = 256 - 2 * kHalo;  // a TMA box is <= 256 high
+  if (ty > ny) ty = ny;
+  return ty < 1 ? 1 : ty;
+}
+__host__ __device__ inline int plane_stride(int nx, int ty) {
+  return ((ty + 2 * kHalo) * nx + 31) & ~31;
+}
+
+template <int R, bool DOTS>
+__global__ void __launch_bounds__(256)
+    k_stencil_planes(const __grid_constant__ CUtensorMap map, StencilOp st,
+                     const float* __restrict__ d32, float* __restrict__ Y,
+                     int64_t N, int ncols, int ty, int zc,
+                     double* __restrict__ dots, int* err) {
+  extern __shared__ unsigned char smraw[];
+  __shared__ uint64_t full[kPlanes];
+  __shared__ int failed;
+  __shared__ double red[8];
+  const int nx = st.nx, ny = st.ny, nz = st.nz, nxq = nx >> 2;
+  const int rows = ty + 2 * kHalo;
+  const int pstride = plane_stride(nx, ty);
+  float* planes = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(smraw) + 127) & ~(uintptr_t)127);
+  const int tid = threadIdx.x;
+  const int y0 = blockIdx.x * ty, col = blockIdx.y;
+  const int z0 = blockIdx.z * zc, z1 = min(nz, z0 + zc);
+  const int qx = tid % nxq, ry = tid / nxq;
+  const bool active = ry < ty && y0 + ry < ny;
+  if (tid == 0) {
+    for (int q = 0; q < kPlanes; ++q) tc::mbar_init(&full[q], 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint32_t box_bytes = (uint32_t)(rows * nx) * 4u;
+  const int first = z0 - kHalo, last = z1 - 1 + kHalo;  // planes read
+  int issued = first - 1;  // thread 0: last plane issued
+  // plane pz goes to slot (pz - first) % kPlanes, its use number
+  // (pz - first) / kPlanes giving the barrier phase
+  auto slot = [&](int pz) { return (pz - first) % kPlanes; };
+  auto phase = [&](int pz) { return ((pz - first) / kPlanes) & 1; };
+  auto issue = [&](int pz) {
+    const int q = slot(pz);
+    tc::mbar_expect_tx(&full[q], box_bytes);
+    tc::tma_load_4d(planes + q * pstride, &map, 0, y0 - kHalo, pz, col,
+                    &full[q]);
+    issued = pz;
+  };
+  if (tid == 0)
+    for (int pz = first; pz < first + kPlanes && pz <= last; ++pz) issue(pz);
+  const float c1 = (float)st.c1, c2 = (float)st.c2;
+  F2 dacc = {0.f, 0.f};
+  int waited = first - 1;  // last plane this thread saw land
+  const int r = ry + kHalo;
+  const int64_t rowoff = (int64_t)(y0 + ry) * nx + 4 * qx;
+  for (int z = z0; z < z1; ++z) {
+    bool ok = true;
+    for (int pz = waited + 1; pz <= z + kHalo && pz <= last && ok; ++pz) {
+      ok = tc::mbar_wait(&full[slot(pz)], phase(pz), err, &failed);
+      if (ok) waited = pz;
+    }
+    if (!__syncthreads_and(ok)) break;  // the same decision in every thread
+    if (active) {
+      auto at = [&](int pz) {
+        return planes + slot(pz) * pstride + r * nx + 4 * qx;
+      };
+      const float* p0 = at(z);
+      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 xc = *reinterpret_cast<const float4*>(p0);
+      const float4 xl = qx > 0 ? *reinterpret_cast<const float4*>(p0 - 4) : zero;
+      const float4 xr = qx + 1 < nxq ? *reinterpret_cast<const float4*>(p0 + 4) : zero;
+      const float4 ym1 = *reinterpret_cast<const float4*>(p0 - nx);
+      const float4 yp1 = *reinterpret_cast<const float4*>(p0 + nx);
+      const float4 zm1 = *reinterpret_cast<const float4*>(at(z - 1));
+      const float4 zp1 = *reinterpret_cast<const float4*>(at(z + 1));
+      const float c[4] = {xc.x, xc.y, xc.z, xc.w};
+      const float a1[4] = {ym1.x, ym1.y, ym1.z, ym1.w};
+      const float b1[4] = {yp1.x, yp1.y, yp1.z, yp1.w};
+      const float e1[4] = {zm1.x, zm1.y, zm1.z, zm1.w};
+      const float f1[4] = {zp1.x, zp1.y, zp1.z, zp1.w};
+      const float l1[4] = {xl.w, xc.x, xc.y, xc.z};
+      const float r1[4] = {xc.y, xc.z, xc.w, xr.x};
+      float a2[4] = {0, 0, 0, 0}, b2[4] = {0, 0, 0, 0}, e2[4] = {0, 0, 0, 0},
+            f2[4] = {0, 0, 0, 0};
+      float l2[4] = {0, 0, 0, 0}, r2[4] = {0, 0, 0, 0};
+      if (R == 2) {
+        const float4 ym2 = *reinterpret_cast<const float4*>(p0 - 2 * nx);
+        const float4 yp2 = *reinterpret_cast<const float4*>(p0 + 2 * nx);
+        const float4 zm2 = *reinterpret_cast<const float4*>(at(z - 2));
+        const float4 zp2 = *reinterpret_cast<const float4*>(at(z + 2));
+        a2[0] = ym2.x; a2[1] = ym2.y; a2[2] = ym2.z; a2[3] = ym2.w;
+        b2[0] = yp2.x; b2[1] = yp2.y; b2[2] = yp2.z; b2[3] = yp2.w;
+        e2[0] = zm2.x; e2[1] = zm2.y; e2[2] = zm2.z; e2[3] = zm2.w;
+        f2[0] = zp2.x; f2[1] = zp2.y; f2[2] = zp2.z; f2[3] = zp2.w;
+        l2[0] = xl.z; l2[1] = xl.w; l2[2] = xc.x; l2[3] = xc.y;
+        r2[0] = xc.z; r2[1] = xc.w; r2[2] = xr.x; r2[3] = xr.y;
+      }
+      const int64_t i0 = (int64_t)z * nx * ny + rowoff;
+      const float4 d4 = *reinterpret_cast<const float4*>(d32 + i0);
+      const float d[4] = {d4.x, d4.y, d4.z, d4.w};
+      float out[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float s1 = 0.f, s2 = 0.f;
+        s1 += a1[k];
+        s1 += b1[k];
+        s1 += e1[k];
+        s1 += f1[k];
+        float acc = d[k] * c[k] + c1 * (s1 + l1[k] + r1[k]);
+        if (R == 2) {
+          s2 += a2[k];
+          s2 += b2[k];
+          s2 += e2[k];
+          s2 += f2[k];
+          acc += c2 * (s2 + l2[k] + r2[k]);
+        }
+        out[k] = acc;
+      }
+      *reinterpret_cast<float4*>(Y + (int64_t)col * N + i0) =
+          make_float4(out[0], out[1], out[2], out[3]);
+      if (DOTS)
+        dacc = df_add(dacc, F2{c[0] * out[0] + c[1] * out[1] +
+                                   c[2] * out[2] + c[3] * out[3],
+                               0.f});
+    }
+    // this thread's reads of the ring before the next TMA write there
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0 && z - kHalo + kPlanes <= last) issue(z - kHalo + kPlanes);
+  }
+  // copies issued but not waited for (only after a timeout) land first
+  if (tid == 0)
+    for (int pz = waited + 1; pz <= issued; ++pz)
+      tc::mbar_wait_own(&full[slot(pz)], phase(pz), err);
+  if (DOTS) {
+    double v = (double)dacc.h + (double)dacc.l;
+    v = warp_sum(v);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+      dots[((size_t)blockIdx.z * gridDim.x + blockIdx.x) * ncols + col] = t;
+    }
+  }
+}
+
+template <int R, bool DOTS>
+int launch_planes(const Operator& op, const float* X, float* Y, int ncols,
+                  double* dots, cudaStream_t s) {
+  const StencilOp& st = op.st;
+  const int ty = plane_rows(st.nx, st.ny);
+  const int tiles = ceil_div(st.ny, ty);
+  // about four CTAs per SM: z chunks of at least 8 planes
+  const int want = ceil_div(4 * sm_count(), tiles * ncols);
+  // (and no more partial dots per column than apply_h_dots_doubles allows)
+  const int cap = std::max<int>(1, (int)(ceil_div(op.N / 4, 256) / tiles));
+  int chunks = std::max(1, std::min({want, ceil_div(st.nz, 8), cap}));
+  const int zc = ceil_div(st.nz, chunks);
+  chunks = ceil_div(st.nz, zc);
+  const int threads = ((st.nx / 4) * ty + 31) & ~31;
+  const size_t smem =
+      (size_t)kPlanes * plane_stride(st.nx, ty) * sizeof(float) + 128;
+  static std::atomic<int> attr_dev{-1};  // launches may come from several threads
+  int dev = 0;
+  TRM_CUDA(cudaGetDevice(&dev));
+  if (attr_dev.load(std::memory_order_relaxed) != dev) {
+    TRM_CUDA(cudaFuncSetAttribute(k_stencil_planes<R, DOTS>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  128 * 1024));
+    attr_dev.store(dev, std::memory_order_relaxed);
+  }
+  const CUtensorMap map = tc::f32_grid_map(X, st.nx, st.ny, st.nz, ncols,
+                                           ty + 2 * kHalo);
+  k_stencil_planes<R, DOTS><<<dim3(tiles, ncols, chunks), threads, smem, s>>>(
+      map, st, op.diag32, Y, op.N, ncols, ty, zc, dots, op.err);
+  TRM_CHECK_LAUNCH();
+  return tiles * chunks;  // partial dots per column
+}
+
+// The staged-plane kernel takes FP32 stencils with nx % 4 == 0 and
+// nx <= 256 on 16-byte-aligned blocks.
+template <typename T>
+bool planes_eligible(const Operator& op, const T* X, const T* Y, int ncols) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    const StencilOp& st = op.st;
+    return op.kind == 0 && st.nx % 4 == 0 && st.nx <= 256 && ncols <= 65535 &&
+           ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y) |
+             reinterpret_cast<uintptr_t>(op.diag32)) & 15) == 0 &&
+           plane_stride(st.nx, plane_rows(st.nx, st.ny)) * kPlanes * 4 + 128 <=
+               128 * 1024 &&
+           tc::encode_fn() != nullptr;
+  }
+}
+
+template <typename T, bool DOTS>
+int launch_vec(const Operator& op, const T* X, T* Y, int ncols, double* dots,
+               cudaStream_t s);
+
+// Autotuned choice between the staged-plane and the four-point FP32 stencil
+// kernels. The first apply of each (grid, order, columns, fused dots) in the
+// process times both on the caller's buffers (a warm-up launch, then the two
+// kernels alternately, twice each, CUDA events on the stream) and keeps the
+// faster for the rest of the process. Both compute every point with the same
+// operations in the same order (the fused dots are grouped differently, so
+// the choice is fixed per process: repeated solves agree bit for bit). No
+// timing inside a stream capture: the plain kernel is used there until a
+// choice exists.
+struct TuneKey {
+  int nx, ny, nz, radius, ncols, dots;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(nx, ny, nz, radius, ncols, dots) <
+           std::tie(o.nx, o.ny, o.nz, o.radius, o.ncols, o.dots);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;  // 1: staged planes
+
+template <bool DOTS>
+int launch_planes_r(const Operator& op, const float* X, float* Y, int ncols,
+                    double* dots, cudaStream_t s) {
+  return op.st.radius == 1 ? launch_planes<1, DOTS>(op, X, Y, ncols, dots, s)
+                           : launch_planes<2, DOTS>(op, X, Y, ncols, dots, s);
+}
+
+template <bool DOTS>
+bool use_planes(const Operator& op, const float* X, float* Y, int ncols,
+                double* dots, cudaStream_t s) {
+  const StencilOp& st = op.st;
+  const TuneKey key{st.nx, st.ny, st.nz, st.radius, ncols, DOTS ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second == 1;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TRM_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return false;
+  cudaEvent_t ev[5];
+  for (auto& e : ev) TRM_CUDA(cudaEventCreate(&e));
+  long long tuning = 0;
+  capture_launches(&tuning);  // the timing launches are not the solve's
+  launch_vec<float, DOTS>(op, X, Y, ncols, dots, s);  // warm-up
+  TRM_CUDA(cudaEventRecord(ev[0], s));
+  for (int k = 0; k < 2; ++k) {
+    launch_vec<float, DOTS>(op, X, Y, ncols, dots, s);
+    TRM_CUDA(cudaEventRecord(ev[1 + 2 * k], s));
+    launch_planes_r<DOTS>(op, X, Y, ncols, dots, s);
+    TRM_CUDA(cudaEventRecord(ev[2 + 2 * k], s));
+  }
+  capture_launches(nullptr);
+  TRM_CUDA(cudaEventSynchronize(ev[4]));
+  float tv = 0.f, tp = 0.f, t = 0.f;
+  for (int k = 0; k < 2; ++k) {
+    TRM_CUDA(cudaEventElapsedTime(&t, ev[2 * k], ev[1 + 2 * k]));
+    tv += t;
+    TRM_CUDA(cudaEventElapsedTime(&t, ev[1 + 2 * k], ev[2 + 2 * k]));
+    tp += t;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  // the first decision for a key stands (another thread may have tuned it)
+  auto it = g_tuned.emplace(key, tp < tv ? 1 : 0).first;
+  return it->second == 1;
+}
+
 template <typename T, bool DOTS>
 int launch_apply(const Operator& op, const T* X, T* Y, int ncols, double* dots,
                  cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (planes_eligible(op, X, Y, ncols) &&
+        use_planes<DOTS>(op, X, Y, ncols, dots, s))
+      return launch_planes_r<DOTS>(op, X, Y, ncols, dots, s);
+  }
+  return launch_vec<T, DOTS>(op, X, Y, ncols, dots, s);
+}
+
+template <typename T, bool DOTS>
+int launch_vec(const Operator& op, const T* X, T* Y, int ncols, double* dots,
+               cudaStream_t s) {
   const int threads = 256;
   const int gy = ceil_div(ncols, kCpb);
   if (gy > 65535) throw Error(-1, "too many columns for one launch");

@@ -76,6 +76,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map,
       "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map,
+                                            int x, int y, int z, int w,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::"
+      "complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w),
+      "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -257,6 +267,10 @@ EncodeFn encode_fn();
 // `ld` >= rows, a multiple of 4) read in boxes of box_rows x box_cols with
 // the 128-byte swizzle (box_rows * 4 = 128). Cached per (pointer, shape,
 // box); out-of-range elements read as zero.
+// The FP32 blocks of a grid operator as a 4-D tensor (x, y, z, column), no
+// swizzle, boxes of (nx, box_y, 1, 1): one y-band of one plane of a column.
+CUtensorMap f32_grid_map(const float* p, int nx, int ny, int nz, int ncols,
+                         int box_y);
 CUtensorMap f32_map(const float* p, int64_t rows, int64_t cols, int64_t ld,
                     int box_rows, int box_cols);
 

@@ -40,8 +40,11 @@ def _handle(trm, shape, order, V, m, precond=0):
     return trm.trm_create_stencil(nx, ny, nz, order, 1.0, V, m, 1e-10, opt)
 
 
+# (64, 37, 6) and (32, 50, 5) give the staged-plane FP32 stencil several
+# y-bands per column with a ragged last one (16 + 16 + 5 and 32 + 18 rows)
 GRIDS = [((16, 12, 10), 2), ((16, 12, 10), 4), ((13, 11, 9), 4),
-         ((24, 20, 1), 2), ((5, 7, 6), 4), ((8, 8, 8), 2)]
+         ((24, 20, 1), 2), ((5, 7, 6), 4), ((8, 8, 8), 2),
+         ((64, 37, 6), 4), ((32, 50, 5), 2)]
 
 
 # ---------------------------------------------------------------------------
