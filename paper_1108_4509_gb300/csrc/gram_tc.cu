@@ -112,16 +112,20 @@ struct TcArgs {
   int m, n;               // output is m x n
   int64_t rows_per_split;
   int tiles_m;
-  int seg_cols;           // columns per B segment (a multiple of BN if > 1)
+  int seg_cols;           // columns per segment (a multiple of BN if > 1)
   double* part;
   int* err;
 };
 
+// Output column segment k is A_k^T B_k (up to four segments; the line search
+// takes [C P P P]^T [P P HP G] in one launch).
+struct TcMaps {
+  CUtensorMap a[4];
+  CUtensorMap b[4];
+};
+
 __global__ void __launch_bounds__(THREADS, 1)
-    k_gram_tc(const __grid_constant__ CUtensorMap mapA,
-              const __grid_constant__ CUtensorMap mapB0,
-              const __grid_constant__ CUtensorMap mapB1,
-              const __grid_constant__ CUtensorMap mapB2, TcArgs args) {
+    k_gram_tc(const __grid_constant__ TcMaps maps, TcArgs args) {
   extern __shared__ unsigned char smem_raw[];
   TcSmem* sm = reinterpret_cast<TcSmem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -135,7 +139,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int nk = (int)((re - rb + BK - 1) / BK);
   const int seg = j0 / args.seg_cols;
   const int jb = j0 - seg * args.seg_cols;
-  const CUtensorMap* mapB = seg == 0 ? &mapB0 : (seg == 1 ? &mapB1 : &mapB2);
+  const CUtensorMap* mapA = &maps.a[seg];
+  const CUtensorMap* mapB = &maps.b[seg];
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < RSTAGES; ++s) {
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         mbar_expect_tx(&sm->full[s], 2 * BM * BK * sizeof(float));
         const int x = (int)(rb + (int64_t)k * BK);
-        tma_load_2d(sm->raw[s][0], &mapA, x, i0, &sm->full[s]);
+        tma_load_2d(sm->raw[s][0], mapA, x, i0, &sm->full[s]);
         tma_load_2d(sm->raw[s][1], mapB, x, jb, &sm->full[s]);
         ++issued;
       }
@@ -334,8 +339,16 @@ CUtensorMap block_map(const float* p, int64_t N, int cols) {
 }  // namespace
 
 bool gram_tc_eligible(int64_t N, int m, const Blocks<float>& B) {
+  return gram_tc_pairs_eligible(N, m, B, B);
+}
+
+bool gram_tc_pairs_eligible(int64_t N, int m, const Blocks<float>& A,
+                            const Blocks<float>& B) {
   if (N % 4 != 0 || N < BK || m < 64) return false;
-  if (B.count > 3) return false;
+  if (B.count > 4) return false;
+  if (A.count > 1 && A.count != B.count) return false;
+  for (int s = 0; s < A.count; ++s)
+    if (reinterpret_cast<uintptr_t>(A.p[s]) % 16 != 0) return false;
   if (B.count > 1 && B.cols % BN != 0) return false;
   for (int s = 0; s < B.count; ++s)
     if (reinterpret_cast<uintptr_t>(B.p[s]) % 16 != 0) return false;
@@ -352,6 +365,16 @@ size_t gram_tc_partials_doubles(int64_t N, int m, int n) {
 void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
              double* out, double* partials, size_t cap, int* err,
              cudaStream_t s, float* out32) {
+  Blocks<float> a;
+  a.p[0] = A;
+  a.cols = m;
+  a.count = 1;
+  gram_tc_pairs(N, m, a, B, out, partials, cap, err, s, out32);
+}
+
+void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
+                   const Blocks<float>& B, double* out, double* partials,
+                   size_t cap, int* err, cudaStream_t s, float* out32) {
   const int n = B.total();
   const int tiles_m = ceil_div(m, BM);
   const int tiles = tiles_m * ceil_div(n, BN);
@@ -361,11 +384,13 @@ void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
   splits = (int)((N + rows - 1) / rows);
   if ((size_t)splits * m * n > cap)
     throw Error(-2, "gram_tc: partials buffer too small");
-  CUtensorMap mA = block_map(A, N, m);
   const int segcols = B.count > 1 ? B.cols : n;
-  CUtensorMap mB[3];
-  for (int k = 0; k < 3; ++k)
-    mB[k] = block_map(B.p[k < B.count ? k : 0], N, B.cols);
+  TcMaps maps;
+  for (int k = 0; k < 4; ++k) {
+    const int kb = k < B.count ? k : 0;
+    maps.a[k] = block_map(A.p[A.count > 1 ? kb : 0], N, m);
+    maps.b[k] = block_map(B.p[kb], N, B.cols);
+  }
   TcArgs a{N, m, n, rows, tiles_m, segcols, partials, err};
   const size_t smem = sizeof(TcSmem) + 1024;
   static std::once_flag attr;
@@ -374,7 +399,7 @@ void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
                          (int)smem);
   });
   dim3 grid(splits, tiles);
-  k_gram_tc<<<grid, THREADS, smem, s>>>(mA, mB[0], mB[1], mB[2], a);
+  k_gram_tc<<<grid, THREADS, smem, s>>>(maps, a);
   TRM_CHECK_LAUNCH();
   const size_t count = (size_t)m * n;
   sum_splits_pairs(reinterpret_cast<const float*>(partials), splits, count,

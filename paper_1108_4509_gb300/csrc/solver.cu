@@ -179,7 +179,8 @@ void* DevArena::alloc(size_t bytes) {
 size_t Solver::part_capacity(int64_t N, int m) {
   const size_t chunks = (size_t)ceil_div(N, 4096);
   return std::max<size_t>(
-      {gram_partials_doubles(N, m, 3 * m), gram_partials_doubles(N, m, m),
+      {gram_partials_doubles(N, m, 4 * m), gram_partials_doubles(N, m, 3 * m),
+       gram_partials_doubles(N, m, m),
        (size_t)4 * ceil_div(N, 64) * ceil_div(m, 64), 3 * chunks * m + m,
        (size_t)ceil_div(N, 256) * m, (size_t)4096});
 }
@@ -222,8 +223,8 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   HD_ = d(m);
   Hp_ = d(mm);
   A0_ = d(mm);
-  Bm_ = d(mm);
-  PG_ = d(3 * mm);
+  Bm_ = d(4 * mm);  // C^T P, then P^T [P HP G] (one m x 4m result)
+  PG_ = Bm_ + mm;
   T1_ = d(mm);
   T2_ = d(mm);
   S_ = d(mm);
@@ -233,8 +234,8 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   mmw_ = d(std::max(2 * mm, chol_work_elems(m)));
   eigws_ = d(sym_eig_work_doubles(m));
   Hp32_ = f(mm);
-  Bm32_ = f(mm);
-  PG32_ = f(3 * mm);
+  Bm32_ = f(4 * mm);
+  PG32_ = Bm32_ + mm;
   eigw_ = d(m);
   lam_ = d(m);
   res_ = d(m);
@@ -406,6 +407,32 @@ void Solver::read_scalars(IterScalars* out) {
 // One iteration with every block in precision T and the m x m line model and
 // factorisation in Tm (full DP: double/double; full SP: float/float).
 // ---------------------------------------------------------------------------
+// The line-search Grams C^T P and P^T [P HP G] as one tensor-core launch
+// [C P P P]^T [P P HP G] (one m x 4m result: Bm_, then PG_), when the FP32
+// blocks are eligible; false means the caller forms them separately.
+template <typename T>
+bool Solver::line_grams_fused(const T* C, const T* P, const T* HP,
+                              const T* G) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    Blocks<float> a, b;
+    a.p[0] = C;
+    a.p[1] = a.p[2] = a.p[3] = P;
+    b.p[0] = b.p[1] = P;
+    b.p[2] = HP;
+    b.p[3] = G;
+    a.cols = b.cols = m_;
+    a.count = b.count = 4;
+    if (!gram_tc_pairs_eligible(N_, m_, a, b)) return false;
+    const double nm = (double)N_ * m_, m2N = nm * m_;
+    TRM_PROF(KC_GRAM32, 8 * m2N, 16 * nm,
+             gram_tc_pairs(N_, m_, a, b, Bm_, part_, part_cap_, &sc_->status,
+                           s_, Bm32_));
+    return true;
+  }
+}
+
 template <typename T, typename Tm>
 void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   const T* minv = nullptr;
@@ -454,22 +481,24 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   TRM_PROF(KC_ROWOPS, 2 * nm, 3 * es * nm,
            update_p<T>(N_, m_, G, P, minv, sc_, s_));                 // P
   TRM_PROF(ksp, sfl, sby, apply_h(op_, P, HP, m_, s_));              // H P
-  Blocks<T> bp;
-  bp.p[0] = P;
-  bp.cols = m_;
-  bp.count = 1;
-  TRM_PROF(kgr, 2 * m2N, 2 * es * nm,
-           gram<T>(N_, m_, C, bp, Bm_, part_, part_cap_, s_, &sc_->status,
-                   bm32));                                            // C^T P
-  Blocks<T> b3;
-  b3.p[0] = P;
-  b3.p[1] = HP;
-  b3.p[2] = G;
-  b3.cols = m_;
-  b3.count = 3;
-  TRM_PROF(kgr, 6 * m2N, 4 * es * nm,
-           gram<T>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status,
-                   pg32));                                            // P^T[P HP G]
+  if (!line_grams_fused<T>(C, P, HP, G)) {
+    Blocks<T> bp;
+    bp.p[0] = P;
+    bp.cols = m_;
+    bp.count = 1;
+    TRM_PROF(kgr, 2 * m2N, 2 * es * nm,
+             gram<T>(N_, m_, C, bp, Bm_, part_, part_cap_, s_, &sc_->status,
+                     bm32));                                          // C^T P
+    Blocks<T> b3;
+    b3.p[0] = P;
+    b3.p[1] = HP;
+    b3.p[2] = G;
+    b3.cols = m_;
+    b3.count = 3;
+    TRM_PROF(kgr, 6 * m2N, 4 * es * nm,
+             gram<T>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status,
+                     pg32));                                          // P^T[P HP G]
+  }
   const double m3 = md * md * md;
   prof.begin(KC_SMALL, s_);
   if constexpr (sizeof(T) == 4 && sizeof(Tm) == 4)
@@ -529,22 +558,24 @@ void Solver::iter_mp2() {
   TRM_PROF(KC_ROWOPS, 2 * dnm, 12 * dnm,
            update_p<float>(N_, m_, G, P, minv, sc_, s_));
   TRM_PROF(KC_SPMM32, f32, b32, apply_h(op_, P, HP, m_, s_));
-  Blocks<float> bp;
-  bp.p[0] = P;
-  bp.cols = m_;
-  bp.count = 1;
-  TRM_PROF(KC_GRAM32, 2 * m2N, 8 * dnm,
-           gram<float>(N_, m_, Ch, bp, Bm_, part_, part_cap_, s_, &sc_->status,
-                       Bm32_));
-  Blocks<float> b3;
-  b3.p[0] = P;
-  b3.p[1] = HP;
-  b3.p[2] = G;
-  b3.cols = m_;
-  b3.count = 3;
-  TRM_PROF(KC_GRAM32, 6 * m2N, 16 * dnm,
-           gram<float>(N_, m_, P, b3, PG_, part_, part_cap_, s_, &sc_->status,
-                       PG32_));
+  if (!line_grams_fused<float>(Ch, P, HP, G)) {
+    Blocks<float> bp;
+    bp.p[0] = P;
+    bp.cols = m_;
+    bp.count = 1;
+    TRM_PROF(KC_GRAM32, 2 * m2N, 8 * dnm,
+             gram<float>(N_, m_, Ch, bp, Bm_, part_, part_cap_, s_,
+                         &sc_->status, Bm32_));
+    Blocks<float> b3;
+    b3.p[0] = P;
+    b3.p[1] = HP;
+    b3.p[2] = G;
+    b3.cols = m_;
+    b3.count = 3;
+    TRM_PROF(KC_GRAM32, 6 * m2N, 16 * dnm,
+             gram<float>(N_, m_, P, b3, PG_, part_, part_cap_, s_,
+                         &sc_->status, PG32_));
+  }
   prof.begin(KC_SMALL, s_);
   line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, PG32_ + mm, PG32_ + 2 * mm,
                 nullptr, R_, sc_, mmw_, T1_, s_);

@@ -98,6 +98,8 @@ class Solver {
   template <typename T, typename Tm>
   void iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP);
   void iter_mp2();
+  template <typename T>
+  bool line_grams_fused(const T* C, const T* P, const T* HP, const T* G);
   // CUDA graphs of block iterations. An iteration is a fixed kernel
   // sequence given the phase and the block pointers it swaps, so a graph is
   // keyed by both and remembers the pointers it leaves behind. The first
