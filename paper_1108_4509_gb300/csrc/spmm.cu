@@ -108,13 +108,15 @@ __global__ void __launch_bounds__(256)
   const V4<T> d = ld4(diag_ptr<T>(d64, d32) + i0);
   const T c1 = (T)st.c1, c2 = (T)st.c2;
   const int cb = blockIdx.y * kCpb;
+  // column dots stay in registers until after the column loop, so their
+  // warp sums (dependent shuffles) do not hold up the next column's loads
+  T dsum[kCpb];
+#pragma unroll
+  for (int q = 0; q < kCpb; ++q) dsum[q] = (T)0;
+#pragma unroll
   for (int q = 0; q < kCpb; ++q) {
     const int c = cb + q;
-    if (c >= ncols) break;
-    if (DOTS && !valid) {
-      warp_dot((T)0, red, q);
-      continue;
-    }
+    if (c >= ncols || (DOTS && !valid)) continue;
     const T* x = X + (int64_t)c * N + i0;
     const V4<T> xc = ld4(x);
     V4<T> xlv = {{0, 0, 0, 0}}, xrv = {{0, 0, 0, 0}};
@@ -147,11 +149,14 @@ __global__ void __launch_bounds__(256)
     }
     st4(Y + (int64_t)c * N + i0, out);
     if (DOTS)
-      warp_dot(xc.v[0] * out.v[0] + xc.v[1] * out.v[1] +
-                   xc.v[2] * out.v[2] + xc.v[3] * out.v[3],
-               red, q);
+      dsum[q] = xc.v[0] * out.v[0] + xc.v[1] * out.v[1] + xc.v[2] * out.v[2] +
+                xc.v[3] * out.v[3];
   }
-  if (DOTS) write_dots(red, dots, cb, ncols);
+  if (DOTS) {
+#pragma unroll
+    for (int q = 0; q < kCpb; ++q) warp_dot(dsum[q], red, q);
+    write_dots(red, dots, cb, ncols);
+  }
 }
 
 // One point per thread, any nx.
