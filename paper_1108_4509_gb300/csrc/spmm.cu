@@ -178,13 +178,13 @@ __global__ void __launch_bounds__(256)
   const T d = diag_ptr<T>(d64, d32)[i];
   const T c1 = (T)st.c1, c2 = (T)st.c2;
   const int cb = blockIdx.y * kCpb;
+  T dsum[kCpb];  // column dots, warp-summed after the column loop
+#pragma unroll
+  for (int q = 0; q < kCpb; ++q) dsum[q] = (T)0;
+#pragma unroll
   for (int q = 0; q < kCpb; ++q) {
     const int c = cb + q;
-    if (c >= ncols) break;
-    if (DOTS && !valid) {
-      warp_dot((T)0, red, q);
-      continue;
-    }
+    if (c >= ncols || (DOTS && !valid)) continue;
     const T* xp = X + (int64_t)c * N + i;
     T s1 = 0, s2 = 0;
     if (x >= 1) s1 += xp[-1];
@@ -204,9 +204,13 @@ __global__ void __launch_bounds__(256)
       acc += c2 * s2;
     }
     Y[(int64_t)c * N + i] = acc;
-    if (DOTS) warp_dot(xp[0] * acc, red, q);
+    if (DOTS) dsum[q] = xp[0] * acc;
   }
-  if (DOTS) write_dots(red, dots, cb, ncols);
+  if (DOTS) {
+#pragma unroll
+    for (int q = 0; q < kCpb; ++q) warp_dot(dsum[q], red, q);
+    write_dots(red, dots, cb, ncols);
+  }
 }
 
 constexpr int kCsrCache = 16;
