@@ -61,6 +61,9 @@ constexpr int OSTAGES = 2;  // split operand stages
 constexpr int THREADS = 576;  // 18 warps
 constexpr int KC = 4;         // stages per accumulation chunk
 constexpr int kSingleChunk = 96;  // row slices this short are one chunk
+// Row slices of at least this many stages: a small problem takes fewer CTAs
+// (each holds a whole SM) and leaves the rest of the GPU to concurrent solves.
+constexpr int kMinStages = 16;
 
 struct TcSmem {
   // [stage][A, B][128 columns x 32 rows] as loaded, and the split operands
@@ -358,7 +361,7 @@ bool gram_tc_pairs_eligible(int64_t N, int m, const Blocks<float>& A,
 size_t gram_tc_partials_doubles(int64_t N, int m, int n) {
   const int tiles = ceil_div(m, BM) * ceil_div(n, BN);
   const int splits = std::max(1, std::min(sm_count() / tiles,
-                                          ceil_div(N, BK)));
+                                          ceil_div(N, BK * kMinStages)));
   return (size_t)splits * m * n;
 }
 
@@ -378,7 +381,8 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
   const int n = B.total();
   const int tiles_m = ceil_div(m, BM);
   const int tiles = tiles_m * ceil_div(n, BN);
-  int splits = std::max(1, std::min(sm_count() / tiles, ceil_div(N, BK)));
+  int splits = std::max(1, std::min(sm_count() / tiles,
+                                    ceil_div(N, BK * kMinStages)));
   int64_t rows = (N + splits - 1) / splits;
   rows = ((rows + BK - 1) / BK) * BK;
   splits = (int)((N + rows - 1) / rows);

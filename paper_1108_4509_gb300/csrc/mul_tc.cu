@@ -522,7 +522,7 @@ void launch(const MulArgs& a0, const float* A, const float* P,
   a.nch = ceil_div(a.n, NC);
   a.has_p = P ? 1 : 0;
   const int tiles = a.ntr * a.nch;
-  const int grid = tiles < sm_count() ? tiles : sm_count();
+  const int grid = mul_tc_parts(a.N, a.n);
   const size_t smem = sizeof(MulSmem) + 1024;
   static std::atomic<int> attr_dev{-1};  // launches may come from several threads
   int dev = 0;
@@ -553,7 +553,11 @@ size_t mul_tc_work_floats(int k, int n) {
 
 int mul_tc_parts(int64_t N, int n) {
   const int64_t tiles = (int64_t)ceil_div(N, (int64_t)BM) * ceil_div(n, NC);
-  return (int)(tiles < sm_count() ? tiles : sm_count());
+  // persistent CTAs, one per SM at most, and at least two tiles each below
+  // 2 x SMs tiles (each CTA holds a whole SM: a small problem leaves the
+  // rest of the GPU to concurrent solves)
+  const int64_t two = (tiles + 1) / 2;
+  return (int)(tiles >= 2 * sm_count() ? sm_count() : (two < 1 ? 1 : two));
 }
 
 void mul_tc_store(int64_t N, int k, int n, const float* A, const float* P,

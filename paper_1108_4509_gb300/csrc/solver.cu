@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "solver.cuh"
 
@@ -156,17 +157,64 @@ void Profiler::reset() {
   }
 }
 
-DevArena::~DevArena() {
-  for (void* p : ptrs_) cudaFree(p);
+// Pinned rings of per-iteration scalars, reused across solvers: a page-locked
+// allocation (and its release) would serialise the streams of concurrent
+// solves. Rings are kept for the life of the process (a few hundred bytes).
+namespace {
+std::mutex g_ring_mu;
+std::vector<IterScalars*> g_rings;
+}  // namespace
+
+IterScalars* ring_acquire() {
+  {
+    std::lock_guard<std::mutex> lock(g_ring_mu);
+    if (!g_rings.empty()) {
+      IterScalars* r = g_rings.back();
+      g_rings.pop_back();
+      return r;
+    }
+  }
+  IterScalars* r = nullptr;
+  TRM_CUDA(cudaHostAlloc(&r, sizeof(IterScalars) * kRing,
+                         cudaHostAllocDefault));
+  return r;
 }
+
+void ring_release(IterScalars* r) {
+  std::lock_guard<std::mutex> lock(g_ring_mu);
+  g_rings.push_back(r);
+}
+
+DevArena::~DevArena() {
+  for (void* p : ptrs_) cudaFreeAsync(p, s_);
+}
+
+namespace {
+// The device's default pool keeps freed memory for reuse (no release to the
+// driver at synchronisation), so repeated solver creation allocates without
+// system calls. Set once per device.
+void keep_pool_memory() {
+  static std::atomic<int> done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  if (done[dev].exchange(1)) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+}
+}  // namespace
 
 void* DevArena::alloc(size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  keep_pool_memory();
+  cudaError_t e = cudaMallocAsync(&p, bytes, s_);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    throw Error(-2, "cudaMalloc of " + std::to_string(bytes) +
+    throw Error(-2, "device allocation of " + std::to_string(bytes) +
                         " bytes failed: " + cudaGetErrorString(e));
   }
   ptrs_.push_back(p);
@@ -201,6 +249,7 @@ size_t Solver::footprint(int64_t N, int m) {
 Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
     : N_(N), m_(m), tol_(tol), opt_(opt) {
   s_ = reinterpret_cast<cudaStream_t>(opt.stream);
+  mem_.set_stream(s_);
   const size_t nm = (size_t)N * m;
   const size_t mm = (size_t)m * m;
   auto d = [&](size_t n) { return static_cast<double*>(mem_.alloc(n * 8)); };
@@ -253,8 +302,7 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   diaglo_ = f(N);
   minv64_ = d(N);
   minv32_ = f(N);
-  TRM_CUDA(cudaHostAlloc(&ring_, sizeof(IterScalars) * kRing,
-                         cudaHostAllocDefault));
+  ring_ = ring_acquire();
   ev_.resize(kRing);
   for (auto& e : ev_) TRM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   set_restart();
@@ -266,7 +314,7 @@ Solver::~Solver() {
   for (auto& g : graphs_)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   for (auto& e : ev_) cudaEventDestroy(e);
-  if (ring_) cudaFreeHost(ring_);
+  if (ring_) ring_release(ring_);
 }
 
 void Solver::init_stencil(int nx, int ny, int nz, int order, double h,

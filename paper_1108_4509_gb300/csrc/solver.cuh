@@ -52,15 +52,21 @@ class Profiler {
 };
 
 // Device memory owned by one solver; freed in the destructor.
+// Device memory owned by one solver, stream-ordered: allocated from and
+// returned to the device's memory pool on the solver's stream, so creating
+// and destroying solvers never synchronises the device (cudaFree does), and
+// concurrent solves on other streams keep running.
 class DevArena {
  public:
   ~DevArena();
+  void set_stream(cudaStream_t s) { s_ = s; }
   void* alloc(size_t bytes);
   size_t bytes() const { return total_; }
 
  private:
   std::vector<void*> ptrs_;
   size_t total_ = 0;
+  cudaStream_t s_ = nullptr;
 };
 
 class Solver {
