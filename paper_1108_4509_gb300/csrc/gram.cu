@@ -113,6 +113,110 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The FP64 Gram of the mixed ladder's FP64-class steps (re-orthonormalization
+// and Rayleigh-Ritz) in double-float on the FP32 pipe: each FP64 value is
+// split into (hi, lo) FP32 terms as it is staged, and every product is
+// accumulated as hi*hi by a fused multiply-add TwoProduct plus the cross
+// terms, into a pair sum by TwoSum (low parts added plainly, renormalised
+// once per stage). Relative error about 2^-46 of sum |a||b| against
+// FP64's 2^-53 (the all-FP64 path and trm_gram keep k_gram<double>); about
+// three times the speed of FP64 on GB300, whose FP64 rate is 1/64 of FP32.
+struct DfAcc {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void fma(float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const F2 t = two_sum(h, p);
+    h = t.h;
+    l += t.l + e;
+  }
+  __device__ __forceinline__ void norm() {
+    const F2 t = quick_two_sum(h, l);
+    h = t.h;
+    l = t.l;
+  }
+};
+
+__global__ void __launch_bounds__(256)
+    k_gram_df(int64_t N, int m, const double* __restrict__ A,
+              Blocks<double> B, int64_t rows_per_split, int tiles_m,
+              double* __restrict__ part) {
+  __shared__ __align__(16) float Ah[TK][LDS], Al[TK][LDS];
+  __shared__ __align__(16) float Bh[TK][LDS], Bl[TK][LDS];
+  const int n = B.total();
+  const int split = blockIdx.x;
+  const int tile = blockIdx.y;
+  const int i0 = (tile % tiles_m) * TM;
+  const int j0 = (tile / tiles_m) * TN;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t rb = (int64_t)split * rows_per_split;
+  const int64_t re = min(N, rb + rows_per_split);
+  const double* pa[8];
+  const double* pb[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + 256 * q;
+    const int col = e / TK;
+    const int ia = i0 + col;
+    pa[q] = ia < m ? A + (int64_t)ia * N : nullptr;
+    const int jb = j0 + col;
+    if (jb < n) {
+      const int seg = jb / B.cols;
+      pb[q] = B.p[seg] + (int64_t)(jb - seg * B.cols) * N;
+    } else {
+      pb[q] = nullptr;
+    }
+  }
+  const int kk_ld = tid % TK;
+  DfAcc acc[4][4];
+  for (int64_t r0 = rb; r0 < re; r0 += TK) {
+    const int64_t r = r0 + kk_ld;
+    const bool rin = r < re;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int col = (tid + 256 * q) / TK;
+      const F2 a = df_of((rin && pa[q]) ? pa[q][r] : 0.0);
+      const F2 b = df_of((rin && pb[q]) ? pb[q][r] : 0.0);
+      Ah[kk_ld][col] = a.h;
+      Al[kk_ld][col] = a.l;
+      Bh[kk_ld][col] = b.h;
+      Bl[kk_ld][col] = b.l;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+      Vec4<float>::ld(&Ah[kk][tx * 4], ah);
+      Vec4<float>::ld(&Al[kk][tx * 4], al);
+      Vec4<float>::ld(&Bh[kk][ty * 4], bh);
+      Vec4<float>::ld(&Bl[kk][ty * 4], bl);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y].fma(ah[x], al[x], bh[y], bl[y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y].norm();
+    __syncthreads();
+  }
+  double* out = part + (size_t)split * m * n;
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int i = i0 + tx * 4 + x;
+    if (i >= m) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int j = j0 + ty * 4 + y;
+      if (j < n) out[i + (size_t)j * m] = (double)acc[x][y].h + (double)acc[x][y].l;
+    }
+  }
+}
+
 // out[e] = sum over splits of part[k * count + e]. A CTA owns 32 consecutive
 // outputs; its 8 warps take the splits k = g (mod 8) (coalesced rows of the
 // partials) and the 8 sums are added in a fixed order.
@@ -264,6 +368,26 @@ template void gram_in_scratch<float>(int64_t, int, const float*,
 template void gram_in_scratch<double>(int64_t, int, const double*,
                                       const Blocks<double>&, double*, double*,
                                       size_t, cudaStream_t);
+
+void gram_df(int64_t N, int m, const double* A, const Blocks<double>& B,
+             double* out, double* partials, size_t partials_cap,
+             cudaStream_t s) {
+  const int n = B.total();
+  if (m <= 0 || n <= 0) return;
+  int splits;
+  int64_t rows;
+  plan(N, m, n, &splits, &rows);
+  if ((size_t)splits * m * n > partials_cap)
+    throw Error(-2, "gram: partials buffer too small");
+  const int tiles_m = ceil_div(m, TM);
+  dim3 grid(splits, tiles_m * ceil_div(n, TN));
+  k_gram_df<<<grid, 256, 0, s>>>(N, m, A, B, rows, tiles_m, partials);
+  TRM_CHECK_LAUNCH();
+  const size_t count = (size_t)m * n;
+  k_sum_splits<<<ceil_div(count, 32), 256, 0, s>>>(partials, splits, count,
+                                                   out, nullptr);
+  TRM_CHECK_LAUNCH();
+}
 
 template void gram<float>(int64_t, int, const float*, const Blocks<float>&,
                           double*, double*, size_t, cudaStream_t, int*,

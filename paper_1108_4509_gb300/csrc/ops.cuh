@@ -102,6 +102,12 @@ void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
           int* err = nullptr, float* out32 = nullptr);
 void sum_splits(const double* part, int splits, size_t count, double* out,
                 cudaStream_t s);
+// A^T B of FP64 blocks in double-float on the FP32 pipe (about 2^-46
+// relative to sum |a||b|; see k_gram_df), for the mixed ladder's FP64-class
+// steps.
+void gram_df(int64_t N, int m, const double* A, const Blocks<double>& B,
+             double* out, double* partials, size_t partials_cap,
+             cudaStream_t s);
 // the same for partials stored as FP32 pairs (hi, then lo, per split)
 void sum_splits_pairs(const float* part, int splits, size_t count,
                       double* out, cudaStream_t s, float* out32 = nullptr);

@@ -646,6 +646,15 @@ void Solver::df_to_c64() {
   join_df(Cdf_, Cdf_ + nm, C64_, (int64_t)nm, s_);
 }
 
+// The N-deep Grams of FP64 blocks: FP64 in the all-FP64 mode, double-float
+// (FP64-class, on the FP32 pipe) in the mixed ladder.
+void Solver::gram64(const double* A, const Blocks<double>& b, double* out) {
+  if (opt_.precision == TRM_FP64)
+    gram<double>(N_, m_, A, b, out, part_, part_cap_, s_, &sc_->status);
+  else
+    gram_df(N_, m_, A, b, out, part_, part_cap_, s_);
+}
+
 // Fig. ONFIG in FP64: S = C^T C, S = L L^T, C <- C L^{-T}.
 void Solver::orth_fp64(double*& C, double*& Cn) {
   Blocks<double> b;
@@ -653,8 +662,7 @@ void Solver::orth_fp64(double*& C, double*& Cn) {
   b.cols = m_;
   b.count = 1;
   const double nm = (double)N_ * m_, m2N = nm * m_;
-  TRM_PROF(KC_GRAM64, 2 * m2N, 16 * nm,
-           gram<double>(N_, m_, C, b, S_, part_, part_cap_, s_, &sc_->status));
+  TRM_PROF(KC_GRAM64, 2 * m2N, 16 * nm, gram64(C, b, S_));
   TRM_PROF(KC_SMALL, 2.0 * m_ * m_ * m_ / 3, 0.0,
            chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_));
   TRM_PROF(KC_ROT64, m2N, 16 * nm,
@@ -682,7 +690,7 @@ void Solver::rr_rotate_fp64() {
   b.p[0] = X64_;
   b.cols = m_;
   b.count = 1;
-  gram<double>(N_, m_, C64_, b, Hp_, part_, part_cap_, s_, &sc_->status);
+  gram64(C64_, b, Hp_);
   make_A0(m_, Hp_, nullptr, A0_, s_);
   TRM_PROF(KC_EIG, 0.0, 0.0, sym_eig(m_, A0_, eigw_, Z_, eigws_, info_, s_));
   const double nm = (double)N_ * m_;
@@ -700,12 +708,12 @@ void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
   bx.p[0] = X64_;
   bx.cols = m_;
   bx.count = 1;
-  gram<double>(N_, m_, C, bx, Hp_, part_, part_cap_, s_, &sc_->status);
+  gram64(C, bx, Hp_);
   Blocks<double> bc;
   bc.p[0] = C;
   bc.cols = m_;
   bc.count = 1;
-  gram<double>(N_, m_, C, bc, S_, part_, part_cap_, s_, &sc_->status);
+  gram64(C, bc, S_);
   chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_);
   mm_gemm(m_, Linv_, false, Hp_, false, T1_, 1.0, 0.0, s_);
   mm_gemm(m_, T1_, false, Linv_, true, T2_, 1.0, 0.0, s_);

@@ -104,6 +104,7 @@ class Solver {
   template <typename T, typename Tm>
   void iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP);
   void iter_mp2();
+  void gram64(const double* A, const Blocks<double>& b, double* out);
   template <typename T>
   bool line_grams_fused(const T* C, const T* P, const T* HP, const T* G);
   // CUDA graphs of block iterations. An iteration is a fixed kernel
