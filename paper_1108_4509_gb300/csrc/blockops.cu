@@ -140,6 +140,83 @@ __device__ __forceinline__ void tile_product(int kb, int ke, LA loadA,
   }
 }
 
+// The same tile product for FP64 inputs in double-float (the FP32 pipe):
+// each staged value is split into FP32 (hi, lo) terms; the accumulators
+// are pair sums (DfAcc), renormalised after every stage.
+template <typename LA, typename LM>
+__device__ __forceinline__ void tile_product_df(
+    int kb, int ke, LA loadA, LM loadM, DfAcc (&acc)[4][4], float (*Ah)[GLD],
+    float (*Al)[GLD], float (*Mh)[GLD], float (*Ml)[GLD]) {
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int k0 = kb; k0 < ke; k0 += GK) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + 256 * q;
+      const int r = e & (GT - 1), kk = e >> 6;  // A: rows fastest
+      const F2 a = df_of((k0 + kk < ke) ? loadA(r, k0 + kk) : 0.0);
+      Ah[kk][r] = a.h;
+      Al[kk][r] = a.l;
+      const int c = e & (GT - 1), k2 = e >> 6;  // M: columns fastest
+      const F2 b = df_of((k0 + k2 < ke) ? loadM(k0 + k2, c) : 0.0);
+      Mh[k2][c] = b.h;
+      Ml[k2][c] = b.l;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+      ldv4(&Ah[kk][tx * 4], ah);
+      ldv4(&Al[kk][tx * 4], al);
+      ldv4(&Mh[kk][ty * 4], bh);
+      ldv4(&Ml[kk][ty * 4], bl);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y].fma(ah[x], al[x], bh[y], bl[y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y].norm();
+    __syncthreads();
+  }
+}
+
+// Y = A M (N x k times k x n, FP64 blocks) in double-float; with tri the
+// product is C R for R upper triangular (only k <= column contributes).
+__global__ void __launch_bounds__(256)
+    k_mult_df(int64_t N, int k, int n, const double* __restrict__ A,
+              const double* __restrict__ M, double* __restrict__ Y,
+              int tri) {
+  __shared__ __align__(16) float Ah[GK][GLD], Al[GK][GLD];
+  __shared__ __align__(16) float Mh[GK][GLD], Ml[GK][GLD];
+  const int64_t r0 = (int64_t)blockIdx.x * GT;
+  const int c0 = blockIdx.y * GT;
+  DfAcc acc[4][4];
+  auto loadA = [&](int r, int kk) -> double {
+    const int64_t row = r0 + r;
+    return row < N ? A[row + (int64_t)kk * N] : 0.0;
+  };
+  auto loadM = [&](int kk, int c) -> double {
+    return (c0 + c < n) ? M[kk + (int64_t)(c0 + c) * k] : 0.0;
+  };
+  const int kend = tri ? min(k, c0 + GT) : k;
+  tile_product_df(0, kend, loadA, loadM, acc, Ah, Al, Mh, Ml);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int64_t row = r0 + tx * 4 + x;
+    if (row >= N) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int col = c0 + ty * 4 + y;
+      if (col < n)
+        Y[row + (int64_t)col * N] = (double)acc[x][y].h + (double)acc[x][y].l;
+    }
+  }
+}
+
 // G = -2 (X' - C H'), with per-CTA partial sums of
 // tr(G^T G), tr(G^T M G), tr(G_prev^T M G), tr(G^T P_prev).
 template <typename T>
@@ -652,6 +729,13 @@ void rotate_split_df(int64_t N, int m, const float* Ch, const float* Cl,
   }
   dim3 grid(ceil_div(N, GT), ceil_div(m, GT));
   k_rotate_split_df<<<grid, 256, 0, s>>>(N, m, Ch, Cl, P, R, Cnh, Cnl, sc);
+  TRM_CHECK_LAUNCH();
+}
+
+void mult_df(int64_t N, int k, int n, const double* A, const double* M,
+             double* Y, bool upper_tri, cudaStream_t s) {
+  dim3 grid(ceil_div(N, GT), ceil_div(n, GT));
+  k_mult_df<<<grid, 256, 0, s>>>(N, k, n, A, M, Y, upper_tri ? 1 : 0);
   TRM_CHECK_LAUNCH();
 }
 

@@ -44,4 +44,26 @@ __device__ __forceinline__ double to_double(F2 a) {
   return (double)a.h + (double)a.l;
 }
 
+// Accumulator of products of pairs: a.b by a fused multiply-add TwoProduct
+// of the high parts plus the cross terms, added by TwoSum into the high part
+// and plainly into the low part; norm() renormalises (call it every few
+// dozen products). About 2^-46 relative to the sum of |a||b|.
+struct DfAcc {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void fma(float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const F2 t = two_sum(h, p);
+    h = t.h;
+    l += t.l + e;
+  }
+  __device__ __forceinline__ void norm() {
+    const F2 t = quick_two_sum(h, l);
+    h = t.h;
+    l = t.l;
+  }
+};
+
 }  // namespace trm

@@ -121,24 +121,6 @@ __global__ void __launch_bounds__(256)
 // once per stage). Relative error about 2^-46 of sum |a||b| against
 // FP64's 2^-53 (the all-FP64 path and trm_gram keep k_gram<double>); about
 // three times the speed of FP64 on GB300, whose FP64 rate is 1/64 of FP32.
-struct DfAcc {
-  float h = 0.f, l = 0.f;
-  __device__ __forceinline__ void fma(float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
-    float e = fmaf(ah, bh, -p);
-    e = fmaf(ah, bl, e);
-    e = fmaf(al, bh, e);
-    const F2 t = two_sum(h, p);
-    h = t.h;
-    l += t.l + e;
-  }
-  __device__ __forceinline__ void norm() {
-    const F2 t = quick_two_sum(h, l);
-    h = t.h;
-    l = t.l;
-  }
-};
-
 __global__ void __launch_bounds__(256)
     k_gram_df(int64_t N, int m, const double* __restrict__ A,
               Blocks<double> B, int64_t rows_per_split, int tiles_m,

@@ -218,6 +218,10 @@ void rotate_split_df(int64_t N, int m, const float* Ch, const float* Cl,
 // Y = A M for A: N x k (FP64), M: k x n FP64
 void mult(int64_t N, int k, int n, const double* A, const double* M,
           double* Y, cudaStream_t s);
+// The same in double-float on the FP32 pipe (about 2^-46 relative; the
+// mixed ladder's FP64-class steps); upper_tri: M is upper triangular (k = n)
+void mult_df(int64_t N, int k, int n, const double* A, const double* M,
+             double* Y, bool upper_tri, cudaStream_t s);
 // per-column 2-norms of X - C diag(lambda) into res (FP64 device m)
 void column_residuals(int64_t N, int m, const double* X, const double* C,
                       const double* lam, double* res, double* partials,

@@ -655,6 +655,14 @@ void Solver::gram64(const double* A, const Blocks<double>& b, double* out) {
     gram_df(N_, m_, A, b, out, part_, part_cap_, s_);
 }
 
+// N x m times m x m products of FP64 blocks, FP64 or double-float as gram64.
+void Solver::mult64(const double* A, const double* M, double* Y) {
+  if (opt_.precision == TRM_FP64)
+    mult(N_, m_, m_, A, M, Y, s_);
+  else
+    mult_df(N_, m_, m_, A, M, Y, false, s_);
+}
+
 // Fig. ONFIG in FP64: S = C^T C, S = L L^T, C <- C L^{-T}.
 void Solver::orth_fp64(double*& C, double*& Cn) {
   Blocks<double> b;
@@ -665,8 +673,11 @@ void Solver::orth_fp64(double*& C, double*& Cn) {
   TRM_PROF(KC_GRAM64, 2 * m2N, 16 * nm, gram64(C, b, S_));
   TRM_PROF(KC_SMALL, 2.0 * m_ * m_ * m_ / 3, 0.0,
            chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_));
-  TRM_PROF(KC_ROT64, m2N, 16 * nm,
-           (rotate<double, double>(N_, m_, C, nullptr, R_, Cn, nullptr, s_)));
+  if (opt_.precision == TRM_FP64)
+    TRM_PROF(KC_ROT64, m2N, 16 * nm,
+             (rotate<double, double>(N_, m_, C, nullptr, R_, Cn, nullptr, s_)));
+  else  // C L^{-T} in double-float
+    TRM_PROF(KC_ROT64, m2N, 16 * nm, mult_df(N_, m_, m_, C, R_, Cn, true, s_));
   std::swap(C, Cn);
 }
 
@@ -694,8 +705,7 @@ void Solver::rr_rotate_fp64() {
   make_A0(m_, Hp_, nullptr, A0_, s_);
   TRM_PROF(KC_EIG, 0.0, 0.0, sym_eig(m_, A0_, eigw_, Z_, eigws_, info_, s_));
   const double nm = (double)N_ * m_;
-  TRM_PROF(KC_ROT64, 2 * nm * m_, 16 * nm,
-           mult(N_, m_, m_, C64_, Z_, C64n_, s_));
+  TRM_PROF(KC_ROT64, 2 * nm * m_, 16 * nm, mult64(C64_, Z_, C64n_));
   std::swap(C64_, C64n_);
 }
 
@@ -720,8 +730,8 @@ void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
   make_A0(m_, T2_, nullptr, A0_, s_);
   sym_eig(m_, A0_, lam_, Z_, eigws_, info_, s_);
   mm_gemm(m_, R_, false, Z_, false, T1_, 1.0, 0.0, s_);
-  mult(N_, m_, m_, C, T1_, Cfin, s_);
-  mult(N_, m_, m_, X64_, T1_, Xfin, s_);
+  mult64(C, T1_, Cfin);
+  mult64(X64_, T1_, Xfin);
   fix_signs(N_, m_, Cfin, Xfin, part_, s_);
   column_residuals(N_, m_, Xfin, Cfin, lam_, res_, part_, s_);
 }

@@ -105,6 +105,7 @@ class Solver {
   void iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP);
   void iter_mp2();
   void gram64(const double* A, const Blocks<double>& b, double* out);
+  void mult64(const double* A, const double* M, double* Y);
   template <typename T>
   bool line_grams_fused(const T* C, const T* P, const T* HP, const T* G);
   // CUDA graphs of block iterations. An iteration is a fixed kernel
