@@ -249,7 +249,7 @@ void make_A0(int m, const double* Hp, const double* HD, double* A0,
 // terms from H' (diag zeroed), H_D, B = C^T P, Q = P^T P, P^T H P and
 // W = P^T G give alpha (into sc); then S = I + a (B + B^T) + a^2 Q is
 // factorised (in deviation form when dev) into Linv (may be null) and R = L^{-T}.
-// part: >= 4 * ceil(m/32)^2 doubles; gwork: max(2 m^2, chol_work_elems(m))
+// part: >= 16 * ceil(m/32)^2 doubles; gwork: max(2 m^2, chol_work_elems(m))
 // doubles (FP32 factorisations keep FP32 copies of B and Q there).
 template <typename Tm>
 void line_factor(int m, const double* Hp, const double* HD, const double* Bm,

@@ -509,8 +509,11 @@ __global__ void __launch_bounds__(1024)
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int I0 = blockIdx.x * 32, J0 = blockIdx.y * 32;
   const int i = I0 + tx, j = J0 + ty;
+  // blockIdx.z splits the k range of M = B B^T - B^T B; every other term is
+  // added by the first split only (the sums are linear in M)
+  const int ks = blockIdx.z, KS = gridDim.z;
   Tm M = 0;
-  for (int k0 = 0; k0 < m; k0 += 32) {
+  for (int k0 = 32 * ks; k0 < m; k0 += 32 * KS) {
     t0[tx][ty] = (I0 + tx < m && k0 + ty < m) ? (Tm)Bm[(I0 + tx) + (k0 + ty) * m] : (Tm)0;
     t1[tx][ty] = (J0 + tx < m && k0 + ty < m) ? (Tm)Bm[(J0 + tx) + (k0 + ty) * m] : (Tm)0;
     t2[tx][ty] = (k0 + tx < m && I0 + ty < m) ? (Tm)Bm[(k0 + tx) + (I0 + ty) * m] : (Tm)0;
@@ -530,25 +533,29 @@ __global__ void __launch_bounds__(1024)
   if (i < m && j < m) {
     const int e = i + j * m;
     const Tm a0 = (Tm)0.5 * ((Tm)Hp[e] + t0[ty][tx]) + (i == j ? (Tm)HD[i] : (Tm)0);
-    const Tm bij = (Tm)Bm[e], qij = (Tm)Q[e];
-    if (Bf) {  // FP32 copies for the factorisation that follows
-      Bf[e] = (float)bij;
-      Qf[e] = (float)qij;
-    }
-    const Tm s1 = bij + t1[ty][tx];
-    const Tm wij = (Tm)W[e], wji = t2[ty][tx];
-    v2 = a0 * M - (Tm)0.5 * s1 * (wij + wji);
-    v1 = -qij * a0;
-    if (i == j) {
-      v0 = -wij;
-      v1 += (Tm)HPP[e];
-      v3 = (Tm)Q[e];
+    v2 = a0 * M;
+    if (ks == 0) {
+      const Tm bij = (Tm)Bm[e], qij = (Tm)Q[e];
+      if (Bf) {  // FP32 copies for the factorisation that follows
+        Bf[e] = (float)bij;
+        Qf[e] = (float)qij;
+      }
+      const Tm s1 = bij + t1[ty][tx];
+      const Tm wij = (Tm)W[e], wji = t2[ty][tx];
+      v2 -= (Tm)0.5 * s1 * (wij + wji);
+      v1 = -qij * a0;
+      if (i == j) {
+        v0 = -wij;
+        v1 += (Tm)HPP[e];
+        v3 = (Tm)Q[e];
+      }
     }
   }
   double v[4] = {(double)v0, (double)v1, (double)v2, (double)v3};
   block_sum<4>(v, red);
   if (threadIdx.x == 0) {
-    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    const size_t b =
+        ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 #pragma unroll
     for (int q = 0; q < 4; ++q) part[b * 4 + q] = v[q];
   }
@@ -839,12 +846,21 @@ void chol_inv_dev(int m, const double* S, double* Linv, double* R,
                         sc, gwork, s);
 }
 
+// k-splits of the line terms: about 64 CTAs when the m x m tiles are few
+// (partials: 4 doubles per CTA, at most 4 ceil(m/32)^2 * 4 in all)
+static int line_ksplit(int m) {
+  const int t = ceil_div(m, 32);
+  const int ks = std::min(std::min(t, 4), std::max(1, 64 / (t * t)));
+  return std::max(1, ks);
+}
+
 template <typename Tm>
 void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
                  const double* Q, const double* HPP, const double* W,
                  double* Linv, double* R, IterScalars* sc, double* gwork,
                  double* part, bool dev, cudaStream_t s) {
   const int t = ceil_div(m, 32);
+  const int ksplit = line_ksplit(m);
   // FP32 factorisations take B and Q as FP32 copies written by the line
   // terms, placed after the factorisation's own FP32 working copy in gwork
   // (gwork holds max(2 m^2, chol_work_elems(m)) doubles)
@@ -854,16 +870,16 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
     Bf = reinterpret_cast<float*>(gwork) + chol_work_elems(m);
     Qf = Bf + (size_t)m * m;
   }
-  k_line_terms<Tm, double><<<dim3(t, t), 1024, 0, s>>>(m, Hp, HD, Bm, Q, HPP,
-                                                        W, part, Bf, Qf);
+  k_line_terms<Tm, double><<<dim3(t, t, ksplit), 1024, 0, s>>>(
+      m, Hp, HD, Bm, Q, HPP, W, part, Bf, Qf);
   TRM_CHECK_LAUNCH();
   // the factorisation kernel takes the line step from the partials first
   if (dev)
     chol_launch<Tm, true>(m, nullptr, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s,
-                          part, t * t);
+                          part, t * t * ksplit);
   else
     chol_launch<Tm, false>(m, nullptr, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s,
-                           part, t * t);
+                           part, t * t * ksplit);
 }
 
 // The FP32 path with the m x m inputs already in FP32 (copies the Gram sums
@@ -873,11 +889,12 @@ void line_factor32(int m, const float* Hp, const double* HD, const float* Bm,
                    double* Linv, double* R, IterScalars* sc, double* gwork,
                    double* part, cudaStream_t s) {
   const int t = ceil_div(m, 32);
-  k_line_terms<float, float><<<dim3(t, t), 1024, 0, s>>>(
+  const int ksplit = line_ksplit(m);
+  k_line_terms<float, float><<<dim3(t, t, ksplit), 1024, 0, s>>>(
       m, Hp, HD, Bm, Q, HPP, W, part, nullptr, nullptr);
   TRM_CHECK_LAUNCH();
   chol_launch<float, true>(m, nullptr, nullptr, nullptr, Bm, Q, Linv, R, sc,
-                           gwork, s, part, t * t);
+                           gwork, s, part, t * t * ksplit);
 }
 
 template void chol_inv_dev<float>(int, const double*, double*, double*,

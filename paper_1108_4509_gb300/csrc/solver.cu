@@ -274,7 +274,9 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   A0_ = d(mm);
   Bm_ = d(4 * mm);  // C^T P, then P^T [P HP G] (one m x 4m result)
   PG_ = Bm_ + mm;
-  T1_ = d(mm);
+  // (also the line terms' partials: 4 doubles per CTA, at most
+  // 4 * 4 ceil(m/32)^2 + 256 doubles, more than m^2 when m is small)
+  T1_ = d(std::max(mm, (size_t)16 * ceil_div(m, 32) * ceil_div(m, 32) + 256));
   T2_ = d(mm);
   S_ = d(mm);
   Linv_ = d(mm);
