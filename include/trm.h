@@ -278,7 +278,12 @@ typedef struct trm_server_ctx* trm_server;
 /* A stencil problem (as trm_create_stencil): V is a host array of
  * nx*ny*nz FP64 values (or NULL), copied at submission; opt.stream is
  * ignored (the server owns the streams); opt may be all defaults
- * (trm_default_options). */
+ * (trm_default_options). Warm start across related requests (e.g. the same
+ * grid with a perturbed potential): C0 (host, N x m column-major FP64, or
+ * NULL for the seeded random block) is copied at submission and starts the
+ * iteration, as trm_solve's C0; C_out (host, N x m, or NULL) receives the
+ * converged block when the solve ends, so the caller keeps it alive until
+ * trm_server_wait for this ticket returns. */
 typedef struct {
   int nx, ny, nz, order;
   double h;
@@ -286,6 +291,8 @@ typedef struct {
   int m;
   double tol;
   trm_options opt;
+  const double* C0;
+  double* C_out;
 } trm_problem;
 
 /* Device bytes a solve of an N x m problem allocates (the admission

@@ -67,7 +67,8 @@ class trm_kernel_stats(ct.Structure):
 class trm_problem(ct.Structure):
     _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
                 ("order", ct.c_int), ("h", ct.c_double), ("V", ct.c_void_p),
-                ("m", ct.c_int), ("tol", ct.c_double), ("opt", trm_options)]
+                ("m", ct.c_int), ("tol", ct.c_double), ("opt", trm_options),
+                ("C0", ct.c_void_p), ("C_out", ct.c_void_p)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -377,15 +378,29 @@ def trm_server_create(device_bytes, max_live):
     return h
 
 
-def trm_server_submit(server, shape, order, h, V, m, tol, opt=None):
+def trm_server_submit(server, shape, order, h, V, m, tol, opt=None, C0=None,
+                      C_out=None):
     """Queue a stencil problem; returns its ticket. V (host, nx*ny*nz FP64
-    or None) is copied before this returns."""
+    or None) and the warm start C0 (host (N, m) or None) are copied before
+    this returns; C_out (a Fortran-ordered float64 (N, m) array or None)
+    receives the converged block, so keep it alive until the wait returns."""
     nx, ny, nz = (tuple(shape) + (1, 1))[:3]
+    N = nx * ny * nz
     Varr, Vp = _host(V, np.float64)
-    if Varr is not None and Varr.size != nx * ny * nz:
+    if Varr is not None and Varr.size != N:
         raise ValueError("V must have nx*ny*nz entries")
+    c0arr, c0p = _colmajor(C0, np.float64) if C0 is not None else (None, None)
+    if c0arr is not None and c0arr.shape != (N, m):
+        raise ValueError("C0 must be an (N, m) block")
+    cop = None
+    if C_out is not None:
+        if not (isinstance(C_out, np.ndarray) and C_out.flags["F_CONTIGUOUS"]
+                and C_out.dtype == np.float64 and C_out.shape == (N, m)):
+            raise ValueError("C_out must be a Fortran-ordered float64 (N, m) array")
+        cop = C_out.ctypes.data_as(ct.c_void_p)
     p = trm_problem(nx=nx, ny=ny, nz=nz, order=order, h=h, V=Vp, m=m,
-                    tol=tol, opt=opt if opt is not None else trm_default_options())
+                    tol=tol, opt=opt if opt is not None else trm_default_options(),
+                    C0=c0p, C_out=cop)
     t = ct.c_int64()
     _check(lib.trm_server_submit(server, ct.byref(p), ct.byref(t)))
     return t.value

@@ -26,7 +26,8 @@ using Clock = std::chrono::steady_clock;
 struct Request {
   int64_t id = 0;
   trm_problem p{};
-  std::vector<double> V;  // copy of the caller's potential
+  std::vector<double> V;   // copy of the caller's potential
+  std::vector<double> C0;  // copy of the caller's warm start (or empty)
   size_t bytes = 0;
   int status = TRM_OK;
   std::string err;
@@ -77,8 +78,8 @@ void run_request(trm_server_ctx* s, std::shared_ptr<Request> r) {
       err = trm_last_global_error();
     } else {
       r->lambda.assign(r->p.m, 0.0);
-      status = trm_solve(h, r->lambda.data(), &r->E_G, nullptr, 0, nullptr,
-                         &r->stats);
+      status = trm_solve(h, r->lambda.data(), &r->E_G, r->p.C_out, 0,
+                         r->C0.empty() ? nullptr : r->C0.data(), &r->stats);
       if (status != TRM_OK) err = trm_last_error(h);
       trm_destroy(h);
     }
@@ -158,6 +159,8 @@ trm_status trm_server_submit(trm_server s, const trm_problem* p,
   r->p = *p;
   if (p->V) r->V.assign(p->V, p->V + N);
   r->p.V = nullptr;
+  if (p->C0) r->C0.assign(p->C0, p->C0 + N * p->m);
+  r->p.C0 = nullptr;
   r->bytes = trm::Solver::footprint(N, p->m);
   std::lock_guard<std::mutex> lock(s->mu);
   if (s->stop) return TRM_EINVAL;

@@ -88,3 +88,35 @@ def test_admission_by_footprint(trm):
     assert all(o[3] == 0 for o in outs)
     assert outs[0][4] < outs[1][4] < outs[2][4]  # served in order, one at a time
     assert np.array_equal(outs[0][0], outs[2][0])
+
+
+def test_warm_start_across_related_requests(trm):
+    """Next row 2 of the scope table: a request started from the converged
+    block of a related one (the same grid, the potential scaled by 1.02)
+    needs fewer iterations than a cold start and reaches the same
+    eigenvalues (the oracle's dense diagonalisation, 1e-9)."""
+    n, order, m = 16, 4, 16
+    shape, N = (n, n, n), n ** 3
+    V = ti.gaussian_wells(shape, 8, seed=11)
+    V2 = 1.02 * V
+    srv = trm.trm_server_create(4 * trm.trm_footprint_bytes(N, m), 4)
+    try:
+        CA = np.zeros((N, m), order="F")
+        ta = trm.trm_server_submit(srv, shape, order, 1.0, V, m, 1e-9,
+                                   _opts(trm), C_out=CA)
+        lam_a, eg_a, st_a, s_a, _ = trm.trm_server_wait(srv, ta, m)
+        tc = trm.trm_server_submit(srv, shape, order, 1.0, V2, m, 1e-9,
+                                   _opts(trm))
+        tw = trm.trm_server_submit(srv, shape, order, 1.0, V2, m, 1e-9,
+                                   _opts(trm), C0=CA)
+        lam_c, eg_c, st_c, s_c, _ = trm.trm_server_wait(srv, tc, m)
+        lam_w, eg_w, st_w, s_w, _ = trm.trm_server_wait(srv, tw, m)
+    finally:
+        trm.trm_server_destroy(srv)
+    assert s_a == 0 and s_c == 0 and s_w == 0
+    # C_out holds the converged (orthonormal) block of the first request
+    assert np.max(np.abs(CA.T @ CA - np.eye(m))) < 1e-10
+    assert st_w["iterations"] < st_c["iterations"], (st_w, st_c)
+    ref = op.lowest_eigenvalues(op.grid_hamiltonian(shape, order, 1.0, V2), m)
+    assert np.max(np.abs(lam_w - ref)) < 1e-9
+    assert np.max(np.abs(lam_c - ref)) < 1e-9
