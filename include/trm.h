@@ -202,6 +202,28 @@ trm_status trm_gram(int64_t N, int m, int n, int dtype, const void* A,
 trm_status trm_orthonormalize(int64_t N, int m, double* C, void* stream);
 
 /*
+ * Initial-guess extrapolation for a chain of related problems (Sec. 4 and
+ * the discussion cite it as the way to start close to the solution): from
+ * the converged blocks of the two previous problems, a block for the next.
+ * C_cur's columns are any basis of its subspace, so C_prev is first aligned
+ * to it by the orthogonal U that minimises ||C_prev U - C_cur||_F (the polar
+ * factor of M = C_prev^T C_cur, formed on the device as
+ * M (M^T M)^{-1/2} from the eigendecomposition of M^T M); then
+ *   C_next = C_cur + alpha (C_cur - C_prev U),
+ * orthonormalized as trm_orthonormalize does (C_next^T C_next = I, Cholesky
+ * factor, so the result is unique). alpha = 1 is linear extrapolation in
+ * equal steps; alpha = dt_next / dt_prev for unequal ones.
+ * C_prev, C_cur: device, N x m column-major FP64, orthonormal, read only.
+ * C_next: device, N x m, written (may not alias the inputs).
+ * Returns TRM_ENOTPD if M^T M has an eigenvalue below 1e-12 of its largest
+ * (the two subspaces are too far apart to align) or if C_next^T C_next is
+ * not positive definite; C_next then holds no result.
+ */
+trm_status trm_extrapolate(int64_t N, int m, const double* C_prev,
+                           const double* C_cur, double alpha, double* C_next,
+                           void* stream);
+
+/*
  * One iteration of Fig. TMFIG from the handle's current state in the given
  * precision mode (TRM_FP64 or TRM_FULL_SP or TRM_MP2), starting a new CG
  * sequence when restart != 0. The state is set by trm_set_block and read by

@@ -25,6 +25,11 @@ notes of the repository):
   trace((G_i - G_{i-1})^T M G_i) / trace(G_{i-1}^T M G_{i-1}) (exactly the
   printed formula when M = I). CG restarts (gamma = 0) when P_i is not a
   descent direction, trace(G_i^T P_i) <= 0.
+* Initial-guess extrapolation (cited in Sec. 4 and the discussion, ref. APJ,
+  not defined in the paper): :func:`extrapolate` aligns the previous block
+  to the current one by the orthogonal Procrustes rotation (the blocks are
+  only defined up to a rotation, Eq. TRHEQ's invariance), extrapolates
+  linearly, and orthonormalizes by Fig. ONFIG.
 * The closing diagonalisation of H (Sec. 2.1, after "HC = CH") is a
   Rayleigh-Ritz step on span(C) solved as the generalised problem
   (C^T H C) y = theta (C^T C) y, so a residual loss of orthonormality in C
@@ -300,6 +305,26 @@ def solve(H, C0: np.ndarray, tol: float = 1e-10, max_iter: int = 20000,
     return Result(lam=lam, E_G=energy_sum(lam), C=Cr, residuals=res,
                   iterations=it, converged=converged, energies=energies,
                   rms=rms, alphas=alphas)
+
+
+# ----------------------------------------------------------------------------
+# Initial guess for the next of a chain of related problems
+# ----------------------------------------------------------------------------
+def procrustes(C_prev: np.ndarray, C_cur: np.ndarray) -> np.ndarray:
+    """The orthogonal U minimising ||C_prev U - C_cur||_F: with the SVD
+    C_prev^T C_cur = W diag(s) V^T, U = W V^T (orthogonal Procrustes)."""
+    W, _, Vt = np.linalg.svd(C_prev.T @ C_cur)
+    return W @ Vt
+
+
+def extrapolate(C_prev: np.ndarray, C_cur: np.ndarray,
+                alpha: float = 1.0) -> np.ndarray:
+    """Block for the next problem of a chain from the converged blocks of the
+    two before: C_prev rotated onto C_cur's basis (:func:`procrustes`), then
+    C_cur + alpha (C_cur - C_prev U), orthonormalized (Fig. ONFIG). alpha = 1
+    extrapolates linearly over equal steps."""
+    U = procrustes(C_prev, C_cur)
+    return orthonormalize(C_cur + alpha * (C_cur - C_prev @ U))
 
 
 # ----------------------------------------------------------------------------

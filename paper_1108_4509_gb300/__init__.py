@@ -23,7 +23,7 @@ __all__ = [
     "trm_default_options", "trm_create_stencil", "trm_create_csr", "trm_solve",
     "trm_destroy", "trm_strerror", "trm_last_error", "trm_dim", "trm_apply_h",
     "trm_energy_gradient", "trm_gram", "trm_gram_noalloc",
-    "trm_orthonormalize", "trm_set_block",
+    "trm_orthonormalize", "trm_extrapolate", "trm_set_block",
     "trm_get_block", "trm_iterate", "trm_rayleigh_ritz", "trm_random_block",
     "trm_profile", "trm_profile_read", "trm_launch_count", "trm_kernel_stats",
     "Solver",
@@ -101,6 +101,7 @@ _SIGS = {
     "trm_gram": (_i, [_i64, _i, _i, _i, _p, _p, _p, _p]),
     "trm_gram_noalloc": (_i, [_i64, _i, _i, _i, _p, _p, _p, _p]),
     "trm_orthonormalize": (_i, [_i64, _i, _p, _p]),
+    "trm_extrapolate": (_i, [_i64, _i, _p, _p, _d, _p, _p]),
     "trm_set_block": (_i, [_h, _p]),
     "trm_get_block": (_i, [_h, _p]),
     "trm_iterate": (_i, [_h, _i, _i, _p, _p, _p]),
@@ -269,6 +270,16 @@ def trm_gram_noalloc(N, m, n, dtype, A_ptr, B_ptr, out_ptr, stream=0):
 def trm_orthonormalize(N, m, C_ptr, stream=0):
     return _check(lib.trm_orthonormalize(N, m, ct.c_void_p(C_ptr),
                                          ct.c_void_p(stream or 0)))
+
+
+def trm_extrapolate(N, m, C_prev_ptr, C_cur_ptr, alpha, C_next_ptr, stream=0):
+    """Device pointers (N x m column-major FP64): C_next = orth(C_cur +
+    alpha (C_cur - C_prev U)), U the orthogonal alignment of C_prev to
+    C_cur."""
+    return _check(lib.trm_extrapolate(N, m, ct.c_void_p(C_prev_ptr),
+                                      ct.c_void_p(C_cur_ptr), float(alpha),
+                                      ct.c_void_p(C_next_ptr),
+                                      ct.c_void_p(stream or 0)))
 
 
 def trm_set_block(handle, C_ptr):

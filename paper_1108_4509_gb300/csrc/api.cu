@@ -319,6 +319,87 @@ trm_status trm_orthonormalize(int64_t N, int m, double* C, void* stream) {
   });
 }
 
+trm_status trm_extrapolate(int64_t N, int m, const double* C_prev,
+                           const double* C_cur, double alpha, double* C_next,
+                           void* stream) {
+  if (N < 1 || m < 1 || m > 1024 || m > N || !C_prev || !C_cur || !C_next ||
+      C_next == C_prev || C_next == C_cur || !(alpha == alpha))
+    return static_cast<trm_status>(fail(nullptr, TRM_EINVAL, "invalid arguments to trm_extrapolate"));
+  return guarded(nullptr, [&]() {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t mm = (size_t)m * m;
+    const size_t Nm = (size_t)N * m;
+    const size_t cap = trm::gram_partials_doubles(N, m, m);
+    const size_t pw = trm::polar_work_doubles(m);
+    const size_t cw = trm::chol_work_elems(m);
+    const size_t bytes = (cap + 5 * mm + pw + cw + Nm) * sizeof(double) +
+                         sizeof(trm::IterScalars) + 2 * sizeof(int);
+    char* w = nullptr;
+    TRM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&w), bytes, s));
+    double* part = reinterpret_cast<double*>(w);
+    double* M = part + cap;
+    double* U = M + mm;
+    double* S = U + mm;
+    double* Linv = S + mm;
+    double* R = Linv + mm;
+    double* pwork = R + mm;
+    double* gw = pwork + pw;
+    double* Y = gw + cw;
+    auto* sc = reinterpret_cast<trm::IterScalars*>(Y + Nm);
+    int* info = reinterpret_cast<int*>(sc + 1);  // [eig sweeps, polar status]
+    int flags[2] = {0, 0};
+    int status = 0;
+    try {
+      TRM_CUDA(cudaMemsetAsync(sc, 0, sizeof(trm::IterScalars) + 2 * sizeof(int), s));
+      // align C_prev to C_cur: U = polar(C_prev^T C_cur)
+      trm::Blocks<double> b;
+      b.p[0] = C_cur;
+      b.cols = m;
+      b.count = 1;
+      trm::gram<double>(N, m, C_prev, b, M, part, cap, s);
+      trm::polar_factor(m, M, U, pwork, info + 1, info, s);
+      TRM_CUDA(cudaMemcpyAsync(flags, info, 2 * sizeof(int),
+                               cudaMemcpyDeviceToHost, s));
+      TRM_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+      cudaFreeAsync(w, s);
+      throw;
+    }
+    if (flags[1] & 1) {
+      TRM_CUDA(cudaFreeAsync(w, s));
+      TRM_CUDA(cudaStreamSynchronize(s));
+      return fail(nullptr, TRM_ENOTPD,
+                  "C_prev^T C_cur is singular: the subspaces are too far "
+                  "apart to align");
+    }
+    try {
+      trm::Blocks<double> b;
+      b.cols = m;
+      b.count = 1;
+      // C_next = (1 + alpha) C_cur - alpha C_prev U
+      trm::mult(N, m, m, C_prev, U, Y, s);
+      trm::lin_comb((int64_t)Nm, 1.0 + alpha, C_cur, -alpha, Y, C_next, s);
+      // Fig. ONFIG: C_next <- C_next L^{-T}
+      b.p[0] = C_next;
+      trm::gram<double>(N, m, C_next, b, S, part, cap, s);
+      trm::chol_inv<double>(m, S, Linv, R, sc, gw, s);
+      trm::rotate<double, double>(N, m, C_next, nullptr, R, Y, nullptr, s);
+      TRM_CUDA(cudaMemcpyAsync(C_next, Y, Nm * 8, cudaMemcpyDeviceToDevice, s));
+      TRM_CUDA(cudaMemcpyAsync(&status, &sc->status, sizeof(int),
+                               cudaMemcpyDeviceToHost, s));
+      TRM_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+      cudaFreeAsync(w, s);
+      throw;
+    }
+    TRM_CUDA(cudaFreeAsync(w, s));
+    TRM_CUDA(cudaStreamSynchronize(s));
+    if (status & 1)
+      return fail(nullptr, TRM_ENOTPD, "C_next^T C_next is not positive definite");
+    return (int)TRM_OK;
+  });
+}
+
 trm_status trm_set_block(trm_handle h, const double* C_device) {
   if (!h || !C_device) return static_cast<trm_status>(fail(h, TRM_EINVAL, "invalid arguments"));
   return guarded(h, [&]() {

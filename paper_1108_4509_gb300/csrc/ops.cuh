@@ -215,6 +215,9 @@ void rotate_split_df(int64_t N, int m, const float* Ch, const float* Cl,
                      const float* P, const double* R, float* Cnh, float* Cnl,
                      const IterScalars* sc, cudaStream_t s,
                      const TcWork* tw = nullptr);
+// out = a X + b Y elementwise over n FP64 values (out may alias X or Y)
+void lin_comb(int64_t n, double a, const double* X, double b, const double* Y,
+              double* out, cudaStream_t s);
 // Y = A M for A: N x k (FP64), M: k x n FP64
 void mult(int64_t N, int k, int n, const double* A, const double* M,
           double* Y, cudaStream_t s);
@@ -284,5 +287,13 @@ void zero_diag(int m, double* A, cudaStream_t s, float* A32 = nullptr);
 size_t sym_eig_work_doubles(int m);
 void sym_eig(int m, const double* A, double* w, double* Z, double* work,
              int* info, cudaStream_t s);
+// U = M (M^T M)^{-1/2}, the orthogonal factor of the polar decomposition
+// of M (m x m FP64): the orthogonal U minimising ||A U - B||_F when
+// M = A^T B. M^T M = Z diag(w) Z^T by sym_eig; an eigenvalue at or below
+// 1e-12 of the largest sets *status bit 1. work: polar_work_doubles(m);
+// info as sym_eig's.
+size_t polar_work_doubles(int m);
+void polar_factor(int m, const double* M, double* U, double* work, int* status,
+                  int* info, cudaStream_t s);
 
 }  // namespace trm

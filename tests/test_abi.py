@@ -85,3 +85,11 @@ def test_footprint_estimate(trm):
     assert 92 * 4096 * 16 < a < b
     assert 92 * 110592 * 128 <= b < 130 * 110592 * 128
     assert trm.trm_footprint_bytes(1, 1) == 0
+
+
+def test_extrapolate_rejects_invalid_arguments_on_the_host(trm):
+    # m > N, and an output aliasing an input: refused before any CUDA call
+    for args in ((10, 20, 8, 16, 1.0, 24), (100, 4, 8, 16, 1.0, 16)):
+        with pytest.raises(trm.TrmError) as e:
+            trm.trm_extrapolate(*args)
+        assert e.value.status == -1

@@ -261,3 +261,74 @@ def test_polak_ribiere_beats_steepest_descent():
     sd = trm.solve(H, C0, tol=1e-8, cg=False, max_iter=3 * cg.iterations)
     assert cg.converged
     assert (not sd.converged) or sd.iterations > 2 * cg.iterations
+
+
+# ----------------------------------------------------------------------------
+# Initial-guess extrapolation for a chain of related problems
+# ----------------------------------------------------------------------------
+def _rotation(m, seed):
+    q, r = np.linalg.qr(np.random.default_rng(seed).standard_normal((m, m)))
+    return q * np.sign(np.diag(r))
+
+
+def _subspace_path(N, m, seed):
+    """A smooth family of m-dimensional subspaces with a closed form:
+    C(t) = exp(t K) E_m (K skew, E_m the first m unit vectors)."""
+    K = np.random.default_rng(seed).standard_normal((N, N))
+    K = (K - K.T) / (2.0 * math.sqrt(N))
+    E = np.eye(N)[:, :m]
+    return lambda t: sla.expm(t * K) @ E
+
+
+def test_procrustes_recovers_a_rotation_and_minimises():
+    N, m = 80, 6
+    C = trm.orthonormalize(np.random.default_rng(3).standard_normal((N, m)))
+    Q = _rotation(m, 4)
+    U = trm.procrustes(C, C @ Q)
+    assert np.max(np.abs(U - Q)) < 1e-13          # U^T would fail here
+    B = trm.orthonormalize(C + 0.3 * np.random.default_rng(5).standard_normal((N, m)))
+    U = trm.procrustes(C, B)
+    assert np.max(np.abs(U.T @ U - np.eye(m))) < 1e-13
+    best = np.linalg.norm(C @ U - B)
+    rng = np.random.default_rng(6)
+    for _ in range(30):
+        S = rng.standard_normal((m, m)) * 0.05
+        W = sla.expm(S - S.T)
+        assert np.linalg.norm(C @ U @ W - B) >= best - 1e-12
+
+
+def test_extrapolate_keeps_a_stationary_subspace():
+    N, m = 70, 5
+    C = trm.orthonormalize(np.random.default_rng(7).standard_normal((N, m)))
+    assert np.max(np.abs(trm.extrapolate(C @ _rotation(m, 8), C) - C)) < 1e-13
+    assert np.max(np.abs(trm.extrapolate(
+        trm.orthonormalize(C + 0.1), C, alpha=0.0) - C)) < 1e-13
+
+
+def test_extrapolate_is_second_order_along_a_smooth_path():
+    """The previous block is off the next subspace by O(dt), the extrapolated
+    one by O(dt^2): halving dt halves the first error and quarters the
+    second, whatever basis each block is given in."""
+    N, m = 60, 5
+    C = _subspace_path(N, m, 9)
+    e_prev, e_extr = [], []
+    for k, dt in enumerate((0.04, 0.02, 0.01)):
+        C0 = C(0.0) @ _rotation(m, 10 + k)
+        C1 = C(dt) @ _rotation(m, 20 + k)
+        e_prev.append(trm.sin_max_angle(C1, C(2 * dt)))
+        e_extr.append(trm.sin_max_angle(trm.extrapolate(C0, C1), C(2 * dt)))
+    for a, b in zip(e_prev, e_prev[1:]):
+        assert 1.8 < a / b < 2.2
+    for a, b in zip(e_extr, e_extr[1:]):
+        assert 3.5 < a / b < 4.5
+    assert e_extr[-1] < 0.05 * e_prev[-1]
+
+
+def test_extrapolate_is_equivariant_under_basis_changes():
+    N, m = 50, 4
+    C = _subspace_path(N, m, 11)
+    C0, C1 = C(0.0), C(0.1)
+    Q0, Q1 = _rotation(m, 12), _rotation(m, 13)
+    a = trm.extrapolate(C0, C1, alpha=0.7)
+    b = trm.extrapolate(C0 @ Q0, C1 @ Q1, alpha=0.7)
+    assert trm.sin_max_angle(a, b) < 1e-13
