@@ -600,13 +600,6 @@ __global__ void k_random(int64_t total, uint64_t seed, double* __restrict__ C) {
   }
 }
 
-__global__ void k_lin_comb(int64_t n, double a, const double* X, double b,
-                           const double* Y, double* out) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = a * X[i] + b * Y[i];
-}
-
 int elem_grid_x(int64_t N) {
   int g = ceil_div(N, 256 * 4);
   return g < 1 ? 1 : (g > 4096 ? 4096 : g);
@@ -812,12 +805,5 @@ template void rotate<double, double>(int64_t, int, const double*,
                                      const double*, const double*, double*,
                                      const IterScalars*, cudaStream_t,
                                      const TcWork*);
-
-void lin_comb(int64_t n, double a, const double* X, double b, const double* Y,
-              double* out, cudaStream_t s) {
-  if (n <= 0) return;
-  k_lin_comb<<<elem_grid_x(n), 256, 0, s>>>(n, a, X, b, Y, out);
-  TRM_CHECK_LAUNCH();
-}
 
 }  // namespace trm
