@@ -30,6 +30,14 @@ notes of the repository):
   to the current one by the orthogonal Procrustes rotation (the blocks are
   only defined up to a rotation, Eq. TRHEQ's invariance), extrapolates
   linearly, and orthonormalizes by Fig. ONFIG.
+* Generalized problem H e = lambda S e with S symmetric positive definite
+  (Sec. 2.1 calls the extension straightforward and gives no formulas): the
+  constraint becomes C^T S C = I, so the orthonormalization factors C^T S C,
+  the gradient is G = -2 (H C - S C H_C), the line-search overlap is
+  (C + aP)^T S (C + aP), the preconditioner is diag(1 / (H_jj - sigma S_jj))
+  with sigma = min_k H_kk / S_kk - 1, and the Rayleigh-Ritz step solves
+  (C^T H C) y = theta (C^T S C) y. Every function takes S = None (the
+  identity) for the standard problem.
 * The closing diagonalisation of H (Sec. 2.1, after "HC = CH") is a
   Rayleigh-Ritz step on span(C) solved as the generalised problem
   (C^T H C) y = theta (C^T C) y, so a residual loss of orthonormality in C
@@ -50,10 +58,16 @@ from .operator import apply_h
 # ----------------------------------------------------------------------------
 # Fig. ONFIG: orthonormalization by Cholesky factorisation
 # ----------------------------------------------------------------------------
-def orthonormalize(C: np.ndarray) -> np.ndarray:
-    """Fig. ONFIG. (1) S = C^T C; (2) S = L L^T; (3) L^{-1}; (4) C_out = C_in L^{-T}."""
-    S = C.T @ C                                              # (1) DSYRK
-    L = np.linalg.cholesky(S)                                # (2) DPOTRF
+def _apply_s(S, C):
+    """S C, or C when S is None (the standard problem)."""
+    return C if S is None else apply_h(S, C)
+
+
+def orthonormalize(C: np.ndarray, S=None) -> np.ndarray:
+    """Fig. ONFIG. (1) S_C = C^T S C; (2) S_C = L L^T; (3) L^{-1};
+    (4) C_out = C_in L^{-T} (S = None: C^T C)."""
+    Sc = C.T @ _apply_s(S, C)                                # (1) DSYRK
+    L = np.linalg.cholesky(Sc)                               # (2) DPOTRF
     Linv = sla.solve_triangular(L, np.eye(L.shape[0]), lower=True)  # (3) DTRTRI
     return C @ Linv.T                                        # (4) DTRMM
 
@@ -61,18 +75,20 @@ def orthonormalize(C: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # Fig. EGFIG: energy and gradient
 # ----------------------------------------------------------------------------
-def energy_gradient_alg1(H, C):
-    """Fig. EGFIG, Algorithm-1: X = HC; H = C^T X; E = tr H; G = -2 (X - C H).
+def energy_gradient_alg1(H, C, S=None):
+    """Fig. EGFIG, Algorithm-1: X = HC; H = C^T X; E = tr H; G = -2 (X - C H)
+    (generalized: G = -2 (X - S C H)).
 
     Returns (E, G, X, Hc)."""
     X = apply_h(H, C)                       # (1)
     Hc = C.T @ X                            # (2)
     E = float(np.trace(Hc))                 # (3)
-    G = -2.0 * (X - C @ Hc)                 # (4)
+    G = -2.0 * (X - _apply_s(S, C) @ Hc)    # (4)
     return E, G, X, Hc
 
 
-def energy_gradient_alg2(H, C, zero_diag: bool = False, need_gradient=True):
+def energy_gradient_alg2(H, C, zero_diag: bool = False, need_gradient=True,
+                         S=None):
     """Fig. EGFIG, Algorithm-2, steps (1)-(7).
 
     (1) X = HC; (2) H_D = diag(C^T X); (3) E = tr H_D; (4) stop here if G is not
@@ -84,11 +100,12 @@ def energy_gradient_alg2(H, C, zero_diag: bool = False, need_gradient=True):
     E = float(np.sum(HD))                                   # (3)
     if not need_gradient:                                   # (4)
         return E, None, X, HD, None, None
-    Xp = X - C * HD[None, :]                                # (5)
+    SC = _apply_s(S, C)                     # generalized: S C for C below
+    Xp = X - SC * HD[None, :]                               # (5)
     Hp = C.T @ Xp                                           # (6)
     if zero_diag:
         np.fill_diagonal(Hp, 0.0)
-    G = -2.0 * (Xp - C @ Hp)                                # (7)
+    G = -2.0 * (Xp - SC @ Hp)                               # (7)
     return E, G, X, HD, Xp, Hp
 
 
@@ -100,11 +117,16 @@ def rms_residual(G: np.ndarray) -> float:
 # ----------------------------------------------------------------------------
 # Polak-Ribiere (Sec. 2.1) and the preconditioner (Eq. PCEQ)
 # ----------------------------------------------------------------------------
-def diagonal_preconditioner(H) -> np.ndarray:
-    """diag(M) = 1 / (H_jj - sigma), sigma = min_k H_kk - 1 (SPD, bounded)."""
+def diagonal_preconditioner(H, S=None) -> np.ndarray:
+    """diag(M) = 1 / (H_jj - sigma), sigma = min_k H_kk - 1 (SPD, bounded);
+    generalized: 1 / (H_jj - sigma S_jj), sigma = min_k H_kk / S_kk - 1."""
     d = np.asarray(H.diagonal(), dtype=np.float64)
-    sigma = d.min() - 1.0
-    return 1.0 / (d - sigma)
+    if S is None:
+        sigma = d.min() - 1.0
+        return 1.0 / (d - sigma)
+    sd = np.asarray(S.diagonal(), dtype=np.float64)
+    sigma = (d / sd).min() - 1.0
+    return 1.0 / (d - sigma * sd)
 
 
 def polak_ribiere(G, G_prev, MG, MG_prev) -> float:
@@ -121,7 +143,7 @@ def polak_ribiere(G, G_prev, MG, MG_prev) -> float:
 @dataclass
 class LineMatrices:
     """m x m projections of the block pencil C + alpha P:
-    S(alpha) = S0 + alpha (B + B^T) + alpha^2 Q   = (C + aP)^T (C + aP)
+    S(alpha) = S0 + alpha (B + B^T) + alpha^2 Q   = (C + aP)^T S (C + aP)
     A(alpha) = A0 + alpha (K + K^T) + alpha^2 Ap  = (C + aP)^T H (C + aP)."""
     S0: np.ndarray
     B: np.ndarray
@@ -131,9 +153,11 @@ class LineMatrices:
     Ap: np.ndarray
 
 
-def line_matrices(C, P, X, HP) -> LineMatrices:
-    """The five Gram products C^T C, C^T P, P^T P, C^T H C, C^T H P, P^T H P."""
-    return LineMatrices(S0=C.T @ C, B=C.T @ P, Q=P.T @ P,
+def line_matrices(C, P, X, HP, S=None) -> LineMatrices:
+    """The Gram products C^T S C, C^T S P, P^T S P, C^T H C, C^T H P, P^T H P
+    (S = None: the identity)."""
+    SC, SP = _apply_s(S, C), _apply_s(S, P)
+    return LineMatrices(S0=C.T @ SC, B=C.T @ SP, Q=P.T @ SP,
                         A0=C.T @ X, K=C.T @ HP, Ap=P.T @ HP)
 
 
@@ -211,27 +235,30 @@ def line_minimize(M: LineMatrices, alpha_guess: float, rtol: float = 1e-10):
 # ----------------------------------------------------------------------------
 # Closing diagonalisation of H (Sec. 2.1)
 # ----------------------------------------------------------------------------
-def rayleigh_ritz(H, C):
-    """Diagonalise H = C^T H C on span(C): (C^T H C) y = theta (C^T C) y.
+def rayleigh_ritz(H, C, S=None):
+    """Diagonalise H = C^T H C on span(C): (C^T H C) y = theta (C^T S C) y.
 
-    Returns (lambda ascending, C Y with unit columns, column residual norms
-    ||H c_j - lambda_j c_j||). Each column's sign makes its largest-magnitude
-    entry positive (presentation only)."""
+    Returns (lambda ascending, C Y (S-orthonormal columns), column residual
+    norms ||H c_j - lambda_j S c_j||). Each column's sign makes its
+    largest-magnitude entry positive (presentation only)."""
     X = apply_h(H, C)
+    SC = _apply_s(S, C)
     Hc = C.T @ X
     Hc = 0.5 * (Hc + Hc.T)
-    S = C.T @ C
-    S = 0.5 * (S + S.T)
-    lam, Y = sla.eigh(Hc, S)
+    Sc = C.T @ SC
+    Sc = 0.5 * (Sc + Sc.T)
+    lam, Y = sla.eigh(Hc, Sc)
     Cr = C @ Y
     Xr = X @ Y
+    SCr = SC @ Y
     m = Cr.shape[1]
     piv = np.argmax(np.abs(Cr), axis=0)
     sgn = np.sign(Cr[piv, np.arange(m)])
     sgn[sgn == 0] = 1.0
     Cr *= sgn
     Xr *= sgn
-    res = np.linalg.norm(Xr - Cr * lam[None, :], axis=0)
+    SCr *= sgn
+    res = np.linalg.norm(Xr - SCr * lam[None, :], axis=0)
     return lam, Cr, res
 
 
@@ -258,15 +285,17 @@ class Result:
 
 def solve(H, C0: np.ndarray, tol: float = 1e-10, max_iter: int = 20000,
           precond: bool = False, algorithm: int = 1, zero_diag: bool = False,
-          cg: bool = True, callback=None) -> Result:
+          cg: bool = True, callback=None, S=None) -> Result:
     """Fig. TMFIG. C_0 = orthonormalize(random guess); for i = 0, 1, ...:
     E_i, G_i (Fig. EGFIG); convergence check; P_i = G'_i + gamma_i P_{i-1} with
     G' = M G (Eq. PCEQ); C_{i+1} = C_i + alpha_i P_i; orthonormalize (Fig. ONFIG).
     Ends with the diagonalisation of H on span(C). ``cg=False`` keeps
-    gamma_i = 0 (steepest descent), used only to show what the CG term buys."""
-    C = orthonormalize(np.array(C0, dtype=np.float64))
+    gamma_i = 0 (steepest descent), used only to show what the CG term buys.
+    ``S``: the overlap of the generalized problem H e = lambda S e (None for
+    the standard one)."""
+    C = orthonormalize(np.array(C0, dtype=np.float64), S)
     m = C.shape[1]
-    Mdiag = diagonal_preconditioner(H) if precond else None
+    Mdiag = diagonal_preconditioner(H, S) if precond else None
     G_prev = MG_prev = P_prev = None
     alpha = None
     energies, rms, alphas = [], [], []
@@ -274,9 +303,9 @@ def solve(H, C0: np.ndarray, tol: float = 1e-10, max_iter: int = 20000,
     it = 0
     for it in range(max_iter + 1):
         if algorithm == 1:
-            E, G, X, _ = energy_gradient_alg1(H, C)
+            E, G, X, _ = energy_gradient_alg1(H, C, S)
         else:
-            E, G, X, _, _, _ = energy_gradient_alg2(H, C, zero_diag)
+            E, G, X, _, _, _ = energy_gradient_alg2(H, C, zero_diag, S=S)
         r = rms_residual(G)
         energies.append(E)
         rms.append(r)
@@ -294,14 +323,14 @@ def solve(H, C0: np.ndarray, tol: float = 1e-10, max_iter: int = 20000,
         if float(np.sum(G * P)) <= 0.0:          # not a descent direction
             P = MG.copy()
         HP = apply_h(H, P)
-        LM = line_matrices(C, P, X, HP)
+        LM = line_matrices(C, P, X, HP, S)
         if alpha is None or alpha <= 0.0:
             alpha = 0.1 * math.sqrt(m) / max(np.linalg.norm(P), 1e-300)
         alpha, _ = line_minimize(LM, alpha)
         alphas.append(alpha)
-        C = orthonormalize(C + alpha * P)
+        C = orthonormalize(C + alpha * P, S)
         G_prev, MG_prev, P_prev = G, MG, P
-    lam, Cr, res = rayleigh_ritz(H, C)
+    lam, Cr, res = rayleigh_ritz(H, C, S)
     return Result(lam=lam, E_G=energy_sum(lam), C=Cr, residuals=res,
                   iterations=it, converged=converged, energies=energies,
                   rms=rms, alphas=alphas)

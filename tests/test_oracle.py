@@ -332,3 +332,109 @@ def test_extrapolate_is_equivariant_under_basis_changes():
     a = trm.extrapolate(C0, C1, alpha=0.7)
     b = trm.extrapolate(C0 @ Q0, C1 @ Q1, alpha=0.7)
     assert trm.sin_max_angle(a, b) < 1e-13
+
+
+# ----------------------------------------------------------------------------
+# Generalized problem H e = lambda S e (S SPD: hat-function overlap)
+# ----------------------------------------------------------------------------
+def _overlap(shape):
+    import scipy.sparse as sp
+    rp, ci, v = ti.hat_overlap_csr(shape)
+    N = int(np.prod(shape))
+    return sp.csr_matrix((v, ci, rp), shape=(N, N))
+
+
+def _hat_closed_form(shape, h):
+    """V = 0, order 2: H and S are tensor products of tridiagonal Toeplitz
+    matrices with the common eigenvectors sin(j k pi / (n + 1)), so
+    lambda = sum_a t (2 - 2 cos th_a) / prod_a (4 + 2 cos th_a) / 6."""
+    t = 0.5 / (h * h)
+    ths = [np.pi * np.arange(1, n + 1) / (n + 1) for n in shape]
+    num = sum(np.meshgrid(*[t * (2 - 2 * np.cos(th)) for th in ths],
+                          indexing="ij"))
+    den = np.prod(np.meshgrid(*[(4 + 2 * np.cos(th)) / 6 for th in ths],
+                              indexing="ij"), axis=0)
+    return np.sort((num / den).ravel())
+
+
+def test_hat_overlap_is_the_tensor_product_and_spd():
+    shape = (5, 4, 6)
+    S = _overlap(shape).toarray()
+    T = [np.diag(np.full(n, 4 / 6)) + np.diag(np.full(n - 1, 1 / 6), 1)
+         + np.diag(np.full(n - 1, 1 / 6), -1) for n in shape]
+    K = np.kron(T[2], np.kron(T[1], T[0]))       # x fastest
+    assert np.max(np.abs(S - K)) == 0.0
+    w = np.linalg.eigvalsh(S)
+    assert w.min() > 0.0 and np.allclose(S, S.T)
+
+
+def test_generalized_dense_spectrum_equals_closed_form():
+    shape, h = (5, 4, 6), 1.0
+    H = op.grid_hamiltonian(shape, 2, h).toarray()
+    S = _overlap(shape).toarray()
+    lam = sla.eigh(H, S, eigvals_only=True)
+    assert np.max(np.abs(lam - _hat_closed_form(shape, h))) < 1e-12
+
+
+def test_generalized_gradient_is_minus_constrained_derivative():
+    """C^T S C = I: d/de E(orthonormalize_S(C + e D)) at e = 0 is
+    -tr(D^T G) with G = -2 (H C - S C H_C); C^T G = 0 still holds."""
+    shape = (6, 5, 4)
+    N, m = int(np.prod(shape)), 4
+    H = op.grid_hamiltonian(shape, 2, 1.0, ti.gaussian_wells(shape, 3, seed=5))
+    S = _overlap(shape)
+    C = trm.orthonormalize(ti.random_block(N, m, seed=6), S)
+    assert np.max(np.abs(C.T @ (S @ C) - np.eye(m))) < 1e-13
+    E, G, _, _ = trm.energy_gradient_alg1(H, C, S)
+    E2, G2, _, _, _, _ = trm.energy_gradient_alg2(H, C, S=S)
+    assert E2 == pytest.approx(E, rel=1e-13)
+    assert np.max(np.abs(G2 - G)) < 1e-12
+    assert np.max(np.abs(C.T @ G)) < 1e-12
+    D = ti.random_block(N, m, seed=78)
+    eps = 1e-5
+    Ep = trm.energy_gradient_alg1(H, trm.orthonormalize(C + eps * D, S), S)[0]
+    Em = trm.energy_gradient_alg1(H, trm.orthonormalize(C - eps * D, S), S)[0]
+    assert (Ep - Em) / (2 * eps) == pytest.approx(-float(np.sum(D * G)),
+                                                  rel=1e-7)
+    # the line-search overlap is that of the S-orthonormalized pencil
+    P = ti.random_block(N, m, seed=79)
+    LM = trm.line_matrices(C, P, H @ C, H @ P, S)
+    a = 0.3
+    Y = C + a * P
+    assert np.max(np.abs(LM.S0 + a * (LM.B + LM.B.T) + a * a * LM.Q
+                         - Y.T @ (S @ Y))) < 1e-12
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_generalized_solve_vs_dense_and_closed_form(precond):
+    shape = (7, 6, 8)
+    N, m = int(np.prod(shape)), 6
+    S = _overlap(shape)
+    H0 = op.grid_hamiltonian(shape, 2, 1.0)
+    r = trm.solve(H0, ti.random_block(N, m, seed=1), tol=1e-11,
+                  precond=precond, S=S)
+    assert r.converged
+    want = _hat_closed_form(shape, 1.0)[:m]
+    assert np.max(np.abs(r.lam - want)) < 1e-10 * abs(want).max()
+    H = op.grid_hamiltonian(shape, 4, 1.0, ti.gaussian_wells(shape, 6, seed=2))
+    r = trm.solve(H, ti.random_block(N, m, seed=3), tol=1e-11,
+                  precond=precond, S=S)
+    assert r.converged
+    lam = sla.eigh(H.toarray(), S.toarray(), eigvals_only=True,
+                   subset_by_index=[0, m - 1])
+    assert np.max(np.abs(r.lam - lam)) < 1e-10
+    assert np.max(np.abs(r.C.T @ (S @ r.C) - np.eye(m))) < 1e-12
+    assert r.residuals.max() < 1e-9
+
+
+def test_generalized_with_diagonal_S_is_the_scaled_standard_problem():
+    """S = D diagonal: H e = lambda D e is D^{-1/2} H D^{-1/2} f = lambda f."""
+    import scipy.sparse as sp
+    shape = (6, 6, 6)
+    N, m = int(np.prod(shape)), 5
+    d = 0.5 + ti.uniform01(9, np.arange(N))
+    H = op.grid_hamiltonian(shape, 2, 1.0, ti.gaussian_wells(shape, 4, seed=8))
+    r = trm.solve(H, ti.random_block(N, m, seed=4), tol=1e-11, precond=True,
+                  S=sp.diags(d).tocsr())
+    Hs = H.toarray() / np.sqrt(d)[:, None] / np.sqrt(d)[None, :]
+    assert np.max(np.abs(r.lam - np.linalg.eigvalsh(Hs)[:m])) < 1e-10

@@ -10,6 +10,8 @@ the *inputs* the method is run on:
 * the Gaussian-well potential V on a grid;
 * an explicit CSR copy of a grid Hamiltonian -1/2 nabla^2 + V, for callers that
   hand the solver a sparse matrix instead of a stencil description;
+* the overlap matrix S of trilinear finite-element hat functions on the same
+  grid, an SPD matrix for the generalized problem H e = lambda S e;
 * the named synthetic workloads (grid size, stencil order, well count, m).
 
 The CUDA path draws C0 on the device with its own implementation of the same
@@ -24,7 +26,7 @@ import numpy as np
 
 __all__ = [
     "splitmix64", "u64", "uniform01", "random_block", "gaussian_wells",
-    "grid_csr", "Workload", "WORKLOADS", "workload",
+    "grid_csr", "hat_overlap_csr", "Workload", "WORKLOADS", "workload",
 ]
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -164,6 +166,56 @@ def grid_csr(shape, order: int, h: float, V, vals_dtype=np.float64):
         fill[mask] += 1
     return (rowptr.astype(np.int32), cols.astype(np.int32),
             vals.astype(vals_dtype))
+
+
+def hat_overlap_csr(shape):
+    """Explicit CSR of the overlap S_ij = <phi_i, phi_j> of the trilinear hat
+    functions of a uniform Dirichlet grid, in units of the cell volume: the
+    tensor product over the grid's axes of the 1-D overlap tridiag(1, 4, 1)/6
+    (27 points in 3-D). S is symmetric positive definite, the basis being
+    non-orthogonal. Same row order, layout and return types as
+    :func:`grid_csr` (float64 values)."""
+    nx, ny, nz = (tuple(shape) + (1, 1))[:3]
+    N = nx * ny * nz
+    if N >= 2 ** 31:
+        raise ValueError("grid too large for int32 CSR")
+    idx = np.arange(N, dtype=np.int64)
+    x = idx % nx
+    y = (idx // nx) % ny
+    z = idx // (nx * ny)
+    axes = [(x, nx, 1), (y, ny, nx), (z, nz, nx * ny)]
+    # per axis: offsets -1, 0, +1 with weights 1/6, 4/6, 1/6 (an axis of
+    # length 1 contributes the single weight 1)
+    per_axis = []
+    for coord, n, stride in axes:
+        if n == 1:
+            per_axis.append([(0, 1.0, np.ones(N, dtype=bool))])
+        else:
+            per_axis.append([(-stride, 1.0 / 6.0, coord - 1 >= 0),
+                             (0, 4.0 / 6.0, np.ones(N, dtype=bool)),
+                             (stride, 1.0 / 6.0, coord + 1 < n)])
+    entries = []
+    for oz, wz, mz in per_axis[2]:
+        for oy, wy, my in per_axis[1]:
+            for ox, wx, mx in per_axis[0]:
+                entries.append((oz + oy + ox, wx * wy * wz, mx & my & mz))
+    entries.sort(key=lambda e: e[0])        # ascending columns in each row
+    counts = np.zeros(N, dtype=np.int64)
+    for _, _, mask in entries:
+        counts += mask
+    rowptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    cols = np.empty(nnz, dtype=np.int64)
+    vals = np.empty(nnz, dtype=np.float64)
+    fill = rowptr[:-1].copy()
+    for off, w, mask in entries:
+        r = idx[mask]
+        pos = fill[mask]
+        cols[pos] = r + off
+        vals[pos] = w
+        fill[mask] += 1
+    return rowptr.astype(np.int32), cols.astype(np.int32), vals
 
 
 @dataclass(frozen=True)
