@@ -134,6 +134,29 @@ trm_status trm_create_csr(trm_handle* out, int64_t N, const int32_t* rowptr,
                           const trm_options* opt);
 
 /*
+ * Generalized problem H e = lambda S e with S symmetric positive definite
+ * (Sec. 2.1: trace minimization extends to it directly, which admits
+ * non-orthogonal basis functions). Attaches S to a handle made by
+ * trm_create_stencil or trm_create_csr with precision TRM_FP64; trm_solve
+ * then minimises tr(C^T H C) under C^T S C = I: the orthonormalization
+ * factors C^T S C, the gradient is G = -2 (H C - S C H_C), the line search
+ * uses the overlap (C + aP)^T S (C + aP), the diagonal preconditioner
+ * becomes 1 / (H_ii - sigma S_ii) with sigma = min_k H_kk / S_kk - 1, and
+ * the closing Rayleigh-Ritz step solves (C^T H C) y = theta (C^T S C) y.
+ * The returned C is S-orthonormal and the residuals are ||H c - theta S c||.
+ * rowptr: host, N + 1 int32 (rowptr[0] = 0, non-decreasing); cols: host,
+ * rowptr[N] int32 in [0, N); vals: host, rowptr[N] FP64 (duplicates add).
+ * The arrays are copied before the call returns. S's symmetry and
+ * definiteness are not checked (an indefinite S shows as TRM_ENOTPD from
+ * trm_solve); every diagonal entry must be positive. TRM_EINVAL for another
+ * precision mode or invalid arrays. The step operations (trm_energy_gradient,
+ * trm_set_block, trm_iterate, trm_rayleigh_ritz) cover the standard problem
+ * only and return TRM_EINVAL on a handle with an overlap.
+ */
+trm_status trm_set_overlap_csr(trm_handle h, const int32_t* rowptr,
+                               const int32_t* cols, const double* vals);
+
+/*
  * Run Fig. TMFIG to convergence, then diagonalise C^T H C (Rayleigh-Ritz,
  * Sec. 2.1) in FP64. Outputs (any may be NULL):
  *   lambda - host, m doubles, ascending;

@@ -20,7 +20,8 @@ import numpy as np
 __all__ = [
     "TRM_FP64", "TRM_MP1", "TRM_MP2", "TRM_FULL_SP", "TRM_MIXED", "TRM_F32",
     "TRM_F64", "TrmError", "trm_options", "trm_stats", "lib", "LIB_PATH",
-    "trm_default_options", "trm_create_stencil", "trm_create_csr", "trm_solve",
+    "trm_default_options", "trm_create_stencil", "trm_create_csr",
+    "trm_set_overlap_csr", "trm_solve",
     "trm_destroy", "trm_strerror", "trm_last_error", "trm_dim", "trm_apply_h",
     "trm_energy_gradient", "trm_gram", "trm_gram_noalloc",
     "trm_orthonormalize", "trm_extrapolate", "trm_set_block",
@@ -90,6 +91,7 @@ _SIGS = {
                                 ct.POINTER(trm_options)]),
     "trm_create_csr": (_i, [ct.POINTER(_h), _i64, _p, _p, _p, _i, _i, _d,
                             ct.POINTER(trm_options)]),
+    "trm_set_overlap_csr": (_i, [_h, _p, _p, _p]),
     "trm_solve": (_i, [_h, _p, _p, _p, _i, _p, ct.POINTER(trm_stats)]),
     "trm_destroy": (_i, [_h]),
     "trm_strerror": (ct.c_char_p, [_i]),
@@ -191,6 +193,21 @@ def trm_create_csr(N, rowptr, cols, vals, m, tol, opt=None):
     _check(lib.trm_create_csr(ct.byref(handle), N, rpp, cip, vap, dt, m, tol,
                               ct.byref(opt) if opt else None))
     return handle
+
+
+def trm_set_overlap_csr(handle, rowptr, cols, vals):
+    """The SPD overlap S of the generalized problem H e = lambda S e (host
+    CSR arrays, copied); the handle must use precision TRM_FP64."""
+    N = trm_dim(handle)
+    rp, rpp = _host(rowptr, np.int32)
+    if rp.shape != (N + 1,):
+        raise ValueError("rowptr must have N + 1 entries")
+    nnz = int(rp[-1])
+    ci, cip = _host(cols, np.int32)
+    va, vap = _host(vals, np.float64)
+    if ci.shape != (nnz,) or va.shape != (nnz,):
+        raise ValueError("cols and vals must have rowptr[N] entries")
+    _check(lib.trm_set_overlap_csr(handle, rpp, cip, vap), handle)
 
 
 def trm_solve(handle, N, m, C_out=None, C_on_device=False, C0=None):

@@ -166,6 +166,36 @@ trm_status trm_create_csr(trm_handle* out, int64_t N, const int32_t* rowptr,
   return TRM_OK;
 }
 
+trm_status trm_set_overlap_csr(trm_handle h, const int32_t* rowptr,
+                               const int32_t* cols, const double* vals) {
+  if (!h) return static_cast<trm_status>(fail(nullptr, TRM_EINVAL, "handle is NULL"));
+  if (!rowptr || !cols || !vals)
+    return static_cast<trm_status>(fail(h, TRM_EINVAL, "CSR arrays must be non-NULL"));
+  if (h->solver->precision() != TRM_FP64)
+    return static_cast<trm_status>(fail(h, TRM_EINVAL, "the generalized problem runs in the TRM_FP64 precision mode"));
+  const int64_t N = h->solver->N();
+  if (rowptr[0] != 0)
+    return static_cast<trm_status>(fail(h, TRM_EINVAL, "rowptr[0] must be 0"));
+  for (int64_t r = 0; r < N; ++r) {
+    if (rowptr[r + 1] < rowptr[r])
+      return static_cast<trm_status>(fail(h, TRM_EINVAL, "rowptr must be non-decreasing"));
+  }
+  for (int64_t r = 0; r < N; ++r) {
+    double d = 0.0;
+    for (int32_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+      if (cols[k] < 0 || cols[k] >= N)
+        return static_cast<trm_status>(fail(h, TRM_EINVAL, "column index out of range"));
+      if (cols[k] == r) d += vals[k];
+    }
+    if (!(d > 0.0))
+      return static_cast<trm_status>(fail(h, TRM_EINVAL, "S must have a positive diagonal"));
+  }
+  return guarded(h, [&]() {
+    h->solver->init_overlap(rowptr, cols, vals);
+    return TRM_OK;
+  });
+}
+
 trm_status trm_solve(trm_handle h, double* lambda, double* E_G, double* C,
                      int C_on_device, const double* C0, trm_stats* stats) {
   if (!h) return static_cast<trm_status>(fail(nullptr, TRM_EINVAL, "handle is NULL"));
@@ -224,6 +254,8 @@ trm_status trm_energy_gradient(trm_handle h, const double* C, double* E,
                                int G_dtype, int zero_diag) {
   if (!h || !C || !G)
     return static_cast<trm_status>(fail(h, TRM_EINVAL, "invalid arguments to trm_energy_gradient"));
+  if (h && h->solver->generalized())
+    return static_cast<trm_status>(fail(h, TRM_EINVAL, "the step operations cover the standard problem; a handle with an overlap S solves with trm_solve"));
   return guarded(h, [&]() {
     h->solver->energy_gradient(C, E, HD, Hprime, G, G_dtype, zero_diag);
     return TRM_OK;
@@ -402,6 +434,8 @@ trm_status trm_extrapolate(int64_t N, int m, const double* C_prev,
 
 trm_status trm_set_block(trm_handle h, const double* C_device) {
   if (!h || !C_device) return static_cast<trm_status>(fail(h, TRM_EINVAL, "invalid arguments"));
+  if (h && h->solver->generalized())
+    return static_cast<trm_status>(fail(h, TRM_EINVAL, "the step operations cover the standard problem; a handle with an overlap S solves with trm_solve"));
   return guarded(h, [&]() {
     h->solver->set_block(C_device);
     return TRM_OK;
@@ -419,6 +453,8 @@ trm_status trm_get_block(trm_handle h, double* C_device) {
 trm_status trm_iterate(trm_handle h, int mode, int restart, double* E_out,
                        double* rms_out, double* alpha_out) {
   if (!h) return static_cast<trm_status>(fail(nullptr, TRM_EINVAL, "handle is NULL"));
+  if (h && h->solver->generalized())
+    return static_cast<trm_status>(fail(h, TRM_EINVAL, "the step operations cover the standard problem; a handle with an overlap S solves with trm_solve"));
   return guarded(h, [&]() {
     h->solver->iterate(mode, restart, E_out, rms_out, alpha_out);
     return TRM_OK;
@@ -428,6 +464,8 @@ trm_status trm_iterate(trm_handle h, int mode, int restart, double* E_out,
 trm_status trm_rayleigh_ritz(trm_handle h, double* C, double* lambda,
                              double* residuals) {
   if (!h || !C) return static_cast<trm_status>(fail(h, TRM_EINVAL, "invalid arguments"));
+  if (h && h->solver->generalized())
+    return static_cast<trm_status>(fail(h, TRM_EINVAL, "the step operations cover the standard problem; a handle with an overlap S solves with trm_solve"));
   return guarded(h, [&]() {
     h->solver->rayleigh_ritz(C, lambda, residuals);
     return TRM_OK;

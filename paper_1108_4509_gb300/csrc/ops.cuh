@@ -78,6 +78,11 @@ void stencil_diag(const StencilOp& st, double t_w0_ndim, const double* V,
 void csr_diag(const Operator& op, double* diag64, float* diag32,
               cudaStream_t s);
 // M_ii = 1 / (H_ii - sigma), sigma = min_k H_kk - 1; work: >= 1024 doubles
+// Generalized problem: M_ii = 1 / (H_ii - sigma S_ii) with
+// sigma = min_k H_kk / S_kk - 1 (S_ii > 0), so M is SPD; work: >= 256 doubles.
+void diag_preconditioner_gen(const double* diagH, const double* diagS,
+                             int64_t N, double* minv64, float* minv32,
+                             double* work, cudaStream_t s);
 void diag_preconditioner(const double* diag64, int64_t N, double* minv64,
                          float* minv32, double* work, cudaStream_t s);
 

@@ -410,6 +410,49 @@ void Solver::init_csr(const int32_t* rowptr, const int32_t* cols,
   TRM_CUDA(cudaStreamSynchronize(s_));
 }
 
+void Solver::init_overlap(const int32_t* rowptr, const int32_t* cols,
+                          const double* vals) {
+  const int64_t nnz = rowptr[N_];
+  auto* rp = static_cast<int32_t*>(mem_.alloc((size_t)(N_ + 1) * 4));
+  auto* ci = static_cast<int32_t*>(mem_.alloc((size_t)nnz * 4));
+  auto* v = static_cast<double*>(mem_.alloc((size_t)nnz * 8));
+  TRM_CUDA(cudaMemcpyAsync(rp, rowptr, (size_t)(N_ + 1) * 4,
+                           cudaMemcpyHostToDevice, s_));
+  TRM_CUDA(cudaMemcpyAsync(ci, cols, (size_t)nnz * 4, cudaMemcpyHostToDevice,
+                           s_));
+  TRM_CUDA(cudaMemcpyAsync(v, vals, (size_t)nnz * 8, cudaMemcpyHostToDevice,
+                           s_));
+  sop_ = Operator{};
+  sop_.kind = 1;
+  sop_.N = N_;
+  sop_.csr.rowptr = rp;
+  sop_.csr.cols = ci;
+  sop_.csr.vals64 = v;
+  int mx = 0;
+  for (int64_t r = 0; r < N_; ++r) mx = std::max(mx, rowptr[r + 1] - rowptr[r]);
+  sop_.csr.max_row_nnz = mx;
+  sop_.err = &sc_->status;
+  if (!Y64_) {
+    const size_t nm = (size_t)N_ * m_;
+    Y64_ = static_cast<double*>(mem_.alloc(nm * 8));
+    Y64n_ = static_cast<double*>(mem_.alloc(nm * 8));
+    SP64_ = static_cast<double*>(mem_.alloc(nm * 8));
+    sdiag64_ = static_cast<double*>(mem_.alloc((size_t)N_ * 8));
+    sdiag32_ = static_cast<float*>(mem_.alloc((size_t)N_ * 4));
+  }
+  csr_diag(sop_, sdiag64_, sdiag32_, s_);
+  sop_.diag64 = sdiag64_;
+  sop_.diag32 = sdiag32_;
+  if (opt_.precond) {  // M = diag(1 / (H_ii - sigma S_ii))
+    diag_preconditioner_gen(diag64_, sdiag64_, N_, minv64_, minv32_, part_,
+                            s_);
+    op_.minv64 = minv64_;
+    op_.minv32 = minv32_;
+  }
+  has_S_ = true;
+  TRM_CUDA(cudaStreamSynchronize(s_));
+}
+
 // Algorithmic flops and bytes of one H application to ncols columns of
 // element size es: every stored nonzero is one multiply-add; the block is read
 // and written once and the operator data (diagonal or CSR) read once.
@@ -501,6 +544,19 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   const int krt = sizeof(T) == 4 ? KC_ROT32 : KC_ROT64;
   double sfl, sby;
   spmm_cost(op_, m_, (int)es, &sfl, &sby);
+  // Generalized problem (FP64 only): C^T S C = I, and Y = S C takes C's
+  // place where the constraint enters, X' = X - Y H_D and G = -2 (X' - Y H');
+  // the line search projects with S P, and Y is rotated along with C.
+  const T* Yc = C;
+  T* SPt = P;
+  bool gen = false;
+  if constexpr (sizeof(T) == 8) {
+    if (has_S_) {
+      Yc = Y64_;
+      SPt = SP64_;
+      gen = true;
+    }
+  }
   if constexpr (sizeof(T) == 4) {  // (1) with the column dots of (2) fused in
     int chunks = 0;
     TRM_PROF(ksp, sfl, sby, chunks = apply_h_dots(op_, C, X, m_, part_, s_));
@@ -512,7 +568,7 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
              energy_diag<T>(N_, m_, C, X, HD_, sc_, part_, s_));      // (2), (3)
   }
   TRM_PROF(KC_ROWOPS, 2 * nm, 3 * es * nm,
-           xprime<T>(N_, m_, C, X, HD_, nullptr, nullptr, s_));       // (5)
+           xprime<T>(N_, m_, Yc, X, HD_, nullptr, nullptr, s_));      // (5)
   Blocks<T> bx;
   bx.p[0] = X;
   bx.cols = m_;
@@ -526,21 +582,26 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
                    hp32));                                            // (6)
   if (sizeof(T) == 4) zero_diag(m_, Hp_, s_, hp32);
   TRM_PROF(kgd, 2 * m2N, 5 * es * nm,
-           gradient<T>(N_, m_, C, X, Hp_, G, Gp, P, minv, sc_, part_,
+           gradient<T>(N_, m_, Yc, X, Hp_, G, Gp, P, minv, sc_, part_,
                        part_cap_, s_, &tw_));                         // (7)
   TRM_PROF(KC_ROWOPS, 2 * nm, 3 * es * nm,
            update_p<T>(N_, m_, G, P, minv, sc_, s_));                 // P
   TRM_PROF(ksp, sfl, sby, apply_h(op_, P, HP, m_, s_));              // H P
-  if (!line_grams_fused<T>(C, P, HP, G)) {
+  if (gen) {
+    double ffl, fby;
+    spmm_cost(sop_, m_, 8, &ffl, &fby);
+    TRM_PROF(ksp, ffl, fby, apply_h(sop_, P, SPt, m_, s_));          // S P
+  }
+  if (gen || !line_grams_fused<T>(C, P, HP, G)) {
     Blocks<T> bp;
     bp.p[0] = P;
     bp.cols = m_;
     bp.count = 1;
     TRM_PROF(kgr, 2 * m2N, 2 * es * nm,
-             gram<T>(N_, m_, C, bp, Bm_, part_, part_cap_, s_, &sc_->status,
-                     bm32));                                          // C^T P
+             gram<T>(N_, m_, Yc, bp, Bm_, part_, part_cap_, s_, &sc_->status,
+                     bm32));                                     // C^T (S) P
     Blocks<T> b3;
-    b3.p[0] = P;
+    b3.p[0] = SPt;
     b3.p[1] = HP;
     b3.p[2] = G;
     b3.cols = m_;
@@ -560,6 +621,14 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(krt, m2N, 3 * es * nm,
            (rotate<T, T>(N_, m_, C, P, R_, Cn, sc_, s_, &tw_)));  // (C+aP)L^-T
+  if constexpr (sizeof(T) == 8) {
+    if (gen) {  // S (C + aP) L^-T = (Y + a S P) L^-T
+      TRM_PROF(krt, m2N, 3 * es * nm,
+               (rotate<double, double>(N_, m_, Y64_, SP64_, R_, Y64n_, sc_,
+                                       s_, &tw_)));
+      std::swap(Y64_, Y64n_);
+    }
+  }
   std::swap(C, Cn);
   std::swap(G, Gp);
 }
@@ -665,13 +734,20 @@ void Solver::mult64(const double* A, const double* M, double* Y) {
     mult_df(N_, m_, m_, A, M, Y, false, s_);
 }
 
-// Fig. ONFIG in FP64: S = C^T C, S = L L^T, C <- C L^{-T}.
+// Fig. ONFIG in FP64: S = C^T C, S = L L^T, C <- C L^{-T} (generalized
+// problem: S = C^T Y with Y = S C recomputed, and Y <- Y L^{-T} too).
 void Solver::orth_fp64(double*& C, double*& Cn) {
   Blocks<double> b;
   b.p[0] = C;
   b.cols = m_;
   b.count = 1;
   const double nm = (double)N_ * m_, m2N = nm * m_;
+  if (has_S_) {
+    double ffl, fby;
+    spmm_cost(sop_, m_, 8, &ffl, &fby);
+    TRM_PROF(KC_SPMM64, ffl, fby, apply_h(sop_, C, Y64_, m_, s_));
+    b.p[0] = Y64_;
+  }
   TRM_PROF(KC_GRAM64, 2 * m2N, 16 * nm, gram64(C, b, S_));
   TRM_PROF(KC_SMALL, 2.0 * m_ * m_ * m_ / 3, 0.0,
            chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_));
@@ -680,6 +756,12 @@ void Solver::orth_fp64(double*& C, double*& Cn) {
              (rotate<double, double>(N_, m_, C, nullptr, R_, Cn, nullptr, s_)));
   else  // C L^{-T} in double-float
     TRM_PROF(KC_ROT64, m2N, 16 * nm, mult_df(N_, m_, m_, C, R_, Cn, true, s_));
+  if (has_S_) {
+    TRM_PROF(KC_ROT64, m2N, 16 * nm,
+             (rotate<double, double>(N_, m_, Y64_, nullptr, R_, Y64n_, nullptr,
+                                     s_)));
+    std::swap(Y64_, Y64n_);
+  }
   std::swap(C, Cn);
 }
 
@@ -709,11 +791,16 @@ void Solver::rr_rotate_fp64() {
   const double nm = (double)N_ * m_;
   TRM_PROF(KC_ROT64, 2 * nm * m_, 16 * nm, mult64(C64_, Z_, C64n_));
   std::swap(C64_, C64n_);
+  if (has_S_) {  // Y = S C follows the rotation
+    TRM_PROF(KC_ROT64, 2 * nm * m_, 16 * nm, mult64(Y64_, Z_, Y64n_));
+    std::swap(Y64_, Y64n_);
+  }
 }
 
 // Rayleigh-Ritz on span(C) (Sec. 2.1) in FP64, as the generalised problem
 // (C^T H C) y = theta (C^T C) y: L = chol(C^T C), A~ = L^{-1} (C^T H C) L^{-T},
-// A~ = Z diag(theta) Z^T, Y = L^{-T} Z, C Y and H C Y, column residuals.
+// A~ = Z diag(theta) Z^T, Y = L^{-T} Z, C Y and H C Y, column residuals
+// (generalized problem: C^T S C in place of C^T C, residuals H c - theta S c).
 void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
   apply_h(op_, C, X64_, m_, s_);
   Blocks<double> bx;
@@ -725,6 +812,10 @@ void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
   bc.p[0] = C;
   bc.cols = m_;
   bc.count = 1;
+  if (has_S_) {
+    apply_h(sop_, C, Y64_, m_, s_);
+    bc.p[0] = Y64_;
+  }
   gram64(C, bc, S_);
   chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_);
   mm_gemm(m_, Linv_, false, Hp_, false, T1_, 1.0, 0.0, s_);
@@ -734,6 +825,12 @@ void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
   mm_gemm(m_, R_, false, Z_, false, T1_, 1.0, 0.0, s_);
   mult64(C, T1_, Cfin);
   mult64(X64_, T1_, Xfin);
+  if (has_S_) {  // ||H c_j - theta_j S c_j|| (sign independent)
+    mult64(Y64_, T1_, SP64_);
+    column_residuals(N_, m_, Xfin, SP64_, lam_, res_, part_, s_);
+    fix_signs(N_, m_, Cfin, Xfin, part_, s_);
+    return;
+  }
   fix_signs(N_, m_, Cfin, Xfin, part_, s_);
   column_residuals(N_, m_, Xfin, Cfin, lam_, res_, part_, s_);
 }
@@ -872,7 +969,8 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
   const int stall_window = 250;
   const bool trace = std::getenv("TRM_TRACE") != nullptr;
 
-  const bool graphs = opt_.graphs && s_ != nullptr && !prof.on;
+  // (the generalized problem swaps Y = S C too and runs without graphs)
+  const bool graphs = opt_.graphs && s_ != nullptr && !prof.on && !has_S_;
   auto enqueue_one = [&]() {
     auto body = [&]() {
       if (phase == PH_SP) {

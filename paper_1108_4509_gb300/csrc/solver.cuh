@@ -81,6 +81,13 @@ class Solver {
                     const double* V_host);
   void init_csr(const int32_t* rowptr, const int32_t* cols, const void* vals,
                 int vals_fp64);
+  // Generalized problem H e = lambda S e: the SPD overlap S as CSR (FP64),
+  // host arrays, validated by the caller. The iteration then keeps
+  // C^T S C = I and carries Y = S C along with C (FP64 mode only).
+  void init_overlap(const int32_t* rowptr, const int32_t* cols,
+                    const double* vals);
+  bool generalized() const { return has_S_; }
+  int precision() const { return opt_.precision; }
 
   // Fig. TMFIG to convergence, then Rayleigh-Ritz. Returns a trm_status.
   int solve(double* lambda, double* E_G, double* C_out, int C_on_device,
@@ -170,6 +177,13 @@ class Solver {
   IterScalars* ring_ = nullptr;  // pinned host ring of per-iteration scalars
   std::vector<cudaEvent_t> ev_;
   int state_ = 0;  // 0: C64 current, 1: C32 current
+  // generalized problem: S as an operator, Y = S C (and its swap buffer),
+  // S P of the line search, diag(S)
+  Operator sop_;
+  bool has_S_ = false;
+  double *Y64_ = nullptr, *Y64n_ = nullptr, *SP64_ = nullptr;
+  double* sdiag64_ = nullptr;
+  float* sdiag32_ = nullptr;
 };
 
 }  // namespace trm
