@@ -46,6 +46,12 @@ FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # lanes x 2 flops (1.26 TFLOP/s, the nominal 1.25).
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# The mixed ladder's FP64-class Grams and block products run in double-float
+# on the FP32 pipe: one pair multiply-add (TwoProduct by FMA with the two
+# cross terms, TwoSum into the accumulator, one add) is 12 FP32 instructions
+# for 2 algorithmic flops, so their ceiling is the FP32 SIMT rate / 12.
+DF_TFLOPS = FP32_SIMT_TFLOPS / 12
+DF_CLASSES = ("gram_f64", "rotate_f64")
 # Kernel classes whose bound is HBM traffic (algorithmic bytes); the others
 # are bound by FP64 (or FP32 SIMT) arithmetic. The FP32 product classes run
 # on the tensor cores, where the TF32 MMAs take a few percent of the time the
@@ -277,7 +283,7 @@ def traffic_from_profile(cls):
 # ---------------------------------------------------------------------------
 # roofline of the dominant kernel class
 # ---------------------------------------------------------------------------
-def roofline(prof, peaks, src):
+def roofline(prof, peaks, src, double_float=True):
     classes = {k: v for k, v in prof.items() if v["launches"] > 0 and v["ms"] > 0}
     if not classes:
         return None, None
@@ -291,7 +297,11 @@ def roofline(prof, peaks, src):
                  "peak_source": src + " (copy bandwidth)"}
         else:
             ach = cc["flops"] / cc["launches"] / pl / 1e12
-            if cname.endswith("f64") or cname in ("small_mm", "eig"):
+            if double_float and cname in DF_CLASSES:
+                pk, ps = DF_TFLOPS, ("derived double-float on the FP32 pipe "
+                                     "(152 SMs x 128 lanes x 2070 MHz / 12 "
+                                     "instructions per pair multiply-add)")
+            elif cname.endswith("f64") or cname in ("small_mm", "eig"):
                 pk, ps = FP64_TFLOPS, "derived FP64 (152 SMs x 2 FMA x 2070 MHz)"
             else:
                 pk, ps = FP32_SIMT_TFLOPS, "derived FP32 SIMT (152 SMs x 128 FMA x 2070 MHz)"

@@ -63,3 +63,19 @@ def test_roofline_scales_traffic_to_the_class_launch():
         expect = tr["bytes_per_launch"] * 1.0e8 / tr["algorithmic_bytes"]
         assert abs(r["traffic"] - expect) < 1e-3 * expect
     assert every["small_mm"]["bound"] == "alu"
+
+
+def test_double_float_classes_use_the_fp32_pipe_ceiling():
+    # the mixed ladder's gram_f64 runs in double-float on the FP32 pipe: its
+    # ceiling is FP32 SIMT / 12, not the FP64 unit rate
+    prof = {"gram_f64": {"ms": 9.0, "launches": 9, "bytes": 0.0,
+                         "flops": 9 * 3.6e9},
+            "eig": {"ms": 1.0, "launches": 1, "bytes": 0.0, "flops": 1e8}}
+    _, every = bench.roofline(prof, {"hbm_gbs": 6700.0}, "measured")
+    g = every["gram_f64"]
+    assert g["bound"] == "alu" and g["peak"] == bench.DF_TFLOPS
+    assert 0.0 < g["frac"] < 1.0
+    assert every["eig"]["peak"] == bench.FP64_TFLOPS
+    _, fp64 = bench.roofline(prof, {"hbm_gbs": 6700.0}, "measured",
+                             double_float=False)
+    assert fp64["gram_f64"]["peak"] == bench.FP64_TFLOPS
