@@ -369,6 +369,12 @@ class Solver:
         opt = trm_default_options(**opts)
         return cls(trm_create_csr(N, rowptr, cols, vals, m, tol, opt), N, m)
 
+    def set_overlap(self, rowptr, cols, vals):
+        """Make it the generalized problem H e = lambda S e (S SPD, CSR; the
+        handle must use precision TRM_FP64)."""
+        trm_set_overlap_csr(self.handle, rowptr, cols, vals)
+        return self
+
     def solve(self, C0=None, want_C=True):
         C = np.zeros((self.N, self.m), order="F") if want_C else None
         lam, eg, st, status = trm_solve(self.handle, self.N, self.m, C_out=C,
