@@ -85,6 +85,22 @@ def parse():
     ap.add_argument("--compare", type=int, default=1,
                     help="serving: also replay the trace one request at a "
                          "time and compare every result")
+    ap.add_argument("--generalized", type=int, default=0,
+                    help="instead of the solve benchmark: grid edge n of a "
+                         "generalized problem H e = lambda S e (S the hat-"
+                         "function overlap) solved in the FP64 mode, timed "
+                         "beside the standard problem of the same H")
+    ap.add_argument("--chain", type=int, default=0,
+                    help="instead of the solve benchmark: grid edge n of a "
+                         "chain of related problems V0 + t V1, the third "
+                         "solved from a cold, the previous and the "
+                         "extrapolated block")
+    ap.add_argument("--gen-m", type=int, default=48,
+                    help="--generalized: eigenpairs m (at n = 32 the gap "
+                         "lambda_49 - lambda_48 is 0.013)")
+    ap.add_argument("--chain-m", type=int, default=44,
+                    help="--chain: eigenpairs m (at n = 32 the smallest gap "
+                         "lambda_45 - lambda_44 along the chain is 0.021)")
     ap.add_argument("--clocks", type=int, default=1,
                     help="sample nvidia-smi clocks during the timed region "
                          "(0 under a profiler, which should see no other "
@@ -467,10 +483,172 @@ def run_serving(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# next rows: the generalized problem and chains of related problems
+# ---------------------------------------------------------------------------
+def _timed_solve(torch, trm, h, N, m, stream, C0=None, C_out=None):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lam, eg, st, status = trm.trm_solve(h, N, m, C_out=C_out, C0=C0)
+    e1.record(stream)
+    e1.synchronize()
+    return lam, eg, st, status, e0.elapsed_time(e1) / 1e3
+
+
+def run_generalized(args, torch, trm, stream):
+    """FP64 solve of H e = lambda S e (13-point H with wells, S the 27-point
+    hat-function overlap) and of H e = lambda e on the same grid."""
+    import trm_inputs as ti
+    n, m = args.generalized, args.gen_m
+    shape, N = (n, n, n), n ** 3
+    wells = max(4, N // 1024)
+    V = ti.gaussian_wells(shape, wells, seed=1)
+    S = ti.hat_overlap_csr(shape)
+    sptr = stream.cuda_stream
+
+    def make(gen):
+        opt = trm.trm_default_options(precision=trm.TRM_FP64, precond=1,
+                                      stream=sptr, seed=7)
+        h = trm.trm_create_stencil(n, n, n, 4, 1.0, V, m, args.tol, opt)
+        if gen:
+            trm.trm_set_overlap_csr(h, *S)
+        return h
+
+    hg, hs = make(True), make(False)
+    try:
+        for _ in range(args.warmup):
+            _timed_solve(torch, trm, hg, N, m, stream)
+        trm.trm_profile(hg, True)
+        sampler = ClockSampler(torch.cuda.current_device())
+        if args.clocks:
+            sampler.start()
+        launches0 = trm.trm_launch_count()
+        times = []
+        for _ in range(args.steps):
+            lam, eg, st, status, t = _timed_solve(torch, trm, hg, N, m, stream)
+            times.append(t)
+        launches = (trm.trm_launch_count() - launches0) / max(1, args.steps)
+        clocks = sampler.stop()
+        prof = trm.trm_profile_read(hg)
+        trm.trm_profile(hg, False)
+        for _ in range(args.warmup):
+            _timed_solve(torch, trm, hs, N, m, stream)
+        _, eg_s, st_s, status_s, t_s = _timed_solve(torch, trm, hs, N, m,
+                                                    stream)
+    finally:
+        trm.trm_destroy(hg)
+        trm.trm_destroy(hs)
+    peaks_file = load_json(PEAKS)
+    peaks = peaks_file if peaks_file else FALLBACK
+    roof, per_class = roofline(prof, peaks,
+                               "measured" if peaks_file else "fallback",
+                               double_float=False)
+    out = {"metric": "generalized H e = lambda S e: time to tol (FP64 mode)",
+           "value": statistics.mean(times), "unit": "s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{n}^3 grid, 13-point -1/2 nabla^2 + "
+                                  f"{wells} Gaussian wells (seed 1), S = "
+                                  "trilinear hat-function overlap (27-point "
+                                  f"CSR), m={m}, diagonal preconditioner",
+                      "N": N, "m": m, "tol_rms": args.tol,
+                      "l2": "working set L2-resident (blocks of "
+                            f"{N * m * 8 / 1e6:.1f} MB)"},
+           "iterations": st.iterations, "status": status,
+           "max_residual": st.max_residual, "E_G": eg,
+           "standard_same_H": {"seconds": t_s, "iterations": st_s.iterations,
+                               "status": status_s, "E_G": eg_s},
+           "roofline": roof, "classes": per_class,
+           "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(out))
+
+
+def run_chain(args, torch, trm, stream):
+    """V(t) = V0 + t V1 at t = 0, dt, 2 dt (mixed precision): the third
+    problem from a cold start, from the second's block, and from the block
+    trm_extrapolate forms from the first two."""
+    import numpy as np
+    import trm_inputs as ti
+    n, m, dt = args.chain, args.chain_m, 0.02
+    shape, N = (n, n, n), n ** 3
+    wells = max(4, N // 1024)
+    V0 = ti.gaussian_wells(shape, wells, seed=31)
+    V1 = ti.gaussian_wells(shape, wells, seed=32)
+    sptr = stream.cuda_stream
+
+    def solve(t, C0=None):
+        opt = trm.trm_default_options(precision=trm.TRM_MIXED, precond=1,
+                                      stream=sptr, seed=3)
+        h = trm.trm_create_stencil(n, n, n, 4, 1.0, V0 + t * V1, m, args.tol,
+                                   opt)
+        C = np.zeros((N, m), order="F")
+        try:
+            _, eg, st, status, secs = _timed_solve(torch, trm, h, N, m, stream,
+                                                   C0=C0, C_out=C)
+        finally:
+            trm.trm_destroy(h)
+        return {"seconds": secs, "iterations": st.iterations,
+                "status": status, "E_G": eg}, C
+
+    for _ in range(args.warmup):
+        solve(0.0)
+    _, Ca = solve(0.0)
+    _, Cb = solve(dt)
+    dA = torch.from_numpy(np.ascontiguousarray(Ca.T)).cuda()
+    dB = torch.from_numpy(np.ascontiguousarray(Cb.T)).cuda()
+    dX = torch.empty((m, N), dtype=torch.float64, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    trm.trm_extrapolate(N, m, dA.data_ptr(), dB.data_ptr(), 1.0,
+                        dX.data_ptr(), sptr)
+    e1.record(stream)
+    e1.synchronize()
+    t_x = e0.elapsed_time(e1) / 1e3
+    Cx = np.asfortranarray(dX.cpu().numpy().T)
+    cold, _ = solve(2 * dt)
+    prev, _ = solve(2 * dt, Cb)
+    extr, _ = solve(2 * dt, Cx)
+    extr["extrapolate_s"] = t_x
+    egs = [cold["E_G"], prev["E_G"], extr["E_G"]]
+    out = {"metric": "chain of related problems: time to tol of the third "
+                     "(mixed precision)",
+           "value": extr["seconds"] + t_x, "unit": "s", "n_gpus": 1,
+           "higher_is_better": False, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": f"{n}^3 grid, 13-point, V0 + t V1 with "
+                                  f"{wells} + {wells} Gaussian wells (seeds "
+                                  f"31, 32), t = 0, {dt}, {2 * dt}, m={m}, "
+                                  "diagonal preconditioner",
+                      "N": N, "m": m, "tol_rms": args.tol},
+           "cold": cold, "previous_block": prev, "extrapolated": extr,
+           "E_G_spread": max(egs) - min(egs)}
+    print(json.dumps(out))
+
+
+def run_extras(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1108_4509_gb300 as trm
+    torch.cuda.set_stream(torch.cuda.Stream())
+    stream = torch.cuda.current_stream()
+    if args.generalized > 0:
+        run_generalized(args, torch, trm, stream)
+    if args.chain > 0:
+        run_chain(args, torch, trm, stream)
+    return 0
+
+
 def main():
     args = parse()
     if args.serving > 0:
         return run_serving(args)
+    if args.generalized > 0 or args.chain > 0:
+        return run_extras(args)
     if args.impl == "reference":
         return run_reference(args)
     import numpy as np
