@@ -438,3 +438,46 @@ def test_generalized_with_diagonal_S_is_the_scaled_standard_problem():
                   S=sp.diags(d).tocsr())
     Hs = H.toarray() / np.sqrt(d)[:, None] / np.sqrt(d)[None, :]
     assert np.max(np.abs(r.lam - np.linalg.eigvalsh(Hs)[:m])) < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# Stencil consistency, independent of the weights' own spectra
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("order,rate", [(2, 4.0), (4, 16.0)])
+def test_stencil_truncation_error_has_the_rule_order(order, rate):
+    """H u for u = sin(pi x) sin(2 pi y) sin(3 pi z) sampled on the unit cube
+    equals -1/2 lap u = pi^2 (1 + 4 + 9) / 2 u at interior points up to
+    O(h^order): halving h divides the error by 4 (3-point rule) or 16
+    (5-point rule). A wrong weight breaks the consistency altogether."""
+    errs = []
+    for n in (15, 31, 63):
+        h = 1.0 / (n + 1)
+        x = h * np.arange(1, n + 1)
+        X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+        u = (np.sin(np.pi * X) * np.sin(2 * np.pi * Y)
+             * np.sin(3 * np.pi * Z))
+        uf = u.transpose(2, 1, 0).reshape(-1)       # x fastest
+        Hu = (op.grid_hamiltonian((n, n, n), order, h) @ uf).reshape(n, n, n)
+        Hu = Hu.transpose(2, 1, 0)
+        want = 0.5 * np.pi ** 2 * 14.0 * u
+        k = 2                                       # stay off the boundary
+        errs.append(np.max(np.abs(Hu - want)[k:-k, k:-k, k:-k]))
+    for a, b in zip(errs, errs[1:]):
+        assert 0.85 * rate < a / b < 1.15 * rate
+
+
+def test_dirichlet_eigenvalues_converge_to_the_continuum():
+    """The lowest eigenvalues of -1/2 d^2/dx^2 on (0, 1) are (k pi)^2 / 2.
+    The 3-point rule converges at second order; the 5-point rule, whose
+    neighbours outside the grid are taken as zero (the Dirichlet wall),
+    only at first order: that zero-ghost closure is first-order accurate at
+    the wall."""
+    exact = 0.5 * (np.pi * np.arange(1, 4)) ** 2
+    for order, rate in ((2, 4.0), (4, 2.0)):
+        errs = []
+        for n in (31, 63, 127):
+            h = 1.0 / (n + 1)
+            T = op.axis_operator(n, order).toarray() * op.kinetic_scale(h)
+            errs.append(np.abs(sla.eigvalsh(T)[:3] - exact))
+        for a, b in zip(errs, errs[1:]):
+            assert np.all((0.9 * rate < a / b) & (a / b < 1.1 * rate))

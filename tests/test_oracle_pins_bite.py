@@ -87,3 +87,12 @@ def test_generalized_rayleigh_ritz_without_S_is_caught(monkeypatch):
     monkeypatch.setattr(trm, "rayleigh_ritz",
                         lambda H, C, S=None: orig(H, C, None))
     _fails(pins.test_generalized_solve_vs_dense_and_closed_form, False)
+
+
+def test_wrong_fourth_order_weight_is_caught(monkeypatch):
+    """The 5-point rule with 1/6 in place of 1/12 for the second neighbour."""
+    w = dict(op._WEIGHTS)
+    w[4] = (2.5, -4.0 / 3.0, 1.0 / 6.0)
+    monkeypatch.setattr(op, "_WEIGHTS", w)
+    _fails(pins.test_stencil_truncation_error_has_the_rule_order, 4, 16.0)
+
