@@ -263,6 +263,28 @@ def test_polak_ribiere_beats_steepest_descent():
     assert (not sd.converged) or sd.iterations > 2 * cg.iterations
 
 
+
+def test_polak_ribiere_restarts_itself_when_the_gradient_repeats():
+    """Polak-Ribiere's known property (as against Fletcher-Reeves, which
+    gives 1): a gradient that repeats the previous one gives gamma = 0, and
+    gamma is unchanged when both gradients are scaled by the same factor and
+    is linear in the new gradient's change; with M-orthogonal gradients it
+    reduces to the Fletcher-Reeves ratio."""
+    rng = np.random.default_rng(4)
+    G = rng.standard_normal((50, 3))
+    Gp = rng.standard_normal((50, 3))
+    Md = 0.5 + rng.random(50)
+    M = lambda X: X * Md[:, None]                       # noqa: E731
+    assert trm.polak_ribiere(G, G, M(G), M(G)) == 0.0
+    g = trm.polak_ribiere(G, Gp, M(G), M(Gp))
+    assert trm.polak_ribiere(3 * G, 3 * Gp, M(3 * G), M(3 * Gp)) == \
+        pytest.approx(g, rel=1e-13)
+    # make G M-orthogonal to Gp: then gamma = tr(G^T M G) / tr(Gp^T M Gp)
+    Go = G - Gp * (np.sum(Gp * M(G)) / np.sum(Gp * M(Gp)))
+    fr = np.sum(Go * M(Go)) / np.sum(Gp * M(Gp))
+    assert trm.polak_ribiere(Go, Gp, M(Go), M(Gp)) == pytest.approx(fr,
+                                                                    rel=1e-12)
+
 # ----------------------------------------------------------------------------
 # Initial-guess extrapolation for a chain of related problems
 # ----------------------------------------------------------------------------

@@ -96,3 +96,11 @@ def test_wrong_fourth_order_weight_is_caught(monkeypatch):
     monkeypatch.setattr(op, "_WEIGHTS", w)
     _fails(pins.test_stencil_truncation_error_has_the_rule_order, 4, 16.0)
 
+
+def test_fletcher_reeves_in_place_of_polak_ribiere_is_caught(monkeypatch):
+    """gamma = tr(G^T M G) / tr(G_prev^T M G_prev) (no G_prev subtracted)."""
+    monkeypatch.setattr(trm, "polak_ribiere",
+                        lambda G, Gp, MG, MGp: float(np.sum(G * MG))
+                        / float(np.sum(Gp * MGp)))
+    _fails(pins.test_polak_ribiere_restarts_itself_when_the_gradient_repeats)
+
