@@ -349,6 +349,19 @@ size_t trm_footprint_bytes(int64_t N, int m);
 trm_status trm_server_create(trm_server* out, size_t device_bytes,
                              int max_live);
 
+/* The scheduler alone: a server whose admitted requests call fn on their
+ * host thread instead of solving on the GPU (admission order, budget,
+ * max_live, waits and latencies are those of trm_server_create). fn gets
+ * the problem as submitted (V and C0 NULL: the copies stay with the
+ * server), writes lambda[m] (zeroed before the call), *E_G and *stats, and
+ * returns a trm_status, which trm_server_wait returns. For testing the
+ * scheduler without a GPU and for callers that run their own solver. No
+ * CUDA call is made. TRM_EINVAL if fn is NULL or a size is 0. */
+typedef int (*trm_server_fn)(const trm_problem* p, double* lambda,
+                             double* E_G, trm_stats* stats, void* ctx);
+trm_status trm_server_create_fn(trm_server* out, size_t device_bytes,
+                                int max_live, trm_server_fn fn, void* ctx);
+
 /* Queue a problem; never blocks. *ticket identifies it for trm_server_wait.
  * TRM_EINVAL for invalid sizes, TRM_ENOMEM when its footprint alone exceeds
  * the budget. */

@@ -119,6 +119,7 @@ _SIGS = {
     "trm_server_wait": (_i, [_h, ct.c_int64, _p, _p, ct.POINTER(trm_stats),
                              _p]),
     "trm_server_destroy": (_i, [_h]),
+    "trm_server_create_fn": (_i, [ct.POINTER(_h), ct.c_size_t, _i, _p, _p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -409,6 +410,21 @@ def trm_footprint_bytes(N, m):
 def trm_server_create(device_bytes, max_live):
     h = _h()
     _check(lib.trm_server_create(ct.byref(h), device_bytes, max_live))
+    return h
+
+
+# int fn(const trm_problem*, double* lambda, double* E_G, trm_stats*, void*)
+TRM_SERVER_FN = ct.CFUNCTYPE(ct.c_int, ct.c_void_p, ct.POINTER(ct.c_double),
+                             ct.POINTER(ct.c_double), ct.c_void_p, ct.c_void_p)
+
+
+def trm_server_create_fn(device_bytes, max_live, fn, ctx=None):
+    """A server whose admitted requests call fn (a TRM_SERVER_FN; the caller
+    keeps it alive until trm_server_destroy returns) instead of solving."""
+    h = _h()
+    _check(lib.trm_server_create_fn(ct.byref(h), device_bytes, max_live,
+                                    ct.cast(fn, ct.c_void_p),
+                                    ct.c_void_p(ctx) if ctx else None))
     return h
 
 

@@ -53,15 +53,37 @@ struct trm_server_ctx {
   bool stop = false;
   int64_t next_id = 1;
   std::thread scheduler;
+  trm_server_fn fn = nullptr;  // set: requests call it instead of solving
+  void* fn_ctx = nullptr;
 };
 
 namespace {
 
+// A request is done: record its result and return its memory and slot.
+void finish(trm_server_ctx* s, const std::shared_ptr<Request>& r, int status,
+            const std::string& err) {
+  std::lock_guard<std::mutex> lock(s->mu);
+  r->status = status;
+  r->err = err;
+  r->t_done = Clock::now();
+  r->done = true;
+  s->in_use -= r->bytes;
+  s->live -= 1;
+  s->cv.notify_all();
+}
+
 void run_request(trm_server_ctx* s, std::shared_ptr<Request> r) {
-  cudaSetDevice(s->device);
-  cudaStream_t st = nullptr;
   int status = TRM_OK;
   std::string err;
+  if (s->fn) {
+    r->lambda.assign(r->p.m, 0.0);
+    status = s->fn(&r->p, r->lambda.data(), &r->E_G, &r->stats, s->fn_ctx);
+    if (status != TRM_OK) err = "the server's solve function failed";
+    finish(s, r, status, err);
+    return;
+  }
+  cudaSetDevice(s->device);
+  cudaStream_t st = nullptr;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     status = TRM_ECUDA;
@@ -85,14 +107,7 @@ void run_request(trm_server_ctx* s, std::shared_ptr<Request> r) {
     }
     cudaStreamDestroy(st);
   }
-  std::lock_guard<std::mutex> lock(s->mu);
-  r->status = status;
-  r->err = err;
-  r->t_done = Clock::now();
-  r->done = true;
-  s->in_use -= r->bytes;
-  s->live -= 1;
-  s->cv.notify_all();
+  finish(s, r, status, err);
 }
 
 void schedule(trm_server_ctx* s) {
@@ -141,6 +156,25 @@ trm_status trm_server_create(trm_server* out, size_t device_bytes,
     trm::set_global_error("no CUDA device");
     return TRM_ECUDA;
   }
+  s->scheduler = std::thread(schedule, s);
+  *out = s;
+  return TRM_OK;
+}
+
+trm_status trm_server_create_fn(trm_server* out, size_t device_bytes,
+                                int max_live, trm_server_fn fn, void* ctx) {
+  if (!out) return TRM_EINVAL;
+  *out = nullptr;
+  if (device_bytes == 0 || max_live < 1 || !fn) {
+    trm::set_global_error("device_bytes and max_live must be positive and fn non-NULL");
+    return TRM_EINVAL;
+  }
+  auto* s = new (std::nothrow) trm_server_ctx;
+  if (!s) return TRM_ENOMEM;
+  s->budget = device_bytes;
+  s->max_live = max_live;
+  s->fn = fn;
+  s->fn_ctx = ctx;
   s->scheduler = std::thread(schedule, s);
   *out = s;
   return TRM_OK;
