@@ -172,6 +172,28 @@ trm_status trm_solve(trm_handle h, double* lambda, double* E_G, double* C,
                      int C_on_device, const double* C0, trm_stats* stats);
 
 trm_status trm_destroy(trm_handle h);
+
+/* One iteration of the last trm_solve, as the host read it (Fig. TMFIG;
+ * the quantities behind the paper's convergence plots: with the returned
+ * E_G, R_i = (E - E_G) / E_G). */
+typedef struct {
+  double E;      /* tr(C_i^T H C_i) (FP32 products summed in FP64 in full SP) */
+  double rms;    /* RMS column residual ||G_i||_F / (2 sqrt(m)) */
+  double alpha;  /* line step taken from C_i (0 on a restart without a step) */
+  double gamma;  /* Polak-Ribiere coefficient of the direction P_i */
+  int phase;     /* 0 full SP, 1 MP2 (or MP1), 2 FP64 */
+  int restart;   /* 1 when P_i was not a descent direction, so P_{i+1}
+                    restarts CG (gamma = 0) */
+} trm_iter_record;
+
+/* Per-iteration history of the last trm_solve on h: writes the first
+ * min(count, cap) records to out (host; may be NULL when cap = 0) and
+ * returns count, one record per iteration run (stats.iterations). The
+ * convergence test passes on record count - 1 - lag (lag =
+ * trm_options.lag): the host reads the scalars that many iterations late,
+ * and the iterations already enqueued then still run. Negative trm_status
+ * for a NULL handle or cap < 0. */
+int trm_history(trm_handle h, trm_iter_record* out, int cap);
 const char* trm_strerror(trm_status s);
 const char* trm_last_error(trm_handle h);
 const char* trm_last_global_error(void);

@@ -21,7 +21,7 @@ __all__ = [
     "TRM_FP64", "TRM_MP1", "TRM_MP2", "TRM_FULL_SP", "TRM_MIXED", "TRM_F32",
     "TRM_F64", "TrmError", "trm_options", "trm_stats", "lib", "LIB_PATH",
     "trm_default_options", "trm_create_stencil", "trm_create_csr",
-    "trm_set_overlap_csr", "trm_solve",
+    "trm_set_overlap_csr", "trm_solve", "trm_history",
     "trm_destroy", "trm_strerror", "trm_last_error", "trm_dim", "trm_apply_h",
     "trm_energy_gradient", "trm_gram", "trm_gram_noalloc",
     "trm_orthonormalize", "trm_extrapolate", "trm_set_block",
@@ -59,6 +59,12 @@ class trm_stats(ct.Structure):
                 "seconds": self.seconds, "launches": self.launches}
 
 
+class trm_iter_record(ct.Structure):
+    _fields_ = [("E", ct.c_double), ("rms", ct.c_double),
+                ("alpha", ct.c_double), ("gamma", ct.c_double),
+                ("phase", ct.c_int), ("restart", ct.c_int)]
+
+
 class trm_kernel_stats(ct.Structure):
     _fields_ = [("name", ct.c_char * 16), ("ms", ct.c_double),
                 ("launches", ct.c_longlong), ("flops", ct.c_double),
@@ -92,6 +98,7 @@ _SIGS = {
     "trm_create_csr": (_i, [ct.POINTER(_h), _i64, _p, _p, _p, _i, _i, _d,
                             ct.POINTER(trm_options)]),
     "trm_set_overlap_csr": (_i, [_h, _p, _p, _p]),
+    "trm_history": (_i, [_h, ct.POINTER(trm_iter_record), _i]),
     "trm_solve": (_i, [_h, _p, _p, _p, _i, _p, ct.POINTER(trm_stats)]),
     "trm_destroy": (_i, [_h]),
     "trm_strerror": (ct.c_char_p, [_i]),
@@ -234,6 +241,18 @@ def trm_solve(handle, N, m, C_out=None, C_on_device=False, C0=None):
     if status not in (0, -4):
         _check(status, handle)
     return lam, eg.value, st, status
+
+
+def trm_history(handle):
+    """Per-iteration records of the last solve on the handle, as arrays:
+    {"E", "rms", "alpha", "gamma", "phase", "restart"}."""
+    n = lib.trm_history(handle, None, 0)
+    if n < 0:
+        _check(n, handle)
+    buf = (trm_iter_record * max(n, 1))()
+    lib.trm_history(handle, buf, n)
+    return {k: np.array([getattr(buf[i], k) for i in range(n)])
+            for k in ("E", "rms", "alpha", "gamma", "phase", "restart")}
 
 
 def trm_destroy(handle):
@@ -381,6 +400,10 @@ class Solver:
         lam, eg, st, status = trm_solve(self.handle, self.N, self.m, C_out=C,
                                         C0=C0)
         return lam, eg, C, st.as_dict(), status
+
+    def history(self):
+        """Per-iteration records of the last solve (see trm_history)."""
+        return trm_history(self.handle)
 
     def close(self):
         if self.handle:

@@ -209,6 +209,23 @@ trm_status trm_solve(trm_handle h, double* lambda, double* E_G, double* C,
   });
 }
 
+int trm_history(trm_handle h, trm_iter_record* out, int cap) {
+  if (!h || cap < 0 || (cap > 0 && !out))
+    return fail(h, TRM_EINVAL, "invalid arguments to trm_history");
+  const auto& hist = h->solver->history();
+  const int n = (int)hist.size();
+  for (int i = 0; i < n && i < cap; ++i) {
+    const auto& r = hist[i];
+    out[i].E = r.v.E;
+    out[i].rms = r.v.rms;
+    out[i].alpha = r.v.alpha;
+    out[i].gamma = r.v.gamma;
+    out[i].phase = r.phase;
+    out[i].restart = r.v.restart;
+  }
+  return n;
+}
+
 trm_status trm_destroy(trm_handle h) {
   if (!h) return TRM_OK;
   return guarded(nullptr, [&]() {

@@ -18,7 +18,7 @@ namespace trm {
 
 namespace {
 
-constexpr int kRing = 64;
+constexpr int kRing = Solver::kRingSize;
 
 __global__ void k_set_restart(IterScalars* sc) {
   sc->restart = 1;
@@ -915,6 +915,7 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
   const auto t_start = std::chrono::steady_clock::now();
   const long long launches0 = thread_launch_count();
   const size_t nm = (size_t)N_ * m_;
+  history_.clear();
   if (C0_host)
     TRM_CUDA(cudaMemcpyAsync(C64_, C0_host, nm * 8, cudaMemcpyHostToDevice,
                              s_));
@@ -1000,12 +1001,17 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
     n_phase[phase == PH_SP ? 0 : 1]++;
     TRM_CUDA(cudaMemcpyAsync(&ring_[enq % kRing], sc_, sizeof(IterScalars),
                              cudaMemcpyDeviceToHost, s_));
+    ring_phase_[enq % kRing] = phase;
     TRM_CUDA(cudaEventRecord(ev_[enq % kRing], s_));
     prof.cut();
     ++enq;
   };
-  auto drain = [&]() {  // wait for everything enqueued
+  auto record = [&](int i) {
+    history_.push_back({ring_[i % kRing], ring_phase_[i % kRing]});
+  };
+  auto drain = [&]() {  // wait for everything enqueued (and record it)
     TRM_CUDA(cudaStreamSynchronize(s_));
+    for (int j = read; j < enq; ++j) record(j);
     read = enq;
   };
 
@@ -1020,6 +1026,7 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
     TRM_CUDA(cudaEventSynchronize(ev_[i % kRing]));
     if (prof.on) prof.resolve();
     const IterScalars v = ring_[i % kRing];
+    record(i);
     E_last = v.E;
     if (trace)
       std::fprintf(stderr,

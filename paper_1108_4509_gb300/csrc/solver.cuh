@@ -103,6 +103,15 @@ class Solver {
   void rayleigh_ritz(double* C_dev, double* lambda_host, double* res_host);
 
   int64_t N() const { return N_; }
+  // entries of the pinned ring of per-iteration scalars
+  static constexpr int kRingSize = 64;
+  // The scalars of every iteration of the last solve, in order, with the
+  // phase the iteration ran in (0 full SP, 1 MP2, 2 FP64).
+  struct IterRecord {
+    IterScalars v;
+    int phase;
+  };
+  const std::vector<IterRecord>& history() const { return history_; }
   Profiler prof;
   cudaStream_t stream() const { return s_; }
   std::string last_error;
@@ -177,6 +186,8 @@ class Solver {
   IterScalars* ring_ = nullptr;  // pinned host ring of per-iteration scalars
   std::vector<cudaEvent_t> ev_;
   int state_ = 0;  // 0: C64 current, 1: C32 current
+  std::vector<IterRecord> history_;
+  int ring_phase_[kRingSize] = {};  // phase of each ring entry's iteration
   // generalized problem: S as an operator, Y = S C (and its swap buffer),
   // S P of the line search, diag(S)
   Operator sop_;

@@ -93,3 +93,9 @@ def test_extrapolate_rejects_invalid_arguments_on_the_host(trm):
         with pytest.raises(trm.TrmError) as e:
             trm.trm_extrapolate(*args)
         assert e.value.status == -1
+
+
+def test_history_rejects_a_null_handle(trm):
+    assert trm.lib.trm_history(None, None, 0) == -1
+    with pytest.raises(trm.TrmError):
+        trm.trm_history(None)

@@ -230,3 +230,32 @@ def test_graph_replay_same_bytes(trm, mode):
     assert st0["iterations"] == st1["iterations"]
     assert st0["launches"] == st1["launches"]
     _check(lam1, eg1, C1, op.lowest_eigenvalues(H, m))
+
+
+def test_history_of_a_mixed_solve(trm, grid16_ref):
+    """trm_history: one record per iteration; the phases climb the ladder
+    (full SP, then MP2), the convergence test passed on the record read
+    lag iterations before the last, and the energies settle on E_G from
+    above (R_i = (E_i - E_G) / E_G of the paper's convergence plots)."""
+    w, V, H, ref = grid16_ref
+    nx, ny, nz = w.shape
+    opt = trm.trm_default_options(precision=trm.TRM_MIXED, stream=gu.stream())
+    h = trm.trm_create_stencil(nx, ny, nz, w.order, w.h, V, w.m, 1e-9, opt)
+    try:
+        lam, eg, st, status = trm.trm_solve(h, w.N, w.m)
+        hist = trm.trm_history(h)
+    finally:
+        trm.trm_destroy(h)
+    assert status == 0
+    n = len(hist["E"])
+    assert n == st.iterations
+    ph = hist["phase"]
+    assert ph[0] == 0 and ph[-1] == 1 and np.all(np.diff(ph) >= 0)
+    assert np.count_nonzero(ph == 0) == st.iterations_phase[0]
+    assert hist["rms"][n - 1 - opt.lag] <= 1e-9
+    assert np.all(np.isfinite(hist["E"])) and np.all(hist["rms"] > 0)
+    # full SP holds C^T C = I to FP32 accuracy only, so its energies may
+    # dip below E_G by about 1e-6 relative
+    R = (hist["E"] - eg) / abs(eg)
+    assert R.min() > -1e-5 and abs(R[-1]) < 1e-9
+
