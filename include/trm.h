@@ -247,8 +247,8 @@ trm_status trm_gram(int64_t N, int m, int n, int dtype, const void* A,
 trm_status trm_orthonormalize(int64_t N, int m, double* C, void* stream);
 
 /*
- * Initial-guess extrapolation for a chain of related problems (Sec. 4 and
- * the discussion cite it as the way to start close to the solution): from
+ * Initial-guess extrapolation for a chain of related problems (Secs. 3 and
+ * 4 cite it as the way to start close to the solution): from
  * the converged blocks of the two previous problems, a block for the next.
  * C_cur's columns are any basis of its subspace, so C_prev is first aligned
  * to it by the orthogonal U that minimises ||C_prev U - C_cur||_F (the polar

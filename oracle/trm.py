@@ -25,8 +25,8 @@ notes of the repository):
   trace((G_i - G_{i-1})^T M G_i) / trace(G_{i-1}^T M G_{i-1}) (exactly the
   printed formula when M = I). CG restarts (gamma = 0) when P_i is not a
   descent direction, trace(G_i^T P_i) <= 0.
-* Initial-guess extrapolation (cited in Sec. 4 and the discussion, ref. APJ,
-  not defined in the paper): :func:`extrapolate` aligns the previous block
+* Initial-guess extrapolation (cited in Secs. 3 and 4, ref. APJ, not
+  defined in the paper): :func:`extrapolate` aligns the previous block
   to the current one by the orthogonal Procrustes rotation (the blocks are
   only defined up to a rotation, Eq. TRHEQ's invariance), extrapolates
   linearly, and orthonormalizes by Fig. ONFIG.
