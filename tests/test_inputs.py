@@ -88,3 +88,20 @@ def test_random_block_column_matches_block():
     B = ti.random_block(1000, 5, 7)
     for j in range(5):
         assert np.array_equal(B[:, j], ti.random_block_column(1000, j, 7))
+
+
+def test_hat_overlap_csr_in_two_and_one_dimensions():
+    """An axis of length 1 is absent: a 2-D grid gives the 9-point tensor
+    product, a 1-D grid the tridiagonal (1, 4, 1)/6; columns ascend."""
+    import scipy.sparse as sp
+    T = lambda n: (np.diag(np.full(n, 4 / 6))                 # noqa: E731
+                   + np.diag(np.full(n - 1, 1 / 6), 1)
+                   + np.diag(np.full(n - 1, 1 / 6), -1))
+    for shape, want in (((5, 4, 1), np.kron(T(4), T(5))), ((7, 1, 1), T(7))):
+        rp, ci, v = ti.hat_overlap_csr(shape)
+        N = int(np.prod(shape))
+        S = sp.csr_matrix((v, ci, rp), shape=(N, N)).toarray()
+        assert np.array_equal(S, want)
+        for r in range(N):
+            assert np.all(np.diff(ci[rp[r]:rp[r + 1]]) > 0)
+        assert rp.dtype == np.int32 and ci.dtype == np.int32
