@@ -99,3 +99,36 @@ def test_history_rejects_a_null_handle(trm):
     assert trm.lib.trm_history(None, None, 0) == -1
     with pytest.raises(trm.TrmError):
         trm.trm_history(None)
+
+
+def test_header_is_plain_c_and_a_c_program_links(trm, tmp_path):
+    """include/trm.h compiles as strict C99 and a C program linked against
+    the library calls it (host-only entry points; no GPU needed)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(
+        "#include <stdio.h>\n#include \"trm.h\"\n"
+        "int main(void) {\n"
+        "  trm_options o;\n"
+        "  trm_iter_record r;\n"
+        "  trm_problem p;\n"
+        "  (void)r; (void)p;\n"
+        "  if (trm_default_options(&o) != TRM_OK) return 1;\n"
+        "  if (o.precision != TRM_MIXED || o.graphs != 1) return 2;\n"
+        "  if (trm_history(NULL, NULL, 0) != TRM_EINVAL) return 3;\n"
+        "  if (trm_footprint_bytes(1000, 8) == 0) return 4;\n"
+        "  printf(\"%s\\n\", trm_strerror(TRM_ENOTPD));\n"
+        "  return 0;\n}\n")
+    libdir = os.path.dirname(trm.LIB_PATH)
+    exe = tmp_path / "abi"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror",
+                    "-pedantic", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-L", libdir, "-ltrm", "-Wl,-rpath," + libdir, "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out
+    assert out.stdout.strip() == trm.trm_strerror(-3)
