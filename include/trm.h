@@ -392,7 +392,9 @@ trm_status trm_server_submit(trm_server s, const trm_problem* p,
 
 /* Block until the ticket's solve is done; writes lambda[m] (host), *E_G,
  * *stats and *latency (seconds from submission to completion; any output
- * may be NULL) and releases the ticket. Returns the solve's status (as
+ * may be NULL) and releases the ticket. One caller waits per ticket: a
+ * second wait on a ticket that another thread is waiting on, or on one
+ * already released, returns TRM_EINVAL. Returns the solve's status (as
  * trm_solve); details in trm_last_global_error(). */
 trm_status trm_server_wait(trm_server s, int64_t ticket, double* lambda,
                            double* E_G, trm_stats* stats, double* latency);

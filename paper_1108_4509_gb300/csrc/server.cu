@@ -36,6 +36,7 @@ struct Request {
   trm_stats stats{};
   Clock::time_point t_submit, t_start, t_done;
   bool done = false;
+  bool claimed = false;  // a caller is waiting on (or has taken) the result
 };
 
 }  // namespace
@@ -223,8 +224,15 @@ trm_status trm_server_wait(trm_server s, int64_t ticket, double* lambda,
       return TRM_EINVAL;
     }
     r = it->second;
+    if (r->claimed) {
+      trm::set_global_error("another caller is already waiting on this ticket");
+      return TRM_EINVAL;
+    }
+    r->claimed = true;
+    // the wait releases the lock: a submit may rehash the map meanwhile, so
+    // the entry is removed by key afterwards, not through the iterator
     s->cv.wait(lock, [&] { return r->done; });
-    s->requests.erase(it);
+    s->requests.erase(ticket);
   }
   if (lambda && !r->lambda.empty())
     std::copy(r->lambda.begin(), r->lambda.end(), lambda);
