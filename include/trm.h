@@ -303,24 +303,31 @@ int trm_profile_read(trm_handle h, trm_kernel_stats* out, int max);
 long long trm_launch_count(void);
 
 /*
- * trm_gram_noalloc: out = A^T B exactly as trm_gram computes it, for callers
- * that must not allocate device memory (no counterpart in the paper). Some
- * callers cannot call cudaMalloc: they have given the device's memory to their
- * own allocator (a framework's caching pool or an arena sized at start-up),
- * or they run under a budget that must not grow, or cannot afford the
+ * trm_gram_noalloc: out = A^T B as trm_gram computes it, for callers that
+ * must not allocate device memory (no counterpart in the paper). Some callers
+ * cannot call cudaMalloc: they have given the device's memory to their own
+ * allocator (a framework's caching pool or an arena sized at start-up), or
+ * they run under a budget that must not grow, or cannot afford the
  * device-wide synchronisation of cudaMalloc/cudaFree inside a timed loop.
- * This variant keeps its split partial sums in a fixed 8 MiB array
- * (2^20 doubles) compiled into the library, which every GPU that loads the
- * library holds until the process exits; it calls no allocation routine.
+ * This variant keeps its split partial sums in a fixed 24 MiB array
+ * (3 * 2^20 doubles) compiled into the library, which every GPU that loads
+ * the library holds until the process exits; it calls no allocation routine.
  * Limit: m * n <= 2^20 (up to 1024 x 1024); larger sizes return TRM_EINVAL
- * with a message in trm_last_global_error(). The first call on each device
- * looks up the array's device address (with that device current) and caches
- * it; make that first call before any stream capture. All calls share the one
- * array and each overwrites every partial it reads, so nothing needs
- * clearing, but calls that overlap on the GPU (different streams or host
- * threads at once) race on it. A, B, out: device; stream as in trm_gram. The
- * sum order may differ from trm_gram's (fewer, longer row slices when the
- * partials would not fit), within the same rounding bound.
+ * with a message in trm_last_global_error().
+ * Kernels: FP32 operands that trm_gram sends to the tensor cores (N % 4 == 0,
+ * m >= 64, A and B 16-byte aligned) run that same kernel with the same row
+ * slices and sum order, so out has the same bytes as trm_gram's (error below
+ * 8e-6 sum_k |a_ki||b_kj|); other FP32 operands and all FP64 operands run
+ * trm_gram's SIMT kernel (products summed in the operands' precision within
+ * a slice of rows, the slices in FP64), with fewer, longer row slices when
+ * its partials would not fit, which changes only the summation order.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any
+ * stream capture. All calls share the one array and each overwrites every
+ * partial it reads, so nothing needs clearing, but calls that overlap on the
+ * GPU (different streams or host threads at once) race on it. Like trm_gram,
+ * the call synchronizes the stream before it returns. A, B, out: device;
+ * stream as in trm_gram.
  */
 trm_status trm_gram_noalloc(int64_t N, int m, int n, int dtype, const void* A,
                             const void* B, double* out, void* stream);

@@ -297,7 +297,7 @@ void gram(int64_t N, int m, const T* A, const Blocks<T>& B, double* out,
   const int n = B.total();
   if (m <= 0 || n <= 0) return;
   if constexpr (sizeof(T) == 4) {
-    if (gram_tc_eligible(N, m, B)) {  // tensor cores, FP32-class accuracy
+    if (gram_tc_eligible(N, m, A, B)) {  // tensor cores, FP32-class accuracy
       gram_tc(N, m, A, B, out, partials, partials_cap, err, s, out32);
       return;
     }

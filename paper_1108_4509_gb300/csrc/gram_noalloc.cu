@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <new>
+#include <string>
 
 #include "../../include/trm.h"
 #include "ops.cuh"
@@ -15,9 +17,15 @@
 namespace trm {
 namespace {
 
-// 1 Mi doubles = 8 MiB of partial sums. Every GPU that loads the library holds
-// this array until the process exits.
-constexpr size_t kScratchDoubles = (size_t)1 << 20;
+// 3 Mi doubles = 24 MiB of partial sums. Every GPU that loads the library
+// holds this array until the process exits. The tensor-core Gram splits N
+// into at most (SM count / output tiles) slices of one 128 x 128 tile each,
+// so its partials are at most SMs x 128^2 doubles (2.5 Mi on 152 SMs) for any
+// m x n within the limit below; the last double holds the kernel's status
+// word.
+constexpr size_t kScratchDoubles = (size_t)3 << 20;
+// Largest m * n accepted: 2^20 (1024 x 1024).
+constexpr size_t kMaxEntries = (size_t)1 << 20;
 static __device__ __align__(256) double g_gram_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -40,6 +48,46 @@ double* scratch_address() {
   return g_addr[dev];
 }
 
+int gram_noalloc(int64_t N, int m, int n, int dtype, const void* A,
+                 const void* B, double* out, cudaStream_t s) {
+  if ((size_t)m * (size_t)n > kMaxEntries)
+    throw Error(-1, "trm_gram_noalloc: m*n = " +
+                        std::to_string((long long)m * n) +
+                        " exceeds the fixed scratch's limit of " +
+                        std::to_string(kMaxEntries) + "; use trm_gram");
+  double* scratch = scratch_address();
+  const size_t cap = kScratchDoubles - 1;  // partials; then the status word
+  if (dtype == TRM_F32) {
+    const float* a = static_cast<const float*>(A);
+    Blocks<float> b;
+    b.p[0] = static_cast<const float*>(B);
+    b.cols = n;
+    b.count = 1;
+    // the tensor-core kernel trm_gram runs for these operands, with the same
+    // slices and sum order, so the result has the same bytes
+    if (gram_tc_eligible(N, m, a, b) && gram_tc_partials_doubles(N, m, n) <= cap) {
+      int* err = reinterpret_cast<int*>(scratch + cap);
+      int herr = 0;
+      TRM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+      gram_tc(N, m, a, b, out, scratch, cap, err, s);
+      TRM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TRM_CUDA(cudaStreamSynchronize(s));
+      if (herr & 2) throw Error(-6, "trm_gram_noalloc: a device wait timed out");
+      return TRM_OK;
+    }
+    gram_in_scratch<float>(N, m, a, b, out, scratch, cap, s);
+  } else {
+    Blocks<double> b;
+    b.p[0] = static_cast<const double*>(B);
+    b.cols = n;
+    b.count = 1;
+    gram_in_scratch<double>(N, m, static_cast<const double*>(A), b, out,
+                            scratch, cap, s);
+  }
+  TRM_CUDA(cudaStreamSynchronize(s));
+  return TRM_OK;
+}
+
 }  // namespace
 }  // namespace trm
 
@@ -47,40 +95,25 @@ extern "C" trm_status trm_gram_noalloc(int64_t N, int m, int n, int dtype,
                                        const void* A, const void* B,
                                        double* out, void* stream) {
   using namespace trm;
-  if (N < 1 || m < 1 || n < 1 || !A || !B || !out ||
-      (dtype != TRM_F32 && dtype != TRM_F64)) {
-    set_global_error("invalid arguments to trm_gram_noalloc");
-    return TRM_EINVAL;
-  }
-  if ((size_t)m * (size_t)n > kScratchDoubles) {
-    set_global_error("trm_gram_noalloc: m*n = " +
-                     std::to_string((long long)m * n) + " exceeds the fixed " +
-                     "scratch of " + std::to_string(kScratchDoubles) +
-                     " doubles; use trm_gram");
-    return TRM_EINVAL;
-  }
   try {
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    double* scratch = scratch_address();
-    if (dtype == TRM_F32) {
-      Blocks<float> b;
-      b.p[0] = static_cast<const float*>(B);
-      b.cols = n;
-      b.count = 1;
-      gram_in_scratch<float>(N, m, static_cast<const float*>(A), b, out,
-                             scratch, kScratchDoubles, s);
-    } else {
-      Blocks<double> b;
-      b.p[0] = static_cast<const double*>(B);
-      b.cols = n;
-      b.count = 1;
-      gram_in_scratch<double>(N, m, static_cast<const double*>(A), b, out,
-                              scratch, kScratchDoubles, s);
+    if (N < 1 || m < 1 || n < 1 || !A || !B || !out ||
+        (dtype != TRM_F32 && dtype != TRM_F64)) {
+      set_global_error("invalid arguments to trm_gram_noalloc");
+      return TRM_EINVAL;
     }
-    TRM_CUDA(cudaStreamSynchronize(s));
+    return static_cast<trm_status>(gram_noalloc(
+        N, m, n, dtype, A, B, out, reinterpret_cast<cudaStream_t>(stream)));
   } catch (const Error& e) {
     set_global_error(e.what());
     return static_cast<trm_status>(e.status);
+  } catch (const std::bad_alloc&) {
+    set_global_error("trm_gram_noalloc: host allocation failed");
+    return TRM_ENOMEM;
+  } catch (const std::exception& e) {
+    set_global_error(e.what());
+    return TRM_ECUDA;
+  } catch (...) {
+    set_global_error("trm_gram_noalloc: unknown error");
+    return TRM_ECUDA;
   }
-  return TRM_OK;
 }

@@ -341,8 +341,13 @@ CUtensorMap block_map(const float* p, int64_t N, int cols) {
 
 }  // namespace
 
-bool gram_tc_eligible(int64_t N, int m, const Blocks<float>& B) {
-  return gram_tc_pairs_eligible(N, m, B, B);
+bool gram_tc_eligible(int64_t N, int m, const float* A,
+                      const Blocks<float>& B) {
+  Blocks<float> a;
+  a.p[0] = A;
+  a.cols = m;
+  a.count = 1;
+  return gram_tc_pairs_eligible(N, m, a, B);
 }
 
 bool gram_tc_pairs_eligible(int64_t N, int m, const Blocks<float>& A,

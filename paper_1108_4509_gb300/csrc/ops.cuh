@@ -117,13 +117,16 @@ void gram_df(int64_t N, int m, const double* A, const Blocks<double>& B,
 void sum_splits_pairs(const float* part, int splits, size_t count,
                       double* out, cudaStream_t s, float* out32 = nullptr);
 // tcgen05 Gram of FP32 blocks (two-term TF32 split, three products, FP32
-// accumulation in tensor memory): needs N % 4 == 0, m >= 64, at most 4 B segments whose
-// widths are multiples of 128 when there are several.
-bool gram_tc_eligible(int64_t N, int m, const Blocks<float>& B);
+// accumulation in tensor memory): needs N % 4 == 0, m >= 64, A and every B
+// segment 16-byte aligned (TMA), at most 4 B segments whose widths are
+// multiples of 128 when there are several.
+bool gram_tc_eligible(int64_t N, int m, const float* A, const Blocks<float>& B);
 // Segment k of the output is A_k^T B_k (A.count == B.count, or one A for all
 // segments); up to four segments.
 bool gram_tc_pairs_eligible(int64_t N, int m, const Blocks<float>& A,
                             const Blocks<float>& B);
+// Doubles of split partials gram_tc / gram_tc_pairs need for an m x n result.
+size_t gram_tc_partials_doubles(int64_t N, int m, int n);
 void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
                    const Blocks<float>& B, double* out, double* partials,
                    size_t cap, int* err, cudaStream_t s,

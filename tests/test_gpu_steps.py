@@ -179,6 +179,28 @@ def test_gram(trm, N, m, n):
     assert np.median(np.abs(got32 - ref32) / scale) < 1e-6
 
 
+def test_gram_f32_misaligned_a_falls_back(trm):
+    """An FP32 A that is 4-byte but not 16-byte aligned (a column slice) at a
+    size the tensor cores take: the TMA path needs 16-byte operands, so the
+    call must run the SIMT kernel and still return A^T B."""
+    torch = gu.torch_mod()
+    N, m, n = 4096, 96, 128
+    A = ti.random_block(N, m, seed=4).astype(np.float32)
+    B = ti.random_block(N, n, seed=5).astype(np.float32)
+    ref = A.astype(np.float64).T @ B.astype(np.float64)
+    scale = np.abs(A).astype(np.float64).T @ np.abs(B).astype(np.float64)
+    buf = torch.zeros(N * m + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(np.ascontiguousarray(A.T).reshape(-1)).cuda()
+    b = gu.to_dev(B)
+    out = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    a_ptr = buf.data_ptr() + 4
+    assert a_ptr % 16 != 0
+    trm.trm_gram(N, m, n, trm.TRM_F32, a_ptr, b.data_ptr(), out.data_ptr(),
+                 gu.stream())
+    got = gu.from_dev(out)
+    assert np.all(np.abs(got - ref) <= gamma(N) * scale)
+
+
 # ---------------------------------------------------------------------------
 # a7: Fig. ONFIG
 # ---------------------------------------------------------------------------

@@ -7,7 +7,8 @@ the synchronisation of cudaMalloc/cudaFree. trm_gram_noalloc serves them with
 the split partial sums of the Gram product kept in a fixed array inside the
 library. These tests call it through the C ABI and hold it to the result of
 the ordinary trm_gram, within the same FP32/FP64 rounding bound the other
-Gram tests use, on two calls in a row. The file name makes pytest collect it
+Gram tests use, on calls in a row (FP32 operands that trm_gram sends to the
+tensor cores must give the same bytes: the same kernel runs). The file name makes pytest collect it
 last, so a run that stops at the first failure has run everything else.
 """
 import numpy as np
@@ -36,7 +37,8 @@ def test_gram_noalloc_matches_gram_on_two_calls(trm):
     torch = gu.torch_mod()
     # two calls in a row with different shapes: the second must not see the
     # first call's partial sums left in the shared scratch
-    for N, m, n, seed in [(110592, 128, 128, 1), (5003, 70, 200, 2)]:
+    for N, m, n, seed in [(110592, 128, 128, 1), (5003, 70, 200, 2),
+                          (65536, 512, 256, 3)]:
         A = ti.random_block(N, m, seed=seed)
         B = ti.random_block(N, n, seed=seed + 10)
         scale = np.abs(A).T @ np.abs(B)
@@ -50,6 +52,9 @@ def test_gram_noalloc_matches_gram_on_two_calls(trm):
             trm.trm_gram_noalloc(N, m, n, dtype, a.data_ptr(), b.data_ptr(),
                                  got.data_ptr(), gu.stream())
             r, g = gu.from_dev(ref), gu.from_dev(got)
+            if dtype == trm.TRM_F32 and N % 4 == 0 and m >= 64:
+                # the tensor-core kernel of trm_gram, same slices and order
+                assert np.array_equal(g, r)
             # each is within gamma_N |A|^T |B| of the exact product
             assert np.all(np.abs(g - r) <= 2 * gamma(N, u) * scale)
             exact = (A.astype(npdt).astype(np.float64).T
