@@ -12,8 +12,10 @@ import os
 import numpy as np
 import pytest
 import scipy.linalg as sla
+import scipy.sparse as sp
 
 import trm_inputs as ti
+from oracle import filtered
 from oracle import operator as op
 from oracle import trm
 
@@ -503,3 +505,109 @@ def test_dirichlet_eigenvalues_converge_to_the_continuum():
             errs.append(np.abs(sla.eigvalsh(T)[:3] - exact))
         for a, b in zip(errs, errs[1:]):
             assert np.all((0.9 * rate < a / b) & (a / b < 1.1 * rate))
+
+
+# ---------------------------------------------------------------------------
+# Comparison helpers and the preconditioner, pinned to known values
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("theta", [1e-9, 1e-4, 0.3, 1.2])
+def test_sin_max_angle_of_a_known_rotation(theta):
+    """span{e1, e2} against span{e1, cos t e2 + sin t e3}: the principal
+    angles are 0 and t, so the sine of the largest is sin t, for any basis of
+    either span (here rotated and rescaled, not orthonormal)."""
+    N = 40
+    A = np.zeros((N, 2))
+    A[0, 0] = A[1, 1] = 1.0
+    B = np.zeros((N, 2))
+    B[0, 0] = 1.0
+    B[1, 1], B[2, 1] = math.cos(theta), math.sin(theta)
+    rng = np.random.default_rng(1)
+    Ma, Mb = rng.standard_normal((2, 2)), rng.standard_normal((2, 2))
+    for a, b in ((A, B), (A @ Ma, B @ Mb), (B @ Mb, A @ Ma)):
+        assert abs(trm.sin_max_angle(a, b) - math.sin(theta)) <= 1e-15 + 1e-12 * theta
+
+
+def test_sin_max_angle_two_angles_takes_the_largest():
+    """Two rotated directions at angles 0.1 and 0.5: the 2-norm of the
+    projection residual is sin 0.5 (a Frobenius norm would give
+    sqrt(sin^2 0.1 + sin^2 0.5))."""
+    N = 30
+    A = np.zeros((N, 2))
+    A[0, 0] = A[1, 1] = 1.0
+    B = np.zeros((N, 2))
+    B[0, 0], B[2, 0] = math.cos(0.1), math.sin(0.1)
+    B[1, 1], B[3, 1] = math.cos(0.5), math.sin(0.5)
+    assert abs(trm.sin_max_angle(A, B) - math.sin(0.5)) < 1e-15
+
+
+def test_diagonal_preconditioner_inverts_a_diagonal_operator():
+    """For a diagonal H (a potential with no kinetic coupling) the diagonal
+    preconditioner is the exact inverse of H - sigma I with
+    sigma = min_k H_kk - 1 (and of H - sigma S for a diagonal S, sigma =
+    min_k H_kk / S_kk - 1): M (H - sigma S) y = y for every y, and M is SPD
+    with entries at most 1."""
+    rng = np.random.default_rng(4)
+    d = rng.uniform(-3.0, 2.0, 50)
+    H = sp.diags(d).tocsr()
+    M = trm.diagonal_preconditioner(H)
+    sigma = d.min() - 1.0
+    y = rng.standard_normal(50)
+    assert np.allclose(M * (spsolve_diag(H, sigma) @ y), y, rtol=1e-14, atol=0)
+    assert np.all(M > 0) and np.max(M) <= 1.0 + 1e-15
+    s = rng.uniform(0.5, 2.0, 50)
+    S = sp.diags(s).tocsr()
+    Ms = trm.diagonal_preconditioner(H, S)
+    sig = np.min(d / s) - 1.0
+    assert np.allclose(Ms * ((d - sig * s) * y), y, rtol=1e-14, atol=0)
+    assert np.all(Ms > 0)
+
+
+def spsolve_diag(H, sigma):
+    """H - sigma I as a dense matrix (helper of the preconditioner pin)."""
+    return H.toarray() - sigma * np.eye(H.shape[0])
+
+
+# ---------------------------------------------------------------------------
+# The large-workload reference eigensolver (oracle.filtered)
+# ---------------------------------------------------------------------------
+def test_filtered_eigenpairs_vs_dense_with_wells():
+    """Brute force: the 20 lowest eigenvalues of an 8^3 13-point grid with
+    wells equal dense diagonalisation; the residuals are what is returned."""
+    shape = (8, 8, 8)
+    H = op.grid_hamiltonian(shape, 4, 1.0, ti.gaussian_wells(shape, 6, seed=3))
+    ref = op.dense_spectrum(H)[:20]
+    r = filtered.lowest_eigenpairs(H, 20, tol=1e-11, want_vectors=True,
+                                   max_iter=60)
+    assert r.converged
+    assert np.max(np.abs(r.lam - ref)) < 1e-12
+    res = np.linalg.norm(H @ r.X - r.X * r.lam[None, :], axis=0)
+    assert np.max(np.abs(res - r.residuals)) < 1e-12
+    assert np.max(np.abs(r.X.T @ r.X - np.eye(20))) < 1e-12
+
+
+def test_filtered_eigenpairs_vs_closed_forms():
+    """V = 0: the 7-point 16^3 spectrum (cosine closed form, m = 17 at a
+    cluster edge, E_G = 2.972191256741) and the 13-point 20^3 spectrum
+    (Kronecker sum of the dense 1-D spectra), at the first 40 or so."""
+    H = op.grid_hamiltonian((16, 16, 16), 2, 1.0, None)
+    r = filtered.lowest_eigenpairs(H, 17, tol=1e-10)
+    spec = op.order2_spectrum((16, 16, 16), 1.0)
+    assert np.max(np.abs(r.lam - spec[:17])) < 1e-12
+    assert abs(math.fsum(r.lam) - 2.972191256741) < 5e-12
+    shape = (20, 20, 20)
+    spec = op.kron_sum_spectrum(shape, 4, 1.0)
+    edges = np.nonzero(np.diff(spec[:80]) > 1e-8)[0] + 1
+    k = int(edges[edges <= 60][-1])
+    r = filtered.lowest_eigenpairs(op.grid_hamiltonian(shape, 4, 1.0, None),
+                                   k, tol=1e-10)
+    assert k >= 30 and np.max(np.abs(r.lam - spec[:k])) < 1e-12
+
+
+def test_gershgorin_upper_bounds_the_spectrum():
+    shape = (6, 7, 5)
+    H = op.grid_hamiltonian(shape, 4, 1.0, ti.gaussian_wells(shape, 4, seed=1))
+    top = op.dense_spectrum(H)[-1]
+    ub = filtered.gershgorin_upper(H)
+    assert top <= ub
+    # interior rows of the 13-point rule: 3.75 + 6 (2/3) + 6 (1/24) = 8 + V_i
+    assert abs(ub - 8.0) < 1e-12 + np.max(np.abs(H.diagonal() - 3.75))

@@ -104,3 +104,45 @@ def test_fletcher_reeves_in_place_of_polak_ribiere_is_caught(monkeypatch):
                         / float(np.sum(Gp * MGp)))
     _fails(pins.test_polak_ribiere_restarts_itself_when_the_gradient_repeats)
 
+
+
+def test_frobenius_angle_is_caught(monkeypatch):
+    """sin_max_angle with the Frobenius norm in place of the 2-norm."""
+    def bad(A, B):
+        Qa, _ = np.linalg.qr(A)
+        Qb, _ = np.linalg.qr(B)
+        return float(np.linalg.norm(Qb - Qa @ (Qa.T @ Qb)))
+    monkeypatch.setattr(trm, "sin_max_angle", bad)
+    _fails(pins.test_sin_max_angle_two_angles_takes_the_largest)
+
+
+def test_angle_without_orthonormalising_is_caught(monkeypatch):
+    """sin_max_angle on the raw bases (no QR)."""
+    monkeypatch.setattr(trm, "sin_max_angle", lambda A, B: float(
+        np.linalg.norm(B - A @ (A.T @ B), 2)))
+    _fails(pins.test_sin_max_angle_of_a_known_rotation, 0.3)
+
+
+def test_preconditioner_shift_sign_is_caught(monkeypatch):
+    """sigma = min_k H_kk + 1: H - sigma I is no longer positive definite."""
+    def bad(H, S=None):
+        d = H.diagonal()
+        return 1.0 / (d - (d.min() + 1.0))
+    monkeypatch.setattr(trm, "diagonal_preconditioner", bad)
+    _fails(pins.test_diagonal_preconditioner_inverts_a_diagonal_operator)
+
+
+def test_filtered_without_orthonormalization_is_caught(monkeypatch):
+    """Rayleigh-Ritz on a basis that was never orthonormalized."""
+    from oracle import filtered
+    monkeypatch.setattr(filtered, "_orthonormalize_rows", lambda X, f: None)
+    _fails(pins.test_filtered_eigenpairs_vs_dense_with_wells)
+
+
+def test_filtered_damping_the_wanted_end_is_caught(monkeypatch):
+    """The damped interval starting at the lowest Ritz value (theta[0] for
+    theta[-1]): the wanted eigenvalues are no longer amplified."""
+    from oracle import filtered
+    monkeypatch.setattr(filtered, "filter_interval", lambda th, up: (
+        0.5 * (th[0] + up), 0.5 * (up - th[0])))
+    _fails(pins.test_filtered_eigenpairs_vs_dense_with_wells)
