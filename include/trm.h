@@ -292,7 +292,10 @@ trm_status trm_rayleigh_ritz(trm_handle h, double* C, double* lambda,
 /*
  * Timing of the library's kernels by class, with a pair of CUDA events on the
  * handle's stream around each launcher call of a solve (no paper
- * counterpart: measurement support). enable != 0 zeroes the counters and
+ * counterpart: measurement support). Classes, one kernel family each:
+ * spmm_f32, spmm_f64, spmm_df (MP2's double-float H C), gram_f32, gram_f64,
+ * grad_f32, grad_f64, rotate_f32, rotate_f64, rotate_df (MP2's split
+ * rotation), rowops, small_mm, eig. enable != 0 zeroes the counters and
  * starts timing; 0 stops it. trm_profile_read copies up to max classes into
  * out (host) and returns how many exist, or a negative status.
  */
@@ -336,6 +339,33 @@ trm_status trm_gram_noalloc(int64_t N, int m, int n, int dtype, const void* A,
  * given seed: entry (i, j) = u(seed, i + N j) - 0.5 (Sec. 3: random C0). */
 trm_status trm_random_block(int64_t N, int m, uint64_t seed, double* C,
                             void* stream);
+
+/* ------------------------------------------------------------------------
+ * Slab partition for several GPUs (host logic; no paper counterpart beyond
+ * Sec. 2.1's observation that every block step is a loop over grid points).
+ * Rank r of `ranks` owns the z-planes [z0, z1) of an nx x ny x nz stencil
+ * grid (planes split as evenly as possible, the first nz % ranks ranks one
+ * more), i.e. the rows [row0, row0 + rows) of every N x m block. Applying H
+ * to its rows needs `radius` planes on either side (1 for order 2, 2 for
+ * order 4) from the neighbouring ranks: halo_lo planes below z0 and halo_hi
+ * above z1 (0 at the grid's walls, where the Dirichlet boundary applies).
+ * The rank's extended grid is nx x ny x ext_nz planes starting at ext_z0
+ * (ext_rows rows): a stencil handle on that grid, with the halo planes
+ * filled from the neighbours, gives H C exactly on the owned rows. The
+ * N-deep sums (Grams, energies) are the sums over ranks of the partials
+ * over owned rows. TRM_EINVAL if a slab would be thinner than the stencil's
+ * reach (ranks > 1 and nz / ranks < radius) or for invalid arguments.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int z0, z1;           /* owned planes [z0, z1) */
+  int halo_lo, halo_hi; /* planes received from rank - 1 and rank + 1 */
+  int64_t row0, rows;   /* owned rows [row0, row0 + rows) of every block */
+  int ext_z0, ext_nz;   /* extended grid: planes [ext_z0, ext_z0 + ext_nz) */
+  int64_t ext_rows;     /* nx * ny * ext_nz */
+} trm_slab;
+
+trm_status trm_slab_plan(int nx, int ny, int nz, int order, int ranks,
+                         int rank, trm_slab* out);
 
 /* ------------------------------------------------------------------------
  * Serving: a request server that solves eigenproblems of different sizes as

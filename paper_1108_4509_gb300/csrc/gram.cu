@@ -230,16 +230,23 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_sum_splits_pairs(const float* __restrict__ part, int splits,
                        size_t count, double* __restrict__ out,
-                       float* __restrict__ out32) {
+                       float* __restrict__ out32, SymSeg sym) {
   __shared__ float rh[8][33], rl[8][33];
   const int el = threadIdx.x & 31, g = threadIdx.x >> 5;
   const size_t e = (size_t)blockIdx.x * 32 + el;
   F2 acc = {0.f, 0.f};
   if (e < count) {
+    size_t src = e;  // a mirrored entry of a symmetric segment reads (j, i)
+    if (sym.seg >= 0) {
+      const int i = (int)(e % sym.m), j = (int)(e / sym.m);
+      const int seg = j / sym.seg_cols, jj = j - seg * sym.seg_cols;
+      if (seg == sym.seg && i / sym.tile > jj / sym.tile)
+        src = (size_t)jj + (size_t)(seg * sym.seg_cols + i) * sym.m;
+    }
 #pragma unroll 4
     for (int k = g; k < splits; k += 8)
-      acc = df_add(acc, F2{part[2 * (size_t)k * count + e],
-                           part[(2 * (size_t)k + 1) * count + e]});
+      acc = df_add(acc, F2{part[2 * (size_t)k * count + src],
+                           part[(2 * (size_t)k + 1) * count + src]});
   }
   rh[g][el] = acc.h;
   rl[g][el] = acc.l;
@@ -277,9 +284,9 @@ size_t gram_partials_doubles(int64_t N, int m, int n) {
 }
 
 void sum_splits_pairs(const float* part, int splits, size_t count,
-                      double* out, cudaStream_t s, float* out32) {
+                      double* out, cudaStream_t s, float* out32, SymSeg sym) {
   k_sum_splits_pairs<<<ceil_div(count, 32), 256, 0, s>>>(part, splits, count,
-                                                         out, out32);
+                                                         out, out32, sym);
   TRM_CHECK_LAUNCH();
 }
 

@@ -110,14 +110,18 @@ __device__ __forceinline__ uint64_t kdesc(uint32_t saddr) {
 // N = 128, M = 128.
 constexpr uint32_t kIdesc = idesc_tf32(BM, BN, false, false);
 
+// Output tiles of one launch, listed (blockIdx.y indexes the list): all of
+// them, or for a symmetric segment only those on or above its diagonal.
+constexpr int kMaxTiles = 256;  // 8 x 32: m = 1024, four m-column segments
+
 struct TcArgs {
   int64_t N;
   int m, n;               // output is m x n
   int64_t rows_per_split;
-  int tiles_m;
   int seg_cols;           // columns per segment (a multiple of BN if > 1)
   double* part;
   int* err;
+  uint8_t ti[kMaxTiles], tj[kMaxTiles];  // row and column tile of each CTA row
 };
 
 // Output column segment k is A_k^T B_k (up to four segments; the line search
@@ -134,9 +138,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int split = blockIdx.x;
-  const int tile = blockIdx.y;
-  const int i0 = (tile % args.tiles_m) * BM;
-  const int j0 = (tile / args.tiles_m) * BN;
+  const int i0 = args.ti[blockIdx.y] * BM;
+  const int j0 = args.tj[blockIdx.y] * BN;
   const int64_t rb = (int64_t)split * args.rows_per_split;
   const int64_t re = min(args.N, rb + args.rows_per_split);
   const int nk = (int)((re - rb + BK - 1) / BK);
@@ -370,6 +373,12 @@ size_t gram_tc_partials_doubles(int64_t N, int m, int n) {
   return (size_t)splits * m * n;
 }
 
+// Row slices for a launch of `tiles` output tiles: enough to fill the SMs,
+// at least kMinStages stages each.
+static int tc_splits(int64_t N, int tiles) {
+  return std::max(1, std::min(sm_count() / tiles, ceil_div(N, BK * kMinStages)));
+}
+
 void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
              double* out, double* partials, size_t cap, int* err,
              cudaStream_t s, float* out32) {
@@ -382,25 +391,46 @@ void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
 
 void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
                    const Blocks<float>& B, double* out, double* partials,
-                   size_t cap, int* err, cudaStream_t s, float* out32) {
+                   size_t cap, int* err, cudaStream_t s, float* out32,
+                   int sym_seg) {
   const int n = B.total();
   const int tiles_m = ceil_div(m, BM);
-  const int tiles = tiles_m * ceil_div(n, BN);
-  int splits = std::max(1, std::min(sm_count() / tiles,
-                                    ceil_div(N, BK * kMinStages)));
+  const int segcols = B.count > 1 ? B.cols : n;
+  if (sym_seg >= 0 && (sym_seg >= B.count || B.cols != m ||
+                       (B.count > 1 && m % BN != 0)))
+    throw Error(-1, "gram_tc: a symmetric segment must be m x m");
+  TcArgs a{};
+  int tiles = 0;
+  for (int tj = 0; tj < ceil_div(n, BN); ++tj) {
+    const int seg = (tj * BN) / segcols;
+    const int tjs = tj - seg * (segcols / BN);  // column tile in its segment
+    for (int ti = 0; ti < tiles_m; ++ti) {
+      if (seg == sym_seg && ti > tjs) continue;  // mirrored from (tjs, ti)
+      if (tiles == kMaxTiles) throw Error(-1, "gram_tc: too many output tiles");
+      a.ti[tiles] = (uint8_t)ti;
+      a.tj[tiles] = (uint8_t)tj;
+      ++tiles;
+    }
+  }
+  int splits = tc_splits(N, tiles);
   int64_t rows = (N + splits - 1) / splits;
   rows = ((rows + BK - 1) / BK) * BK;
   splits = (int)((N + rows - 1) / rows);
   if ((size_t)splits * m * n > cap)
     throw Error(-2, "gram_tc: partials buffer too small");
-  const int segcols = B.count > 1 ? B.cols : n;
   TcMaps maps;
   for (int k = 0; k < 4; ++k) {
     const int kb = k < B.count ? k : 0;
     maps.a[k] = block_map(A.p[A.count > 1 ? kb : 0], N, m);
     maps.b[k] = block_map(B.p[kb], N, B.cols);
   }
-  TcArgs a{N, m, n, rows, tiles_m, segcols, partials, err};
+  a.N = N;
+  a.m = m;
+  a.n = n;
+  a.rows_per_split = rows;
+  a.seg_cols = segcols;
+  a.part = partials;
+  a.err = err;
   const size_t smem = sizeof(TcSmem) + 1024;
   static std::once_flag attr;
   std::call_once(attr, [&] {
@@ -412,7 +442,7 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
   TRM_CHECK_LAUNCH();
   const size_t count = (size_t)m * n;
   sum_splits_pairs(reinterpret_cast<const float*>(partials), splits, count,
-                   out, s, out32);
+                   out, s, out32, SymSeg{sym_seg, m, segcols, BM});
 }
 
 }  // namespace trm

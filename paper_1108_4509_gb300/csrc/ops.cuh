@@ -113,9 +113,18 @@ void sum_splits(const double* part, int splits, size_t count, double* out,
 void gram_df(int64_t N, int m, const double* A, const Blocks<double>& B,
              double* out, double* partials, size_t partials_cap,
              cudaStream_t s);
+// A symmetric m x m output segment of which only the tiles on or above the
+// diagonal were computed (seg < 0: none): an entry (i, j) of segment seg
+// whose tile lies below the diagonal (i / tile > j / tile) takes the sum of
+// entry (j, i).
+struct SymSeg {
+  int seg = -1;
+  int m = 0, seg_cols = 0, tile = 0;
+};
 // the same for partials stored as FP32 pairs (hi, then lo, per split)
 void sum_splits_pairs(const float* part, int splits, size_t count,
-                      double* out, cudaStream_t s, float* out32 = nullptr);
+                      double* out, cudaStream_t s, float* out32 = nullptr,
+                      SymSeg sym = SymSeg{});
 // tcgen05 Gram of FP32 blocks (two-term TF32 split, three products, FP32
 // accumulation in tensor memory): needs N % 4 == 0, m >= 64, A and every B
 // segment 16-byte aligned (TMA), at most 4 B segments whose widths are
@@ -127,10 +136,12 @@ bool gram_tc_pairs_eligible(int64_t N, int m, const Blocks<float>& A,
                             const Blocks<float>& B);
 // Doubles of split partials gram_tc / gram_tc_pairs need for an m x n result.
 size_t gram_tc_partials_doubles(int64_t N, int m, int n);
+// sym_seg >= 0: that segment is symmetric (m x m); only its tiles on or
+// above the diagonal are computed and the rest mirrored (Fig. DIVFIG).
 void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
                    const Blocks<float>& B, double* out, double* partials,
                    size_t cap, int* err, cudaStream_t s,
-                   float* out32 = nullptr);
+                   float* out32 = nullptr, int sym_seg = -1);
 void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
              double* out, double* partials, size_t cap, int* err,
              cudaStream_t s, float* out32 = nullptr);
@@ -257,21 +268,23 @@ void mm_gemm(int m, const double* A, bool trA, const double* B, bool trB,
 void make_A0(int m, const double* Hp, const double* HD, double* A0,
              cudaStream_t s);
 // The line step along P and the factor of the new overlap: the line-model
-// terms from H' (diag zeroed), H_D, B = C^T P, Q = P^T P, P^T H P and
-// W = P^T G give alpha (into sc); then S = I + a (B + B^T) + a^2 Q is
-// factorised (in deviation form when dev) into Linv (may be null) and R = L^{-T}.
+// terms from H' (diag zeroed), H_D, B = C^T P, Q = P^T P, the diagonal of
+// P^T H P (hpd[j * hpd_stride], FP64: a vector of column dots, or the
+// diagonal of the matrix with stride m + 1) and W = P^T G give alpha (into
+// sc); then S = I + a (B + B^T) + a^2 Q is factorised (in deviation form
+// when dev) into Linv (may be null) and R = L^{-T}.
 // part: >= 16 * ceil(m/32)^2 doubles; gwork: max(2 m^2, chol_work_elems(m))
 // doubles (FP32 factorisations keep FP32 copies of B and Q there).
 template <typename Tm>
 void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
-                 const double* Q, const double* HPP, const double* W,
-                 double* Linv, double* R, IterScalars* sc, double* gwork,
-                 double* part, bool dev, cudaStream_t s);
+                 const double* Q, const double* hpd, int hpd_stride,
+                 const double* W, double* Linv, double* R, IterScalars* sc,
+                 double* gwork, double* part, bool dev, cudaStream_t s);
 // line_factor<float> with the m x m inputs given in FP32 (Gram copies)
 void line_factor32(int m, const float* Hp, const double* HD, const float* Bm,
-                   const float* Q, const float* HPP, const float* W,
-                   double* Linv, double* R, IterScalars* sc, double* gwork,
-                   double* part, cudaStream_t s);
+                   const float* Q, const double* hpd, int hpd_stride,
+                   const float* W, double* Linv, double* R, IterScalars* sc,
+                   double* gwork, double* part, cudaStream_t s);
 // Elements (of the arithmetic type) of the factorisation workspace gwork.
 size_t chol_work_elems(int m);
 // S = L L^T (lower); writes Linv = L^{-1} (unless null) and R = L^{-T}. Non-PD sets

@@ -486,6 +486,297 @@ __global__ void __launch_bounds__(chol_threads<Tm>(), 1)
 }
 
 // ---------------------------------------------------------------------------
+// Blocked Cholesky S = L L^T and L^{-1} on many CTAs, for large m (Fig. ONFIG
+// steps (2), (3)): the same arithmetic as k_chol_inv, spread over launches.
+// The padded working copy W (mp x mp, leading dimension mp, lower triangle)
+// is factorised right-looking over 32-column panels: per panel p, one CTA
+// factors the diagonal block and inverts it (k_cb_diag); then every lower
+// tile (I, J) of the trailing matrix, on its own CTA, solves its two panel
+// blocks against the diagonal block's inverse, L_Ip = A_Ip X_pp^T, and
+// subtracts L_Ip L_Jp^T (k_cb_update); the diagonal tile's CTA stores L_Ip.
+// L^{-1} = X follows by recursive doubling: for a diagonal block split as
+// [A 0; B C], its inverse is [A^{-1} 0; -C^{-1} B A^{-1}  C^{-1}], so with the
+// 32 x 32 inverses from k_cb_diag, levels of block size 32, 64, ... each form
+// T = B A^{-1}, then X_CA = -C^{-1} T, for all blocks of the level at once
+// (k_cb_inv). Deviation form (dev) as in k_chol_inv: W holds S - I, L = I + F
+// and X = I + Y with the identities implicit, so FP32 arithmetic keeps L to
+// FP64 accuracy relative to I when S is close to I.
+// ---------------------------------------------------------------------------
+constexpr int CB = 32;
+
+// The line step alpha from the line-term partials (one CTA).
+__global__ void k_cb_alpha(int m, const double* __restrict__ lpart, int nlpart,
+                           IterScalars* sc) {
+  __shared__ double lred[4 * 32];
+  line_alpha_block(m, lpart, nlpart, sc, lred);
+}
+
+// W <- lower triangle of S, or of S(a) = I + a (B + B^T) + a^2 Q (Q
+// symmetric), minus I in deviation form; the padding is the identity (zero
+// in deviation form). Clears the failure flag.
+template <typename Tm, bool dev>
+__global__ void k_cb_form(int m, int mp, const double* __restrict__ S,
+                          const double* __restrict__ Bm,
+                          const double* __restrict__ Q,
+                          const float* __restrict__ Bf,
+                          const float* __restrict__ Qf,
+                          const IterScalars* __restrict__ sc, Tm* __restrict__ W,
+                          int* bad) {
+  const int64_t total = (int64_t)mp * mp;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *bad = 0;
+  const double al = (Bm || Bf) ? sc->alpha : 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % mp), k = (int)(e / mp);
+    if (i < k) continue;  // the upper triangle is never read
+    double v;
+    if (i < m && k < m) {
+      // a (B + B^T) + a^2 (Q + Q^T) / 2, as k_chol_inv forms it
+      if (Bf)
+        v = (double)((float)al * (Bf[i + k * m] + Bf[k + i * m]) +
+                     (float)(0.5 * al * al) * (Qf[i + k * m] + Qf[k + i * m]));
+      else if (Bm)
+        v = al * (Bm[i + (int64_t)k * m] + Bm[k + (int64_t)i * m]) +
+            0.5 * al * al * (Q[i + (int64_t)k * m] + Q[k + (int64_t)i * m]);
+      else
+        v = S[i + (int64_t)k * m] - (dev && i == k ? 1.0 : 0.0);
+      if ((Bm || Bf) && !dev && i == k) v += 1.0;
+    } else {
+      v = (!dev && i == k) ? 1.0 : 0.0;
+    }
+    W[e] = (Tm)v;
+  }
+}
+
+// Factor and invert the 32 x 32 diagonal block of panel p (one CTA of 256
+// threads; the column steps of k_chol_inv's phase (a), the substitution of
+// its phase (d)). Writes the block of L (F in deviation form; zeros above
+// the diagonal) and of X = L^{-1} (Y in deviation form).
+template <typename Tm, bool dev>
+__global__ void __launch_bounds__(256, 1)
+    k_cb_diag(int m, int mp, int p, const double* __restrict__ S,
+              bool from_S, const Tm* __restrict__ W, Tm* __restrict__ L,
+              Tm* __restrict__ X, int* bad) {
+  __shared__ Tm colbuf[2][32];
+  __shared__ Tm B[32][33];
+  __shared__ Tm rd[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = CB * p, r = c0 + lane;
+  const Tm eps = sizeof(Tm) == 4 ? (Tm)1.2e-7 : (Tm)2.3e-16;
+  Tm v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = W[r + (size_t)(c0 + warp + 8 * q) * mp];
+  bool b = false;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    const int q = c >> 3;
+    if (warp == (c & 7)) {
+      Tm d = __shfl_sync(0xffffffffu, v[q], c);
+      Tm rl;
+      if (dev) {
+        if (!(d > (Tm)-0.999)) {  // pivot 1 + d not positive: singular S
+          b = true;
+          d = (Tm)0;
+        }
+        rl = piv_rsqrt((Tm)1 + d);
+      } else {
+        const int cc = c0 + c;
+        const double sjj =
+            (!from_S || cc >= m) ? 1.0 : fabs(S[cc + (int64_t)cc * m]);
+        if (!(d > (Tm)(4 * m) * eps * (Tm)sjj)) {
+          b = true;
+          d = (Tm)1;
+        }
+        rl = piv_rsqrt(d);
+      }
+      if (lane > c) v[q] *= rl;
+      colbuf[c & 1][lane] = v[q];
+      if (lane == 0) rd[c] = rl;
+      if (lane == c)
+        v[q] = dev ? d * piv_rcp((Tm)1 + ((Tm)1 + d) * rl) : d * rl;
+    }
+    __syncthreads();
+    const Tm lrc = colbuf[c & 1][lane];
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq)
+      if (warp + 8 * qq > c) v[qq] -= lrc * colbuf[c & 1][warp + 8 * qq];
+  }
+  // the block of L (lower, zeros above) to global and to shared memory
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = warp + 8 * q;
+    const Tm x = lane >= c ? v[q] : (Tm)0;
+    L[r + (size_t)(c0 + c) * mp] = x;
+    B[lane][c] = x;
+  }
+  if (lane == 0 && b) atomicOr(bad, 1);
+  __syncthreads();
+  // inverse of the block, in place in B by forward substitution, one warp,
+  // lane j owns column j (as phase (d) of k_chol_inv)
+  if (warp == 0) {
+    const int j = lane;
+    for (int i = 0; i < 32; ++i) {
+      Tm s0 = (dev && i > j) ? B[i][j] : (Tm)0, s1 = 0;
+      int k = j;
+      for (; k + 1 < i; k += 2) {
+        s0 += B[i][k] * B[k][j];
+        s1 += B[i][k + 1] * B[k + 1][j];
+      }
+      if (k < i) s0 += B[i][k] * B[k][j];
+      Tm x = 0;
+      if (i == j) x = dev ? -B[i][i] * rd[i] : rd[i];
+      else if (i > j) x = -(s0 + s1) * rd[i];
+      __syncwarp();
+      if (i >= j) B[i][j] = x;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 32 * 32; e += 256) {
+    const int i = e & 31, j = e >> 5;
+    X[(c0 + i) + (size_t)(c0 + j) * mp] = i >= j ? B[i][j] : (Tm)0;
+  }
+}
+
+// Trailing update of panel p: CTA t takes the lower tile (I, J), p < J <= I,
+// of the trailing matrix. L_I = A_I X_pp^T (deviation form: A_I + A_I Y_pp^T)
+// for the panel blocks of rows I and J, then W_IJ -= L_I L_J^T; the CTA of
+// the diagonal tile writes L_I into L.
+template <typename Tm, bool dev>
+__global__ void __launch_bounds__(256)
+    k_cb_update(int mp, int p, Tm* __restrict__ W, Tm* __restrict__ L,
+                const Tm* __restrict__ X) {
+  __shared__ Tm Xp[32][33], AI[32][33], AJ[32][33], LI[32][33], LJ[32][33];
+  const int tid = threadIdx.x;
+  const int P = mp / CB;
+  // tile t -> (I, J), J <= I, counted over rows I = p + 1 .. P - 1
+  const int t = blockIdx.x;
+  int a = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while ((a + 1) * (a + 2) / 2 <= t) ++a;
+  while (a * (a + 1) / 2 > t) --a;
+  const int I = p + 1 + a, J = p + 1 + (t - a * (a + 1) / 2);
+  if (I >= P) return;
+  const int c0 = CB * p, i0 = CB * I, j0 = CB * J;
+  for (int e = tid; e < 32 * 32; e += 256) {
+    const int i = e & 31, k = e >> 5;
+    Xp[i][k] = X[(c0 + i) + (size_t)(c0 + k) * mp];
+    AI[i][k] = W[(i0 + i) + (size_t)(c0 + k) * mp];
+    AJ[i][k] = W[(j0 + i) + (size_t)(c0 + k) * mp];
+  }
+  __syncthreads();
+  const int r = tid & 31, cb = (tid >> 5) * 4;
+  // L_I (and L_J) rows: L[r][c] = sum_{k <= c} A[r][k] X[c][k] (+ A[r][c])
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = cb + u;
+    Tm sI = dev ? AI[r][c] : (Tm)0, sJ = dev ? AJ[r][c] : (Tm)0;
+    for (int k = 0; k <= c; ++k) {
+      sI += AI[r][k] * Xp[c][k];
+      sJ += AJ[r][k] * Xp[c][k];
+    }
+    LI[r][c] = sI;
+    LJ[r][c] = sJ;
+  }
+  __syncthreads();
+  if (I == J)
+    for (int e = tid; e < 32 * 32; e += 256) {
+      const int i = e & 31, k = e >> 5;
+      L[(i0 + i) + (size_t)(c0 + k) * mp] = LI[i][k];
+    }
+  // W_IJ -= L_I L_J^T: thread (r, cb..cb+3)
+  Tm acc[4] = {0, 0, 0, 0};
+#pragma unroll 8
+  for (int k = 0; k < 32; ++k) {
+    const Tm li = LI[r][k];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] += li * LJ[cb + u][k];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const size_t o = (i0 + r) + (size_t)(j0 + cb + u) * mp;
+    W[o] -= acc[u];
+  }
+}
+
+// One level of the recursive inverse, block size s: pair q has A = rows and
+// columns [2 q s, 2 q s + s) and C = [2 q s + s, 2 q s + 2 s) (cut at mp);
+// phase 0: T_CA = L_CA X_A (deviation form: F_CA + F_CA Y_A), phase 1:
+// X_CA = -X_C T_CA (deviation form: -(T + Y_C T)). One CTA per 32 x 32 tile
+// of C x A (blockIdx.y), pairs along blockIdx.x.
+template <typename Tm, bool dev>
+__global__ void __launch_bounds__(256)
+    k_cb_inv(int mp, int s, int phase, const Tm* __restrict__ L,
+             Tm* __restrict__ X, Tm* __restrict__ T) {
+  __shared__ Tm Ls[32][33], Rs[32][33];
+  const int tid = threadIdx.x;
+  const int a0 = 2 * s * blockIdx.x, c0 = a0 + s;
+  if (c0 >= mp) return;
+  const int nc = min(s, mp - c0);           // rows of C (multiple of 32)
+  const int tiles_a = s / CB;
+  const int ti = blockIdx.y / tiles_a, tj = blockIdx.y % tiles_a;
+  if (CB * ti >= nc) return;
+  const int gi = c0 + CB * ti, gj = a0 + CB * tj;  // output tile origin
+  const int r = tid & 31, cb = (tid >> 5) * 4;
+  Tm acc[4] = {0, 0, 0, 0};
+  // phase 0: sum over k in A of L[gi.., k] X[k, gj..] (X_A lower: k >= gj)
+  // phase 1: sum over k in C of X[gi.., k] T[k, gj..] (X_C lower: k <= gi+31)
+  const int kb = phase == 0 ? gj : c0;
+  const int ke = phase == 0 ? a0 + s : gi + CB;
+  for (int k0 = kb; k0 < ke; k0 += CB) {
+    for (int e = tid; e < 32 * 32; e += 256) {
+      const int i = e & 31, k = e >> 5;
+      if (phase == 0) {
+        Ls[i][k] = L[(gi + i) + (size_t)(k0 + k) * mp];
+        Rs[k][i] = X[(k0 + k) + (size_t)(gj + i) * mp];   // Rs[k][col]
+      } else {
+        Ls[i][k] = X[(gi + i) + (size_t)(k0 + k) * mp];
+        Rs[k][i] = T[(k0 + k) + (size_t)(gj + i) * mp];
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const Tm l = Ls[r][k];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += l * Rs[k][cb + u];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const size_t o = (gi + r) + (size_t)(gj + cb + u) * mp;
+    if (phase == 0)
+      T[o] = acc[u] + (dev ? L[o] : (Tm)0);
+    else
+      X[o] = -(acc[u] + (dev ? T[o] : (Tm)0));
+  }
+}
+
+// R = L^{-T} (upper) and Linv = L^{-1} (lower) in FP64 from X; identities
+// and status bit 1 when a pivot failed.
+template <typename Tm, bool dev>
+__global__ void k_cb_out(int m, int mp, const Tm* __restrict__ X,
+                         double* __restrict__ Linv, double* __restrict__ R,
+                         const int* bad, IterScalars* sc) {
+  const int isbad = *bad;
+  const int64_t total = (int64_t)m * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), k = (int)(e / m);  // Linv(i, k) = R(k, i)
+    double v = 0.0;
+    if (isbad) {
+      if (i == k) v = 1.0;
+    } else if (i >= k) {
+      v = (double)X[i + (size_t)k * mp];
+      if (dev && i == k) v += 1.0;
+    }
+    if (Linv) Linv[e] = v;
+    R[k + (int64_t)i * m] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && isbad && sc) sc->status |= 1;
+}
+
+// ---------------------------------------------------------------------------
 // Line-model terms over 32 x 32 tiles of the (i, j) index space, one CTA of
 // 1024 threads per tile, partial sums to part[tile * 4 + q]:
 //   q = 0: tr(D1) = -tr(W)
@@ -501,8 +792,9 @@ template <typename Tm, typename Tin>
 __global__ void __launch_bounds__(1024)
     k_line_terms(int m, const Tin* __restrict__ Hp,
                  const double* __restrict__ HD, const Tin* __restrict__ Bm,
-                 const Tin* __restrict__ Q, const Tin* __restrict__ HPP,
-                 const Tin* __restrict__ W, double* __restrict__ part,
+                 const Tin* __restrict__ Q, const double* __restrict__ hpd,
+                 int hpd_stride, const Tin* __restrict__ W,
+                 double* __restrict__ part,
                  float* __restrict__ Bf, float* __restrict__ Qf) {
   __shared__ Tm t0[32][33], t1[32][33], t2[32][33], t3[32][33];
   __shared__ double red[4 * 32];
@@ -546,7 +838,7 @@ __global__ void __launch_bounds__(1024)
       v1 = -qij * a0;
       if (i == j) {
         v0 = -wij;
-        v1 += (Tm)HPP[e];
+        v1 += (Tm)hpd[(size_t)i * hpd_stride];
         v3 = (Tm)Q[e];
       }
     }
@@ -796,10 +1088,57 @@ void make_A0(int m, const double* Hp, const double* HD, double* A0,
 }
 
 
-// elements of the padded working copy plus the inverse's temporary
+// From this m on the factorisation runs blocked on many CTAs.
+constexpr int kCholBlockedFrom = 256;
+
+// elements of the padded working copy plus the inverse's temporary (one
+// CTA), or of W, L, X, T and the failure flag (blocked)
 size_t chol_work_elems(int m) {
   const size_t mp = (size_t)((m + 31) & ~31);
+  if (m >= kCholBlockedFrom) return 4 * mp * mp + 8;
   return mp * (mp + 1) + 33 * mp;
+}
+
+template <typename Tm, bool dev>
+static void chol_blocked(int m, const double* S, const double* Bm,
+                         const double* Q, const float* Bf, const float* Qf,
+                         double* Linv, double* R, IterScalars* sc,
+                         double* gwork, cudaStream_t s, const double* lpart,
+                         int nlpart) {
+  const int mp = (m + 31) & ~31, P = mp / CB;
+  const size_t mp2 = (size_t)mp * mp;
+  Tm* W = reinterpret_cast<Tm*>(gwork);
+  Tm* L = W + mp2;
+  Tm* X = L + mp2;
+  Tm* T = X + mp2;
+  int* bad = reinterpret_cast<int*>(T + mp2);
+  if (lpart) {
+    k_cb_alpha<<<1, 256, 0, s>>>(m, lpart, nlpart, sc);
+    TRM_CHECK_LAUNCH();
+  }
+  const int fb = (int)std::min<size_t>(ceil_div(mp2, (size_t)256), 1024);
+  k_cb_form<Tm, dev><<<fb, 256, 0, s>>>(m, mp, S, Bm, Q, Bf, Qf, sc, W, bad);
+  TRM_CHECK_LAUNCH();
+  const bool from_S = S != nullptr && !Bm && !Bf;
+  for (int p = 0; p < P; ++p) {
+    k_cb_diag<Tm, dev><<<1, 256, 0, s>>>(m, mp, p, S, from_S, W, L, X, bad);
+    TRM_CHECK_LAUNCH();
+    const int t = P - p - 1;
+    if (t > 0) {
+      k_cb_update<Tm, dev><<<t * (t + 1) / 2, 256, 0, s>>>(mp, p, W, L, X);
+      TRM_CHECK_LAUNCH();
+    }
+  }
+  for (int sz = CB; sz < mp; sz *= 2) {
+    const dim3 g(ceil_div(mp, 2 * sz), (sz / CB) * (sz / CB));
+    k_cb_inv<Tm, dev><<<g, 256, 0, s>>>(mp, sz, 0, L, X, T);
+    TRM_CHECK_LAUNCH();
+    k_cb_inv<Tm, dev><<<g, 256, 0, s>>>(mp, sz, 1, L, X, T);
+    TRM_CHECK_LAUNCH();
+  }
+  const int ob = (int)std::min<size_t>(ceil_div((size_t)m * m, (size_t)256), 1024);
+  k_cb_out<Tm, dev><<<ob, 256, 0, s>>>(m, mp, X, Linv, R, bad, sc);
+  TRM_CHECK_LAUNCH();
 }
 
 template <typename Tm, bool dev>
@@ -809,6 +1148,11 @@ static void chol_launch(int m, const double* S, const double* Bm,
                         double* gwork, cudaStream_t s,
                         const double* lpart = nullptr, int nlpart = 0) {
   if (m > 1024) throw Error(-1, "chol_inv: m > 1024");
+  if (m >= kCholBlockedFrom) {
+    chol_blocked<Tm, dev>(m, S, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s, lpart,
+                          nlpart);
+    return;
+  }
   const size_t bytes = chol_work_elems(m) * sizeof(Tm);
   const bool smem = bytes <= 200 * 1024;
   if (smem) {
@@ -856,9 +1200,9 @@ static int line_ksplit(int m) {
 
 template <typename Tm>
 void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
-                 const double* Q, const double* HPP, const double* W,
-                 double* Linv, double* R, IterScalars* sc, double* gwork,
-                 double* part, bool dev, cudaStream_t s) {
+                 const double* Q, const double* hpd, int hpd_stride,
+                 const double* W, double* Linv, double* R, IterScalars* sc,
+                 double* gwork, double* part, bool dev, cudaStream_t s) {
   const int t = ceil_div(m, 32);
   const int ksplit = line_ksplit(m);
   // FP32 factorisations take B and Q as FP32 copies written by the line
@@ -871,7 +1215,7 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
     Qf = Bf + (size_t)m * m;
   }
   k_line_terms<Tm, double><<<dim3(t, t, ksplit), 1024, 0, s>>>(
-      m, Hp, HD, Bm, Q, HPP, W, part, Bf, Qf);
+      m, Hp, HD, Bm, Q, hpd, hpd_stride, W, part, Bf, Qf);
   TRM_CHECK_LAUNCH();
   // the factorisation kernel takes the line step from the partials first
   if (dev)
@@ -885,13 +1229,13 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
 // The FP32 path with the m x m inputs already in FP32 (copies the Gram sums
 // write): no FP64 conversion in the line terms or the factorisation.
 void line_factor32(int m, const float* Hp, const double* HD, const float* Bm,
-                   const float* Q, const float* HPP, const float* W,
-                   double* Linv, double* R, IterScalars* sc, double* gwork,
-                   double* part, cudaStream_t s) {
+                   const float* Q, const double* hpd, int hpd_stride,
+                   const float* W, double* Linv, double* R, IterScalars* sc,
+                   double* gwork, double* part, cudaStream_t s) {
   const int t = ceil_div(m, 32);
   const int ksplit = line_ksplit(m);
   k_line_terms<float, float><<<dim3(t, t, ksplit), 1024, 0, s>>>(
-      m, Hp, HD, Bm, Q, HPP, W, part, nullptr, nullptr);
+      m, Hp, HD, Bm, Q, hpd, hpd_stride, W, part, nullptr, nullptr);
   TRM_CHECK_LAUNCH();
   chol_launch<float, true>(m, nullptr, nullptr, nullptr, Bm, Q, Linv, R, sc,
                            gwork, s, part, t * t * ksplit);
@@ -903,11 +1247,12 @@ template void chol_inv_dev<double>(int, const double*, double*, double*,
                                    IterScalars*, double*, cudaStream_t);
 template void line_factor<float>(int, const double*, const double*,
                                  const double*, const double*, const double*,
-                                 const double*, double*, double*, IterScalars*,
-                                 double*, double*, bool, cudaStream_t);
+                                 int, const double*, double*, double*,
+                                 IterScalars*, double*, double*, bool,
+                                 cudaStream_t);
 template void line_factor<double>(int, const double*, const double*,
                                   const double*, const double*, const double*,
-                                  const double*, double*, double*,
+                                  int, const double*, double*, double*,
                                   IterScalars*, double*, double*, bool,
                                   cudaStream_t);
 

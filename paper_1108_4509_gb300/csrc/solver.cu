@@ -77,7 +77,8 @@ long long thread_launch_count() { return t_launches; }
 
 const char* const kClassNames[KC_COUNT] = {
     "spmm_f32", "spmm_f64", "gram_f32", "gram_f64", "grad_f32", "grad_f64",
-    "rotate_f32", "rotate_f64", "rowops", "small_mm", "eig"};
+    "rotate_f32", "rotate_f64", "rowops", "small_mm", "eig", "spmm_df",
+    "rotate_df"};
 
 Profiler::~Profiler() {
   for (auto& r : pending_) {
@@ -238,7 +239,7 @@ size_t Solver::part_capacity(int64_t N, int m) {
 size_t Solver::footprint(int64_t N, int m) {
   const size_t nm = (size_t)N * m, mm = (size_t)m * m;
   size_t b = nm * (3 * 8 + 3 * 4 + 3 * 8 + 4 * 8);  // blocks
-  b += mm * 8 * 13 + std::max(2 * mm, chol_work_elems(m)) * 8 + 4 * m * 8;
+  b += mm * 8 * 13 + std::max(2 * mm, chol_work_elems(m)) * 8 + 5 * m * 8;
   b += sym_eig_work_doubles(m) * 8 + 5 * mm * 4;
   b += part_capacity(N, m) * 8 + sizeof(IterScalars) + 16;
   b += mul_tc_work_floats(m, m) * 4;
@@ -270,9 +271,10 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   for (void* p : {Gb_[0], Gb_[1], Pb_, HPb_})
     TRM_CUDA(cudaMemsetAsync(p, 0, nm * 8, s_));
   HD_ = d(m);
+  hpd_ = d(m);
   Hp_ = d(mm);
   A0_ = d(mm);
-  Bm_ = d(4 * mm);  // C^T P, then P^T [P HP G] (one m x 4m result)
+  Bm_ = d(4 * mm);  // C^T P, then P^T [P HP G] (unfused) or P^T [P G] (fused)
   PG_ = Bm_ + mm;
   // (also the line terms' partials: 4 doubles per CTA, at most
   // 4 * 4 ceil(m/32)^2 + 256 doubles, more than m^2 when m is small)
@@ -500,29 +502,45 @@ void Solver::read_scalars(IterScalars* out) {
 // One iteration with every block in precision T and the m x m line model and
 // factorisation in Tm (full DP: double/double; full SP: float/float).
 // ---------------------------------------------------------------------------
-// The line-search Grams C^T P and P^T [P HP G] as one tensor-core launch
-// [C P P P]^T [P P HP G] (one m x 4m result: Bm_, then PG_), when the FP32
-// blocks are eligible; false means the caller forms them separately.
+// The line-search Grams C^T P, P^T P and P^T G as one tensor-core launch
+// [C P P]^T [P P G] (one m x 3m result: Bm_, then PG_ = [P^T P, P^T G]).
+// P^T P is symmetric, so only its tiles on and above the diagonal are
+// computed and the rest are mirrored (the blocked symmetric product of
+// Sec. 2.1, Fig. DIVFIG); of P^T H P the line model needs only the
+// diagonal, which the stencil applied to P delivers as column dots, so HP
+// is not read here at all.
+// ---------------------------------------------------------------------------
 template <typename T>
-bool Solver::line_grams_fused(const T* C, const T* P, const T* HP,
-                              const T* G) {
+bool Solver::line_grams_fusable(const T* C, const T* P, const T* G) const {
   if constexpr (sizeof(T) != 4) {
     return false;
   } else {
     Blocks<float> a, b;
     a.p[0] = C;
-    a.p[1] = a.p[2] = a.p[3] = P;
+    a.p[1] = a.p[2] = P;
     b.p[0] = b.p[1] = P;
-    b.p[2] = HP;
-    b.p[3] = G;
+    b.p[2] = G;
     a.cols = b.cols = m_;
-    a.count = b.count = 4;
-    if (!gram_tc_pairs_eligible(N_, m_, a, b)) return false;
+    a.count = b.count = 3;
+    return gram_tc_pairs_eligible(N_, m_, a, b);
+  }
+}
+
+template <typename T>
+void Solver::line_grams_fused(const T* C, const T* P, const T* G) {
+  if constexpr (sizeof(T) == 4) {
+    Blocks<float> a, b;
+    a.p[0] = C;
+    a.p[1] = a.p[2] = P;
+    b.p[0] = b.p[1] = P;
+    b.p[2] = G;
+    a.cols = b.cols = m_;
+    a.count = b.count = 3;
     const double nm = (double)N_ * m_, m2N = nm * m_;
-    TRM_PROF(KC_GRAM32, 8 * m2N, 16 * nm,
+    // algorithmic: 2 m^2 N per product, m^2 N for the symmetric one
+    TRM_PROF(KC_GRAM32, 5 * m2N, 12 * nm,
              gram_tc_pairs(N_, m_, a, b, Bm_, part_, part_cap_, &sc_->status,
-                           s_, Bm32_));
-    return true;
+                           s_, Bm32_, /*sym_seg=*/1));
   }
 }
 
@@ -586,13 +604,33 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
                        part_cap_, s_, &tw_));                         // (7)
   TRM_PROF(KC_ROWOPS, 2 * nm, 3 * es * nm,
            update_p<T>(N_, m_, G, P, minv, sc_, s_));                 // P
-  TRM_PROF(ksp, sfl, sby, apply_h(op_, P, HP, m_, s_));              // H P
+  const bool fused = !gen && line_grams_fusable<T>(C, P, G);
+  bool hp_dots = false;
+  if constexpr (sizeof(T) == 4) {
+    if (fused) {  // H P with the diagonal of P^T H P as column dots
+      int chunks = 0;
+      TRM_PROF(ksp, sfl, sby, chunks = apply_h_dots(op_, P, HP, m_, part_, s_));
+      TRM_PROF(KC_ROWOPS, 2.0 * m_ * chunks, 8.0 * m_ * chunks,
+               energy_from_dots(part_, chunks, m_, hpd_, nullptr, s_));
+      hp_dots = true;
+    }
+  }
+  if (!hp_dots) TRM_PROF(ksp, sfl, sby, apply_h(op_, P, HP, m_, s_));  // H P
   if (gen) {
     double ffl, fby;
     spmm_cost(sop_, m_, 8, &ffl, &fby);
     TRM_PROF(ksp, ffl, fby, apply_h(sop_, P, SPt, m_, s_));          // S P
   }
-  if (gen || !line_grams_fused<T>(C, P, HP, G)) {
+  // where the diagonal of P^T H P and W = P^T G land
+  const double* hpd = hpd_;
+  int hstride = 1;
+  size_t woff = mm;
+  if (fused) {
+    line_grams_fused<T>(C, P, G);
+  } else {
+    hpd = PG_ + mm;
+    hstride = m_ + 1;
+    woff = 2 * mm;
     Blocks<T> bp;
     bp.p[0] = P;
     bp.cols = m_;
@@ -613,10 +651,10 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   const double m3 = md * md * md;
   prof.begin(KC_SMALL, s_);
   if constexpr (sizeof(T) == 4 && sizeof(Tm) == 4)
-    line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, PG32_ + mm, PG32_ + 2 * mm,
+    line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, hpd, hstride, PG32_ + woff,
                   nullptr, R_, sc_, mmw_, T1_, s_);  // alpha, Fig. ONFIG
   else
-    line_factor<Tm>(m_, Hp_, HD_, Bm_, PG_, PG_ + mm, PG_ + 2 * mm, nullptr,
+    line_factor<Tm>(m_, Hp_, HD_, Bm_, PG_, hpd, hstride, PG_ + woff, nullptr,
                     R_, sc_, mmw_, T1_, sizeof(Tm) == 4, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(krt, m2N, 3 * es * nm,
@@ -658,7 +696,7 @@ void Solver::iter_mp2() {
   double f64, b64, f32, b32;
   spmm_cost(op_, m_, 8, &f64, &b64);
   spmm_cost(op_, m_, 4, &f32, &b32);
-  TRM_PROF(KC_SPMM64, f64, b64, apply_h_df(op_, Ch, Cl, Xh, Xl, m_, s_));  // (1)
+  TRM_PROF(KC_SPMMDF, f64, b64, apply_h_df(op_, Ch, Cl, Xh, Xl, m_, s_));  // (1)
   TRM_PROF(KC_ROWOPS, 2 * dnm, 16 * dnm,
            energy_diag_df(N_, m_, Ch, Cl, Xh, Xl, HD_, sc_, part_, s_));  // (2), (3)
   TRM_PROF(KC_ROWOPS, 2 * dnm, 20 * dnm,
@@ -676,8 +714,22 @@ void Solver::iter_mp2() {
                            part_, part_cap_, s_, &tw_));      // (7)
   TRM_PROF(KC_ROWOPS, 2 * dnm, 12 * dnm,
            update_p<float>(N_, m_, G, P, minv, sc_, s_));
-  TRM_PROF(KC_SPMM32, f32, b32, apply_h(op_, P, HP, m_, s_));
-  if (!line_grams_fused<float>(Ch, P, HP, G)) {
+  const bool fused = line_grams_fusable<float>(Ch, P, G);
+  const double* hpd = hpd_;
+  int hstride = 1;
+  size_t woff = mm;
+  if (fused) {  // H P with the diagonal of P^T H P as column dots
+    int chunks = 0;
+    TRM_PROF(KC_SPMM32, f32, b32,
+             chunks = apply_h_dots(op_, P, HP, m_, part_, s_));
+    TRM_PROF(KC_ROWOPS, 2.0 * m_ * chunks, 8.0 * m_ * chunks,
+             energy_from_dots(part_, chunks, m_, hpd_, nullptr, s_));
+    line_grams_fused<float>(Ch, P, G);
+  } else {
+    TRM_PROF(KC_SPMM32, f32, b32, apply_h(op_, P, HP, m_, s_));
+    hpd = PG_ + mm;
+    hstride = m_ + 1;
+    woff = 2 * mm;
     Blocks<float> bp;
     bp.p[0] = P;
     bp.cols = m_;
@@ -696,10 +748,10 @@ void Solver::iter_mp2() {
                          &sc_->status, PG32_));
   }
   prof.begin(KC_SMALL, s_);
-  line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, PG32_ + mm, PG32_ + 2 * mm,
+  line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, hpd, hstride, PG32_ + woff,
                 nullptr, R_, sc_, mmw_, T1_, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
-  TRM_PROF(KC_ROT32, m2N, 24 * dnm,
+  TRM_PROF(KC_ROTDF, m2N, 24 * dnm,
            rotate_split_df(N_, m_, Ch, Cl, P, R_, Cdfn_, Cdfn_ + nm, sc_, s_,
                            &tw_));
   std::swap(Cdf_, Cdfn_);

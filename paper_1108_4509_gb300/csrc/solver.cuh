@@ -11,9 +11,13 @@ namespace trm {
 // Per-class timing of the library's launches with CUDA events on the solver's
 // stream, plus the algorithmic flops and bytes of each launch, for roofline
 // reporting. Off unless enabled; event pairs are resolved after a solve.
+// Each class is one kernel family, so that a kernel's DRAM counters apply
+// to its class alone: spmm_df and rotate_df are MP2's double-float H C and
+// split rotation, apart from the FP64 and FP32 launches of the same steps.
 enum KClass {
   KC_SPMM32, KC_SPMM64, KC_GRAM32, KC_GRAM64, KC_GRAD32, KC_GRAD64,
-  KC_ROT32, KC_ROT64, KC_ROWOPS, KC_SMALL, KC_EIG, KC_COUNT
+  KC_ROT32, KC_ROT64, KC_ROWOPS, KC_SMALL, KC_EIG, KC_SPMMDF, KC_ROTDF,
+  KC_COUNT
 };
 extern const char* const kClassNames[KC_COUNT];
 
@@ -122,8 +126,14 @@ class Solver {
   void iter_mp2();
   void gram64(const double* A, const Blocks<double>& b, double* out);
   void mult64(const double* A, const double* M, double* Y);
+  // The line-search Grams as one tensor-core launch [C P P]^T [P P G]
+  // (C^T P, P^T P upper tiles mirrored, P^T G), with the diagonal of
+  // P^T H P taken as column dots of the stencil applied to P (hpd_), when
+  // the FP32 blocks are eligible.
   template <typename T>
-  bool line_grams_fused(const T* C, const T* P, const T* HP, const T* G);
+  bool line_grams_fusable(const T* C, const T* P, const T* G) const;
+  template <typename T>
+  void line_grams_fused(const T* C, const T* P, const T* G);
   // CUDA graphs of block iterations. An iteration is a fixed kernel
   // sequence given the phase and the block pointers it swaps, so a graph is
   // keyed by both and remembers the pointers it leaves behind. The first
@@ -173,7 +183,7 @@ class Solver {
   float *Cdf_ = nullptr, *Cdfn_ = nullptr, *Xdf_ = nullptr;  // FP32 pairs
   void *Gb_[2] = {nullptr, nullptr}, *Pb_ = nullptr, *HPb_ = nullptr;
   // m x m (FP64)
-  double *HD_, *Hp_, *A0_, *Bm_, *PG_, *T1_, *T2_, *S_, *Linv_, *R_, *mmw_,
+  double *HD_, *hpd_, *Hp_, *A0_, *Bm_, *PG_, *T1_, *T2_, *S_, *Linv_, *R_, *mmw_,
       *eigws_,
       *eigw_, *Z_, *lam_, *res_;
   int* info_;

@@ -204,8 +204,10 @@ def test_gram_f32_misaligned_a_falls_back(trm):
 # ---------------------------------------------------------------------------
 # a7: Fig. ONFIG
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("N,m", [(3001, 37), (500, 1), (4096, 130)])
+@pytest.mark.parametrize("N,m", [(3001, 37), (500, 1), (4096, 130),
+                                 (4096, 256), (3000, 300), (2100, 544)])
 def test_orthonormalize(trm, N, m):
+    """m >= 256 runs the blocked factorisation on many CTAs."""
     C = ti.random_block(N, m, seed=3)
     ref = otrm.orthonormalize(C)
     t = gu.to_dev(C)
@@ -216,10 +218,13 @@ def test_orthonormalize(trm, N, m):
     assert np.max(np.abs(got - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
 
 
-def test_orthonormalize_rank_deficient_reports_enotpd(trm):
-    N, m = 200, 4
+@pytest.mark.parametrize("N,m", [(200, 4), (1000, 300)])
+def test_orthonormalize_rank_deficient_reports_enotpd(trm, N, m):
     C = ti.random_block(N, m, seed=3)
-    C[:, 3] = C[:, 1]            # exactly dependent columns
+    if m > 32:
+        C[:, m - 5] = C[:, 100]  # dependent columns, pivot in a late panel
+    else:
+        C[:, 3] = C[:, 1]        # exactly dependent columns
     t = gu.to_dev(C)
     with pytest.raises(trm.TrmError) as e:
         trm.trm_orthonormalize(N, m, t.data_ptr(), gu.stream())
