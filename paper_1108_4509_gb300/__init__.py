@@ -27,7 +27,7 @@ __all__ = [
     "trm_orthonormalize", "trm_extrapolate", "trm_set_block",
     "trm_get_block", "trm_iterate", "trm_rayleigh_ritz", "trm_random_block",
     "trm_profile", "trm_profile_read", "trm_launch_count", "trm_kernel_stats",
-    "Solver",
+    "trm_slab", "trm_slab_plan", "Solver",
 ]
 
 TRM_FP64, TRM_MP1, TRM_MP2, TRM_FULL_SP, TRM_MIXED = 0, 1, 2, 3, 4
@@ -69,6 +69,13 @@ class trm_kernel_stats(ct.Structure):
     _fields_ = [("name", ct.c_char * 16), ("ms", ct.c_double),
                 ("launches", ct.c_longlong), ("flops", ct.c_double),
                 ("bytes", ct.c_double)]
+
+
+class trm_slab(ct.Structure):
+    _fields_ = [("z0", ct.c_int), ("z1", ct.c_int), ("halo_lo", ct.c_int),
+                ("halo_hi", ct.c_int), ("row0", ct.c_int64),
+                ("rows", ct.c_int64), ("ext_z0", ct.c_int),
+                ("ext_nz", ct.c_int), ("ext_rows", ct.c_int64)]
 
 
 class trm_problem(ct.Structure):
@@ -120,6 +127,7 @@ _SIGS = {
     "trm_profile_read": (_i, [_h, ct.POINTER(trm_kernel_stats), _i]),
     "trm_launch_count": (ct.c_longlong, []),
     "trm_footprint_bytes": (ct.c_size_t, [_i64, _i]),
+    "trm_slab_plan": (_i, [_i, _i, _i, _i, _i, _i, ct.POINTER(trm_slab)]),
     "trm_server_create": (_i, [ct.POINTER(_h), ct.c_size_t, _i]),
     "trm_server_submit": (_i, [_h, ct.POINTER(trm_problem),
                                ct.POINTER(ct.c_int64)]),
@@ -426,6 +434,13 @@ class Solver:
 # ---------------------------------------------------------------------------
 # Serving: concurrent solves of problems submitted as they arrive
 # ---------------------------------------------------------------------------
+def trm_slab_plan(nx, ny, nz, order, ranks, rank):
+    """The z-slab of `rank` among `ranks` (see trm_slab in trm.h)."""
+    out = trm_slab()
+    _check(lib.trm_slab_plan(nx, ny, nz, order, ranks, rank, ct.byref(out)))
+    return out
+
+
 def trm_footprint_bytes(N, m):
     return int(lib.trm_footprint_bytes(N, m))
 
