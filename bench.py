@@ -8,12 +8,20 @@ diagonal preconditioner", in the mixed-precision ladder, with the operator
 already resident in HBM. Every step's E_G is checked against the stored
 reference; a step that misses 1e-10 relative error is reported.
 
+The headline steps replay each kind of iteration as a CUDA graph with no
+per-launch events. A second, profiled pass (--profile-steps solves, plain
+launches with CUDA events around each) gives the per-class timing; its
+slowdown over the headline is reported (profiled_pass.over_headline).
+
 Printed JSON keys beyond the base contract: roofline (dominant kernel class,
-timed live with CUDA events around each of its launches in the timed region),
-classes (the same for every kernel class), fp64_path (the same solve with every operation
-in FP64), e2e (the solve through the C ABI from host buffers, copies
-included), clocks (nvidia-smi sampled during the timed region), cpu_baseline
-(the FP64 oracle on the host cores, a bounded sample scaled to a solve).
+from the profiled pass), classes (the same for every kernel class), fp64_path
+(the same solve with every operation in FP64), e2e (the solve through the C
+ABI from host buffers, copies included), clocks (nvidia-smi sampled during
+the headline steps), large (one timed mixed solve of the 96^3, m = 512
+workload, its E_G error against the oracle's reference, its per-class
+roofline from a short profiled solve, and the FP64 path's time per iteration
+extrapolated to a solve), cpu_baseline (the FP64 oracle on all host cores and
+on one, bounded samples scaled to a solve, with the host's nproc and CPU).
 
 --impl reference times the oracle itself (the CPU program), bounded samples.
 
@@ -54,11 +62,12 @@ DF_TFLOPS = FP32_SIMT_TFLOPS / 12
 DF_CLASSES = ("gram_f64", "rotate_f64")
 # Kernel classes whose bound is HBM traffic (algorithmic bytes); the others
 # are bound by FP64 (or FP32 SIMT) arithmetic. The FP32 product classes run
-# on the tensor cores, where the TF32 MMAs take a few percent of the time the
-# operands take to stream, so traffic bounds them; spmm_f64 is the MP2 stencil
-# in double-float (FP32 pairs, 8 bytes per element like FP64).
-HBM_CLASSES = ("spmm_f32", "spmm_f64", "gram_f32", "grad_f32", "rotate_f32",
-               "rowops")
+# on the tensor cores, where at m = 128 the TF32 MMAs take less time than the
+# operands take to stream, so traffic bounds them; spmm_df and rotate_df are
+# MP2's double-float stencil and split rotation (FP32 pairs, 8 bytes per
+# element like FP64).
+HBM_CLASSES = ("spmm_f32", "spmm_f64", "spmm_df", "gram_f32", "grad_f32",
+               "rotate_f32", "rotate_df", "rowops")
 METRIC = "time-to-E_G at 1e-10 rel err (mixed precision)"
 
 
@@ -101,6 +110,12 @@ def parse():
     ap.add_argument("--chain-m", type=int, default=44,
                     help="--chain: eigenpairs m (at n = 32 the smallest gap "
                          "lambda_45 - lambda_44 along the chain is 0.021)")
+    ap.add_argument("--profile-steps", type=int, default=2,
+                    help="solves timed again with per-launch events for the "
+                         "per-class roofline (after the headline steps)")
+    ap.add_argument("--large", type=int, default=1,
+                    help="also time one mixed solve of the 96^3, m = 512 "
+                         "workload and the FP64 path's time per iteration")
     ap.add_argument("--clocks", type=int, default=1,
                     help="sample nvidia-smi clocks during the timed region "
                          "(0 under a profiler, which should see no other "
@@ -176,14 +191,39 @@ def cpu_sample(w, budget, threads):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def host_description():
+    """nproc and the CPU model of the host the oracle runs on."""
+    model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20)
+        for ln in r.stdout.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() in ("Model name", "Vendor ID") and v.strip():
+                model = v.strip() if model is None else model + ", " + v.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu": model or platform.processor(),
+            "machine": platform.machine()}
+
+
 def cpu_baseline(w, g, budget, iters_to_solve):
-    s = cpu_sample(w, budget, 1)
-    value = s["per_iter_s"] * iters_to_solve
-    return {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"{s['iters']} FP64 oracle iterations (numpy, one BLAS "
-                       f"thread) of the same workload, {s['per_iter_s']:.3f} s "
-                       f"each, scaled by {iters_to_solve} iterations per "
-                       f"solve")}
+    """The oracle on all host cores (its BLAS threaded) and on one core, each
+    for half the budget, scaled by the oracle's iterations per solve."""
+    host = host_description()
+    cores = host["nproc"] or 1
+    s_all = cpu_sample(w, budget / 2, cores)
+    s_one = cpu_sample(w, budget / 2, 1)
+    value = s_all["per_iter_s"] * iters_to_solve
+    return {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+            "host": host,
+            "sample": (f"{s_all['iters']} FP64 oracle iterations (numpy, "
+                       f"{cores} BLAS threads) of the same workload, "
+                       f"{s_all['per_iter_s']:.3f} s each, scaled by "
+                       f"{iters_to_solve} iterations per solve"),
+            "single_core": {"value": s_one["per_iter_s"] * iters_to_solve,
+                            "per_iter_s": s_one["per_iter_s"],
+                            "iters": s_one["iters"], "cores": 1}}
 
 
 def iterations_to_solve(g, fallback):
@@ -257,11 +297,15 @@ class ClockSampler:
 # per launch; None when there is none or the kernel source has changed since
 # the capture (the summary records the source file and its sha256 prefix).
 # ---------------------------------------------------------------------------
+# Each profiler class is one kernel family (the solver keeps MP2's
+# double-float stencil and split rotation in classes of their own), so the
+# DRAM counters of a capture apply to its class alone.
 PROFILE_OF_CLASS = {
     "grad_f32": "k_mul_tc_grad_grid48_m128.md",
     "gram_f32": "k_gram_tc_line_grams_grid48_m128.md",
-    "spmm_f64": "k_stencil_df_v4_mp2_grid48_m128.md",
-    "rotate_f32": "k_mul_tc_splitdf_mp2_grid48_m128.md",
+    "spmm_df": "k_stencil_df_v4_mp2_grid48_m128.md",
+    "rotate_df": "k_mul_tc_splitdf_mp2_grid48_m128.md",
+    "spmm_f32": "k_stencil_v4_f32_grid48_m128.md",
 }
 
 
@@ -643,6 +687,84 @@ def run_extras(args):
     return 0
 
 
+LARGE = "grid96_o4_w512_m512"
+
+
+def run_large(args, torch, trm, sptr, peaks, src):
+    """The 96^3 grid, 13-point stencil + 512 wells, m = 512 (N = 884,736):
+    one timed mixed-precision solve (iteration graphs, no per-launch events)
+    after a short warm-up solve; a short profiled solve for the per-class
+    roofline; and the all-FP64 path's time per iteration (a few iterations
+    timed, times the mixed solve's iteration count: an extrapolation, since
+    a whole FP64 solve here takes about half an hour)."""
+    import trm_inputs as ti
+    g = load_json(GOLDEN, {}).get(LARGE, {})
+    w = ti.workload(LARGE, seed=int(g.get("seed", 0)))
+    V = w.potential()
+    nx, ny, nz = w.shape
+    E_ref = g.get("E_G")
+
+    def handle(**o):
+        opt = trm.trm_default_options(precision=trm.TRM_MIXED, precond=1,
+                                      stream=sptr, seed=w.seed + 100, **o)
+        return trm.trm_create_stencil(nx, ny, nz, w.order, w.h, V, w.m,
+                                      args.tol, opt)
+
+    stream = torch.cuda.current_stream()
+    hw = handle(max_iter=30)             # warm-up (stencil choice, first launches)
+    trm.trm_solve(hw, w.N, w.m)
+    trm.trm_destroy(hw)
+    h = handle()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lam, eg, st, status = trm.trm_solve(h, w.N, w.m)
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    # FP64 path: time per iteration from an orthonormal random block
+    C = torch.empty(w.N * w.m, dtype=torch.float64, device="cuda")
+    trm.trm_random_block(w.N, w.m, 7, C.data_ptr(), sptr)
+    trm.trm_orthonormalize(w.N, w.m, C.data_ptr(), sptr)
+    trm.trm_set_block(h, C.data_ptr())
+    del C
+    trm.trm_iterate(h, trm.TRM_FP64, restart=True)   # first step untimed
+    it64 = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        trm.trm_iterate(h, trm.TRM_FP64, restart=False)
+        it64.append(time.perf_counter() - t0)
+    trm.trm_destroy(h)
+    # per-class roofline from a profiled capped solve (events around launches)
+    hp = handle(max_iter=60)
+    trm.trm_profile(hp, True)
+    trm.trm_solve(hp, w.N, w.m)
+    prof = trm.trm_profile_read(hp)
+    trm.trm_destroy(hp)
+    roof, per_class = roofline(prof, peaks, src)
+    per64 = statistics.mean(it64)
+    return {"workload": (f"{w.name}: {w.shape[0]}^3 grid, 13-point 4th-order "
+                         f"-1/2 nabla^2 + {w.nwells} Gaussian wells (seed "
+                         f"{w.seed}), m={w.m}, diagonal preconditioner"),
+            "N": w.N, "m": w.m, "tol_rms": args.tol, "seconds": t,
+            "iterations": st.iterations,
+            "iterations_phase": list(st.iterations_phase), "status": status,
+            "rms_residual": st.rms_residual, "E_G": eg, "E_G_ref": E_ref,
+            "E_G_ref_source": g.get("method"),
+            "rel_err_E_G": abs(eg - E_ref) / abs(E_ref) if E_ref else None,
+            "launch_mode": "each kind of iteration replayed as a CUDA graph",
+            "fp64_path": {"seconds_per_iteration": per64,
+                          "seconds_extrapolated": per64 * st.iterations,
+                          "mixed_speedup_extrapolated": per64 * st.iterations / t,
+                          "how": ("2 FP64 iterations (trm_iterate) timed on the "
+                                  "host after one untimed, times the mixed "
+                                  "solve's iteration count")},
+            "roofline": roof, "classes": per_class,
+            "profiled": "first 60 iterations of the same solve, events around each launch"}
+
+
 def main():
     args = parse()
     if args.serving > 0:
@@ -687,38 +809,50 @@ def main():
         lam, eg, st, status = trm.trm_solve(h, w.N, w.m)
         return lam, eg, st, status
 
+    def timed(n):
+        out = []
+        for _ in range(n):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lam, eg, st, status = solve_once()
+            e1.record(stream)
+            e1.synchronize()
+            out.append((e0.elapsed_time(e1) / 1e3, eg, st, status))
+        return out
+
     for _ in range(args.warmup):
         solve_once()
     torch.cuda.synchronize()
-    trm.trm_profile(h, True)
+    # headline: iterations replayed as CUDA graphs, no per-launch events
     sampler = ClockSampler(torch.cuda.current_device())
     if args.clocks:
         sampler.start()
     launches0 = trm.trm_launch_count()
-    times, errs, iters, statuses = [], [], [], []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        lam, eg, st, status = solve_once()
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
-        errs.append(abs(eg - E_ref) / abs(E_ref) if E_ref else None)
-        iters.append(st.iterations)
-        statuses.append(status)
+    runs = timed(args.steps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     launches = trm.trm_launch_count() - launches0
     clocks = sampler.stop()
+    times = [r[0] for r in runs]
+    errs = [abs(r[1] - E_ref) / abs(E_ref) if E_ref else None for r in runs]
+    iters = [r[2].iterations for r in runs]
+    statuses = [r[3] for r in runs]
+    t_step = job_seconds(statistics.mean(times), dist, "cuda")
+
+    # profiled pass (its own timed region): the same solves with CUDA events
+    # around every launch, graphs off; gives the per-class roofline
+    nprof = max(1, min(args.profile_steps, args.steps))
+    trm.trm_profile(h, True)
+    pruns = timed(nprof)
     prof = trm.trm_profile_read(h)
     trm.trm_profile(h, False)
-    t_step = job_seconds(statistics.mean(times), dist, "cuda")
+    t_prof = statistics.mean(r[0] for r in pruns)
 
     peaks_file = load_json(PEAKS)
     peaks = peaks_file if peaks_file else FALLBACK
@@ -762,6 +896,14 @@ def main():
     e2e = {"value": statistics.mean(e2e_times), "unit": "s",
            "h2d_bytes_per_step": 8 * w.N,
            "d2h_bytes_per_step": 8 * w.N * w.m + 8 * w.m + 8}
+    trm.trm_destroy(h)
+
+    large = None
+    if args.large and rank == 0:
+        try:
+            large = run_large(args, torch, trm, sptr, peaks, src)
+        except Exception as exc:  # reported, not fatal
+            large = {"error": str(exc)[:300]}
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
@@ -771,7 +913,6 @@ def main():
         except Exception as exc:  # reported, not fatal
             cpu = {"error": str(exc)[:300]}
 
-    trm.trm_destroy(h)
     if rank == 0:
         out = {"metric": METRIC, "value": t_step, "unit": "s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -784,13 +925,22 @@ def main():
                "E_G_ok": all(e is not None and e <= 1e-10 for e in errs),
                "roofline": roof, "classes": per_class,
                "profile_ms_per_solve": {
-                   k: round(v["ms"] / args.steps, 3) for k, v in prof.items()
+                   k: round(v["ms"] / nprof, 3) for k, v in prof.items()
                    if v["launches"]},
+               "profiled_pass": {"steps": nprof, "seconds_per_solve": t_prof,
+                                 "over_headline": t_prof / t_step},
                "fp64_path": fp64,
                "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                "launch_mode": {
-                   "timed": "plain launches, CUDA events around each (profiled)",
+                   "timed": "each kind of iteration replayed as a CUDA graph",
+                   "profiled_pass": "plain launches, CUDA events around each",
                    "e2e": "each kind of iteration replayed as a CUDA graph"},
+               "tensor_core_split": {
+                   "gram_f32, grad_f32, rotate_f32, rotate_df":
+                       "tcgen05 kind::tf32, FP32 value = TF32 hi + TF32 lo, "
+                       "three products hi.hi + hi.lo + lo.hi, FP32 accumulation "
+                       "in tensor memory"},
+               "large": large,
                "cpu_baseline": cpu}
         print(json.dumps(out))
     if dist:
