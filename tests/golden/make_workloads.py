@@ -43,8 +43,11 @@ def lowest(H, k, N, m):
     """(the k lowest eigenvalues, how they were found, residual norm bound)."""
     if N * m > FILTERED_ABOVE:
         from oracle import filtered
+        # the spacing near lambda_m shrinks with m (the density of states
+        # grows with the energy), so the filter degree grows with it
         r = filtered.lowest_eigenpairs(
-            H, k, tol=1e-9,
+            H, k, tol=1e-9, degree=32 if m <= 600 else 48,
+            block=k + max(32, k // 6),
             callback=lambda it, th, res: print("  filtered", it, th[-1],
                                                float(res.max()), flush=True))
         if not r.converged:
