@@ -276,11 +276,13 @@ void plan(int64_t N, int m, int n, int* splits, int64_t* rows) {
 
 }  // namespace
 
+// Partials for either kernel a Gram of these sizes may run (the SIMT
+// kernel's plan, or the tensor-core kernel's row slices for FP32 blocks).
 size_t gram_partials_doubles(int64_t N, int m, int n) {
   int s;
   int64_t r;
   plan(N, m, n, &s, &r);
-  return (size_t)s * m * n;
+  return std::max((size_t)s * m * n, gram_tc_partials_doubles(N, m, n));
 }
 
 void sum_splits_pairs(const float* part, int splits, size_t count,

@@ -18,11 +18,8 @@ namespace trm {
 namespace {
 
 // 3 Mi doubles = 24 MiB of partial sums. Every GPU that loads the library
-// holds this array until the process exits. The tensor-core Gram splits N
-// into at most (SM count / output tiles) slices of one 128 x 128 tile each,
-// so its partials are at most SMs x 128^2 doubles (2.5 Mi on 152 SMs) for any
-// m x n within the limit below; the last double holds the kernel's status
-// word.
+// holds this array until the process exits; the last double holds the
+// tensor-core kernel's status word.
 constexpr size_t kScratchDoubles = (size_t)3 << 20;
 // Largest m * n accepted: 2^20 (1024 x 1024).
 constexpr size_t kMaxEntries = (size_t)1 << 20;
@@ -63,13 +60,15 @@ int gram_noalloc(int64_t N, int m, int n, int dtype, const void* A,
     b.p[0] = static_cast<const float*>(B);
     b.cols = n;
     b.count = 1;
-    // the tensor-core kernel trm_gram runs for these operands, with the same
-    // slices and sum order, so the result has the same bytes
-    if (gram_tc_eligible(N, m, a, b) && gram_tc_partials_doubles(N, m, n) <= cap) {
+    // the tensor-core kernel trm_gram runs for these operands; with the
+    // same row slices (so the same bytes) whenever their partials fit the
+    // array, else with fewer, longer slices
+    if (gram_tc_eligible(N, m, a, b)) {
       int* err = reinterpret_cast<int*>(scratch + cap);
       int herr = 0;
       TRM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-      gram_tc(N, m, a, b, out, scratch, cap, err, s);
+      gram_tc(N, m, a, b, out, scratch, cap, err, s, nullptr,
+              (int)(cap / ((size_t)m * n)));
       TRM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
       TRM_CUDA(cudaStreamSynchronize(s));
       if (herr & 2) throw Error(-6, "trm_gram_noalloc: a device wait timed out");

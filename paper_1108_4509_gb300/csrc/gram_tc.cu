@@ -366,33 +366,53 @@ bool gram_tc_pairs_eligible(int64_t N, int m, const Blocks<float>& A,
   return tc::encode_fn() != nullptr;
 }
 
-size_t gram_tc_partials_doubles(int64_t N, int m, int n) {
-  const int tiles = ceil_div(m, BM) * ceil_div(n, BN);
-  const int splits = std::max(1, std::min(sm_count() / tiles,
-                                          ceil_div(N, BK * kMinStages)));
-  return (size_t)splits * m * n;
+// Row slices for a launch of `tiles` output tiles: among the counts that
+// keep at least kMinStages stages per slice, launch at most 8 waves of CTAs
+// and stay within max_splits, the one whose CTAs fill the SMs most evenly,
+// less 1 % per extra wave (each wave refills the pipelines). Every CTA of a
+// launch does the same work, so with one slice per tile a launch of 164
+// tiles would run a second wave of 12 CTAs as long as the first.
+static int tc_splits(int64_t N, int tiles, int max_splits) {
+  const int sms = sm_count();
+  const int64_t by_rows = ceil_div(N, (int64_t)BK * kMinStages);
+  const int smax = (int)std::max<int64_t>(
+      1, std::min<int64_t>({by_rows, (int64_t)8 * sms / tiles,
+                            (int64_t)max_splits}));
+  int best = 1;
+  double beff = 0.0;
+  for (int sp = 1; sp <= smax; ++sp) {
+    const int64_t ctas = (int64_t)tiles * sp;
+    const int64_t waves = ceil_div(ctas, (int64_t)sms);
+    const double eff =
+        (double)ctas / ((double)sms * (double)waves) - 0.01 * (double)(waves - 1);
+    if (eff > beff + 1e-3) {
+      beff = eff;
+      best = sp;
+    }
+  }
+  return best;
 }
 
-// Row slices for a launch of `tiles` output tiles: enough to fill the SMs,
-// at least kMinStages stages each.
-static int tc_splits(int64_t N, int tiles) {
-  return std::max(1, std::min(sm_count() / tiles, ceil_div(N, BK * kMinStages)));
+size_t gram_tc_partials_doubles(int64_t N, int m, int n, int skipped_tiles) {
+  const int tiles = ceil_div(m, BM) * ceil_div(n, BN) - skipped_tiles;
+  return (size_t)tc_splits(N, std::max(1, tiles), 1 << 30) * m * n;
 }
 
 void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
              double* out, double* partials, size_t cap, int* err,
-             cudaStream_t s, float* out32) {
+             cudaStream_t s, float* out32, int max_splits) {
   Blocks<float> a;
   a.p[0] = A;
   a.cols = m;
   a.count = 1;
-  gram_tc_pairs(N, m, a, B, out, partials, cap, err, s, out32);
+  gram_tc_pairs(N, m, a, B, out, partials, cap, err, s, out32, -1,
+                max_splits);
 }
 
 void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
                    const Blocks<float>& B, double* out, double* partials,
                    size_t cap, int* err, cudaStream_t s, float* out32,
-                   int sym_seg) {
+                   int sym_seg, int max_splits) {
   const int n = B.total();
   const int tiles_m = ceil_div(m, BM);
   const int segcols = B.count > 1 ? B.cols : n;
@@ -412,7 +432,7 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
       ++tiles;
     }
   }
-  int splits = tc_splits(N, tiles);
+  int splits = tc_splits(N, tiles, max_splits > 0 ? max_splits : 1 << 30);
   int64_t rows = (N + splits - 1) / splits;
   rows = ((rows + BK - 1) / BK) * BK;
   splits = (int)((N + rows - 1) / rows);

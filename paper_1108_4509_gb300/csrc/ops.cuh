@@ -134,17 +134,20 @@ bool gram_tc_eligible(int64_t N, int m, const float* A, const Blocks<float>& B);
 // segments); up to four segments.
 bool gram_tc_pairs_eligible(int64_t N, int m, const Blocks<float>& A,
                             const Blocks<float>& B);
-// Doubles of split partials gram_tc / gram_tc_pairs need for an m x n result.
-size_t gram_tc_partials_doubles(int64_t N, int m, int n);
+// Doubles of split partials gram_tc / gram_tc_pairs need for an m x n result
+// (skipped_tiles: tiles of a symmetric segment that are mirrored, not run).
+size_t gram_tc_partials_doubles(int64_t N, int m, int n, int skipped_tiles = 0);
 // sym_seg >= 0: that segment is symmetric (m x m); only its tiles on or
 // above the diagonal are computed and the rest mirrored (Fig. DIVFIG).
+// max_splits > 0 caps the row slices (a fixed partials buffer).
 void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
                    const Blocks<float>& B, double* out, double* partials,
                    size_t cap, int* err, cudaStream_t s,
-                   float* out32 = nullptr, int sym_seg = -1);
+                   float* out32 = nullptr, int sym_seg = -1,
+                   int max_splits = 0);
 void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
              double* out, double* partials, size_t cap, int* err,
-             cudaStream_t s, float* out32 = nullptr);
+             cudaStream_t s, float* out32 = nullptr, int max_splits = 0);
 
 // Same product with the split partials in a caller-given scratch of
 // scratch_doubles doubles (fewer row slices when it is small); m*n must fit.

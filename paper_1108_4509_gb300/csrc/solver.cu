@@ -227,9 +227,11 @@ void* DevArena::alloc(size_t bytes) {
 // partials, the gradient's per-CTA sums and the column reductions.
 size_t Solver::part_capacity(int64_t N, int m) {
   const size_t chunks = (size_t)ceil_div(N, 4096);
-  return std::max<size_t>(
+  const int tm = ceil_div(m, 128);  // the fused line Gram mirrors P^T P's
+  return std::max<size_t>(          // tm (tm - 1) / 2 lower tiles
       {gram_partials_doubles(N, m, 4 * m), gram_partials_doubles(N, m, 3 * m),
        gram_partials_doubles(N, m, m),
+       gram_tc_partials_doubles(N, m, 3 * m, tm * (tm - 1) / 2),
        (size_t)4 * ceil_div(N, 64) * ceil_div(m, 64), 3 * chunks * m + m,
        (size_t)ceil_div(N, 256) * m, (size_t)4096});
 }
