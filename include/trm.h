@@ -7,8 +7,8 @@
  * subject to C^T C = I_m with nonlinear conjugate gradients (Tsuchida and Choe,
  * "Iterative diagonalization of symmetric matrices in mixed precision",
  * Sec. 2.1, Eqs. TRHEQ/CIJEQ, Fig. TMFIG), in full FP64 or in the mixed
- * precision of Sec. 2.2 (MP1, MP2, full SP, and a ladder full SP -> MP2 ->
- * FP64 Rayleigh-Ritz).
+ * precision of Sec. 2.2 (MP2, full SP, and a ladder full SP -> MP2 ->
+ * FP64 Rayleigh-Ritz; MP1 is not offered).
  *
  * Conventions used by every entry point:
  *  - N x m blocks are column-major with leading dimension N (column j of C is
@@ -49,8 +49,12 @@ typedef enum {
 /* Precision modes (Sec. 2.2). */
 typedef enum {
   TRM_FP64 = 0,    /* "full DP": every operation in FP64 */
-  TRM_MP1 = 1,     /* MP1: G, P stored FP32; split rotation C L_D + C L' */
-  TRM_MP2 = 2,     /* MP2: MP1 plus the two O(m^2 N) gradient GEMMs in FP32 */
+  TRM_MP1 = 1,     /* reserved: Sec. 2.2's MP1 (G, P stored FP32, split
+                      rotation) is not offered -- its O(m^2 N) Grams stay
+                      FP64, the slowest part on this GPU; create returns
+                      TRM_EINVAL */
+  TRM_MP2 = 2,     /* MP2: G, P stored FP32, split rotation C L_D + C L',
+                      and the two O(m^2 N) gradient GEMMs in FP32 */
   TRM_FULL_SP = 3, /* "full SP": all block work in FP32 */
   TRM_MIXED = 4    /* full SP until stagnation, then MP2, then FP64 Rayleigh-Ritz */
 } trm_precision;
@@ -87,7 +91,7 @@ typedef struct {
 
 typedef struct {
   int iterations;           /* total iterations */
-  int iterations_phase[3];  /* full SP, MP2/MP1/FP64, reorth count */
+  int iterations_phase[3];  /* full SP, MP2 or FP64, reorth count */
   int converged;            /* 1 if the residual test passed */
   double rms_residual;      /* final FP64 ||H C - C Lambda||_F / sqrt(m) */
   double max_residual;      /* final FP64 max_j ||H c_j - lambda_j c_j|| */
@@ -181,7 +185,7 @@ typedef struct {
   double rms;    /* RMS column residual ||G_i||_F / (2 sqrt(m)) */
   double alpha;  /* line step taken from C_i (0 on a restart without a step) */
   double gamma;  /* Polak-Ribiere coefficient of the direction P_i */
-  int phase;     /* 0 full SP, 1 MP2 (or MP1), 2 FP64 */
+  int phase;     /* 0 full SP, 1 MP2, 2 FP64 */
   int restart;   /* 1 when P_i was not a descent direction, so P_{i+1}
                     restarts CG (gamma = 0) */
 } trm_iter_record;

@@ -271,23 +271,26 @@ void mm_gemm(int m, const double* A, bool trA, const double* B, bool trB,
 void make_A0(int m, const double* Hp, const double* HD, double* A0,
              cudaStream_t s);
 // The line step along P and the factor of the new overlap: the line-model
-// terms from H' (diag zeroed), H_D, B = C^T P, Q = P^T P, the diagonal of
-// P^T H P (hpd[j * hpd_stride], FP64: a vector of column dots, or the
-// diagonal of the matrix with stride m + 1) and W = P^T G give alpha (into
-// sc); then S = I + a (B + B^T) + a^2 Q is factorised (in deviation form
-// when dev) into Linv (may be null) and R = L^{-T}.
+// terms from H' (diag zeroed), H_D, B = C^T P, Q = P^T P, the trace of
+// P^T H P and W = P^T G give alpha (into sc); then S = I + a (B + B^T) +
+// a^2 Q is factorised (in deviation form when dev) into Linv (may be null)
+// and R = L^{-T}. The trace comes from the diagonal hpd[j * hpd_stride] (the
+// matrix P^T H P with stride m + 1), or, when hpd is null, as the sum of the
+// n_tr_parts partial column dots in tr_parts (the stencil applied to P).
 // part: >= 16 * ceil(m/32)^2 doubles; gwork: max(2 m^2, chol_work_elems(m))
 // doubles (FP32 factorisations keep FP32 copies of B and Q there).
 template <typename Tm>
 void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
                  const double* Q, const double* hpd, int hpd_stride,
-                 const double* W, double* Linv, double* R, IterScalars* sc,
-                 double* gwork, double* part, bool dev, cudaStream_t s);
+                 const double* tr_parts, int n_tr_parts, const double* W,
+                 double* Linv, double* R, IterScalars* sc, double* gwork,
+                 double* part, bool dev, cudaStream_t s);
 // line_factor<float> with the m x m inputs given in FP32 (Gram copies)
 void line_factor32(int m, const float* Hp, const double* HD, const float* Bm,
                    const float* Q, const double* hpd, int hpd_stride,
-                   const float* W, double* Linv, double* R, IterScalars* sc,
-                   double* gwork, double* part, cudaStream_t s);
+                   const double* tr_parts, int n_tr_parts, const float* W,
+                   double* Linv, double* R, IterScalars* sc, double* gwork,
+                   double* part, cudaStream_t s);
 // Elements (of the arithmetic type) of the factorisation workspace gwork.
 size_t chol_work_elems(int m);
 // S = L L^T (lower); writes Linv = L^{-1} (unless null) and R = L^{-T}. Non-PD sets

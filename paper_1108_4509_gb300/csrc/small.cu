@@ -5,6 +5,7 @@
 // All matrices are column-major with leading dimension m and stored as FP64;
 // the template parameter Tm is the arithmetic type.
 #include <atomic>
+#include <cstdlib>
 
 #include "ops.cuh"
 
@@ -793,7 +794,8 @@ __global__ void __launch_bounds__(1024)
     k_line_terms(int m, const Tin* __restrict__ Hp,
                  const double* __restrict__ HD, const Tin* __restrict__ Bm,
                  const Tin* __restrict__ Q, const double* __restrict__ hpd,
-                 int hpd_stride, const Tin* __restrict__ W,
+                 int hpd_stride, const double* __restrict__ tr_parts,
+                 int n_tr_parts, const Tin* __restrict__ W,
                  double* __restrict__ part,
                  float* __restrict__ Bf, float* __restrict__ Qf) {
   __shared__ Tm t0[32][33], t1[32][33], t2[32][33], t3[32][33];
@@ -838,12 +840,21 @@ __global__ void __launch_bounds__(1024)
       v1 = -qij * a0;
       if (i == j) {
         v0 = -wij;
-        v1 += (Tm)hpd[(size_t)i * hpd_stride];
+        if (hpd) v1 += (Tm)hpd[(size_t)i * hpd_stride];
         v3 = (Tm)Q[e];
       }
     }
   }
   double v[4] = {(double)v0, (double)v1, (double)v2, (double)v3};
+  if (tr_parts && ks == 0) {
+    // tr(P^T H P) as the sum of the stencil's partial column dots, each
+    // first-split CTA adding a fixed share
+    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+    const int ncta = gridDim.x * gridDim.y;
+    for (int k = cta * blockDim.x + threadIdx.x; k < n_tr_parts;
+         k += ncta * blockDim.x)
+      v[1] += tr_parts[k];
+  }
   block_sum<4>(v, red);
   if (threadIdx.x == 0) {
     const size_t b =
@@ -1088,14 +1099,25 @@ void make_A0(int m, const double* Hp, const double* HD, double* A0,
 }
 
 
-// From this m on the factorisation runs blocked on many CTAs.
-constexpr int kCholBlockedFrom = 256;
+// From this m on the factorisation runs blocked on many CTAs; the
+// environment variable TRM_CHOL_BLOCKED_FROM, read once per process,
+// overrides the default.
+static int chol_blocked_from() {
+  static const int v = [] {
+    const char* e = std::getenv("TRM_CHOL_BLOCKED_FROM");
+    const int d = 256;
+    if (!e || !*e) return d;
+    const long x = std::strtol(e, nullptr, 10);
+    return x > 0 && x <= 4096 ? (int)x : d;
+  }();
+  return v;
+}
 
 // elements of the padded working copy plus the inverse's temporary (one
 // CTA), or of W, L, X, T and the failure flag (blocked)
 size_t chol_work_elems(int m) {
   const size_t mp = (size_t)((m + 31) & ~31);
-  if (m >= kCholBlockedFrom) return 4 * mp * mp + 8;
+  if (m >= chol_blocked_from()) return 4 * mp * mp + 8;
   return mp * (mp + 1) + 33 * mp;
 }
 
@@ -1148,7 +1170,7 @@ static void chol_launch(int m, const double* S, const double* Bm,
                         double* gwork, cudaStream_t s,
                         const double* lpart = nullptr, int nlpart = 0) {
   if (m > 1024) throw Error(-1, "chol_inv: m > 1024");
-  if (m >= kCholBlockedFrom) {
+  if (m >= chol_blocked_from()) {
     chol_blocked<Tm, dev>(m, S, Bm, Q, Bf, Qf, Linv, R, sc, gwork, s, lpart,
                           nlpart);
     return;
@@ -1201,8 +1223,9 @@ static int line_ksplit(int m) {
 template <typename Tm>
 void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
                  const double* Q, const double* hpd, int hpd_stride,
-                 const double* W, double* Linv, double* R, IterScalars* sc,
-                 double* gwork, double* part, bool dev, cudaStream_t s) {
+                 const double* tr_parts, int n_tr_parts, const double* W,
+                 double* Linv, double* R, IterScalars* sc, double* gwork,
+                 double* part, bool dev, cudaStream_t s) {
   const int t = ceil_div(m, 32);
   const int ksplit = line_ksplit(m);
   // FP32 factorisations take B and Q as FP32 copies written by the line
@@ -1215,7 +1238,8 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
     Qf = Bf + (size_t)m * m;
   }
   k_line_terms<Tm, double><<<dim3(t, t, ksplit), 1024, 0, s>>>(
-      m, Hp, HD, Bm, Q, hpd, hpd_stride, W, part, Bf, Qf);
+      m, Hp, HD, Bm, Q, hpd, hpd_stride, tr_parts, n_tr_parts, W, part, Bf,
+      Qf);
   TRM_CHECK_LAUNCH();
   // the factorisation kernel takes the line step from the partials first
   if (dev)
@@ -1230,12 +1254,14 @@ void line_factor(int m, const double* Hp, const double* HD, const double* Bm,
 // write): no FP64 conversion in the line terms or the factorisation.
 void line_factor32(int m, const float* Hp, const double* HD, const float* Bm,
                    const float* Q, const double* hpd, int hpd_stride,
-                   const float* W, double* Linv, double* R, IterScalars* sc,
-                   double* gwork, double* part, cudaStream_t s) {
+                   const double* tr_parts, int n_tr_parts, const float* W,
+                   double* Linv, double* R, IterScalars* sc, double* gwork,
+                   double* part, cudaStream_t s) {
   const int t = ceil_div(m, 32);
   const int ksplit = line_ksplit(m);
   k_line_terms<float, float><<<dim3(t, t, ksplit), 1024, 0, s>>>(
-      m, Hp, HD, Bm, Q, hpd, hpd_stride, W, part, nullptr, nullptr);
+      m, Hp, HD, Bm, Q, hpd, hpd_stride, tr_parts, n_tr_parts, W, part,
+      nullptr, nullptr);
   TRM_CHECK_LAUNCH();
   chol_launch<float, true>(m, nullptr, nullptr, nullptr, Bm, Q, Linv, R, sc,
                            gwork, s, part, t * t * ksplit);
@@ -1247,14 +1273,14 @@ template void chol_inv_dev<double>(int, const double*, double*, double*,
                                    IterScalars*, double*, cudaStream_t);
 template void line_factor<float>(int, const double*, const double*,
                                  const double*, const double*, const double*,
-                                 int, const double*, double*, double*,
-                                 IterScalars*, double*, double*, bool,
-                                 cudaStream_t);
+                                 int, const double*, int, const double*,
+                                 double*, double*, IterScalars*, double*,
+                                 double*, bool, cudaStream_t);
 template void line_factor<double>(int, const double*, const double*,
                                   const double*, const double*, const double*,
-                                  int, const double*, double*, double*,
-                                  IterScalars*, double*, double*, bool,
-                                  cudaStream_t);
+                                  int, const double*, int, const double*,
+                                  double*, double*, IterScalars*, double*,
+                                  double*, bool, cudaStream_t);
 
 template <typename T>
 static void jacobi_launch(int m, const double* A, const double* Z0, double* w,

@@ -241,7 +241,8 @@ size_t Solver::part_capacity(int64_t N, int m) {
 size_t Solver::footprint(int64_t N, int m) {
   const size_t nm = (size_t)N * m, mm = (size_t)m * m;
   size_t b = nm * (3 * 8 + 3 * 4 + 3 * 8 + 4 * 8);  // blocks
-  b += mm * 8 * 13 + std::max(2 * mm, chol_work_elems(m)) * 8 + 5 * m * 8;
+  b += mm * 8 * 13 + std::max(2 * mm, chol_work_elems(m)) * 8 + 4 * m * 8;
+  b += std::max<size_t>(1, (size_t)ceil_div(N, 256) * m) * 8;  // P's dots
   b += sym_eig_work_doubles(m) * 8 + 5 * mm * 4;
   b += part_capacity(N, m) * 8 + sizeof(IterScalars) + 16;
   b += mul_tc_work_floats(m, m) * 4;
@@ -273,7 +274,9 @@ Solver::Solver(int64_t N, int m, double tol, const trm_options& opt)
   for (void* p : {Gb_[0], Gb_[1], Pb_, HPb_})
     TRM_CUDA(cudaMemsetAsync(p, 0, nm * 8, s_));
   HD_ = d(m);
-  hpd_ = d(m);
+  // partial column dots of the stencil applied to P (their sum is
+  // tr(P^T H P)), kept apart from part_, which the Grams then reuse
+  hpdots_ = d(std::max<size_t>(1, (size_t)ceil_div(N, 256) * m));
   Hp_ = d(mm);
   A0_ = d(mm);
   Bm_ = d(4 * mm);  // C^T P, then P^T [P HP G] (unfused) or P^T [P G] (fused)
@@ -607,31 +610,27 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   TRM_PROF(KC_ROWOPS, 2 * nm, 3 * es * nm,
            update_p<T>(N_, m_, G, P, minv, sc_, s_));                 // P
   const bool fused = !gen && line_grams_fusable<T>(C, P, G);
-  bool hp_dots = false;
+  int hp_chunks = 0;  // > 0: tr(P^T H P) from the stencil's column dots
   if constexpr (sizeof(T) == 4) {
-    if (fused) {  // H P with the diagonal of P^T H P as column dots
-      int chunks = 0;
-      TRM_PROF(ksp, sfl, sby, chunks = apply_h_dots(op_, P, HP, m_, part_, s_));
-      TRM_PROF(KC_ROWOPS, 2.0 * m_ * chunks, 8.0 * m_ * chunks,
-               energy_from_dots(part_, chunks, m_, hpd_, nullptr, s_));
-      hp_dots = true;
-    }
+    if (fused)
+      TRM_PROF(ksp, sfl, sby,
+               hp_chunks = apply_h_dots(op_, P, HP, m_, hpdots_, s_));
   }
-  if (!hp_dots) TRM_PROF(ksp, sfl, sby, apply_h(op_, P, HP, m_, s_));  // H P
+  if (!hp_chunks) TRM_PROF(ksp, sfl, sby, apply_h(op_, P, HP, m_, s_));  // H P
   if (gen) {
     double ffl, fby;
     spmm_cost(sop_, m_, 8, &ffl, &fby);
     TRM_PROF(ksp, ffl, fby, apply_h(sop_, P, SPt, m_, s_));          // S P
   }
-  // where the diagonal of P^T H P and W = P^T G land
-  const double* hpd = hpd_;
-  int hstride = 1;
+  // where the trace of P^T H P and W = P^T G come from
+  const double* hpd = nullptr;
+  const double* trp = hp_chunks ? hpdots_ : nullptr;
+  const int ntrp = hp_chunks * m_;
   size_t woff = mm;
   if (fused) {
     line_grams_fused<T>(C, P, G);
   } else {
-    hpd = PG_ + mm;
-    hstride = m_ + 1;
+    hpd = PG_ + mm;  // the diagonal of P^T H P, stride m + 1
     woff = 2 * mm;
     Blocks<T> bp;
     bp.p[0] = P;
@@ -653,11 +652,13 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   const double m3 = md * md * md;
   prof.begin(KC_SMALL, s_);
   if constexpr (sizeof(T) == 4 && sizeof(Tm) == 4)
-    line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, hpd, hstride, PG32_ + woff,
-                  nullptr, R_, sc_, mmw_, T1_, s_);  // alpha, Fig. ONFIG
+    line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, hpd, m_ + 1, trp, ntrp,
+                  PG32_ + woff, nullptr, R_, sc_, mmw_, T1_,
+                  s_);  // alpha, Fig. ONFIG
   else
-    line_factor<Tm>(m_, Hp_, HD_, Bm_, PG_, hpd, hstride, PG_ + woff, nullptr,
-                    R_, sc_, mmw_, T1_, sizeof(Tm) == 4, s_);
+    line_factor<Tm>(m_, Hp_, HD_, Bm_, PG_, hpd, m_ + 1, trp, ntrp,
+                    PG_ + woff, nullptr, R_, sc_, mmw_, T1_,
+                    sizeof(Tm) == 4, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(krt, m2N, 3 * es * nm,
            (rotate<T, T>(N_, m_, C, P, R_, Cn, sc_, s_, &tw_)));  // (C+aP)L^-T
@@ -717,20 +718,20 @@ void Solver::iter_mp2() {
   TRM_PROF(KC_ROWOPS, 2 * dnm, 12 * dnm,
            update_p<float>(N_, m_, G, P, minv, sc_, s_));
   const bool fused = line_grams_fusable<float>(Ch, P, G);
-  const double* hpd = hpd_;
-  int hstride = 1;
+  const double* hpd = nullptr;
+  const double* trp = nullptr;
+  int ntrp = 0;
   size_t woff = mm;
-  if (fused) {  // H P with the diagonal of P^T H P as column dots
+  if (fused) {  // H P with tr(P^T H P) as the stencil's column dots
     int chunks = 0;
     TRM_PROF(KC_SPMM32, f32, b32,
-             chunks = apply_h_dots(op_, P, HP, m_, part_, s_));
-    TRM_PROF(KC_ROWOPS, 2.0 * m_ * chunks, 8.0 * m_ * chunks,
-             energy_from_dots(part_, chunks, m_, hpd_, nullptr, s_));
+             chunks = apply_h_dots(op_, P, HP, m_, hpdots_, s_));
+    trp = hpdots_;
+    ntrp = chunks * m_;
     line_grams_fused<float>(Ch, P, G);
   } else {
     TRM_PROF(KC_SPMM32, f32, b32, apply_h(op_, P, HP, m_, s_));
-    hpd = PG_ + mm;
-    hstride = m_ + 1;
+    hpd = PG_ + mm;  // the diagonal of P^T H P, stride m + 1
     woff = 2 * mm;
     Blocks<float> bp;
     bp.p[0] = P;
@@ -750,8 +751,8 @@ void Solver::iter_mp2() {
                          &sc_->status, PG32_));
   }
   prof.begin(KC_SMALL, s_);
-  line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, hpd, hstride, PG32_ + woff,
-                nullptr, R_, sc_, mmw_, T1_, s_);
+  line_factor32(m_, Hp32_, HD_, Bm32_, PG32_, hpd, m_ + 1, trp, ntrp,
+                PG32_ + woff, nullptr, R_, sc_, mmw_, T1_, s_);
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(KC_ROTDF, m2N, 24 * dnm,
            rotate_split_df(N_, m_, Ch, Cl, P, R_, Cdfn_, Cdfn_ + nm, sc_, s_,

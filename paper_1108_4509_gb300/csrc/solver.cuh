@@ -183,7 +183,7 @@ class Solver {
   float *Cdf_ = nullptr, *Cdfn_ = nullptr, *Xdf_ = nullptr;  // FP32 pairs
   void *Gb_[2] = {nullptr, nullptr}, *Pb_ = nullptr, *HPb_ = nullptr;
   // m x m (FP64)
-  double *HD_, *hpd_, *Hp_, *A0_, *Bm_, *PG_, *T1_, *T2_, *S_, *Linv_, *R_, *mmw_,
+  double *HD_, *hpdots_, *Hp_, *A0_, *Bm_, *PG_, *T1_, *T2_, *S_, *Linv_, *R_, *mmw_,
       *eigws_,
       *eigw_, *Z_, *lam_, *res_;
   int* info_;
