@@ -2,14 +2,18 @@
 // (tcgen05, accumulators in tensor memory), the O(m^2 N) products of
 // Fig. EGFIG step (6), Fig. ONFIG step (1) and the line-search projections.
 //
-// Each FP32 value is split into two TF32 terms, x = hi + lo with
-// hi = rna_tf32(x) and lo = rna_tf32(x - hi) (11 + 11 significant bits); the
-// three products hi.hi + hi.lo + lo.hi are accumulated in FP32 in tensor
-// memory, which keeps FP32-class accuracy (the dropped lo.lo and the rounding
-// of lo are near 2^-22 relative). A TMA box of 32 rows x 128 columns of a
+// Each FP32 value is split into two TF32 terms, x = hi + lo. The TF32 MMA
+// reads an FP32 bit pattern and ignores its low 13 mantissa bits (measured:
+// the raw value as the TF32 operand with lo = rna_tf32(x - trunc(x)) gives
+// the product to 2e-8 of sum |a||b|, with lo from rna_tf32(x) instead to
+// 1e-5), so hi = trunc_tf32(x) is the TMA-loaded tile itself and only lo is
+// formed (lo = rna_tf32(x - hi), |lo| < 2^-10 |x|, rounding error < 2^-21
+// |x|). The three products hi.hi + hi.lo + lo.hi are accumulated in FP32 in
+// tensor memory; the dropped lo.lo and the rounding of lo are below 2^-19 of
+// |a b|: FP32-class accuracy. A TMA box of 32 rows x 128 columns of a
 // column-major FP32 block, loaded with the 128-byte swizzle, is already the
-// K-major operand layout the TF32 MMA reads, so the split happens in place
-// (hi overwrites x, lo goes to a twin buffer) and no tile is copied.
+// K-major operand layout the TF32 MMA reads, and lo is written at the same
+// offsets of a twin buffer.
 //
 // One CTA owns a 128 x 128 output tile and a slice of the N rows (split-K);
 // its partial tile is written as double-float pairs and the slices are added
@@ -26,12 +30,11 @@
 // the bias is then at most 96 * 12 steps and nothing is folded.
 //
 // Warp roles (576 threads): warp 0 issues the TMA loads (one box of A and one
-// of B per 32-row stage into a ring of three raw stages); warp 1 allocates
-// tensor memory and issues the MMAs from one thread; warps 2-9 split each
-// raw stage into a ring of two operand stages (half a line of A and of B
-// each) and free the raw stage at once, so the loads run up to three stages
-// ahead of the split and are not held back by the MMAs (a DRAM round trip
-// under load is longer than one stage's MMAs); warps 10-17 fold the finished
+// of B per 32-row stage into a ring of raw stages, each freed when the MMAs
+// that read it as hi are done); warp 1 allocates tensor memory and issues the
+// MMAs from one thread; warps 2-9 form lo of each raw stage into a ring of
+// lo stages (half a line of A and of B each), so the split of the next
+// stages overlaps the MMAs of this one; warps 10-17 fold the finished
 // chunks and write the partial as FP32 pairs (warp w owns TMEM lanes
 // 32 (w % 4) .. +31 and one 64-column half). No FP64 instruction runs here
 // (GB300's FP64 pipe is 1/64 of its FP32 rate). Every mbarrier wait is
@@ -56,8 +59,14 @@ using namespace tc;
 constexpr int BM = 128;        // output rows per CTA (columns of A)
 constexpr int BN = 128;        // output columns per CTA (columns of B)
 constexpr int BK = 32;         // block rows per stage (one 128-byte box)
-constexpr int RSTAGES = 3;  // raw TMA stages
-constexpr int OSTAGES = 2;  // split operand stages
+#ifndef TRM_GRAM_RSTAGES
+#define TRM_GRAM_RSTAGES 3
+#endif
+#ifndef TRM_GRAM_OSTAGES
+#define TRM_GRAM_OSTAGES 3
+#endif
+constexpr int RSTAGES = TRM_GRAM_RSTAGES;  // raw TMA stages (the hi operands)
+constexpr int OSTAGES = TRM_GRAM_OSTAGES;  // lo stages
 constexpr int THREADS = 576;  // 18 warps
 constexpr int KC = 4;         // stages per accumulation chunk
 constexpr int kSingleChunk = 96;  // row slices this short are one chunk
@@ -66,25 +75,26 @@ constexpr int kSingleChunk = 96;  // row slices this short are one chunk
 constexpr int kMinStages = 16;
 
 struct TcSmem {
-  // [stage][A, B][128 columns x 32 rows] as loaded, and the split operands
-  // [stage][A hi, B hi, A lo, B lo] at the same offsets; 128-byte swizzle:
-  // 16-byte chunk q of column c sits at chunk q ^ (c % 8).
+  // [stage][A, B][128 columns x 32 rows] as loaded (the hi operands), and
+  // the lo operands [stage][A lo, B lo] at the same offsets; 128-byte
+  // swizzle: 16-byte chunk q of column c sits at chunk q ^ (c % 8).
   float raw[RSTAGES][2][BM * BK];
-  float op[OSTAGES][4][BM * BK];
+  float op[OSTAGES][2][BM * BK];
   uint64_t full[RSTAGES], rawfree[RSTAGES], opfull[OSTAGES], opfree[OSTAGES];
   uint64_t accfull[2], accempty[2], mmadone;
   uint32_t tmem_base;
   int failed;
 };
 
-// Split half of a 128-byte line (16 values) of a raw stage into TF32 hi and
-// lo terms at the same offsets of the operand buffers. Chunks are visited in
-// a bank-spread order.
-__device__ __forceinline__ void split_line_half(const float* raw, float* hi,
-                                                float* lo, int line,
-                                                int half) {
+// lo = rna_tf32(x - trunc_tf32(x)) for half of a 128-byte line (16 values)
+// of a raw stage, at the same offsets of the lo buffer. Chunks are visited
+// in a bank-spread order.
+__device__ __forceinline__ float tf32_lo(float x) {
+  return tf32_rna(x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u));
+}
+__device__ __forceinline__ void split_line_half(const float* raw, float* lo,
+                                                int line, int half) {
   const float4* pr = reinterpret_cast<const float4*>(raw + line * 32);
-  float4* ph = reinterpret_cast<float4*>(hi + line * 32);
   float4* pl = reinterpret_cast<float4*>(lo + line * 32);
   float4 v[4];
 #pragma unroll
@@ -92,13 +102,8 @@ __device__ __forceinline__ void split_line_half(const float* raw, float* hi,
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int q = (half * 4 + j) ^ (line & 7);
-    float4 h, o;
-    h.x = tf32_rna(v[j].x); o.x = tf32_rna(v[j].x - h.x);
-    h.y = tf32_rna(v[j].y); o.y = tf32_rna(v[j].y - h.y);
-    h.z = tf32_rna(v[j].z); o.z = tf32_rna(v[j].z - h.z);
-    h.w = tf32_rna(v[j].w); o.w = tf32_rna(v[j].w - h.w);
-    ph[q] = h;
-    pl[q] = o;
+    pl[q] = make_float4(tf32_lo(v[j].x), tf32_lo(v[j].y), tf32_lo(v[j].z),
+                        tf32_lo(v[j].w));
   }
 }
 
@@ -151,7 +156,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < RSTAGES; ++s) {
       mbar_init(&sm->full[s], 1);
-      mbar_init(&sm->rawfree[s], 256);
+      mbar_init(&sm->rawfree[s], 1);  // the MMAs that read it are done
     }
     for (int s = 0; s < OSTAGES; ++s) {
       mbar_init(&sm->opfull[s], 256);
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       const int kcl = nk <= kSingleChunk ? nk : KC;  // stages per chunk
       for (int k = 0; k < nk && ok; ++k) {
-        const int s = k % OSTAGES;
+        const int s = k % OSTAGES, r = k % RSTAGES;
         const int kc = k % kcl, c = k / kcl, b = c & 1;
         if (kc == 0 && c >= 2 &&
             !mbar_wait(&sm->accempty[b], ((c / 2) - 1) & 1, args.err,
@@ -215,10 +220,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         fence_after();
         const uint32_t d = tmem + (uint32_t)(b * BN);
-        const uint32_t aH = smem_u32(sm->op[s][0]);
-        const uint32_t bH = smem_u32(sm->op[s][1]);
-        const uint32_t aL = smem_u32(sm->op[s][2]);
-        const uint32_t bL = smem_u32(sm->op[s][3]);
+        const uint32_t aH = smem_u32(sm->raw[r][0]);
+        const uint32_t bH = smem_u32(sm->raw[r][1]);
+        const uint32_t aL = smem_u32(sm->op[s][0]);
+        const uint32_t bL = smem_u32(sm->op[s][1]);
         const uint32_t pa[3] = {aH, aH, aL};
         const uint32_t pb[3] = {bH, bL, bH};
 #pragma unroll
@@ -228,7 +233,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             mma_tf32(d, kdesc(pa[p] + kk * 32), kdesc(pb[p] + kk * 32),
                      kIdesc, (kc > 0 || p > 0 || kk > 0) ? 1u : 0u);
         }
-        mma_commit(&sm->opfree[s]);  // operands reusable once these MMAs are done
+        mma_commit(&sm->opfree[s]);   // lo and the raw stage reusable
+        mma_commit(&sm->rawfree[r]);  // once these MMAs are done
         if (kc == kcl - 1 || k == nk - 1) mma_commit(&sm->accfull[b]);
       }
       // every MMA of this thread completes before the TMEM is released
@@ -247,12 +253,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           !mbar_wait(&sm->opfree[o], ((k / OSTAGES) - 1) & 1, args.err,
                      &sm->failed))
         break;
-      split_line_half(sm->raw[s][0], sm->op[o][0], sm->op[o][2], c_line, half);
-      split_line_half(sm->raw[s][1], sm->op[o][1], sm->op[o][3], c_line, half);
-      // the raw reads before the next TMA write of this stage, the operand
-      // writes before the MMAs read them (both across the async proxy)
+      split_line_half(sm->raw[s][0], sm->op[o][0], c_line, half);
+      split_line_half(sm->raw[s][1], sm->op[o][1], c_line, half);
+      // the lo writes before the MMAs read them, and the raw reads before the
+      // TMA refill that follows those MMAs (both across the async proxy)
       fence_proxy_async();
-      mbar_arrive(&sm->rawfree[s]);
       mbar_arrive(&sm->opfull[o]);
     }
   } else {
@@ -372,8 +377,7 @@ bool gram_tc_pairs_eligible(int64_t N, int m, const Blocks<float>& A,
 // less 1 % per extra wave (each wave refills the pipelines). Every CTA of a
 // launch does the same work, so with one slice per tile a launch of 164
 // tiles would run a second wave of 12 CTAs as long as the first.
-static int tc_splits(int64_t N, int tiles, int max_splits) {
-  const int sms = sm_count();
+static int tc_splits(int64_t N, int tiles, int max_splits, int sms) {
   const int64_t by_rows = ceil_div(N, (int64_t)BK * kMinStages);
   const int smax = (int)std::max<int64_t>(
       1, std::min<int64_t>({by_rows, (int64_t)8 * sms / tiles,
@@ -395,7 +399,7 @@ static int tc_splits(int64_t N, int tiles, int max_splits) {
 
 size_t gram_tc_partials_doubles(int64_t N, int m, int n, int skipped_tiles) {
   const int tiles = ceil_div(m, BM) * ceil_div(n, BN) - skipped_tiles;
-  return (size_t)tc_splits(N, std::max(1, tiles), 1 << 30) * m * n;
+  return (size_t)tc_splits(N, std::max(1, tiles), 1 << 30, sm_count()) * m * n;
 }
 
 void gram_tc(int64_t N, int m, const float* A, const Blocks<float>& B,
@@ -432,7 +436,13 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
       ++tiles;
     }
   }
-  int splits = tc_splits(N, tiles, max_splits > 0 ? max_splits : 1 << 30);
+  // within a CTA budget (a solve sharing the GPU) never more slices than
+  // with every SM, which the partials buffers are sized for
+  const int sfull = tc_splits(N, tiles, max_splits > 0 ? max_splits : 1 << 30,
+                              sm_count());
+  int splits = cta_budget() < sm_count()
+                   ? tc_splits(N, tiles, sfull, cta_budget())
+                   : sfull;
   int64_t rows = (N + splits - 1) / splits;
   rows = ((rows + BK - 1) / BK) * BK;
   splits = (int)((N + rows - 1) / rows);

