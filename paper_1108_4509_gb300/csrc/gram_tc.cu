@@ -436,13 +436,8 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
       ++tiles;
     }
   }
-  // within a CTA budget (a solve sharing the GPU) never more slices than
-  // with every SM, which the partials buffers are sized for
-  const int sfull = tc_splits(N, tiles, max_splits > 0 ? max_splits : 1 << 30,
-                              sm_count());
-  int splits = cta_budget() < sm_count()
-                   ? tc_splits(N, tiles, sfull, cta_budget())
-                   : sfull;
+  int splits = tc_splits(N, tiles, max_splits > 0 ? max_splits : 1 << 30,
+                         sm_count());
   int64_t rows = (N + splits - 1) / splits;
   rows = ((rows + BK - 1) / BK) * BK;
   splits = (int)((N + rows - 1) / rows);
