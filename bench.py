@@ -116,6 +116,10 @@ def parse():
     ap.add_argument("--large", type=int, default=1,
                     help="also time one mixed solve of the 96^3, m = 512 "
                          "workload and the FP64 path's time per iteration")
+    ap.add_argument("--accuracy", type=int, default=0,
+                    help="instead of the benchmark: each precision mode's "
+                         "accuracy against the oracle's references at "
+                         "m = 16, 128, 512")
     ap.add_argument("--clocks", type=int, default=1,
                     help="sample nvidia-smi clocks during the timed region "
                          "(0 under a profiler, which should see no other "
@@ -684,7 +688,62 @@ def run_extras(args):
         run_generalized(args, torch, trm, stream)
     if args.chain > 0:
         run_chain(args, torch, trm, stream)
+    if args.accuracy:
+        run_accuracy(args, torch, trm, stream)
     return 0
+
+
+def run_accuracy(args, torch, trm, stream):
+    """Accuracy of each precision mode of Sec. 2.2 against the oracle's
+    references (Sec. 4's claims: full SP is not accurate enough, MP2 keeps
+    near-DP accuracy): for m = 16, 128, 512 (the 16^3, 48^3 and 96^3
+    workloads), each mode's E_G relative error, max |lambda_j - ref_j| and
+    Davis-Kahan bound on the largest principal angle, ||H C - C diag(lambda)||_2
+    / (lambda_ref_{m+1} - lambda_m), with the residual formed on the host by
+    the oracle's H; and the solve time. The all-FP64 solve of the 96^3 case
+    (about half an hour) is left out."""
+    import numpy as np
+    import trm_inputs as ti
+    from oracle import operator as op
+    gold = load_json(GOLDEN, {})
+    modes = {"FP64": trm.TRM_FP64, "MP2": trm.TRM_MP2,
+             "FULL_SP": trm.TRM_FULL_SP, "MIXED": trm.TRM_MIXED}
+    rows = []
+    for name in ("grid16_o2_w8_m16", "grid48_o4_w64_m128",
+                 "grid96_o4_w512_m512"):
+        g = gold.get(name)
+        if not g:
+            continue
+        w = ti.workload(name, seed=g["seed"])
+        V = w.potential()
+        H = op.grid_hamiltonian(w.shape, w.order, w.h, V)
+        ref = np.array(g["lambdas"])
+        lam_m1 = g.get("lambda_m1")
+        for mode, code in modes.items():
+            if mode == "FP64" and w.m > 128:
+                continue
+            with trm.Solver.stencil(w.shape, w.order, w.h, V, w.m, 1e-10,
+                                    precision=code, precond=1,
+                                    seed=w.seed + 100,
+                                    stream=stream.cuda_stream) as s:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lam, eg, C, st, status = s.solve()
+                t = time.perf_counter() - t0
+            R = op.apply_h(H, C) - C * lam[None, :]
+            RtR = R.T @ R
+            r2 = float(np.sqrt(max(np.linalg.eigvalsh(0.5 * (RtR + RtR.T))[-1], 0)))
+            del R
+            rows.append({"workload": name, "m": w.m, "mode": mode,
+                         "status": status, "iterations": st["iterations"],
+                         "seconds": t,
+                         "rel_err_E_G": abs(eg - g["E_G"]) / abs(g["E_G"]),
+                         "max_abs_err_lambda": float(np.max(np.abs(lam - ref))),
+                         "sin_angle_bound": (r2 / (lam_m1 - lam[-1])
+                                             if lam_m1 else None),
+                         "max_residual": st["max_residual"]})
+            print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"accuracy": rows}))
 
 
 LARGE = "grid96_o4_w512_m512"
@@ -769,7 +828,7 @@ def main():
     args = parse()
     if args.serving > 0:
         return run_serving(args)
-    if args.generalized > 0 or args.chain > 0:
+    if args.generalized > 0 or args.chain > 0 or args.accuracy:
         return run_extras(args)
     if args.impl == "reference":
         return run_reference(args)

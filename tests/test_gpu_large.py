@@ -15,11 +15,12 @@ Tolerances: H C entries are sums of at most 13 products, so the FP64 path is
 held to 32 u64 sum|H_ik||c_k| and the FP32 path to 32 u32 sum|H_ik||c_k|
 (inputs and coefficients rounded to FP32 included). H_D is an FP64 sum of N
 products: gamma_N(u64) sum_i |c_i||(H c)_i|. The tensor-core Gram splits each
-FP32 value into two TF32 terms (residual 2^-22) and accumulates chunks of 4
-stages (48 MMA steps, each dropping up to 2^-23 of the running sum) before
-folding them into a double-float sum: |error| <= (48 * 2^-23 + 3 * 2^-21)
-sum|a_i||b_i| < 8e-6 sum|a_i||b_i|; a wrong tile, index or operand is off by
-O(1) of that sum.
+FP32 value into two TF32 terms (hi the value truncated to TF32, lo rounded:
+the dropped lo.lo and the roundings stay below 2^-19 of |a b|) and
+accumulates chunks of 4 stages (48 MMA steps, each dropping up to 2^-23 of
+the running sum) before folding them into a double-float sum: |error| <=
+(48 * 2^-23 + 2^-19) sum|a_i||b_i| < 8e-6 sum|a_i||b_i|; a wrong tile, index
+or operand is off by O(1) of that sum.
 """
 import numpy as np
 import pytest
