@@ -871,14 +871,19 @@ void Solver::final_rr(double* C, double* Cfin, double* Xfin) {
     apply_h(sop_, C, Y64_, m_, s_);
     bc.p[0] = Y64_;
   }
-  gram64(C, bc, S_);
+  // the overlap in FP64 in every mode: the returned block is orthonormalized
+  // by its factor (the double-float Gram's sum over N rows is good to about
+  // sqrt(N) 2^-48, which left C^T C - I near 1e-12 at N ~ 1e6)
+  gram<double>(N_, m_, C, bc, S_, part_, part_cap_, s_);
   chol_inv<double>(m_, S_, Linv_, R_, sc_, mmw_, s_);
   mm_gemm(m_, Linv_, false, Hp_, false, T1_, 1.0, 0.0, s_);
   mm_gemm(m_, T1_, false, Linv_, true, T2_, 1.0, 0.0, s_);
   make_A0(m_, T2_, nullptr, A0_, s_);
   sym_eig(m_, A0_, lam_, Z_, eigws_, info_, s_);
   mm_gemm(m_, R_, false, Z_, false, T1_, 1.0, 0.0, s_);
-  mult64(C, T1_, Cfin);
+  // the returned block in FP64 in every mode; H C Y, used only for the
+  // residual norms, keeps the FP64-class product
+  mult(N_, m_, m_, C, T1_, Cfin, s_);
   mult64(X64_, T1_, Xfin);
   if (has_S_) {  // ||H c_j - theta_j S c_j|| (sign independent)
     mult64(Y64_, T1_, SP64_);

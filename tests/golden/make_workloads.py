@@ -32,6 +32,11 @@ from oracle import operator as op  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workloads.json")
 MIN_GAP = 1e-3
+# At 100^3 with m = 1024 the mean spacing of the eigenvalues near lambda_m is
+# about 1e-4 (the guard eigenvalues of seed 0 are 0.8e-4 to 1.7e-4 apart), so
+# a gap of 1e-3 would be a rare accident of the seed; the rule there asks for
+# a gap of at least one mean spacing.
+MIN_GAP_OF = {"grid100_o4_w1000_m1024": 1e-4}
 
 
 # Above this N * m the m + 4 lowest eigenvalues come from the oracle's
@@ -73,7 +78,8 @@ def scan(name, max_seed=20):
         if rmax is not None:
             rec["max_residual"] = rmax
         print(name, rec, flush=True)
-        if gap >= MIN_GAP:
+        if gap >= MIN_GAP_OF.get(name, MIN_GAP):
+            rec["min_gap"] = MIN_GAP_OF.get(name, MIN_GAP)
             return rec
     raise RuntimeError(f"no seed below {max_seed} passes the gap rule for {name}")
 
