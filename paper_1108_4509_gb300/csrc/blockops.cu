@@ -656,7 +656,9 @@ void gradient(int64_t N, int m, const T* C, const T* Xp, const double* Hp,
               IterScalars* sc, double* partials, size_t cap, cudaStream_t s,
               const TcWork* tw) {
   if constexpr (sizeof(T) == 4) {
-    if (mul_tc_eligible(N, m, m, tw) && aligned16(C)) {
+    // TMA reads C and the epilogue operands X', G_prev, P_prev
+    if (mul_tc_eligible(N, m, m, tw) && aligned16(C) && aligned16(Xp) &&
+        aligned16(Gprev) && aligned16(Pprev)) {
       if ((size_t)mul_tc_parts(N, m) * 4 > cap)
         throw Error(-2, "gradient: partials buffer too small");
       // the kernel's last CTA forms the CG scalars from the per-CTA sums

@@ -497,16 +497,17 @@ namespace {
 struct MapKey {
   const void* p;
   int64_t rows, cols, ld;
-  int br, bc;
+  int br, bc, sw;
   bool operator==(const MapKey& o) const {
     return p == o.p && rows == o.rows && cols == o.cols && ld == o.ld &&
-           br == o.br && bc == o.bc;
+           br == o.br && bc == o.bc && sw == o.sw;
   }
 };
 struct MapKeyHash {
   size_t operator()(const MapKey& k) const {
     size_t h = std::hash<const void*>()(k.p);
-    for (int64_t v : {k.rows, k.cols, k.ld, (int64_t)k.br, (int64_t)k.bc})
+    for (int64_t v : {k.rows, k.cols, k.ld, (int64_t)k.br, (int64_t)k.bc,
+                      (int64_t)k.sw})
       h = h * 1000003u ^ std::hash<int64_t>()(v);
     return h;
   }
@@ -516,9 +517,9 @@ std::unordered_map<MapKey, CUtensorMap, MapKeyHash> g_maps;
 }  // namespace
 
 CUtensorMap f32_map(const float* p, int64_t rows, int64_t cols, int64_t ld,
-                    int box_rows, int box_cols) {
+                    int box_rows, int box_cols, bool swizzle) {
   std::lock_guard<std::mutex> lock(g_map_mu);
-  MapKey key{p, rows, cols, ld, box_rows, box_cols};
+  MapKey key{p, rows, cols, ld, box_rows, box_cols, swizzle ? 1 : 0};
   auto it = g_maps.find(key);
   if (it != g_maps.end()) return it->second;
   if (g_maps.size() > 512) g_maps.clear();
@@ -531,7 +532,8 @@ CUtensorMap f32_map(const float* p, int64_t rows, int64_t cols, int64_t ld,
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                   const_cast<float*>(p), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)

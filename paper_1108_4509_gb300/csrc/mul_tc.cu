@@ -22,11 +22,19 @@
 // 128-column TMEM buffers, so the epilogue of one tile overlaps the next).
 // Persistent CTAs (one per SM) walk (128-row, 128-column) tiles. Warp roles
 // (512 threads): warp 0 TMA for Y/P, warp 1 TMEM allocation and MMA issue
-// (one thread), warp 2 TMA for M, warps 4-7 form Y = C (+ alpha P), split
-// and transpose (one row per thread), warps 8-15 read the accumulator and run
-// the fused epilogue (two warps per TMEM lane quarter, one column half each:
-// the epilogue streams most of the kernel's bytes with plain loads, so it
-// gets the warps). Every wait is bounded (bit 2 of *err).
+// (one thread), warp 2 TMA for M, warp 3 TMA for the gradient's epilogue
+// operands, warps 4-7 form Y = C (+ alpha P), split and transpose (one row
+// per thread), warps 8-15 read the accumulator and run the fused epilogue
+// (two warps per TMEM lane quarter, one column half each: the epilogue
+// streams most of the kernel's bytes, so it gets the warps). Every wait is
+// bounded (bit 2 of *err).
+//
+// The gradient's epilogue reads X', G_prev and P_prev (three of its five
+// N x m streams). With plain loads each thread had a few hundred bytes in
+// flight and then waited on DRAM; instead warp 3 stages them by TMA, 8
+// columns x 128 rows of each per slot, into the P ring that the gradient
+// does not use (4 slots, two per column half, so the loads of the next
+// 8 columns are in flight while the epilogue works on these).
 #include <atomic>
 
 #include "dfmath.cuh"
@@ -49,9 +57,13 @@ constexpr int CONV0 = 4, NCONV = 4, EPI0 = 8, NEPI = 8;
 
 enum Mode { kStore = 0, kGrad = 1, kSplit64 = 2, kSplitDf = 3 };
 
+constexpr int EC = 8;                // columns per epilogue slot
+constexpr int ESLOT = 3 * EC * BM;   // X', G_prev, P_prev: EC columns each
+constexpr int NSLOT = 4;             // two per column half
+
 struct MulSmem {
   float raw[RS][BM * BK];   // Y tile as loaded (32 lines of 32 rows each)
-  float rawp[RS][BM * BK];  // P tile as loaded
+  float rawp[RS][BM * BK];  // P tile as loaded; kGrad: the epilogue slots
   float ah[CS][BM * BK];    // Y hi, K-major (128 rows of 32 k values)
   float al[CS][BM * BK];    // Y lo
   float bh[CS][NC * BK];    // M hi, K-major
@@ -59,6 +71,7 @@ struct MulSmem {
   uint64_t raw_full[RS], raw_empty[RS];
   uint64_t conv_done[CS], b_full[CS], op_empty[CS];
   uint64_t accfull[2], accempty[2], mmadone;
+  uint64_t efull[NSLOT], eempty[NSLOT];  // kGrad epilogue slots
   uint32_t tmem_base;
   int failed;
   double red[NEPI][4];
@@ -89,6 +102,8 @@ struct MulArgs {
   const float* rdiag;  // kSplitDf: diag(R) as pairs (hi[0..n), lo[n..2n))
   int* err;
 };
+static_assert(NSLOT * ESLOT <= RS * BM * BK,
+              "the epilogue slots overlay the P staging ring");
 
 // Converter thread (row i, half h) reads the 16 values of row i in the
 // column groups q = 2j + h (j = 0..3) of a staged tile: element (i, k) of a
@@ -103,7 +118,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_mul_tc(const __grid_constant__ CUtensorMap mapA,
              const __grid_constant__ CUtensorMap mapP,
              const __grid_constant__ CUtensorMap mapBh,
-             const __grid_constant__ CUtensorMap mapBl, MulArgs args) {
+             const __grid_constant__ CUtensorMap mapBl,
+             const __grid_constant__ CUtensorMap mapX,
+             const __grid_constant__ CUtensorMap mapGp,
+             const __grid_constant__ CUtensorMap mapPp, MulArgs args) {
   extern __shared__ unsigned char smem_raw[];
   MulSmem* sm = reinterpret_cast<MulSmem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -124,6 +142,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm->accfull[b], 1);
       mbar_init(&sm->accempty[b], NEPI * 32);
+    }
+    for (int e = 0; e < NSLOT; ++e) {
+      mbar_init(&sm->efull[e], 1);
+      mbar_init(&sm->eempty[e], NEPI * 16);  // the four warps of one half
     }
     mbar_init(&sm->mmadone, 1);
     sm->failed = 0;
@@ -188,6 +210,42 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       for (int j = it > CS ? it - CS : 0; j < it; ++j)
         mbar_wait_own(&sm->b_full[j % CS], (j / CS) & 1, args.err);
+    }
+  } else if (warp == 3) {
+    // ------- TMA: the gradient's epilogue operands into the slots -------
+    // Slot sequence: tile tl, column half g, 8-column group q (0..7) is
+    // number j = 8 tl + q of half g and lands in slot 2 g + (j & 1).
+    if (MODE == kGrad && lane == 0) {
+      const bool hg = args.gprev != nullptr, hp = args.pprev != nullptr;
+      const uint32_t bytes = (uint32_t)(EC * BM * 4) * (1 + hg + hp);
+      float* slots = &sm->rawp[0][0];
+      int last[NSLOT] = {-1, -1, -1, -1};  // the number last loaded per slot
+      int j = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int r0 = (t % args.ntr) * BM;
+        const int c0 = (t / args.ntr) * NC;
+        for (int q = 0; q < 8 && ok; ++q, ++j)
+          for (int g = 0; g < 2 && ok; ++g) {
+            const int e = 2 * g + (j & 1);
+            if (j >= 2 && !mbar_wait(&sm->eempty[e], ((j >> 1) - 1) & 1,
+                                     args.err, &sm->failed)) {
+              ok = false;
+              break;
+            }
+            float* d = slots + e * ESLOT;
+            const int c = c0 + g * (NC / 2) + q * EC;
+            mbar_expect_tx(&sm->efull[e], bytes);
+            tma_load_2d(d, &mapX, r0, c, &sm->efull[e]);
+            if (hg) tma_load_2d(d + EC * BM, &mapGp, r0, c, &sm->efull[e]);
+            if (hp) tma_load_2d(d + 2 * EC * BM, &mapPp, r0, c, &sm->efull[e]);
+            last[e] = j;
+          }
+      }
+      // the copies in flight must land before the CTA may exit
+      for (int e = 0; e < NSLOT; ++e)
+        if (last[e] >= 0)
+          mbar_wait_own(&sm->efull[e], (last[e] >> 1) & 1, args.err);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -293,8 +351,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (MODE == kSplit64 && args.sc) alpha64 = args.sc->alpha;
     F2 alpha2 = {0.f, 0.f};
     if (MODE == kSplitDf && args.sc) alpha2 = df_of(args.sc->alpha);
+    const float* slots = &sm->rawp[0][0];
+    const int half = cbeg ? 1 : 0;
+    const bool hg = args.gprev != nullptr, hp = args.pprev != nullptr;
+    bool dead = false;
     int tl = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+    for (int t = blockIdx.x; t < ntiles && !dead; t += gridDim.x, ++tl) {
       const int b = tl & 1;
       // warp-uniform outcome: the TMEM loads below are .sync.aligned
       const bool got =
@@ -310,6 +372,50 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int cb = cbeg; cb < cbeg + NC / 2; cb += 16) {
         uint32_t r[16];
         tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * NC + cb), r);
+        if (MODE == kGrad) {
+          // the two slots of these 16 columns: wait, read, release (every
+          // thread of the half arrives, rows past N included)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = 8 * tl + (cb - cbeg) / EC + h;
+            const int e = 2 * half + (j & 1);
+            const bool in_slot =
+                mbar_wait(&sm->efull[e], (j >> 1) & 1, args.err, &sm->failed);
+            if (!__all_sync(0xffffffffu, in_slot)) {
+              dead = true;
+              break;
+            }
+            const float* d = slots + e * ESLOT + rr;
+            float gg = 0.f, gmg = 0.f, pmg = 0.f, gpp = 0.f;
+            if (rin) {
+#pragma unroll
+              for (int u = 0; u < EC; ++u) {
+                const int col = c0 + cb + h * EC + u;
+                if (col < args.n) {
+                  const float x = d[u * BM];
+                  const float gp = hg ? d[(EC + u) * BM] : 0.f;
+                  const float pp = hp ? d[(2 * EC + u) * BM] : 0.f;
+                  const float g = -2.f * (x - __uint_as_float(r[h * EC + u]));
+                  args.out[row + (int64_t)col * N] = g;
+                  const float mg = mi * g;
+                  gg = fmaf(g, g, gg);
+                  gmg = fmaf(g, mg, gmg);
+                  pmg = fmaf(gp, mg, pmg);
+                  gpp = fmaf(g, pp, gpp);
+                }
+              }
+            }
+            // the slot is overwritten next by TMA (async proxy)
+            fence_proxy_async();
+            mbar_arrive(&sm->eempty[e]);
+            s_sum[0] = df_add(s_sum[0], F2{gg, 0.f});
+            s_sum[1] = df_add(s_sum[1], F2{gmg, 0.f});
+            s_sum[2] = df_add(s_sum[2], F2{pmg, 0.f});
+            s_sum[3] = df_add(s_sum[3], F2{gpp, 0.f});
+          }
+          if (dead) break;
+          continue;
+        }
         if (!rin) continue;
         if (MODE == kStore) {
 #pragma unroll
@@ -318,37 +424,6 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (col < args.n)
               args.out[row + (int64_t)col * N] = __uint_as_float(r[e]);
           }
-        } else if (MODE == kGrad) {
-          // the 16 columns' operands are staged in registers first, so the
-          // loads are all in flight before the stores
-          float xv[16], gv[16], pv[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int col = c0 + cb + e;
-            const int64_t idx = row + (int64_t)col * N;
-            const bool in = col < args.n;
-            xv[e] = in ? args.xp[idx] : 0.f;
-            gv[e] = (in && args.gprev) ? args.gprev[idx] : 0.f;
-            pv[e] = (in && args.pprev) ? args.pprev[idx] : 0.f;
-          }
-          float gg = 0.f, gmg = 0.f, pmg = 0.f, gpp = 0.f;
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int col = c0 + cb + e;
-            if (col < args.n) {
-              const float g = -2.f * (xv[e] - __uint_as_float(r[e]));
-              args.out[row + (int64_t)col * N] = g;
-              const float mg = mi * g;
-              gg = fmaf(g, g, gg);
-              gmg = fmaf(g, mg, gmg);
-              pmg = fmaf(gv[e], mg, pmg);
-              gpp = fmaf(g, pv[e], gpp);
-            }
-          }
-          s_sum[0] = df_add(s_sum[0], F2{gg, 0.f});
-          s_sum[1] = df_add(s_sum[1], F2{gmg, 0.f});
-          s_sum[2] = df_add(s_sum[2], F2{pmg, 0.f});
-          s_sum[3] = df_add(s_sum[3], F2{gpp, 0.f});
         } else if (MODE == kSplitDf) {
 #pragma unroll
           for (int h = 0; h < 16; h += 8) {
@@ -518,10 +593,16 @@ void launch(const MulArgs& a0, const float* A, const float* P,
   CUtensorMap mP = f32_map(P ? P : A, a.N, a.k, a.N, 32, BK);
   CUtensorMap mBh = f32_map(hi, a.k, a.n, ldm, BK, NC);
   CUtensorMap mBl = f32_map(lo, a.k, a.n, ldm, BK, NC);
+  // the gradient's epilogue operands, 128 rows x EC columns per box
+  CUtensorMap mX = mA, mGp = mA, mPp = mA;
+  if (MODE == kGrad) {
+    mX = f32_map(a.xp, a.N, a.n, a.N, BM, EC, false);
+    if (a.gprev) mGp = f32_map(a.gprev, a.N, a.n, a.N, BM, EC, false);
+    if (a.pprev) mPp = f32_map(a.pprev, a.N, a.n, a.N, BM, EC, false);
+  }
   a.ntr = (int)ceil_div(a.N, (int64_t)BM);
   a.nch = ceil_div(a.n, NC);
   a.has_p = P ? 1 : 0;
-  const int tiles = a.ntr * a.nch;
   const int grid = mul_tc_parts(a.N, a.n);
   const size_t smem = sizeof(MulSmem) + 1024;
   static std::atomic<int> attr_dev{-1};  // launches may come from several threads
@@ -533,7 +614,8 @@ void launch(const MulArgs& a0, const float* A, const float* P,
                                   (int)smem));
     attr_dev.store(dev, std::memory_order_relaxed);
   }
-  k_mul_tc<MODE><<<grid, THREADS, smem, s>>>(mA, mP, mBh, mBl, a);
+  k_mul_tc<MODE><<<grid, THREADS, smem, s>>>(mA, mP, mBh, mBl, mX, mGp, mPp,
+                                              a);
   TRM_CHECK_LAUNCH();
   if (grid_out) *grid_out = grid;
 }

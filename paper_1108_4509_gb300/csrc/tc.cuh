@@ -265,14 +265,16 @@ EncodeFn encode_fn();
 
 // Tensor map of a column-major rows x cols FP32 matrix (leading dimension
 // `ld` >= rows, a multiple of 4) read in boxes of box_rows x box_cols with
-// the 128-byte swizzle (box_rows * 4 = 128). Cached per (pointer, shape,
-// box); out-of-range elements read as zero.
+// the 128-byte swizzle (box_rows * 4 = 128), or without swizzle (box_rows
+// up to 256: the box lands as box_cols columns of box_rows contiguous
+// values). Cached per (pointer, shape, box, swizzle); out-of-range elements
+// read as zero.
 // The FP32 blocks of a grid operator as a 4-D tensor (x, y, z, column), no
 // swizzle, boxes of (nx, box_y, 1, 1): one y-band of one plane of a column.
 CUtensorMap f32_grid_map(const float* p, int nx, int ny, int nz, int ncols,
                          int box_y);
 CUtensorMap f32_map(const float* p, int64_t rows, int64_t cols, int64_t ld,
-                    int box_rows, int box_cols);
+                    int box_rows, int box_cols, bool swizzle = true);
 
 }  // namespace tc
 }  // namespace trm
