@@ -137,16 +137,11 @@ __device__ void line_alpha_block(int m, const double* __restrict__ part,
 // diagonal y_cc = -f_cc / (1 + f_cc). When S - I is small, FP32 arithmetic
 // here yields L to FP64 accuracy relative to I.
 // ---------------------------------------------------------------------------
-// Square root and reciprocal of the pivot chain by Newton's method from the
-// hardware approximations (rsqrt, reciprocal): one step in FP32, two from
-// the FP32 seed in FP64. Arguments are positive normal numbers (the pivot
+// Reciprocal square root and reciprocal of the pivot chain by Newton's
+// method from the hardware approximations (rsqrt, reciprocal): one step in
+// FP32, two from the FP32 seed in FP64. Arguments are positive normal numbers (the pivot
 // tests come first); the results are within a few ulp, and the chain stays
 // free of the slow-path calls of the IEEE operations.
-__device__ __forceinline__ float piv_sqrt(float t) {
-  const float r = rsqrtf(t);
-  const float s = t * r;
-  return fmaf(0.5f * r, fmaf(-s, s, t), s);
-}
 __device__ __forceinline__ float piv_rcp(float t) {
   const float r = __fdividef(1.0f, t);
   return fmaf(r, fmaf(-t, r, 1.0f), r);
@@ -167,12 +162,75 @@ __device__ __forceinline__ double piv_rsqrt(double t) {
   r = r * fma(-0.5 * t * r, r, 1.5);
   return r * fma(-0.5 * t * r, r, 1.5);
 }
-__device__ __forceinline__ double piv_sqrt(double t) {
-  double r = (double)rsqrtf((float)t);
-  r = r * fma(-0.5 * t * r, r, 1.5);
-  r = r * fma(-0.5 * t * r, r, 1.5);
-  const double s = t * r;
-  return fma(0.5 * r, fma(-s, s, t), s);
+
+// Cholesky of a 32 x 32 diagonal block on one warp (Fig. ONFIG step (2)
+// restricted to the block). Lane r holds row r of the block in w (w[j] =
+// entry (r, j), meaningful for j <= r) and ends with row r of L (of F in
+// deviation form, L = I + F); rd[c] = 1 / L_cc. The pivot of column c comes
+// from lane c by a shuffle and the entries L_jc (j > c) of the rank-1 update
+// from lanes j, so the 32 steps need no barrier. Entries above the diagonal
+// are updated too and never read. thr: the pivot floor of column `lane`
+// (plain form). Returns true when a pivot was not positive (singular S).
+// Used by the blocked factorisation's diagonal kernel; the single-CTA
+// kernel keeps its eight-warp column steps, which measured faster there
+// (10.5K against 12.3K cycles per 32-column panel at m = 128: one warp
+// issues all 31 - c shuffles of a step by itself).
+template <typename Tm, bool dev>
+__device__ __forceinline__ bool diag_factor_warp(Tm (&w)[32], Tm thr, Tm* rd) {
+  const int lane = threadIdx.x & 31;
+  bool b = false;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    Tm d = __shfl_sync(0xffffffffu, w[c], c);
+    Tm rl;
+    if (dev) {
+      if (!(d > (Tm)-0.999)) {  // pivot 1 + d not positive
+        b = true;
+        d = (Tm)0;
+      }
+      rl = piv_rsqrt((Tm)1 + d);
+    } else {
+      if (!(d > __shfl_sync(0xffffffffu, thr, c))) {
+        b = true;
+        d = (Tm)1;
+      }
+      rl = piv_rsqrt(d);
+    }
+    const Tm l = lane > c ? w[c] * rl : w[c];  // L_rc for r > c
+    if (lane == 0) rd[c] = rl;
+    // L_cc (deviation form: L_cc - 1 = d / (1 + sqrt(1 + d)), with
+    // sqrt(1 + d) = (1 + d) rl, which keeps small d accurate)
+    w[c] = lane == c ? (dev ? d * piv_rcp((Tm)1 + ((Tm)1 + d) * rl) : d * rl)
+                     : l;
+#pragma unroll
+    for (int j = c + 1; j < 32; ++j) w[j] -= l * __shfl_sync(0xffffffffu, l, j);
+  }
+  return b;
+}
+
+// X = L^{-1} of a 32 x 32 lower-triangular diagonal block (Fig. ONFIG step
+// (3) restricted to the block): L in shared memory at B[i + k ldb], rd[i] =
+// 1 / L_ii. Lane j forms column j of X in x by forward substitution,
+// x_ij = (delta_ij - sum_{k=j}^{i-1} L_ik x_kj) / L_ii, with the column in
+// registers and the rows of L read as broadcasts (x_kj = 0 for k < j, so
+// the sums run over all k < i). Deviation form (L = I + F, X = I + Y):
+// y_jj = -f_jj / (1 + f_jj), y_ij = -(f_ij + sum_k f_ik y_kj) / (1 + f_ii).
+template <typename Tm, bool dev>
+__device__ __forceinline__ void diag_inverse_warp(const Tm* B, int ldb,
+                                                  const Tm* rd, Tm (&x)[32]) {
+  const int j = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    Tm s0 = (dev && i > j) ? B[i + j * ldb] : (Tm)0, s1 = 0;
+#pragma unroll
+    for (int k = 0; k < i; ++k) {
+      if (k & 1) s1 += B[i + k * ldb] * x[k];
+      else s0 += B[i + k * ldb] * x[k];
+    }
+    const Tm r = rd[i];
+    x[i] = i == j ? (dev ? -B[i + i * ldb] * r : r)
+                  : (i > j ? -(s0 + s1) * r : (Tm)0);
+  }
 }
 
 // 256 threads: the register-resident rows of the diagonal-block steps need
@@ -549,93 +607,49 @@ __global__ void k_cb_form(int m, int mp, const double* __restrict__ S,
   }
 }
 
-// Factor and invert the 32 x 32 diagonal block of panel p (one CTA of 256
-// threads; the column steps of k_chol_inv's phase (a), the substitution of
-// its phase (d)). Writes the block of L (F in deviation form; zeros above
-// the diagonal) and of X = L^{-1} (Y in deviation form).
+// Factor and invert the 32 x 32 diagonal block of panel p: warp 0 runs
+// diag_factor_warp and diag_inverse_warp; all 256 threads write the inverse.
+// Writes the block of L (F in deviation form; zeros above the diagonal) and
+// of X = L^{-1} (Y in deviation form).
 template <typename Tm, bool dev>
 __global__ void __launch_bounds__(256, 1)
     k_cb_diag(int m, int mp, int p, const double* __restrict__ S,
               bool from_S, const Tm* __restrict__ W, Tm* __restrict__ L,
               Tm* __restrict__ X, int* bad) {
-  __shared__ Tm colbuf[2][32];
-  __shared__ Tm B[32][33];
+  __shared__ Tm B[32 * 33];  // the block, column-major, leading dimension 33
   __shared__ Tm rd[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c0 = CB * p, r = c0 + lane;
   const Tm eps = sizeof(Tm) == 4 ? (Tm)1.2e-7 : (Tm)2.3e-16;
-  Tm v[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) v[q] = W[r + (size_t)(c0 + warp + 8 * q) * mp];
-  bool b = false;
-#pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    const int q = c >> 3;
-    if (warp == (c & 7)) {
-      Tm d = __shfl_sync(0xffffffffu, v[q], c);
-      Tm rl;
-      if (dev) {
-        if (!(d > (Tm)-0.999)) {  // pivot 1 + d not positive: singular S
-          b = true;
-          d = (Tm)0;
-        }
-        rl = piv_rsqrt((Tm)1 + d);
-      } else {
-        const int cc = c0 + c;
-        const double sjj =
-            (!from_S || cc >= m) ? 1.0 : fabs(S[cc + (int64_t)cc * m]);
-        if (!(d > (Tm)(4 * m) * eps * (Tm)sjj)) {
-          b = true;
-          d = (Tm)1;
-        }
-        rl = piv_rsqrt(d);
-      }
-      if (lane > c) v[q] *= rl;
-      colbuf[c & 1][lane] = v[q];
-      if (lane == 0) rd[c] = rl;
-      if (lane == c)
-        v[q] = dev ? d * piv_rcp((Tm)1 + ((Tm)1 + d) * rl) : d * rl;
-    }
-    __syncthreads();
-    const Tm lrc = colbuf[c & 1][lane];
-#pragma unroll
-    for (int qq = 0; qq < 4; ++qq)
-      if (warp + 8 * qq > c) v[qq] -= lrc * colbuf[c & 1][warp + 8 * qq];
-  }
-  // the block of L (lower, zeros above) to global and to shared memory
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int c = warp + 8 * q;
-    const Tm x = lane >= c ? v[q] : (Tm)0;
-    L[r + (size_t)(c0 + c) * mp] = x;
-    B[lane][c] = x;
-  }
-  if (lane == 0 && b) atomicOr(bad, 1);
-  __syncthreads();
-  // inverse of the block, in place in B by forward substitution, one warp,
-  // lane j owns column j (as phase (d) of k_chol_inv)
   if (warp == 0) {
-    const int j = lane;
-    for (int i = 0; i < 32; ++i) {
-      Tm s0 = (dev && i > j) ? B[i][j] : (Tm)0, s1 = 0;
-      int k = j;
-      for (; k + 1 < i; k += 2) {
-        s0 += B[i][k] * B[k][j];
-        s1 += B[i][k + 1] * B[k + 1][j];
-      }
-      if (k < i) s0 += B[i][k] * B[k][j];
-      Tm x = 0;
-      if (i == j) x = dev ? -B[i][i] * rd[i] : rd[i];
-      else if (i > j) x = -(s0 + s1) * rd[i];
-      __syncwarp();
-      if (i >= j) B[i][j] = x;
-      __syncwarp();
+    Tm w[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) w[j] = W[r + (size_t)(c0 + j) * mp];
+    Tm thr = (Tm)0;
+    if (!dev) {
+      const double sjj = (!from_S || r >= m) ? 1.0 : fabs(S[r + (int64_t)r * m]);
+      thr = (Tm)(4 * m) * eps * (Tm)sjj;
     }
+    const bool b = diag_factor_warp<Tm, dev>(w, thr, rd);
+    // the block of L (lower, zeros above) to global and to shared memory
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const Tm x = lane >= j ? w[j] : (Tm)0;
+      L[r + (size_t)(c0 + j) * mp] = x;
+      B[lane + 33 * j] = x;
+    }
+    if (lane == 0 && b) atomicOr(bad, 1);
+    __syncwarp();
+    Tm x[32];
+    diag_inverse_warp<Tm, dev>(B, 33, rd, x);
+    __syncwarp();  // every lane has read L before the block is replaced
+#pragma unroll
+    for (int i = 0; i < 32; ++i) B[i + 33 * lane] = x[i];
   }
   __syncthreads();
   for (int e = tid; e < 32 * 32; e += 256) {
     const int i = e & 31, j = e >> 5;
-    X[(c0 + i) + (size_t)(c0 + j) * mp] = i >= j ? B[i][j] : (Tm)0;
+    X[(c0 + i) + (size_t)(c0 + j) * mp] = i >= j ? B[i + 33 * j] : (Tm)0;
   }
 }
 
