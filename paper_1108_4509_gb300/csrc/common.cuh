@@ -61,6 +61,25 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// FP32 -> FP64 on the integer pipe. The conversion instruction runs on the
+// FP64 pipe, where one warp instruction holds a sub-partition for about 64
+// cycles on this part; in the FP32 stencil a few conversions per warp kept
+// that pipe half busy. The sign, the exponent rebiased from 127 to 1023,
+// the 23 fraction bits moved to the top of the 52: exact for normal numbers,
+// zeros, infinities and NaN; FP32 subnormals (below 1.2e-38) become signed
+// zeros.
+__device__ __forceinline__ double to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long ex =
+      e == 0xFFu ? 0x7FFull : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(
+      sign | (ex << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
 // Sum of NQ values over the block (blockDim.x a multiple of 32, <= 1024).
 // Result valid in thread 0. scratch: >= 32*NQ doubles of shared memory.
 template <int NQ>

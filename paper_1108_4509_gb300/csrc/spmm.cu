@@ -68,7 +68,7 @@ constexpr int kCpb = 4;
 template <typename T>
 __device__ __forceinline__ void warp_dot(T d, double (*red)[8], int q) {
   d = warp_sum(d);
-  if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = (double)d;
+  if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = to_f64(d);
 }
 __device__ __forceinline__ void write_dots(double (*red)[8], double* dots,
                                            int cb, int ncols) {
@@ -109,7 +109,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1)
   const bool ym2 = y >= 2, yp2 = y + 2 < st.ny;
   const bool zm2 = z >= 2, zp2 = z + 2 < st.nz;
   const V4<T> d = ld4(diag_ptr<T>(d64, d32) + i0);
-  const T c1 = (T)st.c1, c2 = (T)st.c2;
+  // FP32 kernels take the coefficients the host rounded (no FP64 -> FP32
+  // conversion per thread on the FP64 pipe)
+  const T c1 = sizeof(T) == 4 ? (T)st.c1h : (T)st.c1;
+  const T c2 = sizeof(T) == 4 ? (T)st.c2h : (T)st.c2;
   const int cb = blockIdx.y * kCpb;
   // column dots stay in registers until after the column loop, so their
   // warp sums (dependent shuffles) do not hold up the next column's loads
@@ -179,7 +182,10 @@ __global__ void __launch_bounds__(256)
   const int z = (int)(yz / st.ny);
   const int64_t sy = st.nx, sz = (int64_t)st.nx * st.ny;
   const T d = diag_ptr<T>(d64, d32)[i];
-  const T c1 = (T)st.c1, c2 = (T)st.c2;
+  // FP32 kernels take the coefficients the host rounded (no FP64 -> FP32
+  // conversion per thread on the FP64 pipe)
+  const T c1 = sizeof(T) == 4 ? (T)st.c1h : (T)st.c1;
+  const T c2 = sizeof(T) == 4 ? (T)st.c2h : (T)st.c2;
   const int cb = blockIdx.y * kCpb;
   T dsum[kCpb];  // column dots, warp-summed after the column loop
 #pragma unroll
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(256)
   };
   if (tid == 0)
     for (int pz = first; pz < first + kPlanes && pz <= last; ++pz) issue(pz);
-  const float c1 = (float)st.c1, c2 = (float)st.c2;
+  const float c1 = st.c1h, c2 = st.c2h;  // rounded on the host
   F2 dacc = {0.f, 0.f};
   int waited = first - 1;  // last plane this thread saw land
   const int r = ry + kHalo;
@@ -430,9 +436,13 @@ __global__ void __launch_bounds__(256)
     for (int pz = waited + 1; pz <= issued; ++pz)
       tc::mbar_wait_own(&full[slot(pz)], phase(pz), err);
   if (DOTS) {
-    double v = (double)dacc.h + (double)dacc.l;
-    v = warp_sum(v);
-    if ((tid & 31) == 0) red[tid >> 5] = v;
+    // the warp sum in double-float on the FP32 pipe, one FP64 add per warp
+    F2 w = dacc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      w = df_add(w, F2{__shfl_xor_sync(0xffffffffu, w.h, o),
+                       __shfl_xor_sync(0xffffffffu, w.l, o)});
+    if ((tid & 31) == 0) red[tid >> 5] = to_f64(w.h) + to_f64(w.l);
     __syncthreads();
     if (tid == 0) {
       double t = 0.0;
