@@ -21,7 +21,9 @@ the headline steps), large (one timed mixed solve of the 96^3, m = 512
 workload, its E_G error against the oracle's reference, its per-class
 roofline from a short profiled solve, and the FP64 path's time per iteration
 extrapolated to a solve), cpu_baseline (the FP64 oracle on all host cores and
-on one, bounded samples scaled to a solve, with the host's nproc and CPU).
+on one, bounded samples scaled to a solve, with the host's nproc and CPU);
+with --xlarge 1, xlarge (a cold mixed solve of the 100^3, m = 1024 stencil
+and the same operator as an FP32/int32 CSR matrix warm-started from it).
 
 --impl reference times the oracle itself (the CPU program), bounded samples.
 
@@ -116,6 +118,11 @@ def parse():
     ap.add_argument("--large", type=int, default=1,
                     help="also time one mixed solve of the 96^3, m = 512 "
                          "workload and the FP64 path's time per iteration")
+    ap.add_argument("--xlarge", type=int, default=0,
+                    help="also time the 100^3, m = 1024 workload: a cold mixed "
+                         "solve of the stencil (about five minutes) and the "
+                         "same operator as an FP32/int32 CSR matrix solved "
+                         "from the stencil's converged block")
     ap.add_argument("--accuracy", type=int, default=0,
                     help="instead of the benchmark: each precision mode's "
                          "accuracy against the oracle's references at "
@@ -824,6 +831,62 @@ def run_large(args, torch, trm, sptr, peaks, src):
             "profiled": "first 60 iterations of the same solve, events around each launch"}
 
 
+XLARGE = "grid100_o4_w1000_m1024"
+
+
+def run_xlarge(args, torch, trm, sptr):
+    """The 100^3 grid, 13-point stencil + 1000 wells, m = 1024 (N = 10^6):
+    one timed cold mixed-precision solve of the stencil (iteration graphs,
+    after a 20-iteration warm-up solve), then the same operator as an
+    explicit CSR matrix (FP32 values, int32 columns) solved from the
+    stencil's converged block (a related request's warm start). E_G against
+    the oracle's filtered-subspace reference; the CSR values are the FP32
+    roundings, so its E_G differs from the reference by up to m 2^-24 10."""
+    import numpy as np
+    import trm_inputs as ti
+    g = load_json(GOLDEN, {}).get(XLARGE, {})
+    w = ti.workload(XLARGE, seed=int(g.get("seed", 0)))
+    V = w.potential()
+    E_ref = g.get("E_G")
+    opts = dict(precision=trm.TRM_MIXED, precond=1, seed=w.seed + 100,
+                stream=sptr)
+    stream = torch.cuda.current_stream()
+
+    def timed(solver, C0=None):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lam, eg, C, st, status = solver.solve(C0=C0)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3, eg, C, st, status
+
+    with trm.Solver.stencil(w.shape, w.order, w.h, V, w.m, args.tol,
+                            max_iter=20, **opts) as s:
+        s.solve(want_C=False)
+    with trm.Solver.stencil(w.shape, w.order, w.h, V, w.m, args.tol,
+                            **opts) as s:
+        t, eg, C, st, status = timed(s)
+    rp, ci, va = ti.grid_csr(w.shape, w.order, w.h, V, np.float32)
+    with trm.Solver.csr(w.N, rp, ci, va, w.m, args.tol, **opts) as s:
+        tc, egc, _, stc, statusc = timed(s, C0=C)
+    rel = (lambda e: abs(e - E_ref) / abs(E_ref)) if E_ref else (lambda e: None)
+    return {"workload": (f"{w.name}: {w.shape[0]}^3 grid, 13-point 4th-order "
+                         f"-1/2 nabla^2 + {w.nwells} Gaussian wells (seed "
+                         f"{w.seed}), m={w.m}, diagonal preconditioner"),
+            "N": w.N, "m": w.m, "tol_rms": args.tol, "E_G_ref": E_ref,
+            "E_G_ref_source": g.get("method"),
+            "stencil": {"seconds": t, "iterations": st["iterations"],
+                        "iterations_phase": st["iterations_phase"],
+                        "status": status, "E_G": eg, "rel_err_E_G": rel(eg)},
+            "csr_warm_start": {"seconds": tc, "iterations": stc["iterations"],
+                               "status": statusc, "E_G": egc,
+                               "rel_err_E_G": rel(egc),
+                               "nnz": int(rp[-1])},
+            "launch_mode": "each kind of iteration replayed as a CUDA graph"}
+
+
 def main():
     args = parse()
     if args.serving > 0:
@@ -964,6 +1027,13 @@ def main():
         except Exception as exc:  # reported, not fatal
             large = {"error": str(exc)[:300]}
 
+    xlarge = None
+    if args.xlarge and rank == 0:
+        try:
+            xlarge = run_xlarge(args, torch, trm, sptr)
+        except Exception as exc:  # reported, not fatal
+            xlarge = {"error": str(exc)[:300]}
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         try:
@@ -1000,6 +1070,7 @@ def main():
                        "three products hi.hi + hi.lo + lo.hi, FP32 accumulation "
                        "in tensor memory"},
                "large": large,
+               **({"xlarge": xlarge} if xlarge is not None else {}),
                "cpu_baseline": cpu}
         print(json.dumps(out))
     if dist:

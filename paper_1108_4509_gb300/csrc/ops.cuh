@@ -44,7 +44,8 @@ void apply_h(const Operator& op, const double* X, double* Y, int ncols,
              cudaStream_t s);
 // FP32 Y = H X with the column dot products sum_i X_ic Y_ic of each CTA in
 // dots[chunk * ncols + c] (apply_h_dots_doubles entries); returns the number
-// of chunks (energy_from_dots adds them up). (In FP64 the products would
+// of chunks (energy_from_dots adds them up). Y may be null: then only the
+// dots are formed (the line model needs tr(P^T H P), not H P). (In FP64 the products would
 // load the FP64 pipe the stencil is already bound by; energy_diag reads the
 // two blocks instead.)
 int apply_h_dots(const Operator& op, const float* X, float* Y, int ncols,

@@ -612,9 +612,11 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   const bool fused = !gen && line_grams_fusable<T>(C, P, G);
   int hp_chunks = 0;  // > 0: tr(P^T H P) from the stencil's column dots
   if constexpr (sizeof(T) == 4) {
+    // the fused line Grams need only tr(P^T H P): the stencil forms its
+    // column dots and writes no H P
     if (fused)
-      TRM_PROF(ksp, sfl, sby,
-               hp_chunks = apply_h_dots(op_, P, HP, m_, hpdots_, s_));
+      TRM_PROF(ksp, sfl, sby - es * nm,
+               hp_chunks = apply_h_dots(op_, P, nullptr, m_, hpdots_, s_));
   }
   if (!hp_chunks) TRM_PROF(ksp, sfl, sby, apply_h(op_, P, HP, m_, s_));  // H P
   if (gen) {
@@ -722,10 +724,10 @@ void Solver::iter_mp2() {
   const double* trp = nullptr;
   int ntrp = 0;
   size_t woff = mm;
-  if (fused) {  // H P with tr(P^T H P) as the stencil's column dots
+  if (fused) {  // tr(P^T H P) as the stencil's column dots, no H P written
     int chunks = 0;
-    TRM_PROF(KC_SPMM32, f32, b32,
-             chunks = apply_h_dots(op_, P, HP, m_, hpdots_, s_));
+    TRM_PROF(KC_SPMM32, f32, b32 - 4 * dnm,
+             chunks = apply_h_dots(op_, P, nullptr, m_, hpdots_, s_));
     trp = hpdots_;
     ntrp = chunks * m_;
     line_grams_fused<float>(Ch, P, G);

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1)
       }
       out.v[k] = acc;
     }
-    st4(Y + (int64_t)c * N + i0, out);
+    if (!DOTS || Y) st4(Y + (int64_t)c * N + i0, out);  // Y null: dots only
     if (DOTS)
       dsum[q] = xc.v[0] * out.v[0] + xc.v[1] * out.v[1] + xc.v[2] * out.v[2] +
                 xc.v[3] * out.v[3];
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256)
       if (z + 2 < st.nz) s2 += xp[2 * sz];
       acc += c2 * s2;
     }
-    Y[(int64_t)c * N + i] = acc;
+    if (!DOTS || Y) Y[(int64_t)c * N + i] = acc;
     if (DOTS) dsum[q] = xp[0] * acc;
   }
   if (DOTS) {
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int k = 0; k < kCsrCache; ++k)
           if (k < nnz) acc += cv[k] * __ldg(x + ci[k]);
-        Y[(int64_t)c * N + r] = acc;
+        if (!DOTS || Y) Y[(int64_t)c * N + r] = acc;
         d = x[r] * acc;
       }
       if (DOTS) warp_dot(d, red, q);
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(256)
         const T* x = X + (int64_t)c * N;
         T acc = 0;
         for (int k = b; k < e; ++k) acc += (T)vals[k] * __ldg(x + cols[k]);
-        Y[(int64_t)c * N + r] = acc;
+        if (!DOTS || Y) Y[(int64_t)c * N + r] = acc;
         d = x[r] * acc;
       }
       if (DOTS) warp_dot(d, red, q);
@@ -419,8 +419,9 @@ __global__ void __launch_bounds__(256)
         }
         out[k] = acc;
       }
-      *reinterpret_cast<float4*>(Y + (int64_t)col * N + i0) =
-          make_float4(out[0], out[1], out[2], out[3]);
+      if (!DOTS || Y)
+        *reinterpret_cast<float4*>(Y + (int64_t)col * N + i0) =
+            make_float4(out[0], out[1], out[2], out[3]);
       if (DOTS)
         dacc = df_add(dacc, F2{c[0] * out[0] + c[1] * out[1] +
                                    c[2] * out[2] + c[3] * out[3],
@@ -536,7 +537,9 @@ template <bool DOTS>
 bool use_planes(const Operator& op, const float* X, float* Y, int ncols,
                 double* dots, cudaStream_t s) {
   const StencilOp& st = op.st;
-  const TuneKey key{st.nx, st.ny, st.nz, st.radius, ncols, DOTS ? 1 : 0};
+  // (0: plain, 1: with dots, 2: dots only)
+  const TuneKey key{st.nx, st.ny, st.nz, st.radius, ncols,
+                    DOTS ? (Y ? 1 : 2) : 0};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(key);
