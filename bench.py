@@ -554,7 +554,10 @@ def _timed_solve(torch, trm, h, N, m, stream, C0=None, C_out=None):
 
 def run_generalized(args, torch, trm, stream):
     """FP64 solve of H e = lambda S e (13-point H with wells, S the 27-point
-    hat-function overlap) and of H e = lambda e on the same grid."""
+    hat-function overlap) and of H e = lambda e on the same grid; then the
+    generalized problem in the mixed ladder (full SP with S in FP32, then
+    FP64)."""
+    import numpy as np
     import trm_inputs as ti
     n, m = args.generalized, args.gen_m
     shape, N = (n, n, n), n ** 3
@@ -563,9 +566,10 @@ def run_generalized(args, torch, trm, stream):
     S = ti.hat_overlap_csr(shape)
     sptr = stream.cuda_stream
 
-    def make(gen):
-        opt = trm.trm_default_options(precision=trm.TRM_FP64, precond=1,
-                                      stream=sptr, seed=7)
+    def make(gen, prec=None):
+        opt = trm.trm_default_options(
+            precision=trm.TRM_FP64 if prec is None else prec, precond=1,
+            stream=sptr, seed=7)
         h = trm.trm_create_stencil(n, n, n, 4, 1.0, V, m, args.tol, opt)
         if gen:
             trm.trm_set_overlap_csr(h, *S)
@@ -592,6 +596,17 @@ def run_generalized(args, torch, trm, stream):
             _timed_solve(torch, trm, hs, N, m, stream)
         _, eg_s, st_s, status_s, t_s = _timed_solve(torch, trm, hs, N, m,
                                                     stream)
+        hm = make(True, trm.TRM_MIXED)
+        try:
+            for _ in range(args.warmup):
+                _timed_solve(torch, trm, hm, N, m, stream)
+            tm = []
+            for _ in range(args.steps):
+                lam_m, eg_m, st_m, status_m, t = _timed_solve(torch, trm, hm,
+                                                              N, m, stream)
+                tm.append(t)
+        finally:
+            trm.trm_destroy(hm)
     finally:
         trm.trm_destroy(hg)
         trm.trm_destroy(hs)
@@ -615,6 +630,17 @@ def run_generalized(args, torch, trm, stream):
            "max_residual": st.max_residual, "E_G": eg,
            "standard_same_H": {"seconds": t_s, "iterations": st_s.iterations,
                                "status": status_s, "E_G": eg_s},
+           "mixed": {"seconds": statistics.mean(tm),
+                     "iterations": st_m.iterations,
+                     "iterations_sp_fp64": [st_m.iterations_phase[0],
+                                            st_m.iterations_phase[1]],
+                     "status": status_m, "max_residual": st_m.max_residual,
+                     "E_G": eg_m, "rel_diff_E_G_vs_fp64": abs(eg_m - eg) / abs(eg),
+                     "max_abs_diff_lambda_vs_fp64":
+                         float(np.max(np.abs(np.asarray(lam_m) - np.asarray(lam)))),
+                     "ladder": "full SP (S in FP32, Y = S C in FP32) until its "
+                               "floor, then FP64 iterations, then the FP64 "
+                               "Rayleigh-Ritz step"},
            "roofline": roof, "classes": per_class,
            "gpu_launches": launches, "clocks": clocks}
     print(json.dumps(out))

@@ -141,8 +141,11 @@ trm_status trm_create_csr(trm_handle* out, int64_t N, const int32_t* rowptr,
  * Generalized problem H e = lambda S e with S symmetric positive definite
  * (Sec. 2.1: trace minimization extends to it directly, which admits
  * non-orthogonal basis functions). Attaches S to a handle made by
- * trm_create_stencil or trm_create_csr with precision TRM_FP64; trm_solve
- * then minimises tr(C^T H C) under C^T S C = I: the orthonormalization
+ * trm_create_stencil or trm_create_csr with precision TRM_FP64, TRM_MIXED
+ * or TRM_FULL_SP; trm_solve then minimises tr(C^T H C) under C^T S C = I
+ * (TRM_MIXED: full SP with S applied in FP32 -- its values rounded -- and
+ * Y = S C carried in FP32, then FP64 iterations in place of MP2, then the
+ * FP64 Rayleigh-Ritz step; TRM_FULL_SP: full SP, then that step): the orthonormalization
  * factors C^T S C, the gradient is G = -2 (H C - S C H_C), the line search
  * uses the overlap (C + aP)^T S (C + aP), the diagonal preconditioner
  * becomes 1 / (H_ii - sigma S_ii) with sigma = min_k H_kk / S_kk - 1, and
@@ -152,8 +155,8 @@ trm_status trm_create_csr(trm_handle* out, int64_t N, const int32_t* rowptr,
  * rowptr[N] int32 in [0, N); vals: host, rowptr[N] FP64 (duplicates add).
  * The arrays are copied before the call returns. S's symmetry and
  * definiteness are not checked (an indefinite S shows as TRM_ENOTPD from
- * trm_solve); every diagonal entry must be positive. TRM_EINVAL for another
- * precision mode or invalid arrays. The step operations (trm_energy_gradient,
+ * trm_solve); every diagonal entry must be positive. TRM_EINVAL for
+ * TRM_MP2 or invalid arrays. The step operations (trm_energy_gradient,
  * trm_set_block, trm_iterate, trm_rayleigh_ritz) cover the standard problem
  * only and return TRM_EINVAL on a handle with an overlap.
  */

@@ -171,8 +171,8 @@ trm_status trm_set_overlap_csr(trm_handle h, const int32_t* rowptr,
   if (!h) return static_cast<trm_status>(fail(nullptr, TRM_EINVAL, "handle is NULL"));
   if (!rowptr || !cols || !vals)
     return static_cast<trm_status>(fail(h, TRM_EINVAL, "CSR arrays must be non-NULL"));
-  if (h->solver->precision() != TRM_FP64)
-    return static_cast<trm_status>(fail(h, TRM_EINVAL, "the generalized problem runs in the TRM_FP64 precision mode"));
+  if (h->solver->precision() == TRM_MP2)
+    return static_cast<trm_status>(fail(h, TRM_EINVAL, "the generalized problem runs in the TRM_FP64, TRM_MIXED and TRM_FULL_SP modes (MP2's double-float blocks do not carry S C)"));
   const int64_t N = h->solver->N();
   if (rowptr[0] != 0)
     return static_cast<trm_status>(fail(h, TRM_EINVAL, "rowptr[0] must be 0"));

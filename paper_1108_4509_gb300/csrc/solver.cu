@@ -394,6 +394,7 @@ void Solver::init_csr(const int32_t* rowptr, const int32_t* cols,
     split_df(v, vh, vl, nnz, s_);
     op_.csr.valshi = vh;
     op_.csr.valslo = vl;
+    op_.csr.vals32 = vh;  // fl32(v): the FP32 products take it directly
   } else {
     auto* v = static_cast<float*>(mem_.alloc((size_t)nnz * 4));
     TRM_CUDA(cudaMemcpyAsync(v, vals, (size_t)nnz * 4, cudaMemcpyHostToDevice,
@@ -435,6 +436,21 @@ void Solver::init_overlap(const int32_t* rowptr, const int32_t* cols,
   sop_.csr.rowptr = rp;
   sop_.csr.cols = ci;
   sop_.csr.vals64 = v;
+  if (opt_.precision != TRM_FP64) {  // the full-SP phase applies S in FP32
+    std::vector<float> v32(nnz);
+    for (int64_t k = 0; k < nnz; ++k) v32[k] = (float)vals[k];
+    auto* vf = static_cast<float*>(mem_.alloc((size_t)nnz * 4));
+    TRM_CUDA(cudaMemcpyAsync(vf, v32.data(), (size_t)nnz * 4,
+                             cudaMemcpyHostToDevice, s_));
+    TRM_CUDA(cudaStreamSynchronize(s_));  // v32 leaves scope
+    sop_.csr.vals32 = vf;
+    if (!Y32_) {
+      const size_t nm = (size_t)N_ * m_;
+      Y32_ = static_cast<float*>(mem_.alloc(nm * 4));
+      Y32n_ = static_cast<float*>(mem_.alloc(nm * 4));
+      SP32_ = static_cast<float*>(mem_.alloc(nm * 4));
+    }
+  }
   int mx = 0;
   for (int64_t r = 0; r < N_; ++r) mx = std::max(mx, rowptr[r + 1] - rowptr[r]);
   sop_.csr.max_row_nnz = mx;
@@ -579,6 +595,12 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
       SPt = SP64_;
       gen = true;
     }
+  } else {  // the mixed ladder's full-SP phase
+    if (has_S_) {
+      Yc = Y32_;
+      SPt = SP32_;
+      gen = true;
+    }
   }
   if constexpr (sizeof(T) == 4) {  // (1) with the column dots of (2) fused in
     int chunks = 0;
@@ -621,7 +643,7 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   if (!hp_chunks) TRM_PROF(ksp, sfl, sby, apply_h(op_, P, HP, m_, s_));  // H P
   if (gen) {
     double ffl, fby;
-    spmm_cost(sop_, m_, 8, &ffl, &fby);
+    spmm_cost(sop_, m_, (int)es, &ffl, &fby);
     TRM_PROF(ksp, ffl, fby, apply_h(sop_, P, SPt, m_, s_));          // S P
   }
   // where the trace of P^T H P and W = P^T G come from
@@ -664,12 +686,17 @@ void Solver::iter_uniform(T*& C, T*& Cn, T* X, T*& G, T*& Gp, T* P, T* HP) {
   prof.end(KC_SMALL, 4 * m3 + 2 * m3 / 3, 0.0, s_);
   TRM_PROF(krt, m2N, 3 * es * nm,
            (rotate<T, T>(N_, m_, C, P, R_, Cn, sc_, s_, &tw_)));  // (C+aP)L^-T
-  if constexpr (sizeof(T) == 8) {
-    if (gen) {  // S (C + aP) L^-T = (Y + a S P) L^-T
+  if (gen) {  // S (C + aP) L^-T = (Y + a S P) L^-T
+    if constexpr (sizeof(T) == 8) {
       TRM_PROF(krt, m2N, 3 * es * nm,
                (rotate<double, double>(N_, m_, Y64_, SP64_, R_, Y64n_, sc_,
                                        s_, &tw_)));
       std::swap(Y64_, Y64n_);
+    } else {
+      TRM_PROF(krt, m2N, 3 * es * nm,
+               (rotate<float, float>(N_, m_, Y32_, SP32_, R_, Y32n_, sc_, s_,
+                                     &tw_)));
+      std::swap(Y32_, Y32n_);
     }
   }
   std::swap(C, Cn);
@@ -828,10 +855,25 @@ void Solver::orth_uniform(T*& C, T*& Cn) {
   b.p[0] = C;
   b.cols = m_;
   b.count = 1;
+  bool gen = false;  // FP32 generalized: S = C^T Y with Y = S C recomputed
+  if constexpr (sizeof(T) == 4) {
+    if (has_S_) {
+      apply_h(sop_, C, Y32_, m_, s_);
+      b.p[0] = Y32_;
+      gen = true;
+    }
+  }
   gram<T>(N_, m_, C, b, S_, part_, part_cap_, s_, &sc_->status);
   chol_inv<T>(m_, S_, Linv_, R_, sc_, mmw_, s_);
   rotate<T, T>(N_, m_, C, static_cast<const T*>(nullptr), R_, Cn, nullptr,
                s_, &tw_);
+  if constexpr (sizeof(T) == 4) {
+    if (gen) {  // Y follows C
+      rotate<float, float>(N_, m_, Y32_, static_cast<const float*>(nullptr),
+                           R_, Y32n_, nullptr, s_, &tw_);
+      std::swap(Y32_, Y32n_);
+    }
+  }
   std::swap(C, Cn);
 }
 
@@ -1158,11 +1200,13 @@ int Solver::solve(double* lambda, double* E_G, double* C_out, int C_on_device,
       } else if (small || stalled) {
         drain();
         to_f64(C32_, C64_, (int64_t)nm, s_);
-        orth_fp64(C64_, C64n_);
+        orth_fp64(C64_, C64n_);  // (recomputes Y = S C in FP64)
         rr_rotate_fp64();
-        c64_to_df();
+        // the generalized problem goes on in FP64 (its double-float MP2
+        // would need Y and S C as FP32 pairs)
+        if (!has_S_) c64_to_df();
         set_restart();
-        phase = PH_MP2;
+        phase = has_S_ ? PH_FP64 : PH_MP2;
         best = INFINITY;
         best_at = enq;
         since_orth = since_rr = 0;

@@ -205,6 +205,9 @@ class Solver {
   double *Y64_ = nullptr, *Y64n_ = nullptr, *SP64_ = nullptr;
   double* sdiag64_ = nullptr;
   float* sdiag32_ = nullptr;
+  // the full-SP phase of the mixed ladder: Y = S C, its swap buffer and S P
+  // in FP32 (S's values rounded to FP32 in sop_.csr.vals32)
+  float *Y32_ = nullptr, *Y32n_ = nullptr, *SP32_ = nullptr;
 };
 
 }  // namespace trm

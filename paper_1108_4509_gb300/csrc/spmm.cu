@@ -615,7 +615,9 @@ int launch_vec(const Operator& op, const T* X, T* Y, int ncols, double* dots,
     }
   } else {
     grid = dim3(ceil_div(op.N, threads), gy);
-    if (op.csr.vals64)
+    // FP32 blocks take the FP32 roundings of the values when the operator
+    // holds them (the same products, no conversion per nonzero)
+    if (op.csr.vals64 && (sizeof(T) == 8 || !op.csr.vals32))
       k_csr<T, double, DOTS><<<grid, threads, 0, s>>>(
           op.N, op.csr.rowptr, op.csr.cols, op.csr.vals64, X, Y, ncols, dots);
     else

@@ -2,8 +2,9 @@
 trilinear hat functions, trm_set_overlap_csr): the eigenvalues equal the
 closed form of the V = 0 pencil and the oracle's generalized
 eigensolutions, the returned C is S-orthonormal with small residuals
-||H c - lambda S c||, stencil and CSR forms of H agree, and the handle
-refuses what the generalized path does not cover."""
+||H c - lambda S c||, stencil and CSR forms of H agree, in the FP64 mode,
+the mixed ladder (full SP with S in FP32, then FP64) and full SP, and the
+handle refuses what the generalized path does not cover."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -34,9 +35,11 @@ def _overlap(shape):
 
 
 def _solve(trm, shape, order, V, m, S_arrays, precond, csr=False,
-           tol=1e-10):
+           tol=1e-10, precision=None):
     N = int(np.prod(shape))
-    opt = trm.trm_default_options(precision=trm.TRM_FP64, precond=precond,
+    if precision is None:
+        precision = trm.TRM_FP64
+    opt = trm.trm_default_options(precision=precision, precond=precond,
                                   seed=5)
     opt.stream = gu.stream()
     if csr:
@@ -54,24 +57,31 @@ def _solve(trm, shape, order, V, m, S_arrays, precond, csr=False,
     return lam, C, st
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
 @pytest.mark.parametrize("precond", [0, 1])
-def test_closed_form_pencil(trm, precond):
+def test_closed_form_pencil(trm, precond, mode):
     shape, m = (10, 11, 12), 8
     S_arrays, S = _overlap(shape)
+    prec = trm.TRM_FP64 if mode == "fp64" else trm.TRM_MIXED
     lam, C, st = _solve(trm, shape, 2, np.zeros(int(np.prod(shape))), m,
-                        S_arrays, precond)
+                        S_arrays, precond, precision=prec)
+    if mode == "mixed":
+        assert st.iterations_phase[0] > 0  # a full-SP phase ran first
     want = _hat_closed_form(shape, 1.0)[:m]
     assert np.max(np.abs(lam - want)) < 1e-10 * np.abs(want).max()
     assert np.max(np.abs(C.T @ (S @ C) - np.eye(m))) < 1e-10
     assert st.max_residual < 1e-8
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
 @pytest.mark.parametrize("csr", [False, True])
-def test_wells_against_dense_generalized_eigh(trm, csr):
+def test_wells_against_dense_generalized_eigh(trm, csr, mode):
     shape, order, m = (12, 12, 12), 4, 10
     V = ti.gaussian_wells(shape, 6, seed=2)
     S_arrays, S = _overlap(shape)
-    lam, C, st = _solve(trm, shape, order, V, m, S_arrays, 1, csr=csr)
+    prec = trm.TRM_FP64 if mode == "fp64" else trm.TRM_MIXED
+    lam, C, st = _solve(trm, shape, order, V, m, S_arrays, 1, csr=csr,
+                        precision=prec)
     H = op.grid_hamiltonian(shape, order, 1.0, V)
     want = sla.eigh(H.toarray(), S.toarray(), eigvals_only=True,
                     subset_by_index=[0, m - 1])
@@ -79,6 +89,23 @@ def test_wells_against_dense_generalized_eigh(trm, csr):
     assert np.max(np.abs(C.T @ (S @ C) - np.eye(m))) < 1e-10
     R = H @ C - (S @ C) * lam[None, :]
     assert np.max(np.linalg.norm(R, axis=0)) < 1e-7
+
+
+def test_full_sp_pencil(trm):
+    """Full SP with S: the FP32 iteration stops at its floor (tolerance
+    1e-4 on the RMS residual) and the closing FP64 Rayleigh-Ritz step on
+    its span gives eigenvalues within r^2 / gap of the dense ones and an
+    S-orthonormal block."""
+    shape, order, m = (12, 12, 12), 4, 10
+    V = ti.gaussian_wells(shape, 6, seed=2)
+    S_arrays, S = _overlap(shape)
+    lam, C, st = _solve(trm, shape, order, V, m, S_arrays, 1, tol=1e-4,
+                        precision=trm.TRM_FULL_SP)
+    H = op.grid_hamiltonian(shape, order, 1.0, V)
+    want = sla.eigh(H.toarray(), S.toarray(), eigvals_only=True,
+                    subset_by_index=[0, m - 1])
+    assert np.max(np.abs(lam - want)) < 1e-5
+    assert np.max(np.abs(C.T @ (S @ C) - np.eye(m))) < 1e-10
 
 
 def test_ragged_grid_against_shift_invert_lanczos(trm):
@@ -100,7 +127,7 @@ def test_refusals(trm):
     shape, m = (6, 6, 6), 4
     N = int(np.prod(shape))
     S_arrays, _ = _overlap(shape)
-    opt = trm.trm_default_options(precision=trm.TRM_MIXED)
+    opt = trm.trm_default_options(precision=trm.TRM_MP2)
     opt.stream = gu.stream()
     h = trm.trm_create_stencil(*shape, 2, 1.0, None, m, 1e-8, opt)
     try:
