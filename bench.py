@@ -123,6 +123,11 @@ def parse():
                          "solve of the stencil (about five minutes) and the "
                          "same operator as an FP32/int32 CSR matrix solved "
                          "from the stencil's converged block")
+    ap.add_argument("--table", type=int, default=0,
+                    help="instead of the benchmark: the paper's own 2-D "
+                         "Laplacian cases of Table RESTBL (96^2 and 192^2, "
+                         "m = 220 and 534), mixed and FP64, time and "
+                         "iterations per solve")
     ap.add_argument("--accuracy", type=int, default=0,
                     help="instead of the benchmark: each precision mode's "
                          "accuracy against the oracle's references at "
@@ -723,7 +728,67 @@ def run_extras(args):
         run_chain(args, torch, trm, stream)
     if args.accuracy:
         run_accuracy(args, torch, trm, stream)
+    if args.table:
+        run_table(args, torch, trm, stream)
     return 0
+
+
+TABLE_REF = os.path.join(ROOT, "tests", "golden", "table_restbl_reference.json")
+TABLE_PRINTED = os.path.join(ROOT, "tests", "golden", "table_restbl.json")
+TABLE_CASES = ["laplace2d_96_m220", "laplace2d_192_m220", "laplace2d_192_m534"]
+
+
+def run_table(args, torch, trm, stream):
+    """The paper's workload (Sec. 3, Table RESTBL): the 2-D Dirichlet
+    Laplacian of Eq. LAPLACE, no preconditioner, random C0, solved in the
+    mixed ladder and in FP64 to the RMS residual tolerance; E_G against the
+    closed form (stored by tests/golden/make_table_reference.py), time and
+    iterations per solve and per iteration. The paper's own per-iteration
+    seconds (one core of an Opteron 6176 SE, full DP and MP2) are quoted as
+    context. The rows with m = 1064 and 1519 exceed this library's m <= 1024."""
+    import trm_inputs as ti
+    ref = {(r["n"], r["m"]): r for r in load_json(TABLE_REF)["rows"]}
+    printed = {(r["n"], r["m"]): r for r in load_json(TABLE_PRINTED)["rows"]}
+    sptr = stream.cuda_stream
+    rows = []
+    for name in TABLE_CASES:
+        w = ti.workload(name)
+        n = w.shape[0]
+        E_ref = ref[(n, w.m)]["E_G"]
+        row = {"workload": name, "N": w.N, "m": w.m,
+               "E_G_closed_form": E_ref,
+               "paper_N_iter_full_dp": printed[(n, w.m)].get("N_iter")}
+        for mode, prec in (("mixed", trm.TRM_MIXED), ("fp64", trm.TRM_FP64)):
+            opt = trm.trm_default_options(precision=prec, precond=0,
+                                          stream=sptr, seed=w.seed + 100)
+            h = trm.trm_create_stencil(*w.shape, w.order, w.h, None, w.m,
+                                       args.tol, opt)
+            try:
+                for _ in range(args.warmup if mode == "mixed" else 0):
+                    _timed_solve(torch, trm, h, w.N, w.m, stream)
+                lam, eg, st, status, t = _timed_solve(torch, trm, h, w.N,
+                                                      w.m, stream)
+            finally:
+                trm.trm_destroy(h)
+            row[mode] = {"seconds": t, "iterations": st.iterations,
+                         "iterations_phase": list(st.iterations_phase),
+                         "seconds_per_iteration": t / max(1, st.iterations),
+                         "status": status,
+                         "rel_err_E_G": abs(eg - E_ref) / abs(E_ref)}
+        row["fp64_over_mixed"] = row["fp64"]["seconds"] / row["mixed"]["seconds"]
+        rows.append(row)
+    out = {"metric": "Table RESTBL cases: time to tol (mixed and FP64)",
+           "value": sum(r["mixed"]["seconds"] for r in rows), "unit": "s",
+           "n_gpus": 1, "higher_is_better": False, "dtype": "f32+f64",
+           "data": "synthetic (the paper's own matrix, Eq. LAPLACE)",
+           "config": {"tol_rms": args.tol, "preconditioner": "none",
+                      "C0": "random (counter-based, seeded)"},
+           "rows": rows,
+           "paper_context": ("Table RESTBL, seconds per iteration on one core "
+                             "of an AMD Opteron 6176 SE: 96^2/m=220 DP 0.631, "
+                             "MP2 0.491; 192^2/m=220 DP 2.520, MP2 1.968; "
+                             "192^2/m=534 DP 12.04, MP2 8.772")}
+    print(json.dumps(out))
 
 
 def run_accuracy(args, torch, trm, stream):
@@ -917,7 +982,7 @@ def main():
     args = parse()
     if args.serving > 0:
         return run_serving(args)
-    if args.generalized > 0 or args.chain > 0 or args.accuracy:
+    if args.generalized > 0 or args.chain > 0 or args.accuracy or args.table:
         return run_extras(args)
     if args.impl == "reference":
         return run_reference(args)

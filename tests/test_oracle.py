@@ -73,6 +73,23 @@ def test_table_restbl_E_G_and_gap_from_closed_form():
         assert float(f"{gap:.{row['gap_sig']}g}") == pytest.approx(row["gap"], rel=1e-12)
 
 
+def test_table_restbl_reference_file_matches_the_closed_form():
+    """tests/golden/table_restbl_reference.json (the E_G references bench.py
+    --table compares against) holds the closed form's values for every row
+    of the printed table, and they round to the printed E_G."""
+    ref = json.load(open(os.path.join(GOLDEN, "table_restbl_reference.json")))
+    tab = json.load(open(os.path.join(GOLDEN, "table_restbl.json")))
+    assert [(r["n"], r["m"]) for r in ref["rows"]] == \
+        [(r["n"], r["m"]) for r in tab["rows"]]
+    for r, t in zip(ref["rows"], tab["rows"]):
+        lam = op.laplace2d_spectrum(r["n"])
+        m = r["m"]
+        assert r["E_G"] == float(np.sum(lam[:m]))
+        assert r["lambda_m"] == float(lam[m - 1])
+        assert r["gap"] == float(lam[m] - lam[m - 1])
+        assert float(f"{r['E_G']:.{t['E_G_sig']}g}") == pytest.approx(t["E_G"], rel=1e-12)
+
+
 # ---------------------------------------------------------------------------
 # Fig. ONFIG
 # ---------------------------------------------------------------------------

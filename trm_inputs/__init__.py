@@ -252,6 +252,7 @@ WORKLOADS = {
                  precond=1),
         Workload("laplace2d_96_m220", (96, 96, 1), 2, 0, 220, h=_H_LAPLACE),
         Workload("laplace2d_192_m220", (192, 192, 1), 2, 0, 220, h=_H_LAPLACE),
+        Workload("laplace2d_192_m534", (192, 192, 1), 2, 0, 534, h=_H_LAPLACE),
     ]
 }
 
