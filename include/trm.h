@@ -325,7 +325,7 @@ long long trm_launch_count(void);
  * Limit: m * n <= 2^20 (up to 1024 x 1024); larger sizes return TRM_EINVAL
  * with a message in trm_last_global_error().
  * Kernels: FP32 operands that trm_gram sends to the tensor cores (N % 4 == 0,
- * m >= 64, A and B 16-byte aligned) run that same kernel (error below
+ * m >= 32, A and B 16-byte aligned) run that same kernel (error below
  * 8e-6 sum_k |a_ki||b_kj|), with the same row slices and sum order, so the
  * same bytes as trm_gram's, whenever m * n * slices <= 3 * 2^20 - 1 (else
  * with fewer, longer slices); other FP32 operands and all FP64 operands run

@@ -123,7 +123,9 @@ struct TcArgs {
   int64_t N;
   int m, n;               // output is m x n
   int64_t rows_per_split;
-  int seg_cols;           // columns per segment (a multiple of BN if > 1)
+  int seg_cols;           // columns per segment
+  int tps;                // column tiles per segment (the last one ragged:
+                          // its columns past seg_cols load as zeros)
   double* part;
   int* err;
   uint8_t ti[kMaxTiles], tj[kMaxTiles];  // row and column tile of each CTA row
@@ -144,12 +146,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int split = blockIdx.x;
   const int i0 = args.ti[blockIdx.y] * BM;
-  const int j0 = args.tj[blockIdx.y] * BN;
   const int64_t rb = (int64_t)split * args.rows_per_split;
   const int64_t re = min(args.N, rb + args.rows_per_split);
   const int nk = (int)((re - rb + BK - 1) / BK);
-  const int seg = j0 / args.seg_cols;
-  const int jb = j0 - seg * args.seg_cols;
+  const int seg = args.tj[blockIdx.y] / args.tps;
+  const int jb = (args.tj[blockIdx.y] - seg * args.tps) * BN;  // in segment
+  const int j0 = seg * args.seg_cols + jb;  // first output column
   const CUtensorMap* mapA = &maps.a[seg];
   const CUtensorMap* mapB = &maps.b[seg];
 
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
               const int col = j0 + cb + e;
-              if (col < args.n) {
+              if (jb + cb + e < args.seg_cols) {
                 const size_t idx = row + (size_t)col * args.m;
                 out_hi[idx] = __uint_as_float(hi[e]);
                 out_lo[idx] = __uint_as_float(lo[e]);
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
     if (!ok && row < args.m) {  // a wait gave up: zero partial, error set
       for (int cb = 64 * g; cb < 64 * g + 64; ++cb)
-        if (j0 + cb < args.n) {
+        if (jb + cb < args.seg_cols) {
           out_hi[row + (size_t)(j0 + cb) * args.m] = 0.f;
           out_lo[row + (size_t)(j0 + cb) * args.m] = 0.f;
         }
@@ -360,12 +362,13 @@ bool gram_tc_eligible(int64_t N, int m, const float* A,
 
 bool gram_tc_pairs_eligible(int64_t N, int m, const Blocks<float>& A,
                             const Blocks<float>& B) {
-  if (N % 4 != 0 || N < BK || m < 64) return false;
+  // (m >= 32: a 128 x 128 tile at least a quarter used; below that the
+  // SIMT kernel is as fast)
+  if (N % 4 != 0 || N < BK || m < 32) return false;
   if (B.count > 4) return false;
   if (A.count > 1 && A.count != B.count) return false;
   for (int s = 0; s < A.count; ++s)
     if (reinterpret_cast<uintptr_t>(A.p[s]) % 16 != 0) return false;
-  if (B.count > 1 && B.cols % BN != 0) return false;
   for (int s = 0; s < B.count; ++s)
     if (reinterpret_cast<uintptr_t>(B.p[s]) % 16 != 0) return false;
   return tc::encode_fn() != nullptr;
@@ -420,14 +423,15 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
   const int n = B.total();
   const int tiles_m = ceil_div(m, BM);
   const int segcols = B.count > 1 ? B.cols : n;
-  if (sym_seg >= 0 && (sym_seg >= B.count || B.cols != m ||
-                       (B.count > 1 && m % BN != 0)))
+  const int nseg = B.count > 1 ? B.count : 1;
+  const int tps = ceil_div(segcols, BN);  // a segment's last tile is ragged
+  if (sym_seg >= 0 && (sym_seg >= B.count || B.cols != m))
     throw Error(-1, "gram_tc: a symmetric segment must be m x m");
   TcArgs a{};
   int tiles = 0;
-  for (int tj = 0; tj < ceil_div(n, BN); ++tj) {
-    const int seg = (tj * BN) / segcols;
-    const int tjs = tj - seg * (segcols / BN);  // column tile in its segment
+  for (int tj = 0; tj < nseg * tps; ++tj) {
+    const int seg = tj / tps;
+    const int tjs = tj - seg * tps;  // column tile in its segment
     for (int ti = 0; ti < tiles_m; ++ti) {
       if (seg == sym_seg && ti > tjs) continue;  // mirrored from (tjs, ti)
       if (tiles == kMaxTiles) throw Error(-1, "gram_tc: too many output tiles");
@@ -436,8 +440,12 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
       ++tiles;
     }
   }
-  int splits = tc_splits(N, tiles, max_splits > 0 ? max_splits : 1 << 30,
-                         sm_count());
+  // (the partials buffer bounds the slices too)
+  const size_t by_cap = cap / ((size_t)m * n);
+  if (by_cap < 1) throw Error(-2, "gram_tc: partials buffer too small");
+  int smax = max_splits > 0 ? max_splits : 1 << 30;
+  if ((size_t)smax > by_cap) smax = (int)by_cap;
+  int splits = tc_splits(N, tiles, smax, sm_count());
   int64_t rows = (N + splits - 1) / splits;
   rows = ((rows + BK - 1) / BK) * BK;
   splits = (int)((N + rows - 1) / rows);
@@ -454,6 +462,7 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
   a.n = n;
   a.rows_per_split = rows;
   a.seg_cols = segcols;
+  a.tps = tps;
   a.part = partials;
   a.err = err;
   const size_t smem = sizeof(TcSmem) + 1024;

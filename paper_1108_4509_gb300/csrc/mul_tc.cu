@@ -36,6 +36,7 @@
 // does not use (4 slots, two per column half, so the loads of the next
 // 8 columns are in flight while the epilogue works on these).
 #include <atomic>
+#include <numeric>
 
 #include "dfmath.cuh"
 #include "ops.cuh"
@@ -83,6 +84,7 @@ struct MulArgs {
   int k, n;        // Y: N x k, M: k x n
   int ntr, nch;    // row tiles, column chunks of 128
   int has_p;       // Y = A + alpha P
+  int tri;         // M upper triangular: column j of Y M needs rows k <= j
   const IterScalars* sc;
   float* out;      // kStore: Y M; kGrad: G (N x n, ld N)
   const float* xp; // kGrad
@@ -111,6 +113,22 @@ static_assert(NSLOT * ESLOT <= RS * BM * BK,
 __device__ __forceinline__ float staged(const float* t, int i, int k) {
   return t[(i >> 5) * 1024 + k * 32 + (((((i & 31) >> 2) ^ (k & 7))) << 2) +
            (i & 3)];
+}
+
+// Tile t of a launch: row tile t / nch, so the nch column chunks of a row
+// tile are taken by neighbouring CTAs at about the same time and the
+// chunks after the first find the Y (and P) tile in L2 instead of reading
+// it again from DRAM; its chunk rotates with the row so that a persistent
+// CTA cycles through the chunks (with a triangular M the chunks differ in
+// work: chunk c needs the K blocks below (c + 1) NC only).
+__device__ __forceinline__ void tile_rc(const MulArgs& a, int t, int& r0,
+                                        int& c0) {
+  const int row = t / a.nch;
+  r0 = row * BM;
+  c0 = ((t - row * a.nch + row) % a.nch) * NC;
+}
+__device__ __forceinline__ int tile_nk(const MulArgs& a, int c0, int nk) {
+  return a.tri ? min(nk, (c0 + NC + BK - 1) / BK) : nk;
 }
 
 template <int MODE>
@@ -164,8 +182,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       int it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int r0 = (t % args.ntr) * BM;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        int r0, c0;
+        tile_rc(args, t, r0, c0);
+        const int nkt = tile_nk(args, c0, nk);
+        for (int kb = 0; kb < nkt; ++kb, ++it) {
           const int s = it % RS;
           if (it >= RS &&
               !mbar_wait(&sm->raw_empty[s], ((it / RS) - 1) & 1, args.err,
@@ -194,8 +214,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       int it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int c0 = (t / args.ntr) * NC;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        int r0, c0;
+        tile_rc(args, t, r0, c0);
+        const int nkt = tile_nk(args, c0, nk);
+        for (int kb = 0; kb < nkt; ++kb, ++it) {
           const int s = it % CS;
           if (it >= CS &&
               !mbar_wait(&sm->op_empty[s], ((it / CS) - 1) & 1, args.err,
@@ -223,8 +245,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       int j = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int r0 = (t % args.ntr) * BM;
-        const int c0 = (t / args.ntr) * NC;
+        int r0, c0;
+        tile_rc(args, t, r0, c0);
         for (int q = 0; q < 8 && ok; ++q, ++j)
           for (int g = 0; g < 2 && ok; ++g) {
             const int e = 2 * g + (j & 1);
@@ -262,7 +284,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         fence_after();
         const uint32_t d = tmem + (uint32_t)(b * NC);
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        int r0, c0;
+        tile_rc(args, t, r0, c0);
+        const int nkt = tile_nk(args, c0, nk);
+        for (int kb = 0; kb < nkt; ++kb, ++it) {
           const int s = it % CS;
           const uint32_t par = (it / CS) & 1;
           if (!mbar_wait(&sm->conv_done[s], par, args.err, &sm->failed) ||
@@ -298,7 +323,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     int it = 0;
     bool ok = true;
     for (int tt = blockIdx.x; tt < ntiles && ok; tt += gridDim.x) {
-      for (int kb = 0; kb < nk; ++kb, ++it) {
+      int r0, c0;
+      tile_rc(args, tt, r0, c0);
+      const int nkt = tile_nk(args, c0, nk);
+      for (int kb = 0; kb < nkt; ++kb, ++it) {
         const int rs = it % RS, cs = it % CS;
         if (!mbar_wait(&sm->raw_full[rs], (it / RS) & 1, args.err,
                        &sm->failed)) {
@@ -363,8 +391,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           mbar_wait(&sm->accfull[b], (tl / 2) & 1, args.err, &sm->failed);
       if (!__all_sync(0xffffffffu, got)) break;
       fence_after();
-      const int64_t row = (int64_t)(t % args.ntr) * BM + rr;
-      const int c0 = (t / args.ntr) * NC;
+      int r0, c0;
+      tile_rc(args, t, r0, c0);
+      const int64_t row = (int64_t)r0 + rr;
       const bool rin = row < N;
       float mi = 1.f;
       if (MODE == kGrad && rin && args.minv) mi = args.minv[row];
@@ -576,6 +605,18 @@ __global__ void k_split_small(int k, int n, int ldm, const double* __restrict__ 
 
 int ldm_of(int k) { return (k + 3) & ~3; }
 
+// Persistent grid of a product with a triangular M: nch x q CTAs with q
+// coprime to the chunk count nch, so that each CTA steps through every
+// column chunk (tile_rc) and the CTAs share the uneven chunks evenly.
+int tri_grid(int64_t N, int n) {
+  const int nch = ceil_div(n, NC);
+  const int g = mul_tc_parts(N, n);
+  if (nch == 1 || g < sm_count()) return g;
+  int q = g / nch;
+  while (q > 1 && std::gcd(q, nch) != 1) --q;
+  return q * nch;
+}
+
 template <int MODE>
 void launch(const MulArgs& a0, const float* A, const float* P,
             const double* M, int zero_diag, float* ws, cudaStream_t s,
@@ -603,7 +644,7 @@ void launch(const MulArgs& a0, const float* A, const float* P,
   a.ntr = (int)ceil_div(a.N, (int64_t)BM);
   a.nch = ceil_div(a.n, NC);
   a.has_p = P ? 1 : 0;
-  const int grid = mul_tc_parts(a.N, a.n);
+  const int grid = a.tri ? tri_grid(a.N, a.n) : mul_tc_parts(a.N, a.n);
   const size_t smem = sizeof(MulSmem) + 1024;
   static std::atomic<int> attr_dev{-1};  // launches may come from several threads
   int dev = 0;
@@ -647,6 +688,7 @@ void mul_tc_store(int64_t N, int k, int n, const float* A, const float* P,
                   const TcWork& tw, cudaStream_t s) {
   MulArgs a{};
   a.N = N; a.k = k; a.n = n; a.sc = sc; a.out = out; a.err = tw.err;
+  a.tri = 1;  // the rotation's L^{-T}
   launch<kStore>(a, A, P, M, 0, tw.msplit, s, nullptr);
 }
 
@@ -668,6 +710,7 @@ void mul_tc_splitdf(int64_t N, int m, const float* Ch, const float* Cl,
   MulArgs a{};
   a.N = N; a.k = m; a.n = m; a.sc = sc; a.ch = Ch; a.cl = Cl; a.p32 = P;
   a.R = R; a.outh = Cnh; a.outl = Cnl; a.err = tw.err;
+  a.tri = 1;
   launch<kSplitDf>(a, Ch, P, R, 1, tw.msplit, s, nullptr);
 }
 
@@ -677,6 +720,7 @@ void mul_tc_split64(int64_t N, int m, const float* C32, const float* P,
   MulArgs a{};
   a.N = N; a.k = m; a.n = m; a.sc = sc; a.c64 = C64; a.p32 = P; a.R = R;
   a.out64 = Cn; a.err = tw.err;
+  a.tri = 1;
   launch<kSplit64>(a, C32, P, R, 1, tw.msplit, s, nullptr);
 }
 

@@ -127,9 +127,9 @@ void sum_splits_pairs(const float* part, int splits, size_t count,
                       double* out, cudaStream_t s, float* out32 = nullptr,
                       SymSeg sym = SymSeg{});
 // tcgen05 Gram of FP32 blocks (two-term TF32 split, three products, FP32
-// accumulation in tensor memory): needs N % 4 == 0, m >= 64, A and every B
-// segment 16-byte aligned (TMA), at most 4 B segments whose widths are
-// multiples of 128 when there are several.
+// accumulation in tensor memory): needs N % 4 == 0, m >= 32, A and every B
+// segment 16-byte aligned (TMA), at most 4 B segments (each padded to whole
+// 128-column tiles, its columns past the segment's width read as zeros).
 bool gram_tc_eligible(int64_t N, int m, const float* A, const Blocks<float>& B);
 // Segment k of the output is A_k^T B_k (A.count == B.count, or one A for all
 // segments); up to four segments.

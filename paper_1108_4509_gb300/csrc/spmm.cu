@@ -9,6 +9,8 @@
 // walks the columns of its column group.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -507,15 +509,198 @@ template <typename T, bool DOTS>
 int launch_vec(const Operator& op, const T* X, T* Y, int ncols, double* dots,
                cudaStream_t s);
 
-// Autotuned choice between the staged-plane and the four-point FP32 stencil
-// kernels. The first apply of each (grid, order, columns, fused dots) in the
-// process times both on the caller's buffers (a warm-up launch, then the two
-// kernels alternately, twice each, CUDA events on the stream) and keeps the
-// faster for the rest of the process. Both compute every point with the same
-// operations in the same order (the fused dots are grouped differently, so
-// the choice is fixed per process: repeated solves agree bit for bit). No
-// timing inside a stream capture: the plain kernel is used there until a
-// choice exists.
+// ---------------------------------------------------------------------------
+// Register z-march (FP32, nx % 4 == 0): a CTA owns a tile of quads (four
+// consecutive x points of one row) of an x-y plane, one column and a chunk
+// of z planes; each thread walks z over its quad keeping the 2R + 1 values
+// of the quad along z in registers, so per plane it reads one new plane
+// value from DRAM and its x and y neighbours, which the neighbouring
+// threads of the same tile have just read as their own quads (L1 hits),
+// instead of four more planes through L2. There is no barrier inside the
+// march, so every warp keeps its loads in flight on its own. Every point
+// gets the same operations in the same order as k_stencil_v4; with DOTS the
+// column dot is accumulated in double-float per thread and the CTA's sum
+// goes to dots[(blockIdx.y * gridDim.x + blockIdx.x) * ncols + column].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ldg4f(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+
+template <int R, bool DOTS>
+__global__ void __launch_bounds__(256, 4)
+    k_stencil_zm(StencilOp st, int64_t N, const float* __restrict__ d32,
+                 const float* __restrict__ X, float* __restrict__ Y,
+                 int ncols, int zc, double* __restrict__ dots) {
+  __shared__ double red[8];
+  const int nx = st.nx, ny = st.ny, nz = st.nz, nxq = nx >> 2;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;  // quad in the plane
+  const bool active = p < nxq * ny;
+  const int qx = active ? p % nxq : 0, y = active ? p / nxq : 0;
+  const int col = blockIdx.z;
+  const int z0 = blockIdx.y * zc, z1 = min(nz, z0 + zc);
+  const int64_t sz = (int64_t)nx * ny;
+  const int64_t rowoff = (int64_t)y * nx + 4 * qx;
+  const float* xb = X + (int64_t)col * N + rowoff;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool xl_in = qx > 0, xr_in = qx + 1 < nxq;
+  const bool ym1 = y >= 1, yp1 = y + 1 < ny, ym2 = y >= 2, yp2 = y + 2 < ny;
+  const float c1 = st.c1h, c2 = st.c2h;  // rounded on the host
+  // q[k]: the quad in plane z - R + k (zeros outside the grid: Dirichlet);
+  // q[2R + 1], plane z + R + 1, is loaded one step before it is needed so
+  // that a plane's DRAM latency overlaps the arithmetic of the step before
+  float4 q[2 * R + 2];
+#pragma unroll
+  for (int k = 0; k < 2 * R + 1; ++k) {
+    const int pz = z0 - R + k;
+    q[k] = (active && pz >= 0 && pz < nz) ? ldg4f(xb + pz * sz) : zero;
+  }
+  F2 dacc = {0.f, 0.f};
+  for (int z = z0; z < z1; ++z) {
+    q[2 * R + 1] =
+        (active && z + R + 1 < nz && z + 1 < z1) ? ldg4f(xb + (z + R + 1) * sz)
+                                                 : zero;
+    if (active) {
+      const float* pc = xb + z * sz;
+      const float4 xc = q[R];
+      const float4 xl = xl_in ? ldg4f(pc - 4) : zero;
+      const float4 xr = xr_in ? ldg4f(pc + 4) : zero;
+      const float4 a1v = ym1 ? ldg4f(pc - nx) : zero;
+      const float4 b1v = yp1 ? ldg4f(pc + nx) : zero;
+      const float4 e1v = q[R - 1], f1v = q[R + 1];
+      const float4 d4 = ldg4f(d32 + z * sz + rowoff);
+      const float c[4] = {xc.x, xc.y, xc.z, xc.w};
+      const float a1[4] = {a1v.x, a1v.y, a1v.z, a1v.w};
+      const float b1[4] = {b1v.x, b1v.y, b1v.z, b1v.w};
+      const float e1[4] = {e1v.x, e1v.y, e1v.z, e1v.w};
+      const float f1[4] = {f1v.x, f1v.y, f1v.z, f1v.w};
+      const float l1[4] = {xl.w, xc.x, xc.y, xc.z};
+      const float r1[4] = {xc.y, xc.z, xc.w, xr.x};
+      const float d[4] = {d4.x, d4.y, d4.z, d4.w};
+      float a2[4] = {0, 0, 0, 0}, b2[4] = {0, 0, 0, 0}, e2[4] = {0, 0, 0, 0},
+            f2[4] = {0, 0, 0, 0};
+      float l2[4] = {0, 0, 0, 0}, r2[4] = {0, 0, 0, 0};
+      if (R == 2) {
+        const float4 a2v = ym2 ? ldg4f(pc - 2 * nx) : zero;
+        const float4 b2v = yp2 ? ldg4f(pc + 2 * nx) : zero;
+        const float4 e2v = q[0], f2v = q[2 * R];
+        a2[0] = a2v.x; a2[1] = a2v.y; a2[2] = a2v.z; a2[3] = a2v.w;
+        b2[0] = b2v.x; b2[1] = b2v.y; b2[2] = b2v.z; b2[3] = b2v.w;
+        e2[0] = e2v.x; e2[1] = e2v.y; e2[2] = e2v.z; e2[3] = e2v.w;
+        f2[0] = f2v.x; f2[1] = f2v.y; f2[2] = f2v.z; f2[3] = f2v.w;
+        l2[0] = xl.z; l2[1] = xl.w; l2[2] = xc.x; l2[3] = xc.y;
+        r2[0] = xc.z; r2[1] = xc.w; r2[2] = xr.x; r2[3] = xr.y;
+      }
+      float out[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float s1 = 0.f, s2 = 0.f;
+        s1 += a1[k];
+        s1 += b1[k];
+        s1 += e1[k];
+        s1 += f1[k];
+        float acc = d[k] * c[k] + c1 * (s1 + l1[k] + r1[k]);
+        if (R == 2) {
+          s2 += a2[k];
+          s2 += b2[k];
+          s2 += e2[k];
+          s2 += f2[k];
+          acc += c2 * (s2 + l2[k] + r2[k]);
+        }
+        out[k] = acc;
+      }
+      if (!DOTS || Y)
+        *reinterpret_cast<float4*>(Y + (int64_t)col * N + z * sz + rowoff) =
+            make_float4(out[0], out[1], out[2], out[3]);
+      if (DOTS)
+        dacc = df_add(dacc, F2{c[0] * out[0] + c[1] * out[1] +
+                                   c[2] * out[2] + c[3] * out[3],
+                               0.f});
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k) q[k] = q[k + 1];
+  }
+  if (DOTS) {
+    F2 w = dacc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      w = df_add(w, F2{__shfl_xor_sync(0xffffffffu, w.h, o),
+                       __shfl_xor_sync(0xffffffffu, w.l, o)});
+    if ((threadIdx.x & 31) == 0)
+      red[threadIdx.x >> 5] = to_f64(w.h) + to_f64(w.l);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) t += red[k];
+      dots[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * ncols + col] = t;
+    }
+  }
+}
+
+// Launch geometry of the z-march: plane tiles of at most 256 quads (a
+// multiple of 32 threads, evened out over the tiles), z chunks so that
+// about eight CTAs per SM are launched (at least four planes each), and no
+// more partial dots per column than apply_h_dots_doubles allows.
+struct ZmShape {
+  int tiles, threads, chunks, zc;
+};
+ZmShape zm_shape(const Operator& op, int ncols) {
+  const StencilOp& st = op.st;
+  const int nq = (st.nx / 4) * st.ny;
+  ZmShape z{};
+  z.tiles = ceil_div(nq, 256);
+  z.threads = 32 * ceil_div(nq, 32 * z.tiles);
+  const int want = ceil_div(8 * sm_count(), z.tiles * ncols);
+  const int cap = (int)std::max<int64_t>(1, ceil_div(op.N / 4, (int64_t)256) /
+                                                 z.tiles);
+  const int chunks = std::max(1, std::min({want, ceil_div(st.nz, 4), cap}));
+  z.zc = ceil_div(st.nz, chunks);
+  z.chunks = ceil_div(st.nz, z.zc);
+  return z;
+}
+
+template <int R, bool DOTS>
+int launch_zm(const Operator& op, const float* X, float* Y, int ncols,
+              double* dots, cudaStream_t s) {
+  const ZmShape z = zm_shape(op, ncols);
+  k_stencil_zm<R, DOTS><<<dim3(z.tiles, z.chunks, ncols), z.threads, 0, s>>>(
+      op.st, op.N, op.diag32, X, Y, ncols, z.zc, dots);
+  TRM_CHECK_LAUNCH();
+  return z.tiles * z.chunks;  // partial dots per column
+}
+
+template <bool DOTS>
+int launch_zm_r(const Operator& op, const float* X, float* Y, int ncols,
+                double* dots, cudaStream_t s) {
+  return op.st.radius == 1 ? launch_zm<1, DOTS>(op, X, Y, ncols, dots, s)
+                           : launch_zm<2, DOTS>(op, X, Y, ncols, dots, s);
+}
+
+// The z-march takes FP32 stencils with nx % 4 == 0 on 16-byte-aligned
+// blocks, at most 65535 columns, and partial dots within the buffer.
+template <typename T>
+bool zm_eligible(const Operator& op, const T* X, const T* Y, int ncols) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    if (op.kind != 0 || op.st.nx % 4 != 0 || ncols > 65535) return false;
+    if (((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y) |
+          reinterpret_cast<uintptr_t>(op.diag32)) & 15) != 0)
+      return false;
+    const ZmShape z = zm_shape(op, ncols);
+    return (int64_t)z.tiles * z.chunks <= ceil_div(op.N / 4, (int64_t)256);
+  }
+}
+
+// Autotuned choice among the FP32 stencil kernels: the four-point kernel,
+// the staged-plane kernel and the register z-march. The first apply of each
+// (grid, order, columns, fused dots) in the process times every eligible
+// kernel on the caller's buffers (a warm-up launch of each, then the kernels
+// in turn, twice each, CUDA events on the stream) and keeps the fastest for
+// the rest of the process. All compute every point with the same operations
+// in the same order (the fused dots are grouped differently, so the choice
+// is fixed per process: repeated solves agree bit for bit). No timing inside
+// a stream capture: the four-point kernel is used there until a choice
+// exists.
 struct TuneKey {
   int nx, ny, nz, radius, ncols, dots;
   bool operator<(const TuneKey& o) const {
@@ -524,7 +709,9 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tuned;  // 1: staged planes
+std::map<TuneKey, int> g_tuned;  // the StencilKernel kept for a key
+
+enum StencilKernel { kKernVec = 0, kKernPlanes = 1, kKernZm = 2 };
 
 template <bool DOTS>
 int launch_planes_r(const Operator& op, const float* X, float* Y, int ncols,
@@ -534,8 +721,16 @@ int launch_planes_r(const Operator& op, const float* X, float* Y, int ncols,
 }
 
 template <bool DOTS>
-bool use_planes(const Operator& op, const float* X, float* Y, int ncols,
-                double* dots, cudaStream_t s) {
+int launch_kind(int kind, const Operator& op, const float* X, float* Y,
+                int ncols, double* dots, cudaStream_t s) {
+  if (kind == kKernPlanes) return launch_planes_r<DOTS>(op, X, Y, ncols, dots, s);
+  if (kind == kKernZm) return launch_zm_r<DOTS>(op, X, Y, ncols, dots, s);
+  return launch_vec<float, DOTS>(op, X, Y, ncols, dots, s);
+}
+
+template <bool DOTS>
+int choose_kernel(const Operator& op, const float* X, float* Y, int ncols,
+                  double* dots, cudaStream_t s) {
   const StencilOp& st = op.st;
   // (0: plain, 1: with dots, 2: dots only)
   const TuneKey key{st.nx, st.ny, st.nz, st.radius, ncols,
@@ -543,46 +738,65 @@ bool use_planes(const Operator& op, const float* X, float* Y, int ncols,
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(key);
-    if (it != g_tuned.end()) return it->second == 1;
+    if (it != g_tuned.end()) return it->second;
   }
+  int kinds[3], nk = 0;
+  kinds[nk++] = kKernVec;
+  if (planes_eligible(op, X, Y, ncols)) kinds[nk++] = kKernPlanes;
+  if (zm_eligible(op, X, Y, ncols)) kinds[nk++] = kKernZm;
+  if (nk == 1) return kKernVec;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   TRM_CUDA(cudaStreamIsCapturing(s, &cs));
-  if (cs != cudaStreamCaptureStatusNone) return false;
-  cudaEvent_t ev[5];
+  if (cs != cudaStreamCaptureStatusNone) return kKernVec;
+  constexpr int kRounds = 2;
+  cudaEvent_t ev[1 + 3 * kRounds];
   for (auto& e : ev) TRM_CUDA(cudaEventCreate(&e));
   long long tuning = 0;
   capture_launches(&tuning);  // the timing launches are not the solve's
-  launch_vec<float, DOTS>(op, X, Y, ncols, dots, s);  // warm-up
+  for (int k = 0; k < nk; ++k)
+    launch_kind<DOTS>(kinds[k], op, X, Y, ncols, dots, s);  // warm-up
   TRM_CUDA(cudaEventRecord(ev[0], s));
-  for (int k = 0; k < 2; ++k) {
-    launch_vec<float, DOTS>(op, X, Y, ncols, dots, s);
-    TRM_CUDA(cudaEventRecord(ev[1 + 2 * k], s));
-    launch_planes_r<DOTS>(op, X, Y, ncols, dots, s);
-    TRM_CUDA(cudaEventRecord(ev[2 + 2 * k], s));
-  }
+  int e = 1;
+  for (int r = 0; r < kRounds; ++r)
+    for (int k = 0; k < nk; ++k) {
+      launch_kind<DOTS>(kinds[k], op, X, Y, ncols, dots, s);
+      TRM_CUDA(cudaEventRecord(ev[e++], s));
+    }
   capture_launches(nullptr);
-  TRM_CUDA(cudaEventSynchronize(ev[4]));
-  float tv = 0.f, tp = 0.f, t = 0.f;
-  for (int k = 0; k < 2; ++k) {
-    TRM_CUDA(cudaEventElapsedTime(&t, ev[2 * k], ev[1 + 2 * k]));
-    tv += t;
-    TRM_CUDA(cudaEventElapsedTime(&t, ev[1 + 2 * k], ev[2 + 2 * k]));
-    tp += t;
+  TRM_CUDA(cudaEventSynchronize(ev[e - 1]));
+  float tot[3] = {0.f, 0.f, 0.f}, t = 0.f;
+  for (int i = 1; i < e; ++i) {
+    TRM_CUDA(cudaEventElapsedTime(&t, ev[i - 1], ev[i]));
+    tot[(i - 1) % nk] += t;
   }
-  for (auto& e : ev) cudaEventDestroy(e);
+  for (auto& ee : ev) cudaEventDestroy(ee);
+  int best = 0;
+  for (int k = 1; k < nk; ++k)
+    if (tot[k] < tot[best]) best = k;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   // the first decision for a key stands (another thread may have tuned it)
-  auto it = g_tuned.emplace(key, tp < tv ? 1 : 0).first;
-  return it->second == 1;
+  return g_tuned.emplace(key, kinds[best]).first->second;
 }
 
 template <typename T, bool DOTS>
 int launch_apply(const Operator& op, const T* X, T* Y, int ncols, double* dots,
                  cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (planes_eligible(op, X, Y, ncols) &&
-        use_planes<DOTS>(op, X, Y, ncols, dots, s))
-      return launch_planes_r<DOTS>(op, X, Y, ncols, dots, s);
+    if (op.kind == 0 && op.st.nx % 4 == 0) {
+      // TRM_STENCIL_KERNEL=vec|planes|zm overrides the tuned choice (for
+      // tests and measurements; an ineligible kernel falls back to vec)
+      int kind = -1;
+      if (const char* f = std::getenv("TRM_STENCIL_KERNEL"))
+        kind = std::strcmp(f, "planes") == 0 ? kKernPlanes
+               : std::strcmp(f, "zm") == 0   ? kKernZm
+                                             : kKernVec;
+      // (a key's choice holds for its shape; this call's buffers must suit
+      // the kernel too)
+      if (kind < 0) kind = choose_kernel<DOTS>(op, X, Y, ncols, dots, s);
+      if ((kind == kKernPlanes && planes_eligible(op, X, Y, ncols)) ||
+          (kind == kKernZm && zm_eligible(op, X, Y, ncols)))
+        return launch_kind<DOTS>(kind, op, X, Y, ncols, dots, s);
+    }
   }
   return launch_vec<T, DOTS>(op, X, Y, ncols, dots, s);
 }

@@ -179,7 +179,8 @@ def test_device_output_and_repeatability(trm, m):
         trm.trm_destroy(h)
 
 
-def test_grid48_full_size_vs_oracle_reference(trm):
+@pytest.mark.parametrize("stencil", [None, "vec", "zm"])
+def test_grid48_full_size_vs_oracle_reference(trm, stencil, monkeypatch):
     """The benchmark workload at full size (48^3 grid, 13-point stencil, 64
     wells, m = 128, diagonal preconditioner), mixed precision to r <= 1e-10,
     launched as bench.py launches it. Against the oracle's Lanczos values
@@ -187,7 +188,12 @@ def test_grid48_full_size_vs_oracle_reference(trm):
     only): E_G to 1e-10 relative and every lambda_j to 1e-9. C^T C = I to
     1e-12. The largest principal angle to the exact invariant subspace is
     bounded (Davis-Kahan) by ||H C - C diag(lambda)||_F / (lambda_{m+1} -
-    lambda_m), with the residual formed on the CPU by the oracle's H."""
+    lambda_m), with the residual formed on the CPU by the oracle's H.
+    Run with the autotuned FP32 stencil and with the four-point kernel and
+    the register z-march forced (their fused column dots are grouped
+    differently)."""
+    if stencil:
+        monkeypatch.setenv("TRM_STENCIL_KERNEL", stencil)
     import json
     import os
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",

@@ -93,6 +93,42 @@ def test_apply_h_stencil(trm, shape, order, m):
         trm.trm_destroy(h)
 
 
+# The three FP32 stencil kernels the autotuner picks from (TRM_STENCIL_KERNEL
+# forces one): the four-point kernel, the staged planes and the register
+# z-march compute every point with the same operations in the same order, so
+# their outputs agree bit for bit, and each is within the FP32 bound of the
+# oracle. (48, 40, 33) gives the z-march two plane tiles of 240 quads and
+# several z chunks; (12, 10, 9) a ragged tile of 32 threads for 30 quads.
+@pytest.mark.parametrize("shape,order", [((16, 12, 10), 2), ((16, 12, 10), 4),
+                                         ((12, 10, 9), 4), ((48, 40, 33), 4),
+                                         ((64, 37, 6), 2), ((8, 8, 8), 4)])
+def test_fp32_stencil_kernels_agree(trm, shape, order, monkeypatch):
+    V = ti.gaussian_wells(shape, 3, seed=2)
+    H = op.grid_hamiltonian(shape, order, 1.0, V)
+    N, m = H.shape[0], 7
+    h = _handle(trm, shape, order, V, 1)
+    try:
+        C32 = ti.random_block(N, m, seed=9).astype(np.float32)
+        ref = op.apply_h(H, C32.astype(np.float64))
+        scale = np.abs(H) @ np.abs(C32.astype(np.float64))
+        cs = gu.to_dev(C32)
+        outs = {}
+        for kern in ("vec", "planes", "zm"):
+            monkeypatch.setenv("TRM_STENCIL_KERNEL", kern)
+            xs = gu.empty(N, m, np.float32)
+            trm.trm_apply_h(h, trm.TRM_F32, cs.data_ptr(), trm.TRM_F32,
+                            xs.data_ptr(), m)
+            outs[kern] = gu.from_dev(xs)
+            X = outs[kern].astype(np.float64)
+            assert np.all(np.abs(X - ref) <= gamma(15) * scale), kern
+        for kern in ("planes", "zm"):
+            assert np.array_equal(outs[kern].view(np.uint32),
+                                  outs["vec"].view(np.uint32)), kern
+    finally:
+        monkeypatch.delenv("TRM_STENCIL_KERNEL", raising=False)
+        trm.trm_destroy(h)
+
+
 @pytest.mark.parametrize("vals_dtype", [np.float64, np.float32])
 def test_apply_h_csr_matches_oracle(trm, vals_dtype):
     shape, order, m = (14, 12, 10), 4, 9
@@ -334,10 +370,16 @@ def test_rayleigh_ritz_degenerate_spectrum(trm, n, m):
 # ---------------------------------------------------------------------------
 # a5, a7: one step of Fig. TMFIG (FP64, full SP and MP2)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("m", [10, 40])
+# m = 96 and 200 put the line-search Grams on the tensor cores with output
+# segments of m columns that end inside a 128-column tile; at 28^3, m = 200
+# the rotation walks 344 tiles in two column chunks on the persistent grid
+# of a triangular product (the first chunk needs only the K blocks below
+# 128).
+@pytest.mark.parametrize("shape,m", [((14, 12, 11), 10), ((14, 12, 11), 40),
+                                     ((14, 12, 11), 96), ((28, 28, 28), 200)])
 @pytest.mark.parametrize("mode", ["fp64", "sp", "mp2"])
-def test_iterate_one_step(trm, mode, m):
-    shape, order = (14, 12, 11), 4
+def test_iterate_one_step(trm, mode, shape, m):
+    order = 4
     V = ti.gaussian_wells(shape, 4, seed=6)
     H = op.grid_hamiltonian(shape, order, 1.0, V)
     N = H.shape[0]
@@ -357,9 +399,32 @@ def test_iterate_one_step(trm, mode, m):
         trm.trm_get_block(h, out.data_ptr())
         C1 = gu.from_dev(out)
         orth = {"fp64": 1e-13, "sp": 1e-5, "mp2": 1e-6}[mode]
+        if mode == "mp2":
+            # MP2 factors the overlap S(a) = I + a (B + B^T) + a^2 Q from
+            # FP32-class Grams B = C^T P, Q = P^T P (Sec. 2.2), so C1 is
+            # orthonormal to their rounding: on the tensor cores each product
+            # is within 2^-19 |c||p| (the TF32 two-term split), which gives
+            # |C1^T C1 - I| <~ 2^-19 max_j (a^2 |p_j|^2 + 2 a sum |c_j||p_j|)
+            # with P = G0 on this restart step (M = I); twice that bound
+            q = np.sum(G0 * G0, axis=0)
+            cp = np.sum(np.abs(C) * np.abs(G0), axis=0)
+            orth = max(orth, 2.0 * 2.0 ** -19 * np.max(a * a * q + 2 * a * cp))
         assert np.max(np.abs(C1.T @ C1 - np.eye(m))) < orth
         # new span = span(C + a P) with P = G on a restart (M = I)
         ang = {"fp64": 1e-10, "sp": 1e-4, "mp2": 1e-6}[mode]
+        if mode == "mp2":
+            # the step's direction is the GPU's FP32 gradient G = -2 (X' -
+            # C H') (Sec. 2.2: (7) in single precision), within
+            # dG = 2 (2^-24 |X'| + 2^-19 |C| |H'|) of the oracle's (FP32
+            # rounding of X', the TF32 split of the product); since C is
+            # orthonormal and C^T G0 = 0, sigma_min(C + a G0) >= 1 and the
+            # spans differ by at most a ||dG||_2
+            X = op.apply_h(H, C)
+            Xp = X - C * np.sum(C * X, axis=0)
+            Hp = C.T @ Xp
+            np.fill_diagonal(Hp, 0.0)
+            dG = 2.0 * (U32 * np.abs(Xp) + 2.0 ** -19 * (np.abs(C) @ np.abs(Hp)))
+            ang = max(ang, a * np.linalg.norm(dG, 2))
         assert otrm.sin_max_angle(C1, C + a * G0) < ang
         E1 = otrm.energy_gradient_alg1(H, otrm.orthonormalize(C1))[0]
         assert E1 < E0
