@@ -63,13 +63,21 @@ FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 DF_TFLOPS = FP32_SIMT_TFLOPS / 12
 DF_CLASSES = ("gram_f64", "rotate_f64")
 # Kernel classes whose bound is HBM traffic (algorithmic bytes); the others
-# are bound by FP64 (or FP32 SIMT) arithmetic. The FP32 product classes run
-# on the tensor cores, where at m = 128 the TF32 MMAs take less time than the
-# operands take to stream, so traffic bounds them; spmm_df and rotate_df are
-# MP2's double-float stencil and split rotation (FP32 pairs, 8 bytes per
-# element like FP64).
+# are bound by FP64 (or FP32 SIMT) arithmetic; the tensor-core classes below
+# take whichever roof binds them. spmm_df and rotate_df are MP2's
+# double-float stencil and split rotation (FP32 pairs, 8 bytes per element
+# like FP64).
 HBM_CLASSES = ("spmm_f32", "spmm_f64", "spmm_df", "gram_f32", "grad_f32",
                "rotate_f32", "rotate_df", "rowops")
+# The classes on the tensor cores: each algorithmic flop is three TF32
+# products (hi.hi + hi.lo + lo.hi), so their compute roof is the TF32 rate
+# / 3. The TF32 rate is the measured BF16 rate times the nominal TF32/BF16
+# ratio (1.1 / 2.25 PFLOP/s dense). A launch is rated against the roof that
+# binds it: the larger of its HBM floor (bytes / copy bandwidth) and its
+# tensor floor (flops / (TF32 rate / 3)).
+TC_CLASSES = ("gram_f32", "grad_f32", "rotate_f32", "rotate_df")
+TF32_OVER_BF16 = 1.1 / 2.25
+TC_SPLIT = 3
 METRIC = "time-to-E_G at 1e-10 rel err (mixed precision)"
 
 
@@ -91,8 +99,12 @@ def parse():
                          "request server; prints latency p50/p99 and solves/s")
     ap.add_argument("--rate", type=float, default=20.0,
                     help="serving: mean arrivals per second")
-    ap.add_argument("--max-live", type=int, default=8,
+    ap.add_argument("--max-live", type=int, default=16,
                     help="serving: concurrent solves")
+    ap.add_argument("--serving-leg", type=float, default=4.0,
+                    help="seconds of Poisson arrivals at 50/s served after "
+                         "the solve benchmark (the serving key: p50/p99 "
+                         "latency and solves/s; 0 leaves it out)")
     ap.add_argument("--compare", type=int, default=1,
                     help="serving: also replay the trace one request at a "
                          "time and compare every result")
@@ -366,7 +378,25 @@ def roofline(prof, peaks, src, double_float=True):
 
     def entry(cname, cc):
         pl = cc["ms"] / 1e3 / cc["launches"]
-        if cname in HBM_CLASSES and cc["bytes"] > 0:
+        if cname in TC_CLASSES and cc["bytes"] > 0 and cc["flops"] > 0:
+            bf16 = peaks.get("bf16_tflops_sustained") or peaks["bf16_tflops"]
+            tc_pk = bf16 * TF32_OVER_BF16 / TC_SPLIT
+            t_hbm = cc["bytes"] / cc["launches"] / (peaks["hbm_gbs"] * 1e9)
+            t_tc = cc["flops"] / cc["launches"] / (tc_pk * 1e12)
+            hbm = cc["bytes"] / cc["launches"] / pl / 1e9
+            tcv = cc["flops"] / cc["launches"] / pl / 1e12
+            if t_tc > t_hbm:
+                e = {"bound": "tensor", "achieved": tcv, "peak": tc_pk,
+                     "unit": "TFLOP/s", "frac": tcv / tc_pk,
+                     "peak_source": src + " (BF16 sustained x 1.1/2.25 for "
+                     "TF32, / 3 products per algorithmic flop)",
+                     "hbm_frac": hbm / peaks["hbm_gbs"]}
+            else:
+                e = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"],
+                     "peak_source": src + " (copy bandwidth)",
+                     "tensor_frac": tcv / tc_pk}
+        elif cname in HBM_CLASSES and cc["bytes"] > 0:
             ach = cc["bytes"] / cc["launches"] / pl / 1e9
             e = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
                  "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
@@ -473,9 +503,11 @@ def serving_trace(seconds, rate, seed=2024):
         out.append((t, (n, n, n), order, V, m))
 
 
-def serve(trm, trace, max_live, tol, budget):
+def serve(trm, trace, max_live, tol, budget, index=None):
     """Replays the trace through a server; returns the per-request results
-    and the wall time from the first arrival to the last completion."""
+    and the wall time from the first arrival to the last completion.
+    Request k's starting block is seeded by its index in the full trace
+    (index[k], default k)."""
     srv = trm.trm_server_create(budget, max_live)
     tickets = []
     t0 = time.perf_counter()
@@ -484,8 +516,9 @@ def serve(trm, trace, max_live, tol, budget):
             dt = t0 + ta - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            opt = trm.trm_default_options(precision=trm.TRM_MIXED, precond=1,
-                                          seed=1000 + i)
+            opt = trm.trm_default_options(
+                precision=trm.TRM_MIXED, precond=1,
+                seed=1000 + (i if index is None else index[i]))
             tickets.append(trm.trm_server_submit(srv, shape, order, 1.0, V, m,
                                                  tol, opt))
         res = [trm.trm_server_wait(srv, tk, tr[4])
@@ -496,37 +529,47 @@ def serve(trm, trace, max_live, tol, budget):
     return res, wall
 
 
-def run_serving(args):
+def serving_run(trm, torch, seconds, rate, max_live, tol, compare,
+                clocks=True, sample_alone=0):
+    """One serving measurement: the seeded trace replayed through a server.
+    compare: replay the whole trace one request at a time and compare every
+    result; sample_alone > 0: re-solve that many requests (spread over the
+    trace) one at a time and compare those."""
     import numpy as np
-    import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_1108_4509_gb300 as trm
-    trace = serving_trace(args.serving, args.rate)
+    trace = serving_trace(seconds, rate)
     budget = int(0.5 * torch.cuda.mem_get_info()[0])
     # warm-up: one small solve through a server (module load, attributes)
-    serve(trm, trace[:2], 2, args.tol, budget)
+    serve(trm, trace[:2], 2, tol, budget)
     sampler = ClockSampler(0)
-    if args.clocks:
+    if clocks:
         sampler.start()
     launches0 = trm.trm_launch_count()
-    res, wall = serve(trm, trace, args.max_live, args.tol, budget)
+    res, wall = serve(trm, trace, max_live, tol, budget)
     launches = trm.trm_launch_count() - launches0
-    clocks = sampler.stop()
+    clk = sampler.stop()
     lat = np.array([r[4] for r in res])
     seq = None
-    if args.compare:
-        seq, wall1 = serve(trm, trace, 1, args.tol, budget)
+    if compare:
+        seq, wall1 = serve(trm, trace, 1, tol, budget)
         lat1 = np.array([r[4] for r in seq])
-    out = {"metric": "serving latency p50/p99 and throughput (mixed precision)",
-           "value": len(trace) / wall, "unit": "solves/s", "n_gpus": 1,
-           "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+    same = None
+    if seq is not None:
+        same = bool(all(np.array_equal(a[0], b[0]) and a[1] == b[1]
+                        for a, b in zip(res, seq)))
+    elif sample_alone > 0:
+        idx = sorted(set(np.linspace(0, len(trace) - 1,
+                                     min(sample_alone, len(trace))).astype(int)))
+        alone, _ = serve(trm, [(0.0,) + tuple(trace[i][1:]) for i in idx], 1,
+                         tol, budget, index=idx)
+        same = bool(all(np.array_equal(res[i][0], a[0]) and res[i][1] == a[1]
+                        for i, a in zip(idx, alone)))
+        same_how = "%d requests spread over the trace re-solved alone" % len(idx)
+    out = {"value": len(trace) / wall, "unit": "solves/s",
            "config": {"workload": "Poisson arrivals of stencil problems",
-                      "rate_per_s": args.rate, "seconds": args.serving,
+                      "rate_per_s": rate, "seconds": seconds,
                       "requests": len(trace), "grid": "12^3..40^3",
                       "order": [2, 4], "wells": "4..64", "m": "8..96",
-                      "tol": args.tol, "max_live": args.max_live},
+                      "tol": tol, "max_live": max_live},
            "latency_s": {"p50": float(np.percentile(lat, 50)),
                          "p99": float(np.percentile(lat, 99)),
                          "max": float(lat.max())},
@@ -535,10 +578,24 @@ def run_serving(args):
                "p50": float(np.percentile(lat1, 50)),
                "p99": float(np.percentile(lat1, 99))},
            "status": sorted({int(r[3]) for r in res}),
-           "same_bytes_as_one_at_a_time": None if seq is None else bool(all(
-               np.array_equal(a[0], b[0]) and a[1] == b[1]
-               for a, b in zip(res, seq))),
-           "gpu_launches": launches, "clocks": clocks}
+           "same_bytes_as_alone": same,
+           "gpu_launches": launches, "clocks": clk}
+    if seq is None and sample_alone > 0:
+        out["same_bytes_checked"] = same_how
+    return out
+
+
+def run_serving(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1108_4509_gb300 as trm
+    r = serving_run(trm, torch, args.serving, args.rate, args.max_live,
+                    args.tol, args.compare, clocks=args.clocks)
+    out = {"metric": "serving latency p50/p99 and throughput (mixed precision)",
+           "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64",
+           "data": "synthetic", **r}
     print(json.dumps(out))
     return 0
 
@@ -1125,6 +1182,15 @@ def main():
         except Exception as exc:  # reported, not fatal
             xlarge = {"error": str(exc)[:300]}
 
+    serving = None
+    if args.serving_leg > 0 and rank == 0:
+        try:
+            serving = serving_run(trm, torch, args.serving_leg, 50.0,
+                                  args.max_live, args.tol, 0,
+                                  clocks=args.clocks, sample_alone=8)
+        except Exception as exc:  # reported, not fatal
+            serving = {"error": str(exc)[:300]}
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         try:
@@ -1162,6 +1228,7 @@ def main():
                        "in tensor memory"},
                "large": large,
                **({"xlarge": xlarge} if xlarge is not None else {}),
+               "serving": serving,
                "cpu_baseline": cpu}
         print(json.dumps(out))
     if dist:

@@ -79,3 +79,26 @@ def test_double_float_classes_use_the_fp32_pipe_ceiling():
     _, fp64 = bench.roofline(prof, {"hbm_gbs": 6700.0}, "measured",
                              double_float=False)
     assert fp64["gram_f64"]["peak"] == bench.FP64_TFLOPS
+
+
+def test_tensor_core_classes_take_the_binding_roof():
+    # m = 512 line Grams: 5 m^2 N flops against 3 blocks of FP32 (12 N m
+    # bytes); the TF32 roof / 3 binds, so the class is rated in TFLOP/s
+    peaks = {"hbm_gbs": 6700.0, "bf16_tflops": 1900.0,
+             "bf16_tflops_sustained": 1700.0}
+    N, m = 884736, 512
+    fl, by = 5.0 * m * m * N, 12.0 * N * m
+    prof = {"gram_f32": {"ms": 6.0, "launches": 1, "bytes": by, "flops": fl}}
+    r, _ = bench.roofline(prof, peaks, "measured")
+    pk = 1700.0 * bench.TF32_OVER_BF16 / bench.TC_SPLIT
+    assert r["bound"] == "tensor" and abs(r["peak"] - pk) < 1e-9
+    assert abs(r["achieved"] - fl / 6e-3 / 1e12) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / pk) < 1e-12
+    assert 0.0 < r["hbm_frac"] < r["frac"]
+    # m = 16: the same kind of launch is bound by its bytes
+    m = 16
+    fl, by = 5.0 * m * m * N, 12.0 * N * m
+    prof = {"gram_f32": {"ms": 0.1, "launches": 1, "bytes": by, "flops": fl}}
+    r, _ = bench.roofline(prof, peaks, "measured")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert 0.0 < r["tensor_frac"] < r["frac"]
