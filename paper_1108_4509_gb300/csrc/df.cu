@@ -104,14 +104,26 @@ __global__ void __launch_bounds__(256)
 // x0..x0+3 of a row, loads the centre, the neighbouring quads along x and the
 // y/z neighbours as 16-byte (hi, lo) vectors, and takes the x neighbours
 // from registers, which cuts loads and boundary logic per point fourfold.
-template <int R>
+//
+// With DOTS the column dots H_D = c_j . (H c)_j of Fig. EGFIG step (2) are
+// formed from the pairs in registers (the arithmetic of k_coldot_df per
+// thread, double-float warp sums, one FP64 add per warp), so the MP2 step
+// does not read C and X again: CTA b writes dots[b * ncols + column].
+template <int R, bool DOTS>
 __global__ void __launch_bounds__(256)
     k_stencil_df_v4(StencilOp st, int64_t N, const float* __restrict__ dh,
                     const float* __restrict__ dl, const float* __restrict__ Ch,
                     const float* __restrict__ Cl, float* __restrict__ Xh,
-                    float* __restrict__ Xl, int ncols) {
-  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= (N >> 2)) return;
+                    float* __restrict__ Xl, int ncols,
+                    double* __restrict__ dots) {
+  const int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = v0 < (N >> 2);
+  if (!DOTS && !valid) return;  // with DOTS every thread joins the sums
+  const int64_t v = valid ? v0 : 0;
+  __shared__ double red[kCols][8];
+  F2 dacc[kCols];
+#pragma unroll
+  for (int q = 0; q < kCols; ++q) dacc[q] = F2{0.f, 0.f};
   const int nxv = st.nx >> 2;
   const int xv = (int)(v % nxv);
   const int64_t yz = v / nxv;
@@ -140,9 +152,10 @@ __global__ void __launch_bounds__(256)
     a[3].add(h.w, l.w);
   };
   const int cb = blockIdx.y * kCols;
+#pragma unroll
   for (int q = 0; q < kCols; ++q) {
     const int c = cb + q;
-    if (c >= ncols) break;
+    if (c >= ncols || !valid) break;
     const int64_t base = (int64_t)c * N + i0;
     const float* ph = Ch + base;
     const float* pl = Cl + base;
@@ -184,6 +197,32 @@ __global__ void __launch_bounds__(256)
     }
     *reinterpret_cast<float4*>(Xh + base) = make_float4(oh[0], oh[1], oh[2], oh[3]);
     *reinterpret_cast<float4*>(Xl + base) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+    if (DOTS) {
+      F2 a = dacc[q];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        a = df_add(a, df_mul(F2{cH[k], cL[k]}, F2{oh[k], ol[k]}));
+      dacc[q] = a;
+    }
+  }
+  if (DOTS) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kCols; ++q) {
+      F2 w = dacc[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        w = df_add(w, F2{__shfl_xor_sync(0xffffffffu, w.h, o),
+                         __shfl_xor_sync(0xffffffffu, w.l, o)});
+      if (lane == 0) red[q][warp] = to_f64(w.h) + to_f64(w.l);
+    }
+    __syncthreads();
+    if (threadIdx.x < kCols && cb + (int)threadIdx.x < ncols) {
+      double t = red[threadIdx.x][0];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) t += red[threadIdx.x][w];
+      dots[(size_t)blockIdx.x * ncols + cb + threadIdx.x] = t;
+    }
   }
 }
 
@@ -322,11 +361,11 @@ void apply_h_df(const Operator& op, const float* Ch, const float* Cl,
   if (v4) {
     dim3 g4(ceil_div(op.N / 4, 256), gy);
     if (op.st.radius == 1)
-      k_stencil_df_v4<1><<<g4, 256, 0, s>>>(op.st, op.N, op.diag32, op.diaglo,
-                                            Ch, Cl, Xh, Xl, ncols);
+      k_stencil_df_v4<1, false><<<g4, 256, 0, s>>>(
+          op.st, op.N, op.diag32, op.diaglo, Ch, Cl, Xh, Xl, ncols, nullptr);
     else
-      k_stencil_df_v4<2><<<g4, 256, 0, s>>>(op.st, op.N, op.diag32, op.diaglo,
-                                            Ch, Cl, Xh, Xl, ncols);
+      k_stencil_df_v4<2, false><<<g4, 256, 0, s>>>(
+          op.st, op.N, op.diag32, op.diaglo, Ch, Cl, Xh, Xl, ncols, nullptr);
   } else if (op.kind == 0) {
     if (op.st.radius == 1)
       k_stencil_df<1><<<grid, 256, 0, s>>>(op.st, op.N, op.diag32, op.diaglo,
@@ -340,6 +379,28 @@ void apply_h_df(const Operator& op, const float* Ch, const float* Cl,
                                   Xl, ncols);
   }
   TRM_CHECK_LAUNCH();
+}
+
+int apply_h_df_dots(const Operator& op, const float* Ch, const float* Cl,
+                    float* Xh, float* Xl, int ncols, double* dots,
+                    cudaStream_t s) {
+  if (ncols <= 0) return 0;
+  const bool v4 = op.kind == 0 && op.st.nx % 4 == 0 && op.N % 4 == 0 &&
+                  ((reinterpret_cast<uintptr_t>(Ch) | reinterpret_cast<uintptr_t>(Cl) |
+                    reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl) |
+                    reinterpret_cast<uintptr_t>(op.diag32) |
+                    reinterpret_cast<uintptr_t>(op.diaglo)) & 15) == 0;
+  const int gy = ceil_div(ncols, kCols);
+  if (!v4 || gy > 65535) return 0;  // the caller forms the dots separately
+  dim3 g4(ceil_div(op.N / 4, 256), gy);
+  if (op.st.radius == 1)
+    k_stencil_df_v4<1, true><<<g4, 256, 0, s>>>(
+        op.st, op.N, op.diag32, op.diaglo, Ch, Cl, Xh, Xl, ncols, dots);
+  else
+    k_stencil_df_v4<2, true><<<g4, 256, 0, s>>>(
+        op.st, op.N, op.diag32, op.diaglo, Ch, Cl, Xh, Xl, ncols, dots);
+  TRM_CHECK_LAUNCH();
+  return (int)g4.x;  // partial dots per column
 }
 
 void energy_diag_df(int64_t N, int m, const float* Ch, const float* Cl,

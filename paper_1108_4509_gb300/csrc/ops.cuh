@@ -63,6 +63,13 @@ void join_df(const float* hi, const float* lo, double* x, int64_t n,
 // X = H C in double-float (needs Operator::diaglo, and valshi/valslo for CSR)
 void apply_h_df(const Operator& op, const float* Ch, const float* Cl,
                 float* Xh, float* Xl, int ncols, cudaStream_t s);
+// The same with the column dots sum_i C_ij X_ij of each CTA in
+// dots[chunk * ncols + j] (apply_h_dots_doubles entries; energy_from_dots
+// adds them up); returns the number of chunks, or 0 when this operator or
+// these buffers take the unfused kernels (then nothing is launched).
+int apply_h_df_dots(const Operator& op, const float* Ch, const float* Cl,
+                    float* Xh, float* Xl, int ncols, double* dots,
+                    cudaStream_t s);
 // H_D[j] = sum_i C_ij X_ij, E = sum_j H_D[j] into sc->E
 void energy_diag_df(int64_t N, int m, const float* Ch, const float* Cl,
                     const float* Xh, const float* Xl, double* HD,

@@ -728,9 +728,18 @@ void Solver::iter_mp2() {
   double f64, b64, f32, b32;
   spmm_cost(op_, m_, 8, &f64, &b64);
   spmm_cost(op_, m_, 4, &f32, &b32);
-  TRM_PROF(KC_SPMMDF, f64, b64, apply_h_df(op_, Ch, Cl, Xh, Xl, m_, s_));  // (1)
-  TRM_PROF(KC_ROWOPS, 2 * dnm, 16 * dnm,
-           energy_diag_df(N_, m_, Ch, Cl, Xh, Xl, HD_, sc_, part_, s_));  // (2), (3)
+  // (1) with the column dots of (2) fused in where the stencil kernel allows
+  int chunks = 0;
+  TRM_PROF(KC_SPMMDF, f64, b64,
+           chunks = apply_h_df_dots(op_, Ch, Cl, Xh, Xl, m_, part_, s_));
+  if (chunks) {
+    TRM_PROF(KC_ROWOPS, 2.0 * m_ * chunks, 8.0 * m_ * chunks,
+             energy_from_dots(part_, chunks, m_, HD_, sc_, s_));  // (2), (3)
+  } else {
+    TRM_PROF(KC_SPMMDF, f64, b64, apply_h_df(op_, Ch, Cl, Xh, Xl, m_, s_));
+    TRM_PROF(KC_ROWOPS, 2 * dnm, 16 * dnm,
+             energy_diag_df(N_, m_, Ch, Cl, Xh, Xl, HD_, sc_, part_, s_));
+  }
   TRM_PROF(KC_ROWOPS, 2 * dnm, 20 * dnm,
            xprime_df(N_, m_, Ch, Cl, Xh, Xl, HD_, X32_, s_));  // (5) FP32 X'
   Blocks<float> bx;
