@@ -43,7 +43,10 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <unordered_map>
 
 #include "dfmath.cuh"
@@ -400,6 +403,87 @@ static int tc_splits(int64_t N, int tiles, int max_splits, int sms) {
   return best;
 }
 
+// Autotuned row slices. The formula above fills the SMs in whole waves, but
+// how many slices run best also depends on how the CTAs of a wave share
+// their operand tiles in L2, which the formula does not model. The first
+// launch of each (N, m, n, tiles, symmetric segment) in the process
+// therefore times the formula's count, half of it and twice it (within the
+// partials buffer and at least kMinStages stages per slice), twice each in
+// turn with CUDA events on the stream, and keeps the fastest for the
+// process (never inside a stream capture: the formula's count is used
+// there until a choice exists); a later call whose buffer holds fewer
+// slices takes at most what it holds. Every count gives the same sum to the
+// accumulation bound; the bytes depend on the count, so the choice is
+// fixed per process and repeated solves agree bit for bit.
+struct SliceKey {
+  int64_t N;
+  int m, n, tiles, sym;
+  bool operator<(const SliceKey& o) const {
+    return std::tie(N, m, n, tiles, sym) <
+           std::tie(o.N, o.m, o.n, o.tiles, o.sym);
+  }
+};
+std::mutex g_slice_mu;
+std::map<SliceKey, int> g_slices;
+
+template <typename Run>
+int tuned_splits(int64_t N, int m, int n, int tiles, int sym, int smax,
+                 cudaStream_t s, Run& run) {
+  const int sms = sm_count();
+  const int base = tc_splits(N, tiles, smax, sms);
+  // TRM_GRAM_SLICES=formula (or a count) fixes the slices instead (for
+  // profilers, whose serialised replay would distort the timing)
+  if (const char* f = std::getenv("TRM_GRAM_SLICES")) {
+    const int v = std::atoi(f);
+    return v > 0 ? std::min(v, smax) : base;
+  }
+  const SliceKey key{N, m, n, tiles, sym};
+  {
+    std::lock_guard<std::mutex> lock(g_slice_mu);
+    auto it = g_slices.find(key);
+    if (it != g_slices.end()) return std::min(it->second, smax);
+  }
+  const int most = (int)std::max<int64_t>(
+      1, std::min<int64_t>(smax, ceil_div(N, (int64_t)BK * kMinStages)));
+  int cand[3], nc = 0;
+  for (int c : {base, base / 2, 2 * base}) {
+    c = std::max(1, std::min(c, most));
+    bool dup = false;
+    for (int k = 0; k < nc; ++k) dup |= cand[k] == c;
+    if (!dup) cand[nc++] = c;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TRM_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (nc == 1 || cs != cudaStreamCaptureStatusNone) return base;
+  constexpr int kRounds = 2;
+  cudaEvent_t ev[1 + 3 * kRounds];
+  for (auto& e : ev) TRM_CUDA(cudaEventCreate(&e));
+  long long tuning = 0;
+  capture_launches(&tuning);  // the timing launches are not the caller's
+  for (int k = 0; k < nc; ++k) run(cand[k]);  // warm-up
+  TRM_CUDA(cudaEventRecord(ev[0], s));
+  int e = 1;
+  for (int r = 0; r < kRounds; ++r)
+    for (int k = 0; k < nc; ++k) {
+      run(cand[k]);
+      TRM_CUDA(cudaEventRecord(ev[e++], s));
+    }
+  capture_launches(nullptr);
+  TRM_CUDA(cudaEventSynchronize(ev[e - 1]));
+  float tot[3] = {0.f, 0.f, 0.f}, t = 0.f;
+  for (int i = 1; i < e; ++i) {
+    TRM_CUDA(cudaEventElapsedTime(&t, ev[i - 1], ev[i]));
+    tot[(i - 1) % nc] += t;
+  }
+  for (auto& ee : ev) cudaEventDestroy(ee);
+  int best = 0;
+  for (int k = 1; k < nc; ++k)
+    if (tot[k] < tot[best]) best = k;
+  std::lock_guard<std::mutex> lock(g_slice_mu);
+  // the first decision for a key stands (another thread may have tuned it)
+  return std::min(g_slices.emplace(key, cand[best]).first->second, smax);
+}
+
 size_t gram_tc_partials_doubles(int64_t N, int m, int n, int skipped_tiles) {
   const int tiles = ceil_div(m, BM) * ceil_div(n, BN) - skipped_tiles;
   return (size_t)tc_splits(N, std::max(1, tiles), 1 << 30, sm_count()) * m * n;
@@ -445,12 +529,6 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
   if (by_cap < 1) throw Error(-2, "gram_tc: partials buffer too small");
   int smax = max_splits > 0 ? max_splits : 1 << 30;
   if ((size_t)smax > by_cap) smax = (int)by_cap;
-  int splits = tc_splits(N, tiles, smax, sm_count());
-  int64_t rows = (N + splits - 1) / splits;
-  rows = ((rows + BK - 1) / BK) * BK;
-  splits = (int)((N + rows - 1) / rows);
-  if ((size_t)splits * m * n > cap)
-    throw Error(-2, "gram_tc: partials buffer too small");
   TcMaps maps;
   for (int k = 0; k < 4; ++k) {
     const int kb = k < B.count ? k : 0;
@@ -460,7 +538,6 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
   a.N = N;
   a.m = m;
   a.n = n;
-  a.rows_per_split = rows;
   a.seg_cols = segcols;
   a.tps = tps;
   a.part = partials;
@@ -471,12 +548,21 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
     cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   });
-  dim3 grid(splits, tiles);
-  k_gram_tc<<<grid, THREADS, smem, s>>>(maps, a);
-  TRM_CHECK_LAUNCH();
   const size_t count = (size_t)m * n;
-  sum_splits_pairs(reinterpret_cast<const float*>(partials), splits, count,
-                   out, s, out32, SymSeg{sym_seg, m, segcols, BM});
+  // one launch with about `want` row slices (rounded to whole stages)
+  auto run = [&](int want) {
+    int64_t rows = (N + want - 1) / want;
+    rows = ((rows + BK - 1) / BK) * BK;
+    const int splits = (int)((N + rows - 1) / rows);
+    if ((size_t)splits * count > cap)
+      throw Error(-2, "gram_tc: partials buffer too small");
+    a.rows_per_split = rows;
+    k_gram_tc<<<dim3(splits, tiles), THREADS, smem, s>>>(maps, a);
+    TRM_CHECK_LAUNCH();
+    sum_splits_pairs(reinterpret_cast<const float*>(partials), splits, count,
+                     out, s, out32, SymSeg{sym_seg, m, segcols, BM});
+  };
+  run(tuned_splits(N, m, n, tiles, sym_seg, smax, s, run));
 }
 
 }  // namespace trm
