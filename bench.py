@@ -333,7 +333,7 @@ PROFILE_OF_CLASS = {
     "gram_f32": "k_gram_tc_line_grams_grid48_m128.md",
     "spmm_df": "k_stencil_df_v4_mp2_grid48_m128.md",
     "rotate_df": "k_mul_tc_splitdf_mp2_grid48_m128.md",
-    "spmm_f32": "k_stencil_v4_f32_grid48_m128.md",
+    "spmm_f32": "k_stencil_zm_f32_grid48_m128.md",
 }
 
 
