@@ -326,7 +326,7 @@ long long trm_launch_count(void);
  * with a message in trm_last_global_error().
  * Kernels: FP32 operands that trm_gram sends to the tensor cores (N % 4 == 0,
  * m >= 32, A and B 16-byte aligned) run that same kernel (error below
- * 8e-6 sum_k |a_ki||b_kj|), with the same row slices and sum order, so the
+ * 1.4e-5 sum_k |a_ki||b_kj|), with the same row slices and sum order, so the
  * same bytes as trm_gram's, whenever m * n * slices <= 3 * 2^20 - 1 (else
  * with fewer, longer slices); other FP32 operands and all FP64 operands run
  * trm_gram's SIMT kernel (products summed in the operands' precision within

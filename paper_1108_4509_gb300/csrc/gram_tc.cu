@@ -71,7 +71,7 @@ constexpr int BK = 32;         // block rows per stage (one 128-byte box)
 constexpr int RSTAGES = TRM_GRAM_RSTAGES;  // raw TMA stages (the hi operands)
 constexpr int OSTAGES = TRM_GRAM_OSTAGES;  // lo stages
 constexpr int THREADS = 576;  // 18 warps
-constexpr int KC = 4;         // stages per accumulation chunk
+constexpr int KC = 8;         // stages per accumulation chunk (default)
 constexpr int kSingleChunk = 96;  // row slices this short are one chunk
 // Row slices of at least this many stages: a small problem takes fewer CTAs
 // (each holds a whole SM) and leaves the rest of the GPU to concurrent solves.
@@ -126,6 +126,7 @@ struct TcArgs {
   int64_t N;
   int m, n;               // output is m x n
   int64_t rows_per_split;
+  int kc;                 // stages per accumulation chunk of long slices
   int seg_cols;           // columns per segment
   int tps;                // column tiles per segment (the last one ragged:
                           // its columns past seg_cols load as zeros)
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       bool ok = true;
-      const int kcl = nk <= kSingleChunk ? nk : KC;  // stages per chunk
+      const int kcl = nk <= kSingleChunk ? nk : args.kc;  // stages per chunk
       for (int k = 0; k < nk && ok; ++k) {
         const int s = k % OSTAGES, r = k % RSTAGES;
         const int kc = k % kcl, c = k / kcl, b = c & 1;
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;            // TMEM lane quarter of this warp
     const int g = (warp - 10) >> 2;    // column half of the tile
     const uint32_t lrow = (uint32_t)(32 * q) << 16;
-    const int kcl = nk <= kSingleChunk ? nk : KC;
+    const int kcl = nk <= kSingleChunk ? nk : args.kc;
     const int nch = nk > 0 ? (nk + kcl - 1) / kcl : 0;
     const int row = i0 + 32 * q + lane;
     // partials as FP32 pairs: split s holds hi at [2 s count, (2 s + 1)
@@ -407,12 +408,12 @@ static int tc_splits(int64_t N, int tiles, int max_splits, int sms) {
 // how many slices run best also depends on how the CTAs of a wave share
 // their operand tiles in L2, which the formula does not model. The first
 // launch of each (N, m, n, tiles, symmetric segment) in the process
-// therefore times the formula's count, half of it and twice it (within the
-// partials buffer and at least kMinStages stages per slice), twice each in
-// turn with CUDA events on the stream, and keeps the fastest for the
-// process (never inside a stream capture: the formula's count is used
-// there until a choice exists); a later call whose buffer holds fewer
-// slices takes at most what it holds. Every count gives the same sum to the
+// therefore times the formula's count and half of it (at least kMinStages
+// stages per slice), twice each in turn with CUDA events on the stream, and
+// keeps the faster for the process (never inside a stream capture: the
+// formula's count is used there until a choice exists). No candidate
+// exceeds the formula's count, which every caller's partials buffer holds,
+// so the choice does not depend on which caller made it. Every count gives the same sum to the
 // accumulation bound; the bytes depend on the count, so the choice is
 // fixed per process and repeated solves agree bit for bit.
 struct SliceKey {
@@ -445,8 +446,8 @@ int tuned_splits(int64_t N, int m, int n, int tiles, int sym, int smax,
   }
   const int most = (int)std::max<int64_t>(
       1, std::min<int64_t>(smax, ceil_div(N, (int64_t)BK * kMinStages)));
-  int cand[3], nc = 0;
-  for (int c : {base, base / 2, 2 * base}) {
+  int cand[2], nc = 0;
+  for (int c : {base, base / 2}) {
     c = std::max(1, std::min(c, most));
     bool dup = false;
     for (int k = 0; k < nc; ++k) dup |= cand[k] == c;
@@ -456,7 +457,7 @@ int tuned_splits(int64_t N, int m, int n, int tiles, int sym, int smax,
   TRM_CUDA(cudaStreamIsCapturing(s, &cs));
   if (nc == 1 || cs != cudaStreamCaptureStatusNone) return base;
   constexpr int kRounds = 2;
-  cudaEvent_t ev[1 + 3 * kRounds];
+  cudaEvent_t ev[1 + 2 * kRounds];
   for (auto& e : ev) TRM_CUDA(cudaEventCreate(&e));
   long long tuning = 0;
   capture_launches(&tuning);  // the timing launches are not the caller's
@@ -470,7 +471,7 @@ int tuned_splits(int64_t N, int m, int n, int tiles, int sym, int smax,
     }
   capture_launches(nullptr);
   TRM_CUDA(cudaEventSynchronize(ev[e - 1]));
-  float tot[3] = {0.f, 0.f, 0.f}, t = 0.f;
+  float tot[2] = {0.f, 0.f}, t = 0.f;
   for (int i = 1; i < e; ++i) {
     TRM_CUDA(cudaEventElapsedTime(&t, ev[i - 1], ev[i]));
     tot[(i - 1) % nc] += t;
@@ -540,6 +541,13 @@ void gram_tc_pairs(int64_t N, int m, const Blocks<float>& A,
   a.n = n;
   a.seg_cols = segcols;
   a.tps = tps;
+  // TRM_GRAM_KC overrides the chunk length (measurements of the
+  // accumulation error against the fold's cost)
+  a.kc = KC;
+  if (const char* f = std::getenv("TRM_GRAM_KC")) {
+    const int v = std::atoi(f);
+    if (v >= 1 && v <= kSingleChunk) a.kc = v;
+  }
   a.part = partials;
   a.err = err;
   const size_t smem = sizeof(TcSmem) + 1024;

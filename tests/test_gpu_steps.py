@@ -215,6 +215,31 @@ def test_gram(trm, N, m, n):
     assert np.median(np.abs(got32 - ref32) / scale) < 1e-6
 
 
+# The tensor-core Gram's row slices are autotuned per shape between the
+# wave-filling formula's count and half of it; every count must give the
+# product within the kernel's bound (TF32 two-term split: 2^-19 per product;
+# FP32 accumulation in chunks of at most 96 stages of 12 MMA steps, each
+# truncating at most 2^-23 of the running sum). TRM_GRAM_SLICES fixes the
+# count. N = 20000 with m = 96, n = 200: ragged row slices, a padded output
+# tile, several tiles.
+@pytest.mark.parametrize("slices", ["formula", "1", "3", "40", "200"])
+def test_gram_tc_any_slice_count(trm, slices, monkeypatch):
+    torch = gu.torch_mod()
+    N, m, n = 20000, 96, 200
+    A = ti.random_block(N, m, seed=6).astype(np.float32)
+    B = ti.random_block(N, n, seed=7).astype(np.float32)
+    ref = A.astype(np.float64).T @ B.astype(np.float64)
+    scale = np.abs(A).astype(np.float64).T @ np.abs(B).astype(np.float64)
+    monkeypatch.setenv("TRM_GRAM_SLICES", slices)
+    a, b = gu.to_dev(A), gu.to_dev(B)
+    out = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    trm.trm_gram(N, m, n, trm.TRM_F32, a.data_ptr(), b.data_ptr(),
+                 out.data_ptr(), gu.stream())
+    got = gu.from_dev(out)
+    bound = (2.0 ** -19 + 96 * 12 * 2.0 ** -23) * scale
+    assert np.all(np.abs(got - ref) <= bound)
+
+
 def test_gram_f32_misaligned_a_falls_back(trm):
     """An FP32 A that is 4-byte but not 16-byte aligned (a column slice) at a
     size the tensor cores take: the TMA path needs 16-byte operands, so the
