@@ -25,15 +25,22 @@ int fail(trm_ctx* h, int status, const std::string& msg) {
 
 template <class F>
 trm_status guarded(trm_ctx* h, F&& f) {
+  // An exception that leaves library code may have skipped the end of a
+  // launch-counting scope (an autotuner's timing launches): no scope
+  // outlives a call, so the thread's count sink is cleared here.
   try {
     return static_cast<trm_status>(f());
   } catch (const trm::Error& e) {
+    trm::capture_launches(nullptr);
     return static_cast<trm_status>(fail(h, e.status, e.what()));
   } catch (const std::bad_alloc&) {
+    trm::capture_launches(nullptr);
     return static_cast<trm_status>(fail(h, TRM_ENOMEM, "host allocation failed"));
   } catch (const std::exception& e) {
+    trm::capture_launches(nullptr);
     return static_cast<trm_status>(fail(h, TRM_ECUDA, e.what()));
   } catch (...) {
+    trm::capture_launches(nullptr);
     return static_cast<trm_status>(fail(h, TRM_ECUDA, "unknown error"));
   }
 }

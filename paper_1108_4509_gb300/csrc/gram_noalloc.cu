@@ -103,15 +103,19 @@ extern "C" trm_status trm_gram_noalloc(int64_t N, int m, int n, int dtype,
     return static_cast<trm_status>(gram_noalloc(
         N, m, n, dtype, A, B, out, reinterpret_cast<cudaStream_t>(stream)));
   } catch (const Error& e) {
+    capture_launches(nullptr);  // (a tuner's counting scope, as in api.cu)
     set_global_error(e.what());
     return static_cast<trm_status>(e.status);
   } catch (const std::bad_alloc&) {
+    capture_launches(nullptr);
     set_global_error("trm_gram_noalloc: host allocation failed");
     return TRM_ENOMEM;
   } catch (const std::exception& e) {
+    capture_launches(nullptr);
     set_global_error(e.what());
     return TRM_ECUDA;
   } catch (...) {
+    capture_launches(nullptr);
     set_global_error("trm_gram_noalloc: unknown error");
     return TRM_ECUDA;
   }

@@ -99,16 +99,20 @@ def test_apply_h_stencil(trm, shape, order, m):
 # their outputs agree bit for bit, and each is within the FP32 bound of the
 # oracle. (48, 40, 33) gives the z-march two plane tiles of 240 quads and
 # several z chunks; (12, 10, 9) a ragged tile of 32 threads for 30 quads.
-@pytest.mark.parametrize("shape,order", [((16, 12, 10), 2), ((16, 12, 10), 4),
-                                         ((12, 10, 9), 4), ((48, 40, 33), 4),
-                                         ((64, 37, 6), 2), ((8, 8, 8), 4)])
-def test_fp32_stencil_kernels_agree(trm, shape, order, monkeypatch):
+# (64, 64, 64) with 128 columns (134 MB in, 134 MB out) is larger than L2.
+@pytest.mark.parametrize("shape,order,m", [
+    ((16, 12, 10), 2, 7), ((16, 12, 10), 4, 7), ((12, 10, 9), 4, 7),
+    ((48, 40, 33), 4, 7), ((64, 37, 6), 2, 7), ((8, 8, 8), 4, 7),
+    ((64, 64, 64), 4, 128)])
+def test_fp32_stencil_kernels_agree(trm, shape, order, m, monkeypatch):
     V = ti.gaussian_wells(shape, 3, seed=2)
     H = op.grid_hamiltonian(shape, order, 1.0, V)
-    N, m = H.shape[0], 7
+    N = H.shape[0]
     h = _handle(trm, shape, order, V, 1)
     try:
-        C32 = ti.random_block(N, m, seed=9).astype(np.float32)
+        # seeded uniform entries (a fast generator: 34 M values at 64^3)
+        rng = np.random.default_rng(9)
+        C32 = (rng.random((m, N), dtype=np.float32) - np.float32(0.5)).T
         ref = op.apply_h(H, C32.astype(np.float64))
         scale = np.abs(H) @ np.abs(C32.astype(np.float64))
         cs = gu.to_dev(C32)
@@ -237,6 +241,31 @@ def test_gram_tc_any_slice_count(trm, slices, monkeypatch):
                  out.data_ptr(), gu.stream())
     got = gu.from_dev(out)
     bound = (2.0 ** -19 + 96 * 12 * 2.0 ** -23) * scale
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+# Long row slices on the tensor cores: at N = 110592, m = n = 512 (16
+# output tiles, 226 MB per operand) three slices are 1152 stages each, so
+# the accumulator is folded into the double-float TMEM sum every 8 stages;
+# the formula's count gives slices near the single-chunk limit.
+@pytest.mark.parametrize("slices", ["formula", "3"])
+def test_gram_tc_m512_long_slices(trm, slices, monkeypatch):
+    torch = gu.torch_mod()
+    N, m = 110592, 512
+    rng = np.random.default_rng(8)  # seeded uniform entries, fast at this size
+    A = (rng.random((m, N), dtype=np.float32) - np.float32(0.5)).T
+    B = (rng.random((m, N), dtype=np.float32) - np.float32(0.3)).T
+    monkeypatch.setenv("TRM_GRAM_SLICES", slices)
+    a, b = gu.to_dev(A), gu.to_dev(B)
+    out = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+    trm.trm_gram(N, m, m, trm.TRM_F32, a.data_ptr(), b.data_ptr(),
+                 out.data_ptr(), gu.stream())
+    got = gu.from_dev(out)
+    del a, b
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    ref = A64.T @ B64
+    scale = np.abs(A64).T @ np.abs(B64)
+    bound = (96 * 2.0 ** -23 + 2.0 ** -19) * scale
     assert np.all(np.abs(got - ref) <= bound)
 
 
