@@ -193,7 +193,10 @@ size_t mul_tc_work_floats(int k, int n);
 bool mul_tc_eligible(int64_t N, int k, int n, const TcWork* tw);
 // number of partial-sum records mul_tc_grad writes
 int mul_tc_parts(int64_t N, int n);
-// out = (A + alpha P) M (P may be null; alpha = sc->alpha)
+// out = (A + alpha P) M (P may be null; alpha = sc->alpha) for an upper
+// triangular M (the rotation's L^{-T}): column j of the product takes only
+// the rows k <= j of M, whole 32-row K blocks of zeros are skipped. The
+// split updates below make the same assumption of their R.
 void mul_tc_store(int64_t N, int k, int n, const float* A, const float* P,
                   const IterScalars* sc, const double* M, float* out,
                   const TcWork& tw, cudaStream_t s);
